@@ -1,0 +1,311 @@
+"""Seeded synthetic inputs and workload configurations.
+
+This module is shared by the CUDA path, the benchmark and the FP64 oracle.
+It holds only *inputs*: geometry numbers, delay lists, patch-centre lists and
+seeded random phantoms (speed-of-sound maps, initial-pressure images, noise).
+It contains none of the method's arithmetic (no delay-and-sum, no ray
+integration, no transfer functions, no deconvolution, no loss).
+
+The paper's phantoms (k-Wave simulations of a mouse-like body, a leaf phantom,
+in-vivo data) are not available; these generators stand in for them with the
+value ranges the paper states (Sec. S1.1: SOS 1490-1650 m/s, water background,
+512-element ring, 3.2 mm patches with 75 % overlap, Sec. 3.3: M = 16 delays).
+Random numbers come from NumPy's PCG64 seeded per case.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Tuple
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Config:
+    """One workload.  SI units (metres, seconds, m/s)."""
+
+    name: str
+    img_h: int
+    img_w: int
+    dx: float                 # image pixel pitch [m]
+    n_t: int                  # transducers on the ring
+    ring_radius: float        # [m]
+    ring_phase: float         # angle of transducer 0 [rad]
+    v0: float                 # SOS assumed by DAS [m/s]
+    v_bg: float               # fixed background (water) SOS [m/s]
+    sos_g: int                # pixel-grid SOS nodes per side
+    p: int                    # patch size [px], even
+    centres_rows: Tuple[int, ...]   # patch-centre rows (Cartesian grid with cols)
+    centres_cols: Tuple[int, ...]
+    m: int                    # delay channels
+    tau_us: float             # delays span [-tau_us, +tau_us] microseconds
+    eps: float                # Wiener-style regulariser added to sum |H|^2
+    tv_lambda: float          # TV weight
+    lr: float                 # Adam learning rate [m/s per step]
+    steps: int                # Adam iterations
+    noise_sigma: float        # additive Gaussian noise on the delay stack
+    sos_kind: str             # "blobs" | "ellipses" | "uniform"
+    ip_kind: str              # "disks_lines" | "vessels"
+    sos_lo: float = 1450.0
+    sos_hi: float = 1600.0
+
+    # ---- derived geometry (configuration readings, not method arithmetic) ----
+    @property
+    def fov(self) -> float:
+        return self.img_w * self.dx
+
+    @property
+    def sos_dx(self) -> float:
+        """SOS nodes cover the image field of view."""
+        return self.fov / self.sos_g
+
+    @property
+    def mask_radius(self) -> float:
+        """Circular SOS mask: the disk inscribed in the field of view."""
+        return 0.5 * self.fov
+
+    @property
+    def ray_step(self) -> float:
+        return 0.5 * self.sos_dx
+
+    @property
+    def window_fwhm(self) -> float:
+        """Window FWHM scaled from the paper's 1.5 mm on 3.2 mm patches."""
+        return (1.5 / 3.2) * self.p * self.dx
+
+    @property
+    def n_patches(self) -> int:
+        return len(self.centres_rows) * len(self.centres_cols)
+
+    @property
+    def n_freq(self) -> int:
+        return self.p * (self.p // 2 + 1)
+
+    def centres(self) -> np.ndarray:
+        """Patch centres as int32 [N][2] (row, col), row-major over the grid."""
+        rr, cc = np.meshgrid(np.asarray(self.centres_rows), np.asarray(self.centres_cols), indexing="ij")
+        return np.stack([rr.ravel(), cc.ravel()], axis=1).astype(np.int32)
+
+    def tau(self) -> np.ndarray:
+        """Delay times [s], uniform over [-tau, +tau]."""
+        if self.m == 1:
+            return np.zeros(1)
+        return np.linspace(-self.tau_us, self.tau_us, self.m) * 1e-6
+
+    def delays(self) -> np.ndarray:
+        """Delay distances d_j [m] as float32: the stated times at the assumed SOS."""
+        return (self.tau() * self.v0).astype(np.float32)
+
+    def geometry_dict(self) -> dict:
+        return dict(n_t=self.n_t, ring_radius=self.ring_radius, ring_phase=self.ring_phase,
+                    v0=self.v0, v_bg=self.v_bg, img_h=self.img_h, img_w=self.img_w, dx=self.dx,
+                    sos_g=self.sos_g, sos_dx=self.sos_dx, mask_radius=self.mask_radius,
+                    ray_step=self.ray_step, p=self.p, window_fwhm=self.window_fwhm)
+
+    def replace(self, **kw) -> "Config":
+        return dataclasses.replace(self, **kw)
+
+
+def config_small() -> Config:
+    """128x128 image at 0.2 mm, 256-element ring of radius 15 mm, 3x3 patches of
+    32x32, 8 delays over +-0.5 us, 32x32 SOS grid with two Gaussian blobs."""
+    return Config(name="pg128_ring256_p32_m8", img_h=128, img_w=128, dx=0.2e-3, n_t=256,
+                  ring_radius=15e-3, ring_phase=0.0, v0=1500.0, v_bg=1500.0, sos_g=32, p=32,
+                  centres_rows=(32, 64, 96), centres_cols=(32, 64, 96), m=8, tau_us=0.5,
+                  eps=1e-3, tv_lambda=1e-4, lr=1.0, steps=50, noise_sigma=0.01,
+                  sos_kind="blobs", ip_kind="disks_lines", sos_lo=1450.0, sos_hi=1550.0)
+
+
+def config_full() -> Config:
+    """512x512 image at 0.1 mm, 512-element ring of radius 40 mm, 12x12 patches of
+    80x80 at stride 40 (144 patches), 32 delays, 128x128 SOS grid with 1-6
+    Gaussian ellipses in 1450-1600 m/s, vessel-tree initial pressure."""
+    cs = tuple(36 + 40 * k for k in range(12))
+    return Config(name="pg512_ring512_p80_m32", img_h=512, img_w=512, dx=0.1e-3, n_t=512,
+                  ring_radius=40e-3, ring_phase=0.0, v0=1500.0, v_bg=1500.0, sos_g=128, p=80,
+                  centres_rows=cs, centres_cols=cs, m=32, tau_us=0.5, eps=1e-3, tv_lambda=1e-4,
+                  lr=1.0, steps=1000, noise_sigma=0.01, sos_kind="ellipses", ip_kind="vessels")
+
+
+def config_rf() -> Config:
+    """1024x1024 image at 0.05 mm from 1024-element ring channel data, 64x64
+    patches at stride 16 (61x61 = 3721 patches), 32 delays, 256x256 SOS grid."""
+    cs = tuple(32 + 16 * k for k in range(61))
+    return Config(name="rf1024_ring1024_p64_m32", img_h=1024, img_w=1024, dx=0.05e-3, n_t=1024,
+                  ring_radius=40e-3, ring_phase=0.0, v0=1500.0, v_bg=1500.0, sos_g=256, p=64,
+                  centres_rows=cs, centres_cols=cs, m=32, tau_us=0.5, eps=1e-3, tv_lambda=0.0,
+                  lr=1.0, steps=100, noise_sigma=0.01, sos_kind="ellipses", ip_kind="vessels")
+
+
+def config_tiny(p: int = 16, m: int = 4, n_t: int = 64, grid: int = 2) -> Config:
+    """A few patches of P x P on a 64x64 image: for brute-force and FD checks."""
+    img = 64
+    step = img // (grid + 1)
+    cs = tuple(step * (k + 1) for k in range(grid))
+    return Config(name=f"tiny_p{p}_m{m}", img_h=img, img_w=img, dx=0.2e-3, n_t=n_t,
+                  ring_radius=9e-3, ring_phase=0.1, v0=1500.0, v_bg=1500.0, sos_g=16, p=p,
+                  centres_rows=cs, centres_cols=cs, m=m, tau_us=0.5, eps=1e-3, tv_lambda=1e-4,
+                  lr=1.0, steps=5, noise_sigma=0.01, sos_kind="blobs", ip_kind="disks_lines",
+                  sos_lo=1450.0, sos_hi=1550.0)
+
+
+# --------------------------------------------------------------------------
+# seeded phantoms
+# --------------------------------------------------------------------------
+
+def _node_xy(cfg: Config) -> Tuple[np.ndarray, np.ndarray]:
+    """SOS node coordinates [m] (x along columns, y along rows), node centres."""
+    g = cfg.sos_g
+    c = (np.arange(g) - (g - 1) / 2.0) * cfg.sos_dx
+    yy, xx = np.meshgrid(c, c, indexing="ij")
+    return xx, yy
+
+
+def _pixel_xy(cfg: Config) -> Tuple[np.ndarray, np.ndarray]:
+    cx = (np.arange(cfg.img_w) - (cfg.img_w - 1) / 2.0) * cfg.dx
+    cy = (np.arange(cfg.img_h) - (cfg.img_h - 1) / 2.0) * cfg.dx
+    yy, xx = np.meshgrid(cy, cx, indexing="ij")
+    return xx, yy
+
+
+def sos_mask(cfg: Config) -> np.ndarray:
+    """Nodes whose centre lies inside the circular mask (trainable nodes)."""
+    xx, yy = _node_xy(cfg)
+    return (xx * xx + yy * yy) <= cfg.mask_radius ** 2
+
+
+def sos_phantom(cfg: Config, rng: np.random.Generator) -> np.ndarray:
+    """Ground-truth SOS on the node grid [G][G] (float64, m/s)."""
+    xx, yy = _node_xy(cfg)
+    rm = cfg.mask_radius
+    v = np.full(xx.shape, cfg.v_bg)
+    if cfg.sos_kind == "blobs":
+        for _ in range(2):
+            r = 0.55 * rm * math.sqrt(rng.uniform())
+            a = rng.uniform(0, 2 * math.pi)
+            cx, cy = r * math.cos(a), r * math.sin(a)
+            sig = rng.uniform(2e-3, 4e-3)
+            amp = 50.0 * (1 if rng.uniform() < 0.5 else -1)
+            v = v + amp * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sig * sig))
+    elif cfg.sos_kind == "ellipses":
+        n = int(rng.integers(1, 7))
+        for _ in range(n):
+            r = 0.6 * rm * math.sqrt(rng.uniform())
+            a = rng.uniform(0, 2 * math.pi)
+            cx, cy = r * math.cos(a), r * math.sin(a)
+            sa, sb = rng.uniform(0.06, 0.25) * rm, rng.uniform(0.06, 0.25) * rm
+            th = rng.uniform(0, math.pi)
+            amp = rng.uniform(cfg.sos_lo - cfg.v_bg, cfg.sos_hi - cfg.v_bg)
+            ux = (xx - cx) * math.cos(th) + (yy - cy) * math.sin(th)
+            uy = -(xx - cx) * math.sin(th) + (yy - cy) * math.cos(th)
+            v = v + amp * np.exp(-0.5 * ((ux / sa) ** 2 + (uy / sb) ** 2))
+        v = np.clip(v, cfg.sos_lo, cfg.sos_hi)
+    elif cfg.sos_kind == "uniform":
+        pass
+    else:
+        raise ValueError(cfg.sos_kind)
+    v[~sos_mask(cfg)] = cfg.v_bg
+    return v
+
+
+def _segment_dist(xx, yy, p0, p1):
+    d = np.asarray(p1) - np.asarray(p0)
+    L2 = float(d @ d) + 1e-30
+    t = np.clip(((xx - p0[0]) * d[0] + (yy - p0[1]) * d[1]) / L2, 0.0, 1.0)
+    return np.hypot(xx - (p0[0] + t * d[0]), yy - (p0[1] + t * d[1]))
+
+
+def ip_phantom(cfg: Config, rng: np.random.Generator) -> np.ndarray:
+    """Ground-truth initial-pressure image [H][W] in [0, 1] (float64)."""
+    xx, yy = _pixel_xy(cfg)
+    img = np.zeros(xx.shape)
+    rmax = 0.8 * cfg.mask_radius
+    if cfg.ip_kind == "disks_lines":
+        for _ in range(int(rng.integers(4, 8))):
+            r = rmax * math.sqrt(rng.uniform())
+            a = rng.uniform(0, 2 * math.pi)
+            rad = rng.uniform(0.3e-3, 1.5e-3)
+            amp = rng.uniform(0.3, 1.0)
+            d = np.hypot(xx - r * math.cos(a), yy - r * math.sin(a))
+            img = np.maximum(img, amp * (d <= rad))
+        for _ in range(int(rng.integers(3, 6))):
+            p0 = rng.uniform(-rmax, rmax, 2)
+            p1 = rng.uniform(-rmax, rmax, 2)
+            w = rng.uniform(0.1e-3, 0.25e-3)
+            amp = rng.uniform(0.3, 1.0)
+            img = np.maximum(img, amp * (_segment_dist(xx, yy, p0, p1) <= w))
+    elif cfg.ip_kind == "vessels":
+        # random branching polylines (vessel tree), widths 0.1-0.5 mm
+        stack = []
+        for _ in range(int(rng.integers(2, 4))):
+            a = rng.uniform(0, 2 * math.pi)
+            stack.append((np.array([0.9 * rmax * math.cos(a), 0.9 * rmax * math.sin(a)]),
+                          a + math.pi + rng.uniform(-0.5, 0.5), rng.uniform(0.3e-3, 0.5e-3), 0))
+        segs = []
+        while stack and len(segs) < 160:
+            p0, ang, wid, depth = stack.pop()
+            length = rng.uniform(0.08, 0.2) * rmax
+            p1 = p0 + length * np.array([math.cos(ang), math.sin(ang)])
+            if np.hypot(*p1) > rmax:
+                continue
+            segs.append((p0, p1, wid, rng.uniform(0.5, 1.0)))
+            nxt = ang + rng.normal(0.0, 0.25)
+            stack.append((p1, nxt, wid, depth + 1))
+            if depth < 6 and rng.uniform() < 0.45:
+                stack.append((p1, ang + rng.choice([-1, 1]) * rng.uniform(0.4, 1.1),
+                              max(0.1e-3, wid * rng.uniform(0.6, 0.85)), depth + 1))
+        for p0, p1, wid, amp in segs:
+            dist = _segment_dist(xx, yy, p0, p1)
+            img = np.maximum(img, amp * np.clip(1.0 - dist / (0.5 * wid), 0.0, 1.0) ** 0.5)
+    else:
+        raise ValueError(cfg.ip_kind)
+    return img
+
+
+def make_case(cfg: Config, seed: int) -> dict:
+    """All seeded inputs of one recovery problem, as float32 / int32 arrays.
+
+    sos_true  [G][G]   ground-truth SOS (nodes outside the mask at v_bg)
+    sos_init  [G][G]   uniform v_bg start
+    mask      [G][G]   uint8 trainable-node mask
+    ip        [H][W]   ground-truth initial pressure
+    noise     [M][H][W] N(0, sigma^2) per pixel of every delay channel
+    d         [M]      delay distances [m]
+    centres   [N][2]   patch centres (row, col)
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sos_true = sos_phantom(cfg, rng)
+    ip = ip_phantom(cfg, rng)
+    noise = rng.standard_normal((cfg.m, cfg.img_h, cfg.img_w)) * cfg.noise_sigma
+    return dict(
+        sos_true=sos_true.astype(np.float32),
+        sos_init=np.full((cfg.sos_g, cfg.sos_g), cfg.v_bg, np.float32),
+        mask=sos_mask(cfg).astype(np.uint8),
+        ip=ip.astype(np.float32),
+        noise=noise.astype(np.float32),
+        d=cfg.delays(),
+        centres=cfg.centres(),
+    )
+
+
+def random_wavefronts(n: int, n_t: int, rng: np.random.Generator, scale: float = 3e-4) -> np.ndarray:
+    """Smooth random per-transducer wavefront errors [N][N_t] (metres): a few
+    random low-order Fourier harmonics in the ring angle plus a constant."""
+    a = 2 * np.pi * np.arange(n_t) / n_t
+    w = np.zeros((n, n_t))
+    for h in range(0, 6):
+        c = rng.normal(0, scale / (1 + h), (n, 1))
+        s = rng.normal(0, scale / (1 + h), (n, 1))
+        w += c * np.cos(h * a) + s * np.sin(h * a)
+    return w.astype(np.float32)
+
+
+def random_spectra(shape: Tuple[int, ...], rng: np.random.Generator) -> np.ndarray:
+    """Complex64 array with standard-normal real and imaginary parts."""
+    z = rng.standard_normal(shape + (2,)).astype(np.float32)
+    return z
+
+
+def random_rf(n_t: int, n_s: int, rng: np.random.Generator) -> np.ndarray:
+    return rng.standard_normal((n_t, n_s)).astype(np.float32)
