@@ -1,0 +1,345 @@
+"""Benchmark of the per-iteration hot path: recovery iterations per second.
+
+One step = one recovery iteration of the plain method with the pixel-grid SOS
+on the 512x512 / 512-element / 144 patches of 80x80 / 32-channel / 128x128 SOS
+workload: sos_to_delays -> fused mc_deconv_loss + adjoint -> sos_to_delays_adj
+-> TV -> Adam (8 libpact kernel launches).  Inputs are resident in HBM; L2 is
+flushed (256 MB write) before every timed step; every step is timed with CUDA
+events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+--impl reference times the FP64 CPU oracle (as it stands) on a bounded sample
+of the same workload (a subset of the patches per step, scaled to the full
+iteration).  Under torchrun with N > 1 every rank runs its own independent
+recovery problem (weak scaling; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "recovery iters/s (fwd+adjoint+Adam), pixel-grid SOS"
+WORKLOAD = "pg512_ring512_p80_m32: 512x512 @0.1mm, 512-el ring R=40mm, 144 patches 80x80, M=32, SOS 128x128"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+
+def oracle_sample_time(cfg, case, n_patch: int, min_seconds: float, max_iters: int):
+    """Times the FP64 oracle iteration (Eq. 3-7 with autograd adjoint + Adam) on
+    the first `n_patch` patches; returns (seconds per full-workload iteration,
+    iterations run, threads)."""
+    import torch
+    from oracle import pact_oracle as O
+    g = O.geom(cfg)
+    idx = np.linspace(0, cfg.n_patches - 1, n_patch).round().astype(int)
+    cen = case["centres"][idx]
+    rng = np.random.default_rng(1)
+    Y = torch.as_tensor(rng.standard_normal((n_patch, cfg.m, cfg.p, cfg.p // 2 + 1))
+                        + 1j * rng.standard_normal((n_patch, cfg.m, cfg.p, cfg.p // 2 + 1)))
+    sos = case["sos_init"].astype(np.float64)
+    m = np.zeros_like(sos)
+    v = np.zeros_like(sos)
+    times = []
+    t_all = time.perf_counter()
+    it = 0
+    while it < max_iters and (time.perf_counter() - t_all < min_seconds or it < 1):
+        t0 = time.perf_counter()
+        L, _, _, gs = O.objective(g, sos, Y, cen, case["d"], cfg.eps, cfg.tv_lambda)
+        sos, m, v = (x.numpy() for x in O.adam_step(sos, gs, m, v, it + 1, cfg.lr, mask=case["mask"]))
+        times.append(time.perf_counter() - t0)
+        it += 1
+    per = statistics.median(times) * cfg.n_patches / n_patch
+    return per, it, torch.get_num_threads(), times
+
+
+def run_reference(args, cfg, case, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, each step a 1-patch sample."""
+    if rank != 0:
+        return
+    import torch
+    from oracle import pact_oracle as O
+    g = O.geom(cfg)
+    n_patch = 1
+    idx = np.linspace(0, cfg.n_patches - 1, n_patch).round().astype(int)
+    cen = case["centres"][idx]
+    rng = np.random.default_rng(1)
+    Y = torch.as_tensor(rng.standard_normal((n_patch, cfg.m, cfg.p, cfg.p // 2 + 1))
+                        + 1j * rng.standard_normal((n_patch, cfg.m, cfg.p, cfg.p // 2 + 1)))
+    sos = case["sos_init"].astype(np.float64)
+    m = np.zeros_like(sos)
+    v = np.zeros_like(sos)
+
+    def step(t):
+        nonlocal sos, m, v
+        L, _, _, gs = O.objective(g, sos, Y, cen, case["d"], cfg.eps, cfg.tv_lambda)
+        sos, m, v = (x.numpy() for x in O.adam_step(sos, gs, m, v, t, cfg.lr, mask=case["mask"]))
+
+    for t in range(args.warmup):
+        step(t + 1)
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        step(args.warmup + t + 1)
+    el = time.perf_counter() - t0
+    per_full = el / args.steps * cfg.n_patches / n_patch
+    val = 1.0 / per_full
+    line = {"metric": METRIC, "value": val, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "oracle_sample": f"{n_patch} of {cfg.n_patches} patches per step"},
+            "cpu_baseline": {"value": val, "unit": "iters/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{n_patch} of {cfg.n_patches} patches per step, scaled by "
+                                       f"{cfg.n_patches / n_patch:.0f}"},
+            "e2e": {"value": val, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, cfg, case, rank, world, local):
+    import torch
+    from paper_2409_10876_gb300 import pact
+    from paper_2409_10876_gb300.recovery import PGRecovery, measurement_spectra, recover, synthesize_stack
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pact.load()
+    pb = pact.Problem(cfg, dev)
+    Y = measurement_spectra(pb, case, dev)
+    rec = PGRecovery(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
+                     torch.as_tensor(case["mask"]))
+    # three graphs: rays | fused deconvolution + adjoint | ray adjoint + TV + Adam
+    st0 = rec.state()
+    rec.step()
+    torch.cuda.synchronize()
+    rec.set_state(st0)
+    g_rays, g_mcd, g_rest = (torch.cuda.CUDAGraph() for _ in range(3))
+    with torch.cuda.graph(g_rays):
+        pact.sos_to_delays(pb, rec.sos, rec.w)
+    with torch.cuda.graph(g_mcd):
+        pact.mc_deconv_loss(pb, rec.w, rec.Y, rec.d, rec.eps, want_grad=True, out=rec.out, ws=rec.ws_mcd)
+    with torch.cuda.graph(g_rest):
+        pact.sos_to_delays_adj(pb, rec.sos, rec.out["dL_dw"], rec.grad, accumulate=False, ws=rec.ws_adj)
+        pact.tv(pb, rec.sos, rec.lam, value=rec.out["loss"], grad=rec.grad, accumulate=True)
+        pact.adam_step(rec.sos, rec.grad, rec.adam_m, rec.adam_v, 1, rec.lr, mask=rec.mask,
+                       step_counter=rec.counter)
+    torch.cuda.synchronize()
+    launches_per_step = 8
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one(ev=None):
+        flush.zero_()
+        if ev is not None:
+            ev[0].record(stream)
+        g_rays.replay()
+        if ev is not None:
+            ev[1].record(stream)
+        g_mcd.replay()
+        if ev is not None:
+            ev[2].record(stream)
+        g_rest.replay()
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    loss_start = rec.loss()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if world > 1 else \
+        os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = ClockSampler(gpu_id) if rank == 0 else None
+    time.sleep(0.3 if clk else 0)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        one(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop() if clk else None
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    mcd_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    rays_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    rest_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    loss_end = rec.loss()
+    value = world * args.steps / (tot_ms / 1e3)
+
+    # roofline of the fused deconvolution + adjoint call (dominant kernel)
+    N, M, F, n_t = pb.n, rec.m, pb.f, pb.n_t
+    alg_bytes = 8 * N * M * F + 2 * 4 * N * n_t
+    mcd_avg_s = statistics.mean(mcd_ms) / 1e3
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = alg_bytes / mcd_avg_s / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "mc_deconv_loss_traffic.json")
+    if os.path.exists(tr_path):
+        tr = json.load(open(tr_path))
+        if tr.get("kernel_rev") == kernel_revision():
+            traffic = tr.get("bytes_per_launch")
+
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed (256 MB write) before every timed step",
+                       "seed": args.seed, "eps": cfg.eps, "tv_lambda": cfg.tv_lambda},
+            "breakdown_ms": {"sos_to_delays": statistics.mean(rays_ms), "mc_deconv_loss": statistics.mean(mcd_ms),
+                             "adj_tv_adam": statistics.mean(rest_ms)},
+            "roofline": {"bound": "hbm", "kernel": "mc_deconv_loss (fused Eq. 4-7 + adjoint, 2 launches)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": "measured" if peaks else "fallback",
+                         "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},
+            "gpu_launches": launches_per_step * args.steps,
+            "wall_s_timed_region": wall,
+            "loss": {"start": loss_start, "end": loss_end}}
+    if clocks:
+        line["clocks"] = clocks
+
+    if rank == 0 and not args.no_cpu_baseline:
+        per, its, cores, _ = oracle_sample_time(cfg, case, 8, 10.0, 20)
+        line["cpu_baseline"] = {"value": 1.0 / per, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                                "sample": f"median of {its} FP64 oracle iterations on 8 of {cfg.n_patches} "
+                                          f"patches, scaled by {cfg.n_patches / 8:.0f}"}
+    if not args.no_e2e:
+        stack = synthesize_stack(pb, case, dev).cpu().pin_memory()
+        iters = max(50, min(args.steps, 500))
+        recover(pb, stack, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
+                torch.as_tensor(case["mask"]), 5)               # warm-up (graph capture paths, allocator)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recover(pb, stack, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
+                torch.as_tensor(case["mask"]), iters)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = world * iters / el
+        line["e2e"] = {"value": e2e, "unit": "iters/s", "h2d_bytes_per_step": stack.numel() * 4 / iters,
+                       "d2h_bytes_per_step": 4, "what": f"recover(): pinned host stack upload, patch FFT, graph "
+                                                       f"capture, {iters} iterations with a loss read-back each"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def kernel_revision() -> str:
+    """Hash of the fused kernel source: stored traffic counters apply only to it."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2409_10876_gb300", "csrc", "deconv.cu")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_2409_10876_gb300 import inputs
+    cfg = inputs.config_full()
+    case = inputs.make_case(cfg, args.seed + rank)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank == 0:
+                run_reference(args, cfg, case, rank, world)
+            return
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, cfg, case, rank, world)
+        return
+    run_gpu(args, cfg, case, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * pact.h -- C ABI of the GB300 (sm_103a) library for the per-iteration hot
+ * path of self-supervised joint speed-of-sound (SOS) / image recovery in
+ * ring-array photoacoustic computed tomography (Li, Cui, Ma, Alexander,
+ * "Coordinate-based Speed of Sound Recovery for Aberration-Corrected
+ * Photoacoustic Computed Tomography", arXiv 2409.10876).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - SI units: metres, seconds, m/s.  All arrays are dense and row-major.
+ *  - Complex arrays are interleaved float pairs (re, im): a "c64" array of
+ *    n complex values is a float array of 2n values, 8-byte aligned.
+ *  - Device pointers are caller-owned device memory; the library never
+ *    allocates.  Scratch space, where needed, is a caller-provided
+ *    workspace whose size the matching *_workspace_size call returns.
+ *  - Host pointers (geometry structs, delay lists) are read during the call
+ *    only; their values are copied into kernel arguments, so a call
+ *    captured into a CUDA graph keeps the values it saw at capture.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream) and never synchronises.
+ *  - Outputs are overwritten unless an `accumulate` flag is 1 (then +=).
+ *  - Return value: PACT_OK or an error code; pact_last_error_message()
+ *    gives a thread-local description of the last failure.  Invalid
+ *    arguments are rejected on the host before anything is launched.
+ *    No kernel traps; launch failures come back as PACT_ERR_CUDA.
+ *
+ * Geometry (Sec. 3.1, Sec. S1.1)
+ * ------------------------------
+ *  Image pixel (row a, col b) sits at x = (b - (W-1)/2) dx,
+ *  y = (a - (H-1)/2) dx.  Transducer n sits at
+ *  r_n = R (cos(2 pi n / N_t + phase), sin(2 pi n / N_t + phase)).
+ *  The SOS pixel grid has G x G nodes at x = (q - (G-1)/2) sos_dx (column q),
+ *  y = (p - (G-1)/2) sos_dx (row p), bilinearly interpolated and clamped at
+ *  the edge; rays count only inside the mask disk |r| <= mask_radius and
+ *  use v_bg outside it (Sec. 3.3: circular mask, fixed background SOS).
+ *  Patch i covers rows c_a - P/2 .. c_a + P/2 - 1 (and the same for
+ *  columns) around its centre pixel (c_a, c_b) = r'_i, zero outside the
+ *  image, and is weighted by a Gaussian window of the given FWHM
+ *  (Sec. S1.4).  Spectra are the orthonormal 2-D DFT (kernel
+ *  exp(-j k.rho), scale 1/P) on the rfft half-spectrum: [P][P/2+1] with
+ *  rows in fftfreq order, F = P (P/2 + 1) bins per patch, k in rad/m.
+ */
+#ifndef PACT_H
+#define PACT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pact_status {
+    PACT_OK = 0,
+    PACT_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, bad flag */
+    PACT_ERR_SHAPE = 2,         /* sizes outside what the kernels support */
+    PACT_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+    PACT_ERR_TIMEOUT = 4,       /* reserved: a bounded device-side wait gave up */
+    PACT_ERR_NONFINITE = 5,     /* reserved: non-finite values detected */
+    PACT_ERR_UNSUPPORTED = 6    /* feature not available on this device/build */
+} pact_status;
+
+/* Ring array, image grid and SOS grid (all host values). */
+typedef struct pact_geometry {
+    int   n_t;          /* transducers on the ring, >= 4 */
+    float ring_radius;  /* R [m]; every patch centre lies inside the ring */
+    float ring_phase;   /* angle of transducer 0 [rad] */
+    float v0;           /* SOS assumed by DAS (Eq. 1) [m/s] */
+    float v_bg;         /* fixed background SOS outside the mask [m/s] */
+    int   img_h;        /* image rows H */
+    int   img_w;        /* image columns W */
+    float dx;           /* pixel pitch [m] */
+    int   sos_g;        /* SOS nodes per side G, 2 <= G <= 512 */
+    float sos_dx;       /* node pitch [m] */
+    float mask_radius;  /* SOS mask radius [m] */
+    float ray_step;     /* midpoint-rule step of the ray integral [m] */
+} pact_geometry;
+
+/* Patch set (Sec. S1.4). */
+typedef struct pact_patches {
+    int        n;            /* number of patches N >= 1 */
+    int        p;            /* patch size P, even, 4 <= P <= 128 */
+    const int* centres;      /* DEVICE int32 [N][2]: (row, col) of r'_i */
+    float      window_fwhm;  /* Gaussian window FWHM [m] */
+} pact_patches;
+
+#define PACT_MAX_CHANNELS 64   /* largest delay-channel count M */
+
+/* Library version string (static storage). */
+const char* pact_version(void);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* pact_last_error_message(void);
+
+/*
+ * Delay-and-sum stack, Eq. 1 (Sec. 3.1, "DAS stack" of Sec. 3.2):
+ *   stack[j][a][b] = sum_n S(((|r'_ab - r_n| - d_j) / v0 - t0) * fs, n)
+ * with S linearly interpolated between samples and zero outside
+ * [0, n_s - 1].
+ *   rf     DEVICE float [N_t][n_s]  channel data, sample q at time t0 + q/fs
+ *   d      HOST float [m]           extra delay distances d_j [m]
+ *   stack  DEVICE float [m][H][W]   output
+ * Errors: INVALID_ARG for null pointers or non-positive sizes, SHAPE for
+ * m > PACT_MAX_CHANNELS.
+ */
+pact_status pact_das_stack(const pact_geometry* g, const float* rf, int n_s, float fs, float t0,
+                           const float* d, int m, float* stack, void* stream);
+
+/*
+ * Patch spectra (Sec. S1.4, the Y_i(k; d_j) of Eq. 5): crop each of the m
+ * channels around every patch centre, multiply by the Gaussian window
+ * exp(-|rho|^2 / (2 sigma^2)), FWHM = 2 sqrt(2 ln 2) sigma, rho measured from
+ * local index P/2, and take the orthonormal 2-D DFT on the half-spectrum.
+ *   stack  DEVICE float [m][H][W]
+ *   Y      DEVICE c64 [N][m][P][P/2+1]   output
+ */
+pact_status pact_patch_fft(const pact_geometry* g, const pact_patches* pt, const float* stack, int m,
+                           float* Y, void* stream);
+
+/*
+ * Wavefront errors, Eq. 2-3:  w_{i,n} = int_{r'_i}^{r_n} (1 - v0 / v(l)) dl,
+ * evaluated as the integral of the slowness excess (v - v0)/v with
+ * v - v0 interpolated directly from the node excesses, by the midpoint rule
+ * with step ray_step over the part of the segment inside the mask (the last
+ * partial step weighted by its length), plus (1 - v0/v_bg) times the
+ * length outside the mask.
+ *   sos  DEVICE float [G][G]   node SOS [m/s]
+ *   w    DEVICE float [N][N_t] output [m]
+ */
+pact_status pact_sos_to_delays(const pact_geometry* g, const pact_patches* pt, const float* sos,
+                               float* w, void* stream);
+
+/* Workspace bytes of pact_sos_to_delays_adj for this geometry. */
+size_t pact_sos_to_delays_adj_workspace_size(const pact_geometry* g, const pact_patches* pt);
+
+/*
+ * Adjoint of Eq. 3 (backpropagation to the pixel-grid SOS, Sec. 3.3):
+ *   dL_dsos[p][q] (+)= sum_{i,n} dL_dw[i][n] * sum_s h_s v0 / v(l_s)^2 * b_pq(l_s)
+ * with b_pq the bilinear weight of node (p, q) at sample l_s.
+ *   dL_dw    DEVICE float [N][N_t]
+ *   dL_dsos  DEVICE float [G][G]   output (accumulate = 1 adds to it)
+ *   ws       DEVICE workspace of at least the size above (256-byte aligned)
+ * Errors: INVALID_ARG if ws is null or smaller than required.
+ */
+pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact_patches* pt, const float* sos,
+                                   const float* dL_dw, float* dL_dsos, int accumulate, void* ws,
+                                   size_t ws_bytes, void* stream);
+
+/*
+ * Wavefront transfer functions, Eq. 4, in the sign that Eq. 1 implies for
+ * the forward DFT kernel exp(-j k.rho) (the complex conjugate of the
+ * printed form):
+ *   H_ij(k) = 1/2 ( exp(+j|k|(d_j - W_i(ang k))) + exp(-j|k|(d_j - W_i(ang k + pi))) )
+ * where W_i(phi) interpolates w_{i,.} linearly in ring angle at the point
+ * where the ray from r'_i in direction phi meets the ring.
+ *   w  DEVICE float [N][N_t];  d HOST float [m];  H DEVICE c64 [N][m][P][P/2+1]
+ */
+pact_status pact_psf_synth(const pact_geometry* g, const pact_patches* pt, const float* w,
+                           const float* d, int m, float* H, void* stream);
+
+/*
+ * Adjoint of pact_psf_synth: dL_dw[i][n] (+)= sum over bins and channels of
+ * Re(conj(dL_dH) dH/dw), where dL_dH holds (dL/dRe H, dL/dIm H) pairs
+ * (the convention of PyTorch complex gradients).
+ *   dL_dH DEVICE c64 [N][m][P][P/2+1];  dL_dw DEVICE float [N][N_t]
+ */
+pact_status pact_psf_synth_adj(const pact_geometry* g, const pact_patches* pt, const float* w,
+                               const float* d, int m, const float* dL_dH, float* dL_dw,
+                               int accumulate, void* stream);
+
+/*
+ * Multi-channel forward model, Eq. 5:  Y_ij(k) (+)= H_ij(k) X_i(k) with H as
+ * in pact_psf_synth (synthesises measurements from a clean patch spectrum).
+ *   X DEVICE c64 [N][P][P/2+1];  Y DEVICE c64 [N][m][P][P/2+1]
+ */
+pact_status pact_forward_model(const pact_geometry* g, const pact_patches* pt, const float* w,
+                               const float* d, int m, const float* X, float* Y, int accumulate,
+                               void* stream);
+
+/* Workspace bytes of pact_mc_deconv_loss / pact_mc_deconv_loss_adj. */
+size_t pact_mc_deconv_loss_workspace_size(const pact_geometry* g, const pact_patches* pt, int m);
+
+/*
+ * Fused multi-channel deconvolution and loss, Eq. 6-7, with the transfer
+ * functions of Eq. 4 synthesised on the fly and never stored:
+ *   X_i(k) = sum_j conj(H_ij) Y_ij / (sum_j |H_ij|^2 + eps)          (Eq. 6)
+ *   L      = sum_i sum_k c_k |k|_mm sum_j |Y_ij - H_ij X_i|^2        (Eq. 7)
+ * (|k| in rad/mm, c_k = 1 on columns k_x = 0 and Nyquist, 2 elsewhere;
+ * X_i = 0 where the denominator is 0).  eps is the Wiener-style regulariser.
+ * When dL_dw is not NULL the same pass also returns the exact gradient
+ * dL/dw (hand-written adjoint: X_i is recomputed, never stored).
+ *   w        DEVICE float [N][N_t]          wavefront errors
+ *   Y        DEVICE c64 [N][m][P][P/2+1]    patch spectra
+ *   d        HOST float [m]                 delays [m]
+ *   loss     DEVICE float [1]               output (data term only)
+ *   loss_pp  DEVICE float [N] or NULL       per-patch data term
+ *   Xhat     DEVICE c64 [N][P][P/2+1] or NULL
+ *   dL_dw    DEVICE float [N][N_t] or NULL  output gradient
+ *   ws       DEVICE workspace (256-byte aligned) of the size above
+ * When eps < 1e-6 the per-bin channel-sum denominator and the division run
+ * in FP64.  Errors: INVALID_ARG (null w/Y/loss/ws, eps < 0, small ws),
+ * SHAPE (m > PACT_MAX_CHANNELS, P odd or out of range).
+ */
+pact_status pact_mc_deconv_loss(const pact_geometry* g, const pact_patches* pt, const float* w,
+                                const float* Y, const float* d, int m, float eps, float* loss,
+                                float* loss_pp, float* Xhat, float* dL_dw, void* ws,
+                                size_t ws_bytes, void* stream);
+
+/*
+ * Standalone adjoint of pact_mc_deconv_loss: dL_dw (+)= dL_dloss * dL/dw,
+ * dL_dloss a DEVICE float scalar (NULL = 1).  Same workspace rules.
+ */
+pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* pt, const float* w,
+                                    const float* Y, const float* d, int m, float eps,
+                                    const float* dL_dloss, float* dL_dw, int accumulate, void* ws,
+                                    size_t ws_bytes, void* stream);
+
+/*
+ * Total variation regulariser of Eq. 7 on the pixel-grid SOS:
+ *   TV(v) = sum |v[p+1][q] - v[p][q]| + |v[p][q+1] - v[p][q]|
+ *   value    DEVICE float [1] or NULL: value (+)= lambda * TV(v)
+ *   dL_dsos  DEVICE float [G][G] or NULL: (+)= lambda * subgradient
+ *            (sign(0) = 0)
+ * `accumulate` applies to both outputs.
+ */
+pact_status pact_tv(const pact_geometry* g, const float* sos, float lambda, float* value,
+                    float* dL_dsos, int accumulate, void* stream);
+
+/*
+ * One Adam step (Kingma & Ba; Sec. 3.3 trains the SOS parameters with
+ * Adam) on n parameters, bias-corrected with step count t:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   param -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ * Entries whose mask byte is 0 are left unchanged (mask NULL = all train).
+ *   param, m, v   DEVICE float [n] (updated in place);  grad DEVICE float [n]
+ *   step          t >= 1, used when step_counter is NULL
+ *   step_counter  DEVICE int [1] or NULL: steps taken so far; the update
+ *                 uses t = *step_counter + 1 and then increments it (so a
+ *                 call captured in a CUDA graph advances on every replay)
+ */
+pact_status pact_adam_step(int n, float* param, const float* grad, float* m, float* v, int step,
+                           int* step_counter, float lr, float beta1, float beta2, float eps,
+                           const unsigned char* mask, void* stream);
+
+/* Workspace bytes of pact_stitch. */
+size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt);
+
+/*
+ * Stitching (Sec. S1.4): every deconvolved patch irfft2(Xhat_i) (orthonormal
+ * inverse of the half-spectrum, window already applied at cropping) is
+ * translated to its centre and summed; the sum is divided by the summed
+ * Gaussian windows (0 where no window reaches).
+ *   Xhat   DEVICE c64 [N][P][P/2+1];  image DEVICE float [H][W] output
+ */
+pact_status pact_stitch(const pact_geometry* g, const pact_patches* pt, const float* Xhat,
+                        float* image, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PACT_H */

@@ -1,0 +1,96 @@
+// TV regulariser of Eq. 7 (pact_tv) and the Adam update of Sec. 3.3
+// (pact_adam_step) on the GPU.
+#include <math.h>
+
+#include "pact_internal.cuh"
+
+namespace pact {
+namespace {
+
+__device__ __forceinline__ float sgn(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+// One CTA: deterministic value reduction; subgradient per node.
+__global__ void __launch_bounds__(1024) tv_kernel(int G, const float* sos, float lambda, float* value,
+                                                  float* grad, int accumulate) {
+    __shared__ float red[32];
+    float part = 0.f;
+    const int GG = G * G;
+    for (int q = threadIdx.x; q < GG; q += blockDim.x) {
+        const int p = q / G, c = q - (q / G) * G;
+        const float v = sos[q];
+        float gq = 0.f;
+        if (p + 1 < G) {
+            const float dn = sos[q + G] - v;
+            part += fabsf(dn);
+            gq -= sgn(dn);
+        }
+        if (c + 1 < G) {
+            const float rt = sos[q + 1] - v;
+            part += fabsf(rt);
+            gq -= sgn(rt);
+        }
+        if (p > 0) gq += sgn(v - sos[q - G]);
+        if (c > 0) gq += sgn(v - sos[q - 1]);
+        if (grad) grad[q] = accumulate ? fmaf(lambda, gq, grad[q]) : lambda * gq;
+    }
+    const float tot = block_sum(part, red);
+    if (value && threadIdx.x == 0) value[0] = accumulate ? fmaf(lambda, tot, value[0]) : lambda * tot;
+}
+
+__global__ void adam_kernel(int n, float* param, const float* grad, float* m, float* v, float lr, float b1,
+                            float b2, float eps, float bc1, float bc2, const int* counter,
+                            const unsigned char* mask) {
+    if (counter) {  // t = steps so far + 1
+        const float t = (float)(*counter + 1);
+        bc1 = 1.f - powf(b1, t);
+        bc2 = 1.f - powf(b2, t);
+    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        if (mask && !mask[q]) continue;
+        const float g = grad[q];
+        const float mq = fmaf(b1, m[q], (1.f - b1) * g);
+        const float vq = fmaf(b2, v[q], (1.f - b2) * g * g);
+        m[q] = mq;
+        v[q] = vq;
+        param[q] -= lr * (mq / bc1) / (sqrtf(vq / bc2) + eps);
+    }
+}
+
+__global__ void counter_increment_kernel(int* counter) { *counter += 1; }
+
+}  // namespace
+}  // namespace pact
+
+using namespace pact;
+
+extern "C" pact_status pact_tv(const pact_geometry* g, const float* sos, float lambda, float* value,
+                               float* dL_dsos, int accumulate, void* stream) {
+    PACT_TRY(check_geometry(g));
+    if (!sos) return fail(PACT_ERR_INVALID_ARG, "tv: sos is NULL");
+    if (!value && !dL_dsos) return PACT_OK;
+    tv_kernel<<<1, 1024, 0, as_stream(stream)>>>(g->sos_g, sos, lambda, value, dL_dsos, accumulate);
+    return check_launch("tv kernel");
+}
+
+extern "C" pact_status pact_adam_step(int n, float* param, const float* grad, float* m, float* v, int step,
+                                      int* step_counter, float lr, float beta1, float beta2, float eps,
+                                      const unsigned char* mask, void* stream) {
+    if (n < 0) return fail(PACT_ERR_INVALID_ARG, "adam: n must be >= 0");
+    if (n == 0) return PACT_OK;
+    if (!param || !grad || !m || !v) return fail(PACT_ERR_INVALID_ARG, "adam: null pointer");
+    if (!step_counter && step < 1) return fail(PACT_ERR_INVALID_ARG, "adam: step must be >= 1");
+    if (step < 1) step = 1;
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f))
+        return fail(PACT_ERR_INVALID_ARG, "adam: betas must be in [0, 1)");
+    const float bc1 = (float)(1.0 - pow((double)beta1, step));
+    const float bc2 = (float)(1.0 - pow((double)beta2, step));
+    const int blocks = (n + 255) / 256 < 4 * num_sms() ? (n + 255) / 256 : 4 * num_sms();
+    adam_kernel<<<blocks, 256, 0, as_stream(stream)>>>(n, param, grad, m, v, lr, beta1, beta2, eps, bc1, bc2,
+                                                       step_counter, mask);
+    PACT_TRY(check_launch("adam kernel"));
+    if (step_counter) {
+        counter_increment_kernel<<<1, 1, 0, as_stream(stream)>>>(step_counter);
+        return check_launch("adam step counter");
+    }
+    return PACT_OK;
+}

@@ -1,0 +1,165 @@
+// Internal helpers shared by the CUDA translation units of libpact.
+// Nothing here is part of the C ABI (see include/pact.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pact.h"
+
+namespace pact {
+
+// ---------------------------------------------------------------- host side
+
+// Records a thread-local error message and returns `s`.
+pact_status fail(pact_status s, const char* fmt, ...);
+// Maps a pending launch error (cudaGetLastError) to PACT_ERR_CUDA.
+pact_status check_launch(const char* what);
+// Number of SMs of the current device (cached per device).
+int num_sms();
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device
+// to at least `bytes` (cached: the attribute call happens once per kernel and
+// device, so later launches, e.g. under CUDA-graph capture, make no calls).
+pact_status ensure_smem(const void* fn, size_t bytes, const char* what);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Validates the geometry struct; returns PACT_OK or records the failure.
+pact_status check_geometry(const pact_geometry* g);
+pact_status check_patches(const pact_patches* pt);
+
+#define PACT_TRY(expr)                       \
+    do {                                     \
+        pact_status _s = (expr);             \
+        if (_s != PACT_OK) return _s;        \
+    } while (0)
+
+// Kernel-argument copy of the geometry (by value).
+struct Geo {
+    int n_t;
+    float R, phase, v0, v_bg;
+    int H, W;
+    float dx;
+    int G;
+    float sos_dx, mask_r, h;
+};
+
+inline Geo make_geo(const pact_geometry* g) {
+    Geo o;
+    o.n_t = g->n_t;
+    o.R = g->ring_radius;
+    o.phase = g->ring_phase;
+    o.v0 = g->v0;
+    o.v_bg = g->v_bg;
+    o.H = g->img_h;
+    o.W = g->img_w;
+    o.dx = g->dx;
+    o.G = g->sos_g;
+    o.sos_dx = g->sos_dx;
+    o.mask_r = g->mask_radius;
+    o.h = g->ray_step;
+    return o;
+}
+
+// Delay list by value (HOST array copied into kernel arguments).
+struct Delays {
+    float d[PACT_MAX_CHANNELS];
+    int m;
+};
+
+inline Delays make_delays(const float* d, int m) {
+    Delays o;
+    o.m = m;
+    for (int j = 0; j < PACT_MAX_CHANNELS; ++j) o.d[j] = j < m ? d[j] : 0.f;
+    return o;
+}
+
+// ---------------------------------------------------------------- device side
+
+// Position of pixel (row, col): x along columns, y along rows.
+__device__ __forceinline__ float2 pixel_xy(const Geo& g, int row, int col) {
+    return make_float2((col - 0.5f * (g.W - 1)) * g.dx, (row - 0.5f * (g.H - 1)) * g.dx);
+}
+
+// Spatial frequency of half-spectrum bin k of a P x P patch, in cycles/m
+// (rows in fftfreq order).  Sets u, v.
+__device__ __forceinline__ float2 bin_freq(int k, int P, float inv_pdx, int& u, int& v) {
+    const int half = P / 2 + 1;
+    u = k / half;
+    v = k - u * half;
+    const int us = u < P / 2 ? u : u - P;
+    return make_float2(v * inv_pdx, us * inv_pdx);
+}
+
+// Ring lookup: the ray from c in direction (ex, ey) meets the ring at ring
+// angle alpha; returns the left transducer n1 and the fraction f in
+// [0, 1) of the way to n1 + 1 (cyclic).  `disc_sq` = sqrt((c.e)^2 - |c|^2 + R^2).
+__device__ __forceinline__ void ring_hit(float cx, float cy, float ex, float ey, float s,
+                                         float phase, int n_t, float n_over_2pi, int& n1,
+                                         float& f) {
+    const float px = fmaf(s, ex, cx);
+    const float py = fmaf(s, ey, cy);
+    float t = (atan2f(py, px) - phase) * n_over_2pi;
+    t -= floorf(t / (float)n_t) * (float)n_t;
+    const float fl = floorf(t);
+    f = t - fl;
+    int n = (int)fl;
+    n %= n_t;
+    if (n < 0) n += n_t;
+    n1 = n;
+}
+
+// Both ring hits of the line through c with direction e: +e and -e.
+struct Hits {
+    int n1a, n1b;
+    float fa, fb;
+};
+
+__device__ __forceinline__ Hits ring_hits(float cx, float cy, float ex, float ey, const Geo& g,
+                                          float n_over_2pi) {
+    const float ce = cx * ex + cy * ey;
+    const float disc = fmaxf(ce * ce - (cx * cx + cy * cy) + g.R * g.R, 0.f);
+    const float sq = sqrtf(disc);
+    Hits o;
+    ring_hit(cx, cy, ex, ey, sq - ce, g.phase, g.n_t, n_over_2pi, o.n1a, o.fa);
+    ring_hit(cx, cy, -ex, -ey, sq + ce, g.phase, g.n_t, n_over_2pi, o.n1b, o.fb);
+    return o;
+}
+
+// Complex helpers (float2 = re, im).
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) * b
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cis_pi(float x) {  // exp(j pi x)
+    float s, c;
+    sincospif(x, &s, &c);
+    return make_float2(c, s);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ float block_sum(float x, float* red) {
+    x = warp_sum(x);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    x = threadIdx.x < nw ? red[threadIdx.x] : 0.f;
+    if (wid == 0) x = warp_sum(x);
+    __syncthreads();
+    return x;
+}
+
+}  // namespace pact

@@ -1,0 +1,351 @@
+"""Python binding of libpact (include/pact.h): argument marshalling only.
+
+Every function here checks tensor devices, dtypes and shapes, allocates the
+outputs it is not given (PyTorch owns device memory) and calls the C entry
+point of the same name on the current PyTorch CUDA stream.  All arithmetic
+of the method runs in the CUDA kernels of libpact; there is no CPU path.
+If the library is not built, or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+
+class PactError(RuntimeError):
+    pass
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_t", ctypes.c_int), ("ring_radius", ctypes.c_float), ("ring_phase", ctypes.c_float),
+                ("v0", ctypes.c_float), ("v_bg", ctypes.c_float), ("img_h", ctypes.c_int),
+                ("img_w", ctypes.c_int), ("dx", ctypes.c_float), ("sos_g", ctypes.c_int),
+                ("sos_dx", ctypes.c_float), ("mask_radius", ctypes.c_float), ("ray_step", ctypes.c_float)]
+
+
+class _PatchesC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("p", ctypes.c_int), ("centres", ctypes.c_void_p),
+                ("window_fwhm", ctypes.c_float)]
+
+
+_VP, _I, _F, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+_GP = ctypes.POINTER(Geometry)
+_PP = ctypes.POINTER(_PatchesC)
+
+_SIGS = {
+    "pact_version": ([], ctypes.c_char_p),
+    "pact_last_error_message": ([], ctypes.c_char_p),
+    "pact_das_stack": ([_GP, _VP, _I, _F, _F, _VP, _I, _VP, _VP], _I),
+    "pact_patch_fft": ([_GP, _PP, _VP, _I, _VP, _VP], _I),
+    "pact_sos_to_delays": ([_GP, _PP, _VP, _VP, _VP], _I),
+    "pact_sos_to_delays_adj_workspace_size": ([_GP, _PP], _SZ),
+    "pact_sos_to_delays_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _VP, _SZ, _VP], _I),
+    "pact_psf_synth": ([_GP, _PP, _VP, _VP, _I, _VP, _VP], _I),
+    "pact_psf_synth_adj": ([_GP, _PP, _VP, _VP, _I, _VP, _VP, _I, _VP], _I),
+    "pact_forward_model": ([_GP, _PP, _VP, _VP, _I, _VP, _VP, _I, _VP], _I),
+    "pact_mc_deconv_loss_workspace_size": ([_GP, _PP, _I], _SZ),
+    "pact_mc_deconv_loss": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _VP, _VP, _VP, _SZ, _VP], _I),
+    "pact_mc_deconv_loss_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
+    "pact_tv": ([_GP, _VP, _F, _VP, _VP, _I, _VP], _I),
+    "pact_adam_step": ([_I, _VP, _VP, _VP, _VP, _I, _VP, _F, _F, _F, _F, _VP, _VP], _I),
+    "pact_stitch_workspace_size": ([_GP, _PP], _SZ),
+    "pact_stitch": ([_GP, _PP, _VP, _VP, _VP, _SZ, _VP], _I),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libpact.so (building it first if allowed); raises if impossible."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise PactError(f"libpact is not built ({path}); run paper_2409_10876_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = load().pact_last_error_message().decode()
+        raise PactError(f"{what} failed (status {status}): {msg}")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise PactError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise PactError(f"{name} must be {dtype} (got {t.dtype})")
+    if not t.is_contiguous():
+        raise PactError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise PactError(f"{name} must have shape {tuple(shape)} (got {tuple(t.shape)})")
+    return t
+
+
+def _host_f32(d):
+    a = np.ascontiguousarray(np.asarray(d, dtype=np.float32).ravel())
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------ problem description
+
+class Problem:
+    """Geometry + patch set of one workload, with the patch centres on the device."""
+
+    def __init__(self, cfg, device="cuda", centres=None):
+        self.cfg = cfg
+        gd = cfg.geometry_dict()
+        self.geom = Geometry(gd["n_t"], gd["ring_radius"], gd["ring_phase"], gd["v0"], gd["v_bg"],
+                             gd["img_h"], gd["img_w"], gd["dx"], gd["sos_g"], gd["sos_dx"],
+                             gd["mask_radius"], gd["ray_step"])
+        cen = cfg.centres() if centres is None else np.asarray(centres, np.int32)
+        self.centres = torch.as_tensor(np.ascontiguousarray(cen, dtype=np.int32), device=device)
+        self.patches = _PatchesC(int(cen.shape[0]), int(cfg.p), self.centres.data_ptr(), gd["window_fwhm"])
+        self.n = int(cen.shape[0])
+        self.p = int(cfg.p)
+        self.f = self.p * (self.p // 2 + 1)
+        self.n_t = int(cfg.n_t)
+        self.g = int(cfg.sos_g)
+        self.device = torch.device(device)
+
+    def gp(self):
+        return ctypes.byref(self.geom)
+
+    def pp(self):
+        return ctypes.byref(self.patches)
+
+    def spectra_shape(self, m):
+        return (self.n, m, self.p, self.p // 2 + 1)
+
+
+def _empty(shape, dtype, dev):
+    return torch.empty(shape, dtype=dtype, device=dev)
+
+
+def _ws(nbytes: int, dev) -> torch.Tensor:
+    # 256-byte alignment: PyTorch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+# ------------------------------------------------------------------ entry points
+
+def das_stack(pb: Problem, rf, fs: float, t0: float, d, stack=None):
+    """Eq. 1: DAS stack [M, H, W] from channel data rf [N_t, n_s]."""
+    L = load()
+    rf = _dev(rf, "rf", torch.float32)
+    dh, dp = _host_f32(d)
+    m = dh.size
+    if stack is None:
+        stack = _empty((m, pb.cfg.img_h, pb.cfg.img_w), torch.float32, rf.device)
+    _dev(stack, "stack", torch.float32, (m, pb.cfg.img_h, pb.cfg.img_w))
+    _check(L.pact_das_stack(pb.gp(), _ptr(rf), rf.shape[1], fs, t0, dp, m, _ptr(stack), _stream()), "das_stack")
+    return stack
+
+
+def patch_fft(pb: Problem, stack, Y=None):
+    """Sec. S1.4: windowed patch spectra Y [N, M, P, P/2+1] (complex64)."""
+    L = load()
+    stack = _dev(stack, "stack", torch.float32)
+    m = stack.shape[0]
+    if Y is None:
+        Y = _empty(pb.spectra_shape(m), torch.complex64, stack.device)
+    _dev(Y, "Y", torch.complex64, pb.spectra_shape(m))
+    _check(L.pact_patch_fft(pb.gp(), pb.pp(), _ptr(stack), m, _ptr(Y), _stream()), "patch_fft")
+    return Y
+
+
+def sos_to_delays(pb: Problem, sos, w=None):
+    """Eq. 3: wavefront errors w [N, N_t] from the SOS grid [G, G]."""
+    L = load()
+    sos = _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    if w is None:
+        w = _empty((pb.n, pb.n_t), torch.float32, sos.device)
+    _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    _check(L.pact_sos_to_delays(pb.gp(), pb.pp(), _ptr(sos), _ptr(w), _stream()), "sos_to_delays")
+    return w
+
+
+def sos_to_delays_adj_workspace_size(pb: Problem) -> int:
+    return int(load().pact_sos_to_delays_adj_workspace_size(pb.gp(), pb.pp()))
+
+
+def sos_to_delays_adj(pb: Problem, sos, dL_dw, dL_dsos=None, accumulate=False, ws=None):
+    """Adjoint of Eq. 3: dL/dsos [G, G] from dL/dw [N, N_t]."""
+    L = load()
+    sos = _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    dL_dw = _dev(dL_dw, "dL_dw", torch.float32, (pb.n, pb.n_t))
+    if dL_dsos is None:
+        dL_dsos = torch.zeros((pb.g, pb.g), dtype=torch.float32, device=sos.device)
+    _dev(dL_dsos, "dL_dsos", torch.float32, (pb.g, pb.g))
+    if ws is None:
+        ws = _ws(sos_to_delays_adj_workspace_size(pb), sos.device)
+    _check(L.pact_sos_to_delays_adj(pb.gp(), pb.pp(), _ptr(sos), _ptr(dL_dw), _ptr(dL_dsos), int(accumulate),
+                                    _ptr(ws), ws.numel(), _stream()), "sos_to_delays_adj")
+    return dL_dsos
+
+
+def psf_synth(pb: Problem, w, d, H=None):
+    """Eq. 4: transfer functions H [N, M, P, P/2+1] (complex64)."""
+    L = load()
+    w = _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    dh, dp = _host_f32(d)
+    if H is None:
+        H = _empty(pb.spectra_shape(dh.size), torch.complex64, w.device)
+    _dev(H, "H", torch.complex64, pb.spectra_shape(dh.size))
+    _check(L.pact_psf_synth(pb.gp(), pb.pp(), _ptr(w), dp, dh.size, _ptr(H), _stream()), "psf_synth")
+    return H
+
+
+def psf_synth_adj(pb: Problem, w, d, dL_dH, dL_dw=None, accumulate=False):
+    """Adjoint of Eq. 4; dL_dH holds (dL/dRe, dL/dIm) pairs (PyTorch convention)."""
+    L = load()
+    w = _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    dh, dp = _host_f32(d)
+    dL_dH = _dev(dL_dH, "dL_dH", torch.complex64, pb.spectra_shape(dh.size))
+    if dL_dw is None:
+        dL_dw = torch.zeros((pb.n, pb.n_t), dtype=torch.float32, device=w.device)
+    _dev(dL_dw, "dL_dw", torch.float32, (pb.n, pb.n_t))
+    _check(L.pact_psf_synth_adj(pb.gp(), pb.pp(), _ptr(w), dp, dh.size, _ptr(dL_dH), _ptr(dL_dw), int(accumulate),
+                                _stream()), "psf_synth_adj")
+    return dL_dw
+
+
+def forward_model(pb: Problem, w, d, X, Y=None, accumulate=False):
+    """Eq. 5: Y_ij (+)= H_ij X_i."""
+    L = load()
+    w = _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    dh, dp = _host_f32(d)
+    X = _dev(X, "X", torch.complex64, (pb.n, pb.p, pb.p // 2 + 1))
+    if Y is None:
+        Y = _empty(pb.spectra_shape(dh.size), torch.complex64, w.device)
+        accumulate = False
+    _dev(Y, "Y", torch.complex64, pb.spectra_shape(dh.size))
+    _check(L.pact_forward_model(pb.gp(), pb.pp(), _ptr(w), dp, dh.size, _ptr(X), _ptr(Y), int(accumulate),
+                                _stream()), "forward_model")
+    return Y
+
+
+def mc_deconv_loss_workspace_size(pb: Problem, m: int) -> int:
+    return int(load().pact_mc_deconv_loss_workspace_size(pb.gp(), pb.pp(), int(m)))
+
+
+def mc_deconv_loss(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=False, want_loss_pp=False,
+                   out=None, ws=None):
+    """Eq. 6-7 fused (+ adjoint when want_grad).  Returns a dict with
+    'loss' [1], and 'dL_dw' [N, N_t], 'Xhat' [N, P, P/2+1], 'loss_pp' [N] as asked.
+    `out` may hold preallocated tensors under the same keys."""
+    L = load()
+    w = _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    Y = _dev(Y, "Y", torch.complex64)
+    m = Y.shape[1]
+    _dev(Y, "Y", torch.complex64, pb.spectra_shape(m))
+    dh, dp = _host_f32(d)
+    if dh.size != m:
+        raise PactError(f"delay list has {dh.size} entries but Y has {m} channels")
+    out = {} if out is None else out
+    dev = w.device
+    if "loss" not in out:
+        out["loss"] = torch.zeros(1, dtype=torch.float32, device=dev)
+    if want_grad and "dL_dw" not in out:
+        out["dL_dw"] = _empty((pb.n, pb.n_t), torch.float32, dev)
+    if want_xhat and "Xhat" not in out:
+        out["Xhat"] = _empty((pb.n, pb.p, pb.p // 2 + 1), torch.complex64, dev)
+    if want_loss_pp and "loss_pp" not in out:
+        out["loss_pp"] = _empty((pb.n,), torch.float32, dev)
+    if ws is None:
+        ws = _ws(mc_deconv_loss_workspace_size(pb, m), dev)
+    _check(L.pact_mc_deconv_loss(pb.gp(), pb.pp(), _ptr(w), _ptr(Y), dp, m, float(eps), _ptr(out["loss"]),
+                                 _ptr(out.get("loss_pp") if want_loss_pp else None),
+                                 _ptr(out.get("Xhat") if want_xhat else None),
+                                 _ptr(out.get("dL_dw") if want_grad else None), _ptr(ws), ws.numel(), _stream()),
+           "mc_deconv_loss")
+    return out
+
+
+def mc_deconv_loss_adj(pb: Problem, w, Y, d, eps: float, dL_dloss=None, dL_dw=None, accumulate=False, ws=None):
+    """dL_dw (+)= dL_dloss * d(loss)/dw (standalone adjoint of mc_deconv_loss)."""
+    L = load()
+    w = _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    Y = _dev(Y, "Y", torch.complex64)
+    m = Y.shape[1]
+    dh, dp = _host_f32(d)
+    if dL_dw is None:
+        dL_dw = torch.zeros((pb.n, pb.n_t), dtype=torch.float32, device=w.device)
+    if dL_dloss is not None:
+        dL_dloss = _dev(dL_dloss.reshape(1).contiguous(), "dL_dloss", torch.float32)
+    if ws is None:
+        ws = _ws(mc_deconv_loss_workspace_size(pb, m), w.device)
+    _check(L.pact_mc_deconv_loss_adj(pb.gp(), pb.pp(), _ptr(w), _ptr(Y), dp, m, float(eps), _ptr(dL_dloss),
+                                     _ptr(dL_dw), int(accumulate), _ptr(ws), ws.numel(), _stream()),
+           "mc_deconv_loss_adj")
+    return dL_dw
+
+
+def tv(pb: Problem, sos, lam: float, value=None, grad=None, accumulate=False):
+    """Eq. 7 TV term: value (+)= lam TV(sos), grad (+)= lam dTV/dsos."""
+    L = load()
+    sos = _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    _check(L.pact_tv(pb.gp(), _ptr(sos), float(lam), _ptr(value), _ptr(grad), int(accumulate), _stream()), "tv")
+    return value, grad
+
+
+def adam_step(param, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, mask=None,
+              step_counter=None):
+    """One in-place Adam update of `param` (Sec. 3.3).  With `step_counter`
+    (int32 CUDA tensor [1]) the step count is read from and advanced on the
+    device, so the call can be replayed from a CUDA graph."""
+    L = load()
+    for t, nm in ((param, "param"), (grad, "grad"), (m, "m"), (v, "v")):
+        _dev(t, nm, torch.float32, tuple(param.shape))
+    if mask is not None:
+        _dev(mask, "mask", torch.uint8, tuple(param.shape))
+    if step_counter is not None:
+        _dev(step_counter, "step_counter", torch.int32, (1,))
+    _check(L.pact_adam_step(param.numel(), _ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(step),
+                            _ptr(step_counter), float(lr),
+                            float(beta1), float(beta2), float(eps), _ptr(mask), _stream()), "adam_step")
+    return param
+
+
+def stitch_workspace_size(pb: Problem) -> int:
+    return int(load().pact_stitch_workspace_size(pb.gp(), pb.pp()))
+
+
+def stitch(pb: Problem, Xhat, image=None, ws=None):
+    """Sec. S1.4: stitched image [H, W] from deconvolved patches."""
+    L = load()
+    Xhat = _dev(Xhat, "Xhat", torch.complex64, (pb.n, pb.p, pb.p // 2 + 1))
+    if image is None:
+        image = _empty((pb.cfg.img_h, pb.cfg.img_w), torch.float32, Xhat.device)
+    if ws is None:
+        ws = _ws(stitch_workspace_size(pb), Xhat.device)
+    _check(L.pact_stitch(pb.gp(), pb.pp(), _ptr(Xhat), _ptr(image), _ptr(ws), ws.numel(), _stream()), "stitch")
+    return image

@@ -1,0 +1,176 @@
+"""Recovery loop on the GPU (Sec. 3.3) and autograd wrappers.
+
+``PGRecovery`` runs the plain method with the pixel-grid SOS: every iteration
+is  sos_to_delays (Eq. 3) -> fused mc_deconv_loss + adjoint (Eq. 4-7) ->
+sos_to_delays_adj -> TV value/subgradient -> Adam, all in libpact kernels,
+captured once into a CUDA graph and replayed.  The loss stays on the device
+and is read back only when asked.
+
+``SosToDelays`` and ``McDeconvLoss`` expose the forward calls and their
+hand-written adjoints to torch.autograd for users who compose the forward
+model with their own parametrisations.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import pact
+
+
+class SosToDelays(torch.autograd.Function):
+    """w = sos_to_delays(sos) (Eq. 3); backward = pact_sos_to_delays_adj."""
+
+    @staticmethod
+    def forward(ctx, pb, sos):
+        ctx.pb = pb
+        ctx.save_for_backward(sos)
+        return pact.sos_to_delays(pb, sos.contiguous())
+
+    @staticmethod
+    def backward(ctx, gw):
+        (sos,) = ctx.saved_tensors
+        return None, pact.sos_to_delays_adj(ctx.pb, sos.contiguous(), gw.contiguous())
+
+
+class McDeconvLoss(torch.autograd.Function):
+    """Eq. 6-7 data term as a function of w; backward = pact_mc_deconv_loss_adj
+    (X_hat recomputed, never stored)."""
+
+    @staticmethod
+    def forward(ctx, pb, w, Y, d, eps):
+        ctx.pb, ctx.d, ctx.eps = pb, np.asarray(d, np.float32), float(eps)
+        ctx.save_for_backward(w, Y)
+        out = pact.mc_deconv_loss(pb, w.contiguous(), Y, d, eps, want_grad=False)
+        return out["loss"].reshape(())
+
+    @staticmethod
+    def backward(ctx, gl):
+        w, Y = ctx.saved_tensors
+        gw = pact.mc_deconv_loss_adj(ctx.pb, w.contiguous(), Y, ctx.d, ctx.eps,
+                                     dL_dloss=gl.reshape(1).float().contiguous())
+        return None, gw, None, None, None
+
+
+class PGRecovery:
+    """Plain method, pixel-grid SOS (Sec. 3.3), one CUDA graph per iteration."""
+
+    def __init__(self, pb: "pact.Problem", Y: torch.Tensor, d, eps: float, lam: float, lr: float,
+                 sos_init: torch.Tensor, mask: torch.Tensor = None, betas=(0.9, 0.999), adam_eps=1e-8):
+        dev = Y.device
+        self.pb, self.Y, self.d = pb, Y, np.asarray(d, np.float32)
+        self.eps, self.lam, self.lr, self.betas, self.adam_eps = float(eps), float(lam), float(lr), betas, adam_eps
+        self.m = int(Y.shape[1])
+        self.sos = sos_init.to(dev, torch.float32).contiguous().clone()
+        self.mask = None if mask is None else mask.to(dev, torch.uint8).contiguous()
+        self.adam_m = torch.zeros_like(self.sos)
+        self.adam_v = torch.zeros_like(self.sos)
+        self.counter = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.w = torch.empty((pb.n, pb.n_t), dtype=torch.float32, device=dev)
+        self.grad = torch.empty_like(self.sos)
+        self.out = {"loss": torch.zeros(1, dtype=torch.float32, device=dev),
+                    "dL_dw": torch.empty((pb.n, pb.n_t), dtype=torch.float32, device=dev)}
+        self.ws_mcd = pact._ws(pact.mc_deconv_loss_workspace_size(pb, self.m), dev)
+        self.ws_adj = pact._ws(pact.sos_to_delays_adj_workspace_size(pb), dev)
+        self.graph = None
+
+    # one iteration, enqueued on the current stream
+    def step(self):
+        pb = self.pb
+        pact.sos_to_delays(pb, self.sos, self.w)
+        pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd)
+        pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
+        if self.lam != 0.0:
+            pact.tv(pb, self.sos, self.lam, value=self.out["loss"], grad=self.grad, accumulate=True)
+        pact.adam_step(self.sos, self.grad, self.adam_m, self.adam_v, 1, self.lr, self.betas[0], self.betas[1],
+                       self.adam_eps, mask=self.mask, step_counter=self.counter)
+
+    def state(self):
+        return [t.clone() for t in (self.sos, self.adam_m, self.adam_v, self.counter)]
+
+    def set_state(self, st):
+        for dst, src in zip((self.sos, self.adam_m, self.adam_v, self.counter), st):
+            dst.copy_(src)
+
+    def capture(self):
+        """Captures one iteration into a CUDA graph (after one eager warm-up
+        iteration whose effect on the state is undone)."""
+        st0 = self.state()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.set_state(st0)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+        torch.cuda.synchronize()
+        return g
+
+    def iterate(self):
+        if self.graph is None:
+            self.step()
+        else:
+            self.graph.replay()
+
+    def run(self, iters: int, record_every: int = 0):
+        hist = []
+        for it in range(iters):
+            self.iterate()
+            if record_every and (it % record_every == 0 or it == iters - 1):
+                hist.append(float(self.out["loss"].item()))
+        return hist
+
+    def loss(self) -> float:
+        return float(self.out["loss"].item())
+
+
+def synthesize_stack(pb: "pact.Problem", case: dict, device) -> torch.Tensor:
+    """Delay stack [M, H, W] made by the forward model (Eq. 5) from the
+    ground-truth SOS and IP: every channel j is the stitch of the patches
+    H_ij(v_true) X_i, plus the seeded noise stack.  All arithmetic in libpact."""
+    d = case["d"]
+    sos = torch.as_tensor(case["sos_true"], device=device)
+    w_true = pact.sos_to_delays(pb, sos)
+    X = pact.patch_fft(pb, torch.as_tensor(case["ip"], device=device)[None])[:, 0].contiguous()
+    Yc = pact.forward_model(pb, w_true, d, X)
+    noise = torch.as_tensor(case["noise"], device=device)
+    stack = torch.empty_like(noise)
+    ws = pact._ws(pact.stitch_workspace_size(pb), device)
+    for j in range(len(d)):
+        pact.stitch(pb, Yc[:, j].contiguous(), stack[j], ws=ws)
+    stack += noise
+    return stack
+
+
+def measurement_spectra(pb: "pact.Problem", case: dict, device) -> torch.Tensor:
+    """Patch spectra of the synthetic measurement, Y = H(v_true) X + N (Eq. 5 per
+    patch, N the windowed spectra of the seeded noise stack)."""
+    sos = torch.as_tensor(case["sos_true"], device=device)
+    w_true = pact.sos_to_delays(pb, sos)
+    X = pact.patch_fft(pb, torch.as_tensor(case["ip"], device=device)[None])[:, 0].contiguous()
+    Y = pact.patch_fft(pb, torch.as_tensor(case["noise"], device=device))
+    return pact.forward_model(pb, w_true, case["d"], X, Y, accumulate=True)
+
+
+def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: float, lr: float,
+            sos_init: torch.Tensor, mask: torch.Tensor, iters: int, graph: bool = True):
+    """Public end-to-end API: upload a delay stack (host, ideally pinned), form
+    the patch spectra, run `iters` recovery iterations reading the loss back
+    after each, and return (sos, loss history, X_hat)."""
+    dev = pb.device
+    stack = stack_host.to(dev, non_blocking=True)
+    Y = pact.patch_fft(pb, stack)
+    rec = PGRecovery(pb, Y, d, eps, lam, lr, sos_init, mask)
+    if graph:
+        rec.capture()
+    hist = []
+    for _ in range(iters):
+        rec.iterate()
+        hist.append(rec.loss())
+    w = pact.sos_to_delays(pb, rec.sos)
+    Xh = pact.mc_deconv_loss(pb, w, Y, d, eps, want_grad=False, want_xhat=True)["Xhat"]
+    return rec.sos, hist, Xh

@@ -1,0 +1,400 @@
+"""GPU (libpact, through the C ABI) vs the FP64 oracle, element by element on
+the same seeded inputs.
+
+Tolerances (relative L2 unless stated), from the FP32 arithmetic:
+  delays w, patches X_hat, loss, spectra, transfer functions: 1e-4
+  gradients dL/dw and dL/dsos: 2e-3
+  DAS stack: 5e-4 (|r' - r_n| carries ~1 ulp of FP32 at the ring radius,
+  i.e. ~1e-4 of a sample for a 40 MHz / 1500 m/s sampling; the parity RF is
+  band-limited so the tap error stays below that fraction of the signal)
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pact_oracle as O
+from paper_2409_10876_gb300 import inputs, pact
+from paper_2409_10876_gb300.recovery import McDeconvLoss, PGRecovery, SosToDelays
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128 if np.iscomplexobj(a) or np.iscomplexobj(b) else np.float64)
+    b = np.asarray(b, a.dtype)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+def rand_Y(shape, seed):
+    z = np.random.default_rng(seed).standard_normal(shape + (2,)).astype(np.float32)
+    return z[..., 0] + 1j * z[..., 1]
+
+
+def to_dev_c(y):
+    return torch.as_tensor(np.ascontiguousarray(y.astype(np.complex64)), device=DEV)
+
+
+CASES = {
+    "tiny_p16_m4": lambda: inputs.config_tiny(p=16, m=4),
+    "tiny_p8_m1": lambda: inputs.config_tiny(p=8, m=1),
+    "tiny_p12_m3": lambda: inputs.config_tiny(p=12, m=3, grid=3),
+    "small_p32_m8": inputs.config_small,
+}
+
+
+# ------------------------------------------------------------------ Eq. 3 and its adjoint
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sos_to_delays(name):
+    cfg = CASES[name]()
+    for seed in (0, 1):
+        case = inputs.make_case(cfg, seed)
+        pb = pact.Problem(cfg, DEV)
+        w = pact.sos_to_delays(pb, torch.as_tensor(case["sos_true"], device=DEV))
+        ref = O.wavefront_errors(O.geom(cfg), case["sos_true"], case["centres"]).numpy()
+        assert rel(cpu(w), ref) <= 1e-4
+
+
+def test_sos_to_delays_uniform_is_zero_and_background():
+    cfg = inputs.config_small()
+    pb = pact.Problem(cfg, DEV)
+    w = pact.sos_to_delays(pb, torch.full((cfg.sos_g, cfg.sos_g), cfg.v0, device=DEV))
+    assert float(w.abs().max()) == 0.0
+    cfg2 = cfg.replace(v_bg=1510.0)
+    pb2 = pact.Problem(cfg2, DEV)
+    sos = torch.full((cfg.sos_g, cfg.sos_g), 1510.0, device=DEV)
+    w2 = pact.sos_to_delays(pb2, sos)
+    ref = O.wavefront_errors(O.geom(cfg2), np.full((cfg.sos_g, cfg.sos_g), 1510.0), cfg.centres()).numpy()
+    assert rel(cpu(w2), ref) <= 1e-4
+
+
+def test_sos_to_delays_full_size_sampled():
+    cfg = inputs.config_full()
+    case = inputs.make_case(cfg, 3)
+    pb = pact.Problem(cfg, DEV)
+    w = cpu(pact.sos_to_delays(pb, torch.as_tensor(case["sos_true"], device=DEV)))
+    idx = [0, 13, 77, 143]                        # corner patches lie outside the mask
+    ref = O.wavefront_errors(O.geom(cfg), case["sos_true"], case["centres"][idx]).numpy()
+    assert rel(w[idx], ref) <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8"])
+def test_sos_to_delays_adj(name):
+    cfg = CASES[name]()
+    case = inputs.make_case(cfg, 2)
+    pb = pact.Problem(cfg, DEV)
+    r = np.random.default_rng(5).standard_normal((cfg.n_patches, cfg.n_t)).astype(np.float32)
+    sos = torch.as_tensor(case["sos_true"], device=DEV)
+    g = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV)))
+    ref = O.sos_to_delays_adj(O.geom(cfg), case["sos_true"], case["centres"], r).numpy()
+    assert rel(g, ref) <= 2e-3
+    # accumulate adds
+    base = torch.ones((cfg.sos_g, cfg.sos_g), device=DEV)
+    g2 = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV), base, accumulate=True))
+    assert rel(g2, ref + 1.0) <= 2e-3
+
+
+def test_sos_to_delays_adj_full_size():
+    cfg = inputs.config_full()
+    case = inputs.make_case(cfg, 1)
+    pb = pact.Problem(cfg, DEV)
+    rng = np.random.default_rng(6)
+    r = np.zeros((cfg.n_patches, cfg.n_t), np.float32)
+    idx = [5, 70, 140]
+    r[idx] = rng.standard_normal((len(idx), cfg.n_t))
+    sos = torch.as_tensor(case["sos_true"], device=DEV)
+    g = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV)))
+    ref = O.sos_to_delays_adj(O.geom(cfg), case["sos_true"], case["centres"][idx], r[idx]).numpy()
+    assert rel(g, ref) <= 2e-3
+
+
+# ------------------------------------------------------------------ Eq. 4-5
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_psf_synth_and_forward_model(name):
+    cfg = CASES[name]()
+    rng = np.random.default_rng(7)
+    w = inputs.random_wavefronts(cfg.n_patches, cfg.n_t, rng)
+    d = cfg.delays()
+    pb = pact.Problem(cfg, DEV)
+    wt = torch.as_tensor(w, device=DEV)
+    H = cpu(pact.psf_synth(pb, wt, d))
+    Href = O.transfer_functions(O.geom(cfg), w.astype(np.float64), cfg.centres(), d).numpy()
+    assert rel(H, Href) <= 1e-4
+    X = rand_Y((cfg.n_patches, cfg.p, cfg.p // 2 + 1), 8)
+    Y = cpu(pact.forward_model(pb, wt, d, to_dev_c(X)))
+    assert rel(Y, Href * X.astype(np.complex64)[:, None]) <= 1e-4
+    Y2 = cpu(pact.forward_model(pb, wt, d, to_dev_c(X), to_dev_c(np.ones_like(Y)), accumulate=True))
+    assert rel(Y2, Href * X.astype(np.complex64)[:, None] + 1) <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8"])
+def test_psf_synth_adj(name):
+    cfg = CASES[name]()
+    rng = np.random.default_rng(9)
+    w = inputs.random_wavefronts(cfg.n_patches, cfg.n_t, rng)
+    d = cfg.delays()
+    G = rand_Y((cfg.n_patches, cfg.m, cfg.p, cfg.p // 2 + 1), 10)
+    pb = pact.Problem(cfg, DEV)
+    gw = cpu(pact.psf_synth_adj(pb, torch.as_tensor(w, device=DEV), d, to_dev_c(G)))
+    wr = torch.tensor(w.astype(np.float64), requires_grad=True)
+    H = O.transfer_functions(O.geom(cfg), wr, cfg.centres(), d)
+    Gt = torch.as_tensor(G.astype(np.complex128))
+    (ref,) = torch.autograd.grad((Gt.real * H.real + Gt.imag * H.imag).sum(), wr)
+    assert rel(gw, ref.numpy()) <= 2e-3
+
+
+# ------------------------------------------------------------------ Eq. 6-7 fused + adjoint
+
+def _mcd_case(cfg, seed, d=None, realistic=False):
+    rng = np.random.default_rng(seed)
+    if realistic:
+        case = inputs.make_case(cfg, seed)
+        Y, _, _ = O.make_measurement(O.geom(cfg), case)
+        Y = Y.numpy()
+        w = O.wavefront_errors(O.geom(cfg), case["sos_init"], case["centres"]).numpy().astype(np.float32)
+        w = (w + inputs.random_wavefronts(cfg.n_patches, cfg.n_t, rng, 1e-4)).astype(np.float32)
+    else:
+        Y = rand_Y((cfg.n_patches, cfg.m, cfg.p, cfg.p // 2 + 1), seed)
+        w = inputs.random_wavefronts(cfg.n_patches, cfg.n_t, rng)
+    d = cfg.delays() if d is None else np.asarray(d, np.float32)
+    return Y.astype(np.complex64), w, d
+
+
+def _scales(cfg, Y):
+    """Loss and gradient scales of the data term (X_hat = 0): floors for cases
+    whose exact loss or gradient is 0 (M = 1 with eps = 0)."""
+    kx, ky, kmag, _, ck = (t.numpy() for t in O.kgrid(O.geom(cfg)))
+    om = ck * kmag * 1e-3
+    e = (np.abs(Y.astype(np.complex128)) ** 2).sum(1)
+    return float((om * e).sum()), float((om * kmag * e).sum()) / np.sqrt(cfg.n_patches * cfg.n_t)
+
+
+def _check_mcd(cfg, Y, w, d, eps, idx=None, tol_g=2e-3):
+    pb = pact.Problem(cfg, DEV)
+    out = pact.mc_deconv_loss(pb, torch.as_tensor(w, device=DEV), to_dev_c(Y), d, eps, want_grad=True,
+                              want_xhat=True, want_loss_pp=True)
+    torch.cuda.synchronize()
+    sel = slice(None) if idx is None else idx
+    cen = cfg.centres()[sel]
+    L, lp, Xh, gw = O.mc_deconv_loss(O.geom(cfg), w[sel].astype(np.float64), torch.as_tensor(Y[sel]), cen, d, eps)
+    l_sc, g_sc = _scales(cfg, Y[sel])
+    if idx is None:
+        assert abs(float(out["loss"].item()) - float(L)) <= 1e-4 * abs(float(L)) + 1e-7 * l_sc
+    lpg = cpu(out["loss_pp"])[sel]
+    assert np.linalg.norm(lpg - lp.numpy()) <= 1e-4 * np.linalg.norm(lp.numpy()) + 1e-7 * l_sc
+    assert rel(cpu(out["Xhat"])[sel], Xh.numpy()) <= 1e-4
+    gg = cpu(out["dL_dw"])[sel]
+    assert np.linalg.norm(gg - gw.numpy()) <= tol_g * np.linalg.norm(gw.numpy()) + 1e-7 * g_sc
+    return out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("eps", [1e-3, 0.0])
+def test_mc_deconv_loss(name, eps):
+    cfg = CASES[name]()
+    Y, w, d = _mcd_case(cfg, 11)
+    _check_mcd(cfg, Y, w, d, eps)
+
+
+def test_mc_deconv_loss_realistic_small():
+    cfg = inputs.config_small()
+    Y, w, d = _mcd_case(cfg, 0, realistic=True)
+    _check_mcd(cfg, Y, w, d, cfg.eps)
+    _check_mcd(cfg, Y, w, d, 1e-8)          # FP64 denominator path
+
+
+def test_mc_deconv_loss_nonuniform_delays_and_wide_channels():
+    cfg = inputs.config_tiny(p=16, m=5)
+    d = np.array([-7e-4, -2e-4, 0.0, 1.5e-4, 6e-4], np.float32)
+    Y, w, _ = _mcd_case(cfg, 12)
+    _check_mcd(cfg, Y, w, d, 1e-3)
+    cfg64 = inputs.config_tiny(p=8, m=64)
+    Y, w, d = _mcd_case(cfg64, 13)
+    _check_mcd(cfg64, Y, w, d, 1e-3)
+    cfg40 = inputs.config_tiny(p=10, m=40)
+    Y, w, d = _mcd_case(cfg40, 14)
+    _check_mcd(cfg40, Y, w, d, 1e-3)
+
+
+def test_mc_deconv_loss_full_size_sampled():
+    """512x512 image, 144 patches of 80x80, 32 channels: the launch the benchmark
+    times; the oracle checks a sample of patches."""
+    cfg = inputs.config_full()
+    Y, w, d = _mcd_case(cfg, 15)
+    _check_mcd(cfg, Y, w, d, cfg.eps, idx=[0, 11, 72, 100, 143])
+
+
+def test_mc_deconv_loss_adj_scale_and_accumulate():
+    cfg = inputs.config_tiny(p=16, m=4)
+    Y, w, d = _mcd_case(cfg, 16)
+    pb = pact.Problem(cfg, DEV)
+    wt, Yt = torch.as_tensor(w, device=DEV), to_dev_c(Y)
+    g1 = pact.mc_deconv_loss(pb, wt, Yt, d, 1e-3)["dL_dw"]
+    s = torch.tensor([2.5], device=DEV)
+    g2 = pact.mc_deconv_loss_adj(pb, wt, Yt, d, 1e-3, dL_dloss=s)
+    assert rel(cpu(g2), 2.5 * cpu(g1)) <= 1e-6
+    g3 = pact.mc_deconv_loss_adj(pb, wt, Yt, d, 1e-3, dL_dw=torch.ones_like(g1), accumulate=True)
+    assert rel(cpu(g3), cpu(g1) + 1) <= 1e-6
+
+
+def test_mc_deconv_loss_noise_free_truth_is_minimum():
+    """Y = H(w) X exactly, eps = 0: the loss at w is ~0 relative to a perturbed w."""
+    cfg = inputs.config_small()
+    pb = pact.Problem(cfg, DEV)
+    rng = np.random.default_rng(17)
+    w = inputs.random_wavefronts(cfg.n_patches, cfg.n_t, rng)
+    X = rand_Y((cfg.n_patches, cfg.p, cfg.p // 2 + 1), 18)
+    wt = torch.as_tensor(w, device=DEV)
+    Y = pact.forward_model(pb, wt, cfg.delays(), to_dev_c(X))
+    l0 = float(pact.mc_deconv_loss(pb, wt, Y, cfg.delays(), 0.0, want_grad=False)["loss"].item())
+    l1 = float(pact.mc_deconv_loss(pb, wt + 5e-5, Y, cfg.delays(), 0.0, want_grad=False)["loss"].item())
+    assert l0 <= 1e-6 * l1
+
+
+# ------------------------------------------------------------------ Sec. S1.4 spectra, stitching
+
+@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8"])
+def test_patch_fft(name):
+    cfg = CASES[name]()
+    case = inputs.make_case(cfg, 3)
+    pb = pact.Problem(cfg, DEV)
+    Y = cpu(pact.patch_fft(pb, torch.as_tensor(case["noise"], device=DEV)))
+    ref = O.patch_spectra(O.geom(cfg), case["noise"], case["centres"]).numpy()
+    assert rel(Y, ref) <= 1e-4
+
+
+def test_patch_fft_full_size_sampled():
+    cfg = inputs.config_full()
+    case = inputs.make_case(cfg, 4)
+    pb = pact.Problem(cfg, DEV)
+    Y = cpu(pact.patch_fft(pb, torch.as_tensor(case["noise"][:4], device=DEV)))
+    idx = [0, 50, 143]
+    ref = O.patch_spectra(O.geom(cfg), case["noise"][:4], case["centres"][idx]).numpy()
+    assert rel(Y[idx], ref) <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8"])
+def test_stitch(name):
+    cfg = CASES[name]()
+    pb = pact.Problem(cfg, DEV)
+    X = rand_Y((cfg.n_patches, cfg.p, cfg.p // 2 + 1), 19)
+    img = cpu(pact.stitch(pb, to_dev_c(X)))
+    ref = O.stitch(O.geom(cfg), torch.as_tensor(X.astype(np.complex128)), cfg.centres()).numpy()
+    assert rel(img, ref) <= 1e-4
+
+
+# ------------------------------------------------------------------ Eq. 1
+
+def test_das_stack():
+    cfg = inputs.config_tiny(p=16, m=3).replace(img_h=48, img_w=40, n_t=32)
+    pb = pact.Problem(cfg, DEV)
+    fs, n_s, t0 = 40e6, 400, 2e-6
+    t = np.arange(n_s) / fs
+    rng = np.random.default_rng(20)
+    rf = np.zeros((cfg.n_t, n_s))
+    for n in range(cfg.n_t):                       # band-limited: a few Gaussian-windowed tones
+        for _ in range(4):
+            f0, tc = rng.uniform(1e6, 6e6), rng.uniform(t[0], t[-1])
+            rf[n] += np.cos(2 * np.pi * f0 * (t - tc)) * np.exp(-((t - tc) / 4e-7) ** 2)
+    rf = rf.astype(np.float32)
+    d = np.array([-3e-4, 0.0, 4e-4], np.float32)
+    st = cpu(pact.das_stack(pb, torch.as_tensor(rf, device=DEV), fs, t0, d))
+    ref = O.das_stack(O.geom(cfg), rf, fs, t0, d).numpy()
+    assert rel(st, ref) <= 5e-4
+
+
+# ------------------------------------------------------------------ TV, Adam
+
+def test_tv():
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 5)
+    pb = pact.Problem(cfg, DEV)
+    sos = torch.as_tensor(case["sos_true"], device=DEV)
+    val = torch.zeros(1, device=DEV)
+    grad = torch.zeros_like(sos)
+    pact.tv(pb, sos, 1e-4, val, grad)
+    s = torch.tensor(case["sos_true"].astype(np.float64), requires_grad=True)
+    T = 1e-4 * O.tv(s)
+    (gref,) = torch.autograd.grad(T, s)
+    assert abs(float(val.item()) - float(T.detach())) <= 1e-5 * float(T.detach())
+    assert rel(cpu(grad), gref.numpy()) <= 1e-6
+
+
+def test_adam_matches_oracle_and_counter():
+    rng = np.random.default_rng(21)
+    n = 1000
+    p0 = rng.standard_normal(n).astype(np.float32)
+    mask = (rng.uniform(size=n) > 0.3).astype(np.uint8)
+    p, m, v = (torch.as_tensor(x, device=DEV) for x in (p0.copy(), np.zeros(n, np.float32), np.zeros(n, np.float32)))
+    p2, m2, v2 = p.clone(), m.clone(), v.clone()
+    cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
+    rp, rm, rv = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for t in range(1, 6):
+        g = rng.standard_normal(n).astype(np.float32)
+        gt = torch.as_tensor(g, device=DEV)
+        pact.adam_step(p, gt, m, v, t, 0.05, mask=torch.as_tensor(mask, device=DEV))
+        pact.adam_step(p2, gt, m2, v2, 99, 0.05, mask=torch.as_tensor(mask, device=DEV), step_counter=cnt)
+        rp, rm, rv = (x.numpy() for x in O.adam_step(rp, g, rm, rv, t, 0.05, mask=mask))
+    assert rel(cpu(p), rp) <= 1e-6
+    assert rel(cpu(p2), rp) <= 1e-6
+    assert int(cnt.item()) == 5
+
+
+# ------------------------------------------------------------------ recovery loop, graphs, autograd
+
+def test_recovery_iteration_matches_oracle():
+    """One full iteration (Eq. 3-7 + TV + Adam) equals the oracle's, and the
+    50-step FP32 loss curve tracks the FP64 oracle's."""
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 0)
+    g = O.geom(cfg)
+    Y64, _, _ = O.make_measurement(g, case)
+    pb = pact.Problem(cfg, DEV)
+    rec = PGRecovery(pb, to_dev_c(Y64.numpy()), case["d"], cfg.eps, cfg.tv_lambda, cfg.lr,
+                     torch.as_tensor(case["sos_init"]), torch.as_tensor(case["mask"]))
+    rec.step()
+    L0, _, _, gs = O.objective(g, case["sos_init"], Y64, case["centres"], case["d"], cfg.eps, cfg.tv_lambda)
+    assert abs(rec.loss() - float(L0)) <= 1e-4 * float(L0)
+    sos1, _, _ = O.adam_step(case["sos_init"], gs, np.zeros_like(gs), np.zeros_like(gs), 1, cfg.lr,
+                             mask=case["mask"])
+    assert rel(cpu(rec.sos) - case["sos_init"], sos1.numpy() - case["sos_init"]) <= 1e-3
+    hist = [rec.loss()] + rec.run(49, record_every=1)
+    _, ref = O.recover(g, case, Y64, 50, cfg.lr, cfg.eps, cfg.tv_lambda)
+    assert rel(np.array(hist), np.array(ref)) <= 1e-2
+
+
+def test_graph_replay_equals_eager():
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 1)
+    Y64, _, _ = O.make_measurement(O.geom(cfg), case)
+    pb = pact.Problem(cfg, DEV)
+    args = (pb, to_dev_c(Y64.numpy()), case["d"], cfg.eps, cfg.tv_lambda, cfg.lr,
+            torch.as_tensor(case["sos_init"]), torch.as_tensor(case["mask"]))
+    a, b = PGRecovery(*args), PGRecovery(*args)
+    b.capture()
+    ha = a.run(6, record_every=1)
+    hb = b.run(6, record_every=1)
+    assert np.allclose(ha, hb, rtol=1e-5)
+    assert rel(cpu(a.sos), cpu(b.sos)) <= 1e-5      # atomics reorder FP32 sums
+
+
+def test_autograd_functions():
+    cfg = inputs.config_tiny(p=16, m=4)
+    case = inputs.make_case(cfg, 2)
+    pb = pact.Problem(cfg, DEV)
+    Y, _, d = _mcd_case(cfg, 22)
+    Yt = to_dev_c(Y)
+    sos = torch.as_tensor(case["sos_true"], device=DEV).requires_grad_(True)
+    w = SosToDelays.apply(pb, sos)
+    L = McDeconvLoss.apply(pb, w, Yt, d, 1e-3)
+    (3.0 * L).backward()
+    _, _, _, gref = O.objective(O.geom(cfg), case["sos_true"], torch.as_tensor(Y.astype(np.complex128)),
+                                case["centres"], d, 1e-3, 0.0)
+    assert rel(cpu(sos.grad), 3.0 * gref.numpy()) <= 2e-3
