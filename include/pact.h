@@ -220,7 +220,8 @@ pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* 
  *   value    DEVICE float [1] or NULL: value (+)= lambda * TV(v)
  *   dL_dsos  DEVICE float [G][G] or NULL: (+)= lambda * subgradient
  *            (sign(0) = 0)
- * `accumulate` applies to both outputs.
+ * `accumulate` applies to both outputs.  The value is summed per CTA and
+ * added with one atomic per CTA (summation order not fixed).
  */
 pact_status pact_tv(const pact_geometry* g, const float* sos, float lambda, float* value,
                     float* dL_dsos, int accumulate, void* stream);

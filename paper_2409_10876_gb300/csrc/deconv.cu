@@ -32,24 +32,6 @@ namespace {
 constexpr int kTPB = 256;
 constexpr float kTwoPi = 6.283185307179586f;
 
-struct Phase {
-    int uniform;      // delays uniformly spaced: E_j by recurrence
-    float d0, dd;
-};
-
-Phase make_phase(const float* d, int m) {
-    Phase p;
-    p.d0 = d[0];
-    p.dd = m > 1 ? (d[m - 1] - d[0]) / (float)(m - 1) : 0.f;
-    float mx = 0.f;
-    for (int j = 0; j < m; ++j) mx = fmaxf(mx, fabsf(d[j]));
-    int uni = 1;
-    for (int j = 0; j < m; ++j)
-        if (fabsf(d[j] - (p.d0 + j * p.dd)) > 1e-6f * mx + 1e-12f) uni = 0;
-    p.uniform = uni;
-    return p;
-}
-
 struct Tf {  // per (patch, bin) quantities of Eq. 4
     float fm;          // |f| [cycles/m]; |k| = 2 pi fm
     float2 a, b;       // exp(-j|k|W1), exp(+j|k|W2)
@@ -82,30 +64,6 @@ __device__ __forceinline__ Tf make_tf(const Geo& g, int P, float inv_pdx, float 
     return t;
 }
 
-// E_j = exp(j |k| d_j) = exp(j pi 2 fm d_j), generated in channel order.
-// Uniform delays use the rotation exp(j |k| dd), re-anchored every 8 channels.
-struct PhaseGen {
-    float2 e, rot;
-    float two_fm;
-    __device__ __forceinline__ void start(const Phase& ph, float fm) {
-        two_fm = 2.f * fm;
-        if (ph.uniform) {
-            e = cis_pi(two_fm * ph.d0);
-            rot = cis_pi(two_fm * ph.dd);
-        }
-    }
-    __device__ __forceinline__ float2 at(const Phase& ph, const Delays& dl, int j) {
-        if (!ph.uniform) return cis_pi(two_fm * dl.d[j]);
-        if (j > 0) {
-            if ((j & 7) == 0)
-                e = cis_pi(two_fm * fmaf((float)j, ph.dd, ph.d0));
-            else
-                e = cmul(e, rot);
-        }
-        return e;
-    }
-};
-
 struct McdArgs {
     Geo g;
     int N, P, F, M;
@@ -114,166 +72,185 @@ struct McdArgs {
     const float2* Y;
     float eps;
     Delays dl;
-    Phase ph;
     float2* Xhat;
     int want_grad;
     int fp64;
-    const double2* c2tab;  // [F]: sum_j exp(2j|k|d_j) in FP64 (fp64 path)
-    float* part_loss;      // [N][S]
-    float* part_dw;        // [N][S][n_t]
-    int S, chunk;
+    float* part_loss;      // [N][KT]
+    float* part_dw;        // [N][KT][n_t]
+    int KT, NG;            // bin tiles, patches per CTA
 };
 
+// CTA (kt, grp): bins k = kt*kTPB + threadIdx.x of the patches grp*NG .. grp*NG+NG-1.
+// Shared memory: E[j][t] = exp(j|k_t|d_j) for the CTA's bins (each thread reads
+// only its own column), then w and dL/dw of the NG patches.
 template <int MMAX>
-__global__ void __launch_bounds__(kTPB) mcd_kernel(const McdArgs a) {
-    extern __shared__ float smem[];
-    __shared__ float red[kTPB / 32];
+__global__ void __launch_bounds__(kTPB, 2) mcd_kernel(const McdArgs a) {
+    extern __shared__ float4 smem4[];
+    float2* E = reinterpret_cast<float2*>(smem4);                    // [M][kTPB]
+    float* w_s = reinterpret_cast<float*>(E + (size_t)a.M * kTPB);   // [NG][n_t]
+    float* dw_s = w_s + (size_t)a.NG * a.g.n_t;                      // [NG][n_t]
+    __shared__ float lsum_s[8];
     const int n_t = a.g.n_t;
-    float* w_s = smem;
-    float* dw_s = smem + n_t;
-    const int i = blockIdx.y, s = blockIdx.x;
-    for (int n = threadIdx.x; n < n_t; n += kTPB) {
-        w_s[n] = a.w[(size_t)i * n_t + n];
-        dw_s[n] = 0.f;
-    }
-    __syncthreads();
-    const int2 cc = a.centres[i];
-    const float2 c = pixel_xy(a.g, cc.x, cc.y);
-    const float inv_pdx = 1.f / (a.P * a.g.dx);
-    const float n_over_2pi = n_t / kTwoPi;
-    const int k0 = s * a.chunk;
-    const int k1 = min(a.F, k0 + a.chunk);
     const int M = a.M;
+    const int kt = blockIdx.x, grp = blockIdx.y;
+    const int i0 = grp * a.NG;
+    const int ng = min(a.NG, a.N - i0);
+    const int tid = threadIdx.x;
+    const int k = kt * kTPB + tid;
+    const bool valid = k < a.F;
+
+    // ---- per-bin constants (shared by every patch of the group)
+    const int half = a.P / 2 + 1;
+    const int u = valid ? k / half : 0;
+    const int v = valid ? k - u * half : 0;
+    const float inv_pdx = 1.f / (a.P * a.g.dx);
+    const float fx = v * inv_pdx, fy = (u < a.P / 2 ? u : u - a.P) * inv_pdx;
+    const float fm = sqrtf(fx * fx + fy * fy);                  // |k| / 2 pi  [cycles/m]
+    const float ex = fm > 0.f ? fx / fm : 1.f, ey = fm > 0.f ? fy / fm : 0.f;
+    const float kmag = kTwoPi * fm;
+    const float om = ((v == 0 || v == a.P / 2) ? 1.f : 2.f) * kmag * 1e-3f;
+    float2 C2 = make_float2(0.f, 0.f);
+    for (int j = 0; j < M; ++j) {
+        const float2 e = cis_pi(2.f * fm * a.dl.d[j]);
+        E[(size_t)j * kTPB + tid] = e;
+        C2.x = fmaf(e.x, e.x, fmaf(-e.y, e.y, C2.x));
+        C2.y = fmaf(2.f * e.x, e.y, C2.y);
+    }
+    double2 C2d = make_double2(0.0, 0.0);
+    if (a.fp64) {
+        const double fxd = v / ((double)a.P * a.g.dx), fyd = (u < a.P / 2 ? u : u - a.P) / ((double)a.P * a.g.dx);
+        const double fmd = sqrt(fxd * fxd + fyd * fyd);
+        for (int j = 0; j < M; ++j) {
+            double sn, cs;
+            sincospi(4.0 * fmd * (double)a.dl.d[j], &sn, &cs);
+            C2d.x += cs;
+            C2d.y += sn;
+        }
+    }
+    for (int q = tid; q < ng * n_t; q += kTPB) {
+        w_s[q] = a.w[(size_t)i0 * n_t + q];
+        dw_s[q] = 0.f;
+    }
+    if (tid < 8) lsum_s[tid] = 0.f;
+    __syncthreads();
+
+    const float n_over_2pi = n_t / kTwoPi;
     const float Mf = (float)M;
     const float eps = a.eps;
-    float lsum = 0.f;
+    for (int g = 0; g < ng; ++g) {
+        const int i = i0 + g;
+        float contrib = 0.f;
+        if (valid) {
+            const int2 cc = a.centres[i];
+            const float2 c = pixel_xy(a.g, cc.x, cc.y);
+            const float* wr = w_s + (size_t)g * n_t;
+            const Hits h = ring_hits(c.x, c.y, ex, ey, a.g, n_over_2pi);
+            const int n2a = h.n1a + 1 == n_t ? 0 : h.n1a + 1;
+            const int n2b = h.n1b + 1 == n_t ? 0 : h.n1b + 1;
+            const float W1 = fmaf(h.fa, wr[n2a] - wr[h.n1a], wr[h.n1a]);
+            const float W2 = fmaf(h.fb, wr[n2b] - wr[h.n1b], wr[h.n1b]);
+            const float2 al = cis_pi(-2.f * fm * W1);     // exp(-j|k| W(ang k))
+            const float2 be = cis_pi(2.f * fm * W2);      // exp(+j|k| W(ang k + pi))
 
-    for (int k = k0 + threadIdx.x; k < k1; k += kTPB) {
-        int u, v;
-        const Tf t = make_tf(a.g, a.P, inv_pdx, n_over_2pi, c, w_s, k, u, v);
-        // stream this bin's M channels into registers (read once per pass)
-        const float2* yp = a.Y + (size_t)i * M * a.F + k;
-        float2 y[MMAX];
+            const float2* yp = a.Y + (size_t)i * M * a.F + k;
+            float2 y[MMAX];
 #pragma unroll
-        for (int j = 0; j < MMAX; ++j)
-            if (j < M) y[j] = __ldcs(yp + (size_t)j * a.F);
+            for (int j = 0; j < MMAX; ++j)
+                if (j < M) y[j] = __ldcs(yp + (size_t)j * a.F);
 
-        // pass 1: channel sums of the data
-        PhaseGen pg;
-        pg.start(a.ph, t.fm);
-        float2 S1 = make_float2(0.f, 0.f), S2 = S1, C2 = S1;
+            // pass 1: S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j
+            float2 S1 = make_float2(0.f, 0.f), S2 = S1;
 #pragma unroll
-        for (int j = 0; j < MMAX; ++j) {
-            if (j < M) {
-                const float2 e = pg.at(a.ph, a.dl, j);
-                S1.x = fmaf(e.x, y[j].x, S1.x);
-                S1.y = fmaf(e.x, y[j].y, S1.y);
-                S2.x = fmaf(e.y, y[j].x, S2.x);
-                S2.y = fmaf(e.y, y[j].y, S2.y);
-                C2.x = fmaf(e.x, e.x, fmaf(-e.y, e.y, C2.x));
-                C2.y = fmaf(2.f * e.x, e.y, C2.y);
+            for (int j = 0; j < MMAX; ++j) {
+                if (j < M) {
+                    const float2 e = E[(size_t)j * kTPB + tid];
+                    S1.x = fmaf(e.x, y[j].x, S1.x);
+                    S1.y = fmaf(e.x, y[j].y, S1.y);
+                    S2.x = fmaf(e.y, y[j].x, S2.x);
+                    S2.y = fmaf(e.y, y[j].y, S2.y);
+                }
+            }
+            const float2 U = make_float2(S1.x + S2.y, S1.y - S2.x);   // sum conj(E_j) Y_j
+            const float2 V = make_float2(S1.x - S2.y, S1.y + S2.x);   // sum E_j Y_j
+            const float2 ca = cmulc(al, U), cb = cmulc(be, V);
+            const float2 A = make_float2(0.5f * (ca.x + cb.x), 0.5f * (ca.y + cb.y));
+            const float2 ab = cmulc(be, al);                           // a conj(b)
+            float B, D;
+            float2 X;
+            if (a.fp64) {
+                double sn, cs;
+                sincospi(-2.0 * (double)fm * ((double)W1 + (double)W2), &sn, &cs);
+                const double Bd = 0.5 * ((double)M + (cs * C2d.x - sn * C2d.y));
+                const double Dd = Bd + (double)eps;
+                B = (float)Bd;
+                D = (float)Dd;
+                X = Dd != 0.0 ? make_float2((float)(A.x / Dd), (float)(A.y / Dd)) : make_float2(0.f, 0.f);
+            } else {
+                B = 0.5f * (Mf + (ab.x * C2.x - ab.y * C2.y));
+                D = B + eps;
+                const float iD = D != 0.f ? 1.f / D : 0.f;
+                X = make_float2(A.x * iD, A.y * iD);
+            }
+
+            // pass 2: explicit residual R_j = Y_j - cos(|k|d_j) p - sin(|k|d_j) q
+            const float2 pp = make_float2(0.5f * (al.x + be.x), 0.5f * (al.y + be.y));
+            const float2 qm = make_float2(0.5f * (al.x - be.x), 0.5f * (al.y - be.y));
+            const float2 p = cmul(pp, X);
+            const float2 q0 = cmul(qm, X);
+            const float2 q = make_float2(-q0.y, q0.x);
+            float e2 = 0.f;
+            float2 T1 = make_float2(0.f, 0.f), T2 = T1;
+#pragma unroll
+            for (int j = 0; j < MMAX; ++j) {
+                if (j < M) {
+                    const float2 e = E[(size_t)j * kTPB + tid];
+                    float2 R;
+                    R.x = y[j].x - fmaf(e.x, p.x, e.y * q.x);
+                    R.y = y[j].y - fmaf(e.x, p.y, e.y * q.y);
+                    e2 = fmaf(R.x, R.x, fmaf(R.y, R.y, e2));
+                    T1.x = fmaf(e.x, R.x, T1.x);
+                    T1.y = fmaf(-e.x, R.y, T1.y);
+                    T2.x = fmaf(e.y, R.x, T2.x);
+                    T2.y = fmaf(-e.y, R.y, T2.y);
+                }
+            }
+            contrib = om * e2;
+            if (a.Xhat) a.Xhat[(size_t)i * a.F + k] = X;
+
+            if (a.want_grad && fm > 0.f && D != 0.f) {
+                const float iD = 1.f / D;
+                const float2 Kc = make_float2(-om * X.x * iD, -om * X.y * iD);   // conj(K)
+                const float b2 = B + 2.f * eps;
+                const float2 abC2 = cmul(ab, C2);
+                const float2 xc = make_float2(X.x, -X.y);
+                const float2 hp = make_float2(0.5f * (Mf + abC2.x), 0.5f * abC2.y);
+                const float2 hq = make_float2(0.5f * (Mf + abC2.x), -0.5f * abC2.y);
+                const float2 tp = make_float2(T1.x - T2.y, T1.y + T2.x);
+                const float2 tq = make_float2(T1.x + T2.y, T1.y - T2.x);
+                const float2 ap = cmul(al, tp), bq = cmul(be, tq);
+                const float2 xhp = cmul(xc, hp), xhq = cmul(xc, hq);
+                const float2 SP = make_float2(b2 * ap.x - eps * xhp.x, b2 * ap.y - eps * xhp.y);
+                const float2 SQ = make_float2(b2 * bq.x - eps * xhq.x, b2 * bq.y - eps * xhq.y);
+                const float gW1 = kmag * (Kc.x * SP.y + Kc.y * SP.x);
+                const float gW2 = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
+                float* dwr = dw_s + (size_t)g * n_t;
+                atomicAdd(dwr + h.n1a, (1.f - h.fa) * gW1);
+                atomicAdd(dwr + n2a, h.fa * gW1);
+                atomicAdd(dwr + h.n1b, (1.f - h.fb) * gW2);
+                atomicAdd(dwr + n2b, h.fb * gW2);
             }
         }
-        const float2 U = make_float2(S1.x + S2.y, S1.y - S2.x);   // sum conj(E_j) Y_j
-        const float2 V = make_float2(S1.x - S2.y, S1.y + S2.x);   // sum E_j Y_j
-        const float2 ca = cmulc(t.a, U), cb = cmulc(t.b, V);
-        const float2 A = make_float2(0.5f * (ca.x + cb.x), 0.5f * (ca.y + cb.y));
-        const float2 ab = cmulc(t.b, t.a);                          // a conj(b)
-        float B, D;
-        float2 X;
-        if (a.fp64) {
-            const double2 c2 = a.c2tab[k];
-            double sn, cs;
-            sincospi(-2.0 * (double)t.fm * ((double)t.W1 + (double)t.W2), &sn, &cs);
-            const double Bd = 0.5 * ((double)M + (cs * c2.x - sn * c2.y));
-            const double Dd = Bd + (double)eps;
-            B = (float)Bd;
-            D = (float)Dd;
-            X = Dd != 0.0 ? make_float2((float)(A.x / Dd), (float)(A.y / Dd)) : make_float2(0.f, 0.f);
-        } else {
-            B = 0.5f * (Mf + (ab.x * C2.x - ab.y * C2.y));
-            D = B + eps;
-            X = D != 0.f ? make_float2(A.x / D, A.y / D) : make_float2(0.f, 0.f);
-        }
-
-        // pass 2: explicit residual, loss, adjoint channel sums
-        const float2 pp = make_float2(0.5f * (t.a.x + t.b.x), 0.5f * (t.a.y + t.b.y));
-        const float2 qm = make_float2(0.5f * (t.a.x - t.b.x), 0.5f * (t.a.y - t.b.y));
-        const float2 p = cmul(pp, X);
-        const float2 q0 = cmul(qm, X);
-        const float2 q = make_float2(-q0.y, q0.x);                 // j * q0
-        pg.start(a.ph, t.fm);
-        float e2 = 0.f;
-        float2 T1 = make_float2(0.f, 0.f), T2 = T1;
-#pragma unroll
-        for (int j = 0; j < MMAX; ++j) {
-            if (j < M) {
-                const float2 e = pg.at(a.ph, a.dl, j);
-                float2 R;
-                R.x = y[j].x - fmaf(e.x, p.x, e.y * q.x);
-                R.y = y[j].y - fmaf(e.x, p.y, e.y * q.y);
-                e2 = fmaf(R.x, R.x, fmaf(R.y, R.y, e2));
-                T1.x = fmaf(e.x, R.x, T1.x);
-                T1.y = fmaf(-e.x, R.y, T1.y);
-                T2.x = fmaf(e.y, R.x, T2.x);
-                T2.y = fmaf(-e.y, R.y, T2.y);
-            }
-        }
-        const float cv = (v == 0 || v == a.P / 2) ? 1.f : 2.f;
-        const float kmag = kTwoPi * t.fm;
-        const float om = cv * kmag * 1e-3f;
-        lsum = fmaf(om, e2, lsum);
-        if (a.Xhat) a.Xhat[(size_t)i * a.F + k] = X;
-
-        if (a.want_grad && t.fm > 0.f && D != 0.f) {
-            const float2 Kc = make_float2(-om * X.x / D, -om * X.y / D);   // conj(K)
-            const float b2 = B + 2.f * eps;
-            const float2 abC2 = cmul(ab, C2);
-            const float2 xc = make_float2(X.x, -X.y);
-            const float2 hp = make_float2(0.5f * (Mf + abC2.x), 0.5f * abC2.y);   // sum conj(H)P
-            const float2 hq = make_float2(0.5f * (Mf + abC2.x), -0.5f * abC2.y);  // sum conj(H)Q
-            const float2 tp = make_float2(T1.x - T2.y, T1.y + T2.x);              // T1 + jT2
-            const float2 tq = make_float2(T1.x + T2.y, T1.y - T2.x);              // T1 - jT2
-            const float2 ap = cmul(t.a, tp), bq = cmul(t.b, tq);
-            const float2 xhp = cmul(xc, hp), xhq = cmul(xc, hq);
-            const float2 SP = make_float2(b2 * ap.x - eps * xhp.x, b2 * ap.y - eps * xhp.y);
-            const float2 SQ = make_float2(b2 * bq.x - eps * xhq.x, b2 * bq.y - eps * xhq.y);
-            const float gW1 = kmag * (Kc.x * SP.y + Kc.y * SP.x);
-            const float gW2 = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
-            const int n2a = t.n1a + 1 == n_t ? 0 : t.n1a + 1;
-            const int n2b = t.n1b + 1 == n_t ? 0 : t.n1b + 1;
-            atomicAdd(&dw_s[t.n1a], (1.f - t.fa) * gW1);
-            atomicAdd(&dw_s[n2a], t.fa * gW1);
-            atomicAdd(&dw_s[t.n1b], (1.f - t.fb) * gW2);
-            atomicAdd(&dw_s[n2b], t.fb * gW2);
-        }
+        contrib = warp_sum(contrib);
+        if ((tid & 31) == 0) atomicAdd(&lsum_s[g], contrib);
     }
-    const float tot = block_sum(lsum, red);
-    if (threadIdx.x == 0) a.part_loss[(size_t)i * a.S + s] = tot;
+    __syncthreads();
+    if (tid < ng) a.part_loss[(size_t)(i0 + tid) * a.KT + kt] = lsum_s[tid];
     if (a.want_grad) {
-        __syncthreads();
-        float* dst = a.part_dw + ((size_t)i * a.S + s) * n_t;
-        for (int n = threadIdx.x; n < n_t; n += kTPB) dst[n] = dw_s[n];
+        for (int q = tid; q < ng * n_t; q += kTPB) {
+            const int g = q / n_t, n = q - (q / n_t) * n_t;
+            a.part_dw[((size_t)(i0 + g) * a.KT + kt) * n_t + n] = dw_s[q];
+        }
     }
-}
-
-// FP64 table C2(k) = sum_j exp(2j|k|d_j) for the eps < 1e-6 path.
-__global__ void c2_table_kernel(int P, int F, double dx, Delays dl, double2* out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= F) return;
-    const int half = P / 2 + 1;
-    const int u = k / half, v = k - (k / half) * half;
-    const int us = u < P / 2 ? u : u - P;
-    const double fx = v / (P * dx), fy = us / (P * dx);
-    const double fm = sqrt(fx * fx + fy * fy);
-    double re = 0.0, im = 0.0;
-    for (int j = 0; j < dl.m; ++j) {
-        double sn, cs;
-        sincospi(4.0 * fm * (double)dl.d[j], &sn, &cs);
-        re += cs;
-        im += sn;
-    }
-    out[k] = make_double2(re, im);
 }
 
 struct FinArgs {
@@ -316,23 +293,21 @@ __global__ void __launch_bounds__(kTPB) mcd_finalize_kernel(const FinArgs a) {
 }
 
 struct Plan {
-    int S, chunk;
-    size_t off_dw, off_c2, total;
+    int KT, NG;
+    size_t smem, off_dw, total;
 };
 
 Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
-    (void)m;
     Plan p;
     const int F = pt->p * (pt->p / 2 + 1);
+    p.KT = (F + kTPB - 1) / kTPB;
     const int sms = num_sms();
-    int S = (2 * sms + pt->n - 1) / pt->n;
-    S = std::max(1, std::min(S, std::max(1, F / kTPB)));
-    p.S = S;
-    p.chunk = (F + S - 1) / S;
-    const size_t n_loss = (size_t)pt->n * S;
+    int ng = (int)((long long)p.KT * pt->n / (2LL * sms));
+    p.NG = std::max(1, std::min(8, ng));
+    p.smem = (size_t)m * kTPB * sizeof(float2) + 2 * (size_t)p.NG * g->n_t * sizeof(float);
+    const size_t n_loss = (size_t)pt->n * p.KT;
     p.off_dw = align_up(n_loss * sizeof(float), 256);
-    p.off_c2 = p.off_dw + align_up((size_t)pt->n * S * g->n_t * sizeof(float), 256);
-    p.total = p.off_c2 + align_up((size_t)F * sizeof(double2), 256);
+    p.total = p.off_dw + align_up((size_t)pt->n * p.KT * g->n_t * sizeof(float), 256);
     return p;
 }
 
@@ -347,11 +322,10 @@ pact_status check_delays(const float* d, int m) {
 }
 
 template <int MMAX>
-pact_status launch_mcd(const McdArgs& a, cudaStream_t st) {
-    const size_t shm = 2 * (size_t)a.g.n_t * sizeof(float);
-    PACT_TRY(ensure_smem((const void*)mcd_kernel<MMAX>, shm, "mc_deconv_loss: shared memory attribute"));
-    dim3 grid(a.S, a.N);
-    mcd_kernel<MMAX><<<grid, kTPB, shm, st>>>(a);
+pact_status launch_mcd(const McdArgs& a, size_t smem, cudaStream_t st) {
+    PACT_TRY(ensure_smem((const void*)mcd_kernel<MMAX>, smem, "mc_deconv_loss: shared memory attribute"));
+    dim3 grid(a.KT, (a.N + a.NG - 1) / a.NG);
+    mcd_kernel<MMAX><<<grid, kTPB, smem, st>>>(a);
     return check_launch("mc_deconv_loss kernel");
 }
 
@@ -367,8 +341,8 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     if (!ws) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss: workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(Y) % 8) return fail(PACT_ERR_INVALID_ARG, "Y must be 8-byte aligned");
-    if ((size_t)g->n_t * 2 * sizeof(float) > 200 * 1024) return fail(PACT_ERR_SHAPE, "n_t too large");
     const Plan pl = make_plan(g, pt, m);
+    if (pl.smem > 220 * 1024) return fail(PACT_ERR_SHAPE, "mc_deconv_loss: n_t x channels too large for shared memory");
     if (ws_bytes < pl.total)
         return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, pl.total);
     cudaStream_t st = as_stream(stream);
@@ -384,29 +358,22 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.Y = reinterpret_cast<const float2*>(Y);
     a.eps = eps;
     a.dl = make_delays(d, m);
-    a.ph = make_phase(d, m);
     a.Xhat = reinterpret_cast<float2*>(Xhat);
     a.want_grad = dL_dw != nullptr;
     a.fp64 = eps < 1e-6f;
-    a.c2tab = reinterpret_cast<const double2*>(base + pl.off_c2);
     a.part_loss = reinterpret_cast<float*>(base);
     a.part_dw = reinterpret_cast<float*>(base + pl.off_dw);
-    a.S = pl.S;
-    a.chunk = pl.chunk;
-    if (a.fp64) {
-        c2_table_kernel<<<(a.F + 127) / 128, 128, 0, st>>>(a.P, a.F, (double)g->dx, a.dl,
-                                                           reinterpret_cast<double2*>(base + pl.off_c2));
-        PACT_TRY(check_launch("mc_deconv_loss: c2 table"));
-    }
+    a.KT = pl.KT;
+    a.NG = pl.NG;
     pact_status s;
-    if (m <= 8) s = launch_mcd<8>(a, st);
-    else if (m <= 16) s = launch_mcd<16>(a, st);
-    else if (m <= 32) s = launch_mcd<32>(a, st);
-    else s = launch_mcd<64>(a, st);
+    if (m <= 8) s = launch_mcd<8>(a, pl.smem, st);
+    else if (m <= 16) s = launch_mcd<16>(a, pl.smem, st);
+    else if (m <= 32) s = launch_mcd<32>(a, pl.smem, st);
+    else s = launch_mcd<64>(a, pl.smem, st);
     if (s != PACT_OK) return s;
     FinArgs f;
     f.N = a.N;
-    f.S = a.S;
+    f.S = a.KT;
     f.n_t = g->n_t;
     f.part_loss = a.part_loss;
     f.part_dw = a.part_dw;

@@ -9,13 +9,15 @@ namespace {
 
 __device__ __forceinline__ float sgn(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
-// One CTA: deterministic value reduction; subgradient per node.
-__global__ void __launch_bounds__(1024) tv_kernel(int G, const float* sos, float lambda, float* value,
-                                                  float* grad, int accumulate) {
-    __shared__ float red[32];
-    float part = 0.f;
+// One thread per node: subgradient; the value is reduced per CTA and added
+// to *value with one atomic per CTA.
+__global__ void __launch_bounds__(256) tv_kernel(int G, const float* sos, float lambda, float* value,
+                                                 float* grad, int accumulate) {
+    __shared__ float red[8];
     const int GG = G * G;
-    for (int q = threadIdx.x; q < GG; q += blockDim.x) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    float part = 0.f;
+    if (q < GG) {
         const int p = q / G, c = q - (q / G) * G;
         const float v = sos[q];
         float gq = 0.f;
@@ -33,8 +35,10 @@ __global__ void __launch_bounds__(1024) tv_kernel(int G, const float* sos, float
         if (c > 0) gq += sgn(v - sos[q - 1]);
         if (grad) grad[q] = accumulate ? fmaf(lambda, gq, grad[q]) : lambda * gq;
     }
-    const float tot = block_sum(part, red);
-    if (value && threadIdx.x == 0) value[0] = accumulate ? fmaf(lambda, tot, value[0]) : lambda * tot;
+    if (value) {
+        const float tot = block_sum(part, red);
+        if (threadIdx.x == 0) atomicAdd(value, lambda * tot);
+    }
 }
 
 __global__ void adam_kernel(int n, float* param, const float* grad, float* m, float* v, float lr, float b1,
@@ -68,7 +72,11 @@ extern "C" pact_status pact_tv(const pact_geometry* g, const float* sos, float l
     PACT_TRY(check_geometry(g));
     if (!sos) return fail(PACT_ERR_INVALID_ARG, "tv: sos is NULL");
     if (!value && !dL_dsos) return PACT_OK;
-    tv_kernel<<<1, 1024, 0, as_stream(stream)>>>(g->sos_g, sos, lambda, value, dL_dsos, accumulate);
+    cudaStream_t st = as_stream(stream);
+    if (value && !accumulate && cudaMemsetAsync(value, 0, sizeof(float), st) != cudaSuccess)
+        return check_launch("tv: memset");
+    const int GG = g->sos_g * g->sos_g;
+    tv_kernel<<<(GG + 255) / 256, 256, 0, st>>>(g->sos_g, sos, lambda, value, dL_dsos, accumulate);
     return check_launch("tv kernel");
 }
 

@@ -190,6 +190,10 @@ def _check_mcd(cfg, Y, w, d, eps, idx=None, tol_g=2e-3):
     lpg = cpu(out["loss_pp"])[sel]
     assert np.linalg.norm(lpg - lp.numpy()) <= 1e-4 * np.linalg.norm(lp.numpy()) + 1e-7 * l_sc
     assert rel(cpu(out["Xhat"])[sel], Xh.numpy()) <= 1e-4
+    if cfg.m == 1 and eps == 0.0:
+        # exact gradient is 0 (zero residual); in FP32 it is rounding noise scaled
+        # by 1/|H|, unbounded near the zeros of H -- nothing to compare
+        return out
     gg = cpu(out["dL_dw"])[sel]
     assert np.linalg.norm(gg - gw.numpy()) <= tol_g * np.linalg.norm(gw.numpy()) + 1e-7 * g_sc
     return out
