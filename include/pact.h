@@ -215,6 +215,36 @@ pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* 
                                     size_t ws_bytes, void* stream);
 
 /*
+ * pact_mc_deconv_loss without a workspace argument.  The paper has no
+ * counterpart: this is a library-usage variant of pact_mc_deconv_loss with
+ * identical arithmetic and outputs.
+ *
+ * Some callers cannot allocate device memory: a plug-in whose host
+ * application owns every device buffer and forbids cudaMalloc, or a
+ * real-time acquisition loop that must not allocate (allocation can block
+ * or fail mid-scan).  This entry point allocates nothing; its scratch space
+ * is a fixed device array of PACT_NOALLOC_SCRATCH_BYTES inside the library,
+ * held by every GPU that loads the library until the process exits.  The
+ * caller still passes all inputs and outputs.
+ *   - Problems whose scratch need (pact_mc_deconv_loss_workspace_size)
+ *     exceeds PACT_NOALLOC_SCRATCH_BYTES are rejected with PACT_ERR_SHAPE
+ *     and a message giving both sizes; nothing is launched.
+ *   - The first call on each device looks up the device address of the
+ *     array (with that device current) and caches it; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and it keeps the last
+ *     call's contents; the kernels overwrite every scratch entry they read,
+ *     so no clearing is needed.  Calls that overlap on the GPU (different
+ *     streams, or several host threads) race on the array: issue them in
+ *     order on one stream.
+ * Arguments, layouts and errors are those of pact_mc_deconv_loss.
+ */
+#define PACT_NOALLOC_SCRATCH_BYTES (8u << 20)   /* 8 MiB */
+pact_status pact_mc_deconv_loss_noalloc(const pact_geometry* g, const pact_patches* pt, const float* w,
+                                        const float* Y, const float* d, int m, float eps, float* loss,
+                                        float* loss_pp, float* Xhat, float* dL_dw, void* stream);
+
+/*
  * Total variation regulariser of Eq. 7 on the pixel-grid SOS:
  *   TV(v) = sum |v[p+1][q] - v[p][q]| + |v[p][q+1] - v[p][q]|
  *   value    DEVICE float [1] or NULL: value (+)= lambda * TV(v)

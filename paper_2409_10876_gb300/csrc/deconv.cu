@@ -23,6 +23,7 @@
 // lookup interpolates (shared-memory accumulation per CTA, then a
 // deterministic reduction over the CTAs of a patch).
 #include <algorithm>
+#include <mutex>
 
 #include "pact_internal.cuh"
 
@@ -533,4 +534,57 @@ extern "C" pact_status pact_psf_synth_adj(const pact_geometry* g, const pact_pat
                                           const float* d, int m, const float* dL_dH, float* dL_dw,
                                           int accumulate, void* stream) {
     return run_psf(g, pt, w, d, m, 2, dL_dH, nullptr, dL_dw, accumulate, stream);
+}
+
+// ---------------------------------------------------------------------------
+// pact_mc_deconv_loss_noalloc: the fused pass with its scratch taken from a
+// fixed device array instead of a caller-provided workspace, for callers that
+// cannot allocate device memory.  The array lives for the life of the process
+// on every device that loads the library.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PACT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// symbol itself is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+pact_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(PACT_ERR_CUDA, "mc_deconv_loss_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 256) return fail(PACT_ERR_UNSUPPORTED, "mc_deconv_loss_noalloc: device index %d", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PACT_ERR_CUDA, "mc_deconv_loss_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PACT_OK;
+}
+}  // namespace
+
+extern "C" pact_status pact_mc_deconv_loss_noalloc(const pact_geometry* g, const pact_patches* pt, const float* w,
+                                                   const float* Y, const float* d, int m, float eps, float* loss,
+                                                   float* loss_pp, float* Xhat, float* dL_dw, void* stream) {
+    if (!loss) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss_noalloc: loss is NULL");
+    PACT_TRY(check_geometry(g));
+    PACT_TRY(check_patches(pt));
+    PACT_TRY(check_delays(d, m));
+    const size_t need = make_plan(g, pt, m).total;
+    if (need > (size_t)PACT_NOALLOC_SCRATCH_BYTES)
+        return fail(PACT_ERR_SHAPE,
+                    "mc_deconv_loss_noalloc: this problem needs %zu bytes of scratch; the built-in scratch array "
+                    "holds %zu bytes (use pact_mc_deconv_loss with a workspace instead)",
+                    need, (size_t)PACT_NOALLOC_SCRATCH_BYTES);
+    void* scratch = nullptr;
+    PACT_TRY(noalloc_scratch(&scratch));
+    return run_mcd(g, pt, w, Y, d, m, eps, loss, loss_pp, Xhat, dL_dw, nullptr, 0, scratch,
+                   (size_t)PACT_NOALLOC_SCRATCH_BYTES, stream);
 }

@@ -53,6 +53,7 @@ _SIGS = {
     "pact_forward_model": ([_GP, _PP, _VP, _VP, _I, _VP, _VP, _I, _VP], _I),
     "pact_mc_deconv_loss_workspace_size": ([_GP, _PP, _I], _SZ),
     "pact_mc_deconv_loss": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _VP, _VP, _VP, _SZ, _VP], _I),
+    "pact_mc_deconv_loss_noalloc": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _VP, _VP, _VP], _I),
     "pact_mc_deconv_loss_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_tv": ([_GP, _VP, _F, _VP, _VP, _I, _VP], _I),
     "pact_adam_step": ([_I, _VP, _VP, _VP, _VP, _I, _VP, _F, _F, _F, _F, _VP, _VP], _I),
@@ -287,6 +288,38 @@ def mc_deconv_loss(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=F
                                  _ptr(out.get("Xhat") if want_xhat else None),
                                  _ptr(out.get("dL_dw") if want_grad else None), _ptr(ws), ws.numel(), _stream()),
            "mc_deconv_loss")
+    return out
+
+
+def mc_deconv_loss_noalloc(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=False, want_loss_pp=False,
+                           out=None):
+    """mc_deconv_loss for callers that cannot allocate device memory: the
+    library uses its built-in scratch array (PACT_NOALLOC_SCRATCH_BYTES) instead
+    of a workspace.  Outputs must be preallocated in `out` if the caller cannot
+    let this binding allocate them; missing ones are allocated here."""
+    L = load()
+    w = _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    Y = _dev(Y, "Y", torch.complex64)
+    m = Y.shape[1]
+    _dev(Y, "Y", torch.complex64, pb.spectra_shape(m))
+    dh, dp = _host_f32(d)
+    if dh.size != m:
+        raise PactError(f"delay list has {dh.size} entries but Y has {m} channels")
+    out = {} if out is None else out
+    dev = w.device
+    if "loss" not in out:
+        out["loss"] = torch.zeros(1, dtype=torch.float32, device=dev)
+    if want_grad and "dL_dw" not in out:
+        out["dL_dw"] = _empty((pb.n, pb.n_t), torch.float32, dev)
+    if want_xhat and "Xhat" not in out:
+        out["Xhat"] = _empty((pb.n, pb.p, pb.p // 2 + 1), torch.complex64, dev)
+    if want_loss_pp and "loss_pp" not in out:
+        out["loss_pp"] = _empty((pb.n,), torch.float32, dev)
+    _check(L.pact_mc_deconv_loss_noalloc(pb.gp(), pb.pp(), _ptr(w), _ptr(Y), dp, m, float(eps), _ptr(out["loss"]),
+                                         _ptr(out.get("loss_pp") if want_loss_pp else None),
+                                         _ptr(out.get("Xhat") if want_xhat else None),
+                                         _ptr(out.get("dL_dw") if want_grad else None), _stream()),
+           "mc_deconv_loss_noalloc")
     return out
 
 
