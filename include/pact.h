@@ -189,7 +189,7 @@ size_t pact_mc_deconv_loss_workspace_size(const pact_geometry* g, const pact_pat
  * When dL_dw is not NULL the same pass also returns the exact gradient
  * dL/dw (hand-written adjoint: X_i is recomputed, never stored).
  *   w        DEVICE float [N][N_t]          wavefront errors
- *   Y        DEVICE c64 [N][m][P][P/2+1]    patch spectra
+ *   Y        DEVICE c64 [N][m][P][P/2+1]    patch spectra, 16-byte aligned
  *   d        HOST float [m]                 delays [m]
  *   loss     DEVICE float [1]               output (data term only)
  *   loss_pp  DEVICE float [N] or NULL       per-patch data term
@@ -197,8 +197,10 @@ size_t pact_mc_deconv_loss_workspace_size(const pact_geometry* g, const pact_pat
  *   dL_dw    DEVICE float [N][N_t] or NULL  output gradient
  *   ws       DEVICE workspace (256-byte aligned) of the size above
  * When eps < 1e-6 the per-bin channel-sum denominator and the division run
- * in FP64.  Errors: INVALID_ARG (null w/Y/loss/ws, eps < 0, small ws),
- * SHAPE (m > PACT_MAX_CHANNELS, P odd or out of range).
+ * in FP64.  Errors: INVALID_ARG (null w/Y/loss/ws, eps < 0, small ws,
+ * misaligned Y), SHAPE (m > PACT_MAX_CHANNELS, P odd or out of range, n_t too
+ * large for shared memory).  A bulk copy that does not complete within
+ * 200 ms (never expected) makes the loss and dL_dw NaN instead of hanging.
  */
 pact_status pact_mc_deconv_loss(const pact_geometry* g, const pact_patches* pt, const float* w,
                                 const float* Y, const float* d, int m, float eps, float* loss,
@@ -239,7 +241,7 @@ pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* 
  *     order on one stream.
  * Arguments, layouts and errors are those of pact_mc_deconv_loss.
  */
-#define PACT_NOALLOC_SCRATCH_BYTES (8u << 20)   /* 8 MiB */
+#define PACT_NOALLOC_SCRATCH_BYTES (16u << 20)   /* 16 MiB */
 pact_status pact_mc_deconv_loss_noalloc(const pact_geometry* g, const pact_patches* pt, const float* w,
                                         const float* Y, const float* d, int m, float eps, float* loss,
                                         float* loss_pp, float* Xhat, float* dL_dw, void* stream);
@@ -271,6 +273,38 @@ pact_status pact_tv(const pact_geometry* g, const float* sos, float lambda, floa
 pact_status pact_adam_step(int n, float* param, const float* grad, float* m, float* v, int step,
                            int* step_counter, float lr, float beta1, float beta2, float eps,
                            const unsigned char* mask, void* stream);
+
+/*
+ * Neural-field SOS (Sec. 3.3: the SOS as a coordinate-based network; here a
+ * Fourier-feature MLP on BF16 tensor cores with FP32 accumulation).  For
+ * every SOS node (row-major over the G x G grid) with position (x, y) over
+ * the field of view G sos_dx:
+ *   f = [sin 2 pi f_l x, cos 2 pi f_l x, sin 2 pi f_l y, cos 2 pi f_l y]_{l<16},
+ *       f_l = 64^(l/15) cycles per field of view                      (64)
+ *   h_l = relu(W_l h_{l-1} + b_l), l = 1..4, width 128
+ *   v = v_mid + v_half tanh(w5 . h_4 + b5) inside the mask, v_bg outside.
+ * Parameters are one FP32 vector in the order W1[128][64], b1[128],
+ * W2[128][128], b2, W3, b3, W4, b4, w5[128], b5[1] (pact_nf_param_count()
+ * entries, 16-byte aligned); weights and activations are rounded to BF16.
+ *   mask  DEVICE uint8 [G][G] or NULL (all nodes trainable)
+ *   sos   DEVICE float [G][G] output
+ *   ws    DEVICE workspace (pact_nf_workspace_size), which also carries the
+ *         activations from pact_nf_forward to the next pact_nf_backward
+ * pact_nf_backward: dL_dparams (+)= (dL/dsos) d sos / d params for the
+ * parameters of the last forward call on this workspace.
+ * A tensor-core completion wait that gives up (never expected) poisons the
+ * outputs with NaN and sets a status word that pact_nf_status reports
+ * (PACT_ERR_TIMEOUT); pact_nf_status synchronises the stream.
+ */
+int pact_nf_param_count(void);
+size_t pact_nf_workspace_size(const pact_geometry* g);
+pact_status pact_nf_forward(const pact_geometry* g, const float* params, const unsigned char* mask, float v_mid,
+                            float v_half, float* sos, void* ws, size_t ws_bytes, void* stream);
+pact_status pact_nf_backward(const pact_geometry* g, const float* params, const unsigned char* mask, float v_mid,
+                             float v_half, const float* dL_dsos, float* dL_dparams, int accumulate, void* ws,
+                             size_t ws_bytes, void* stream);
+pact_status pact_nf_status(const pact_geometry* g, const void* ws, size_t ws_bytes, int* host_status,
+                           void* stream);
 
 /* Workspace bytes of pact_stitch. */
 size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt);

@@ -467,3 +467,63 @@ def recover(g, case: dict, Y, steps: int, lr: float, eps: float, lam: float):
         hist.append(float(L))
         sos, m, v = adam_step(sos, gs, m, v, it, lr, mask=mask)
     return sos, hist
+
+
+# --------------------------------------------------------------------------
+# Neural-field SOS (Sec. 3.3 coordinate-based representation; the Fourier-
+# feature MLP of the BF16 workload): features -> 4 x 128 ReLU -> tanh-bounded
+# output, evaluated at the SOS nodes; nodes outside the mask stay at v_bg.
+# --------------------------------------------------------------------------
+
+def nf_unflatten(params, shapes):
+    out, o = {}, 0
+    for name, shape in shapes:
+        n = int(np.prod(shape))
+        out[name] = params[o:o + n].reshape(shape)
+        o += n
+    return out
+
+
+def nf_features(g, freqs) -> torch.Tensor:
+    """[G*G, 4F]: for every node (row-major) and frequency f_l the features
+    sin(2 pi f_l x), cos(2 pi f_l x), sin(2 pi f_l y), cos(2 pi f_l y) with x, y the
+    node position divided by the field of view (G sos_dx)."""
+    G = g.sos_g
+    c = (torch.arange(G, dtype=DT) - (G - 1) / 2.0) / G      # position / field of view
+    yy, xx = torch.meshgrid(c, c, indexing="ij")
+    x, y = xx.reshape(-1, 1), yy.reshape(-1, 1)
+    f = _t(freqs)[None, :]
+    feats = torch.stack([torch.sin(2 * math.pi * f * x), torch.cos(2 * math.pi * f * x),
+                         torch.sin(2 * math.pi * f * y), torch.cos(2 * math.pi * f * y)], dim=2)
+    return feats.reshape(G * G, -1)
+
+
+def nf_sos(g, params, shapes, freqs, mask, v_mid: float, v_half: float) -> torch.Tensor:
+    """SOS [G, G] from the neural field; params may require grad."""
+    p = nf_unflatten(params, shapes)
+    h = nf_features(g, freqs)
+    n_hidden = sum(1 for name, _ in shapes if name.startswith("W"))
+    for l in range(1, n_hidden + 1):
+        h = torch.relu(h @ p[f"W{l}"].T + p[f"b{l}"])
+    z = h @ p["w5"] + p["b5"]
+    v = v_mid + v_half * torch.tanh(z)
+    keep = _t(mask).reshape(-1) > 0
+    v = torch.where(keep, v, torch.full_like(v, g.v_bg))
+    return v.reshape(g.sos_g, g.sos_g)
+
+
+def nf_objective(g, params, shapes, freqs, mask, v_mid, v_half, Y, centres, d, eps: float,
+                 want_grad: bool = True):
+    """Eq. 7 (lambda = 0, as for the neural field in Sec. 3.3) as a function of
+    the neural-field parameters; gradient by autograd."""
+    prm = _t(params).clone().requires_grad_(want_grad)
+    sos = nf_sos(g, prm, shapes, freqs, mask, v_mid, v_half)
+    w = wavefront_errors(g, sos, centres)
+    Yc = Y.to(CT) if isinstance(Y, torch.Tensor) else torch.as_tensor(Y).to(CT)
+    H = transfer_functions(g, w, centres, d)
+    Xh = deconvolve(H, Yc, eps)
+    L = data_loss(g, H, Yc, Xh)
+    gp = None
+    if want_grad:
+        (gp,) = torch.autograd.grad(L, prm)
+    return L.detach(), sos.detach(), gp

@@ -12,7 +12,7 @@
 //     X  = A / (B + eps)                                                  (Eq. 6)
 // The residual R_j = Y_j - H_j X = Y_j - cos(|k|d_j) p - sin(|k|d_j) q with
 // p = (a + b) X / 2, q = j (a - b) X / 2 is formed explicitly in a second
-// pass over the register-resident Y (no E - |A|^2/B cancellation), giving
+// pass over the shared-memory copy of Y (no E - |A|^2/B cancellation), giving
 // the loss term w_k sum_j |R_j|^2 (Eq. 7, w_k = c_k |k|_mm).
 // Adjoint: dL/dconj(H_j) = -(w_k conj(X)/D) ((B + 2 eps) R_j - eps X H_j),
 // D = B + eps, and with T1 = sum_j cos(|k|d_j) conj(R_j),
@@ -78,180 +78,235 @@ struct McdArgs {
     int fp64;
     float* part_loss;      // [N][KT]
     float* part_dw;        // [N][KT][n_t]
-    int KT, NG;            // bin tiles, patches per CTA
+    const float2* lut;     // [N][F] ring coordinates (t_a, t_b)
+    const float2* etab;    // [M][F] exp(j|k|d_j)
+    const float4* btab;    // [F] (|k|/2pi, c_k |k|_mm, Re C2, Im C2)
+    const double2* c2d;    // [F] C2 in FP64 (eps < 1e-6 only)
+    int KT;                // 256-bin tiles
 };
 
-// CTA (kt, grp): bins k = kt*kTPB + threadIdx.x of the patches grp*NG .. grp*NG+NG-1.
-// Shared memory: E[j][t] = exp(j|k_t|d_j) for the CTA's bins (each thread reads
-// only its own column), then w and dL/dw of the NG patches.
-template <int MMAX>
-__global__ void __launch_bounds__(kTPB, 2) mcd_kernel(const McdArgs a) {
-    extern __shared__ float4 smem4[];
-    float2* E = reinterpret_cast<float2*>(smem4);                    // [M][kTPB]
-    float* w_s = reinterpret_cast<float*>(E + (size_t)a.M * kTPB);   // [NG][n_t]
-    float* dw_s = w_s + (size_t)a.NG * a.g.n_t;                      // [NG][n_t]
-    __shared__ float lsum_s[8];
-    const int n_t = a.g.n_t;
-    const int M = a.M;
-    const int kt = blockIdx.x, grp = blockIdx.y;
-    const int i0 = grp * a.NG;
-    const int ng = min(a.NG, a.N - i0);
-    const int tid = threadIdx.x;
-    const int k = kt * kTPB + tid;
-    const bool valid = k < a.F;
+// Ring coordinate t = alpha N_t / (2 pi) in [0, N_t) of the point where the ray
+// from c in direction (dx, dy) meets the ring (same arithmetic as ring_hit).
+__device__ __forceinline__ float ring_coord(float cx, float cy, float dx, float dy, const Geo& g,
+                                            float n_over_2pi) {
+    const float ce = cx * dx + cy * dy;
+    const float disc = fmaxf(ce * ce - (cx * cx + cy * cy) + g.R * g.R, 0.f);
+    const float s = sqrtf(disc) - ce;
+    float t = (atan2f(fmaf(s, dy, cy), fmaf(s, dx, cx)) - g.phase) * n_over_2pi;
+    t -= floorf(t / (float)g.n_t) * (float)g.n_t;
+    return t;
+}
 
-    // ---- per-bin constants (shared by every patch of the group)
-    const int half = a.P / 2 + 1;
-    const int u = valid ? k / half : 0;
-    const int v = valid ? k - u * half : 0;
-    const float inv_pdx = 1.f / (a.P * a.g.dx);
-    const float fx = v * inv_pdx, fy = (u < a.P / 2 ? u : u - a.P) * inv_pdx;
-    const float fm = sqrtf(fx * fx + fy * fy);                  // |k| / 2 pi  [cycles/m]
-    const float ex = fm > 0.f ? fx / fm : 1.f, ey = fm > 0.f ? fy / fm : 0.f;
-    const float kmag = kTwoPi * fm;
-    const float om = ((v == 0 || v == a.P / 2) ? 1.f : 2.f) * kmag * 1e-3f;
-    float2 C2 = make_float2(0.f, 0.f);
+// Per-call tables of the fused pass, one launch:
+//  * blockIdx.y < N: geometry-only part of Eq. 4 for patch i = blockIdx.y, the
+//    ring coordinates of the directions ang k and ang k + pi,
+//    lut[i][k] = (t_a, t_b);
+//  * blockIdx.y == N: per-bin tables etab[j][k] = exp(j|k|d_j) and
+//    btab[k] = (|k|/2pi, c_k |k|_mm, Re C2, Im C2) with C2 = sum_j exp(2j|k|d_j).
+__global__ void mcd_tables_kernel(Geo g, int N, int P, int F, int M, Delays dl, const int2* centres, float2* lut,
+                                  float2* etab, float4* btab) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= F) return;
+    int u, v;
+    const float2 f = bin_freq(k, P, 1.f / (P * g.dx), u, v);
+    const float fm = sqrtf(f.x * f.x + f.y * f.y);
+    if ((int)blockIdx.y < N) {
+        const float ex = fm > 0.f ? f.x / fm : 1.f, ey = fm > 0.f ? f.y / fm : 0.f;
+        const int2 cc = centres[blockIdx.y];
+        const float2 c = pixel_xy(g, cc.x, cc.y);
+        const float nop = g.n_t / kTwoPi;
+        lut[(size_t)blockIdx.y * F + k] =
+            make_float2(ring_coord(c.x, c.y, ex, ey, g, nop), ring_coord(c.x, c.y, -ex, -ey, g, nop));
+        return;
+    }
+    float c2x = 0.f, c2y = 0.f;
     for (int j = 0; j < M; ++j) {
-        const float2 e = cis_pi(2.f * fm * a.dl.d[j]);
-        E[(size_t)j * kTPB + tid] = e;
-        C2.x = fmaf(e.x, e.x, fmaf(-e.y, e.y, C2.x));
-        C2.y = fmaf(2.f * e.x, e.y, C2.y);
+        const float2 e = cis_pi(2.f * fm * dl.d[j]);
+        etab[(size_t)j * F + k] = e;
+        c2x = fmaf(e.x, e.x, fmaf(-e.y, e.y, c2x));
+        c2y = fmaf(2.f * e.x, e.y, c2y);
     }
-    double2 C2d = make_double2(0.0, 0.0);
-    if (a.fp64) {
-        const double fxd = v / ((double)a.P * a.g.dx), fyd = (u < a.P / 2 ? u : u - a.P) / ((double)a.P * a.g.dx);
-        const double fmd = sqrt(fxd * fxd + fyd * fyd);
-        for (int j = 0; j < M; ++j) {
-            double sn, cs;
-            sincospi(4.0 * fmd * (double)a.dl.d[j], &sn, &cs);
-            C2d.x += cs;
-            C2d.y += sn;
-        }
-    }
-    for (int q = tid; q < ng * n_t; q += kTPB) {
-        w_s[q] = a.w[(size_t)i0 * n_t + q];
-        dw_s[q] = 0.f;
-    }
-    if (tid < 8) lsum_s[tid] = 0.f;
-    __syncthreads();
+    const float om = ((v == 0 || v == P / 2) ? 1.f : 2.f) * kTwoPi * fm * 1e-3f;
+    btab[k] = make_float4(fm, om, c2x, c2y);
+}
 
-    const float n_over_2pi = n_t / kTwoPi;
+// FP64 C2(k) = sum_j exp(2j|k|d_j) for the eps < 1e-6 path.
+__global__ void mcd_c2d_kernel(int P, int F, double dx, Delays dl, double2* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= F) return;
+    const int half = P / 2 + 1;
+    const int u = k / half, v = k - (k / half) * half;
+    const int us = u < P / 2 ? u : u - P;
+    const double fx = v / (P * dx), fy = us / (P * dx);
+    const double fm = sqrt(fx * fx + fy * fy);
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < dl.m; ++j) {
+        double sn, cs;
+        sincospi(4.0 * fm * (double)dl.d[j], &sn, &cs);
+        re += cs;
+        im += sn;
+    }
+    out[k] = make_double2(re, im);
+}
+
+// Sum over the two threads of a bin (lanes b and b + 16).
+__device__ __forceinline__ float pair_sum(float x) { return x + __shfl_xor_sync(0xffffffffu, x, 16); }
+
+// CTA (kt, i): bins kt*256 .. kt*256+255 of patch i, 512 threads.  Two
+// threads share a bin (lanes b and b+16 of a warp; warp w owns bins
+// 16w .. 16w+15): half h owns channels j = h, h+2, ..., loads Y_ij(k) and
+// exp(j|k|d_j) for them straight into registers (Y streamed once from HBM,
+// the exp table from L2) and completes every channel sum with one shuffle.
+// Half 0 evaluates the lookup of w at ang k, half 1 at ang k + pi.  With
+// S1 = sum cos(|k|d_j) Y_j and S2 = sum sin(|k|d_j) Y_j the residual sums of
+// the adjoint follow in closed form, T1 = conj(S1) - conj(p) Scc - conj(q) Scs,
+// T2 = conj(S2) - conj(p) Scs - conj(q) Sss; only sum |R_j|^2 needs the explicit
+// second pass over the registers.  CPH channels per half; EXACT: M == 2 CPH.
+template <int CPH, bool EXACT>
+__global__ void __launch_bounds__(512, 1) mcd_kernel(const McdArgs a) {
+    extern __shared__ float dw_s[];                          // [n_t]
+    __shared__ float lsum_s;
+    const int n_t = a.g.n_t, M = EXACT ? 2 * CPH : a.M;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int hf = lane >> 4;
+    const int kt = blockIdx.x, i = blockIdx.y;
+    const int k = kt * 256 + warp * 16 + (lane & 15);
+    const bool valid = k < a.F;
+    for (int n = tid; n < n_t; n += 512) dw_s[n] = 0.f;
+    if (tid == 0) lsum_s = 0.f;
+
+    float2 y[CPH], E[CPH];
+    const float2* yp = a.Y + ((size_t)i * M + hf) * a.F + k;
+    const float2* ep = a.etab + (size_t)hf * a.F + k;
+    float4 bt = make_float4(0.f, 0.f, 0.f, 0.f);
+    float tr = 0.f;
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < CPH; ++m) {
+            if (EXACT || 2 * m + hf < M) {
+                y[m] = __ldcs(yp + (size_t)(2 * m) * a.F);
+                E[m] = __ldg(ep + (size_t)(2 * m) * a.F);
+            } else {
+                y[m] = make_float2(0.f, 0.f);
+                E[m] = make_float2(0.f, 0.f);
+            }
+        }
+        bt = __ldg(a.btab + k);
+        tr = __ldg(reinterpret_cast<const float*>(a.lut) + 2 * ((size_t)i * a.F + k) + hf);
+    }
+    const float fm = bt.x, om = bt.y;
+    const float2 C2 = make_float2(bt.z, bt.w);
     const float Mf = (float)M;
     const float eps = a.eps;
-    for (int g = 0; g < ng; ++g) {
-        const int i = i0 + g;
-        float contrib = 0.f;
-        if (valid) {
-            const int2 cc = a.centres[i];
-            const float2 c = pixel_xy(a.g, cc.x, cc.y);
-            const float* wr = w_s + (size_t)g * n_t;
-            const Hits h = ring_hits(c.x, c.y, ex, ey, a.g, n_over_2pi);
-            const int n2a = h.n1a + 1 == n_t ? 0 : h.n1a + 1;
-            const int n2b = h.n1b + 1 == n_t ? 0 : h.n1b + 1;
-            const float W1 = fmaf(h.fa, wr[n2a] - wr[h.n1a], wr[h.n1a]);
-            const float W2 = fmaf(h.fb, wr[n2b] - wr[h.n1b], wr[h.n1b]);
-            const float2 al = cis_pi(-2.f * fm * W1);     // exp(-j|k| W(ang k))
-            const float2 be = cis_pi(2.f * fm * W2);      // exp(+j|k| W(ang k + pi))
 
-            const float2* yp = a.Y + (size_t)i * M * a.F + k;
-            float2 y[MMAX];
-#pragma unroll
-            for (int j = 0; j < MMAX; ++j)
-                if (j < M) y[j] = __ldcs(yp + (size_t)j * a.F);
+    // w at this thread's direction (Eq. 4): linear in ring angle between two transducers
+    const float* wr = a.w + (size_t)i * n_t;
+    const float fl = floorf(tr);
+    const float fr = tr - fl;
+    int n1 = (int)fl;
+    n1 = n1 >= n_t ? n1 - n_t : n1;
+    const int n2 = n1 + 1 == n_t ? 0 : n1 + 1;
+    const float w1 = __ldg(wr + n1), w2 = __ldg(wr + n2);
+    const float Wd = fmaf(fr, w2 - w1, w1);
+    const float dsgn = hf ? -1.f : 1.f;
+    const float2 ph = cis_pi(-dsgn * 2.f * fm * Wd);   // half 0: exp(-j|k|W1), half 1: exp(+j|k|W2)
+    const float2 oth = make_float2(__shfl_xor_sync(0xffffffffu, ph.x, 16), __shfl_xor_sync(0xffffffffu, ph.y, 16));
+    const float Wo = __shfl_xor_sync(0xffffffffu, Wd, 16);
+    const float2 al = hf ? oth : ph, be = hf ? ph : oth;
+    const float W1 = hf ? Wo : Wd, W2 = hf ? Wd : Wo;
 
-            // pass 1: S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j
-            float2 S1 = make_float2(0.f, 0.f), S2 = S1;
+    // pass 1 (own channels), completed across the pair
+    float s1x = 0.f, s1y = 0.f, s2x = 0.f, s2y = 0.f;
 #pragma unroll
-            for (int j = 0; j < MMAX; ++j) {
-                if (j < M) {
-                    const float2 e = E[(size_t)j * kTPB + tid];
-                    S1.x = fmaf(e.x, y[j].x, S1.x);
-                    S1.y = fmaf(e.x, y[j].y, S1.y);
-                    S2.x = fmaf(e.y, y[j].x, S2.x);
-                    S2.y = fmaf(e.y, y[j].y, S2.y);
-                }
-            }
-            const float2 U = make_float2(S1.x + S2.y, S1.y - S2.x);   // sum conj(E_j) Y_j
-            const float2 V = make_float2(S1.x - S2.y, S1.y + S2.x);   // sum E_j Y_j
-            const float2 ca = cmulc(al, U), cb = cmulc(be, V);
-            const float2 A = make_float2(0.5f * (ca.x + cb.x), 0.5f * (ca.y + cb.y));
-            const float2 ab = cmulc(be, al);                           // a conj(b)
-            float B, D;
-            float2 X;
-            if (a.fp64) {
-                double sn, cs;
-                sincospi(-2.0 * (double)fm * ((double)W1 + (double)W2), &sn, &cs);
-                const double Bd = 0.5 * ((double)M + (cs * C2d.x - sn * C2d.y));
-                const double Dd = Bd + (double)eps;
-                B = (float)Bd;
-                D = (float)Dd;
-                X = Dd != 0.0 ? make_float2((float)(A.x / Dd), (float)(A.y / Dd)) : make_float2(0.f, 0.f);
-            } else {
-                B = 0.5f * (Mf + (ab.x * C2.x - ab.y * C2.y));
-                D = B + eps;
-                const float iD = D != 0.f ? 1.f / D : 0.f;
-                X = make_float2(A.x * iD, A.y * iD);
-            }
+    for (int m = 0; m < CPH; ++m) {
+        s1x = fmaf(E[m].x, y[m].x, s1x);
+        s1y = fmaf(E[m].x, y[m].y, s1y);
+        s2x = fmaf(E[m].y, y[m].x, s2x);
+        s2y = fmaf(E[m].y, y[m].y, s2y);
+    }
+    const float2 S1 = make_float2(pair_sum(s1x), pair_sum(s1y));
+    const float2 S2 = make_float2(pair_sum(s2x), pair_sum(s2y));
+    const float2 U = make_float2(S1.x + S2.y, S1.y - S2.x);   // sum conj(E_j) Y_j
+    const float2 V = make_float2(S1.x - S2.y, S1.y + S2.x);   // sum E_j Y_j
+    const float2 ca = cmulc(al, U), cb = cmulc(be, V);
+    const float2 A = make_float2(0.5f * (ca.x + cb.x), 0.5f * (ca.y + cb.y));
+    const float2 ab = cmulc(be, al);                           // a conj(b)
+    float B, D;
+    float2 X;
+    if (a.fp64) {
+        double sn, cs;
+        sincospi(-2.0 * (double)fm * ((double)W1 + (double)W2), &sn, &cs);
+        const double2 C2d = valid ? a.c2d[k] : make_double2(0.0, 0.0);
+        const double Bd = 0.5 * ((double)M + (cs * C2d.x - sn * C2d.y));
+        const double Dd = Bd + (double)eps;
+        B = (float)Bd;
+        D = (float)Dd;
+        X = Dd != 0.0 ? make_float2((float)(A.x / Dd), (float)(A.y / Dd)) : make_float2(0.f, 0.f);
+    } else {
+        B = 0.5f * (Mf + (ab.x * C2.x - ab.y * C2.y));
+        D = B + eps;
+        const float iD = D != 0.f ? __frcp_rn(D) : 0.f;
+        X = make_float2(A.x * iD, A.y * iD);
+    }
 
-            // pass 2: explicit residual R_j = Y_j - cos(|k|d_j) p - sin(|k|d_j) q
-            const float2 pp = make_float2(0.5f * (al.x + be.x), 0.5f * (al.y + be.y));
-            const float2 qm = make_float2(0.5f * (al.x - be.x), 0.5f * (al.y - be.y));
-            const float2 p = cmul(pp, X);
-            const float2 q0 = cmul(qm, X);
-            const float2 q = make_float2(-q0.y, q0.x);
-            float e2 = 0.f;
-            float2 T1 = make_float2(0.f, 0.f), T2 = T1;
+    // pass 2: explicit residual energy of the own channels
+    const float2 pp = make_float2(0.5f * (al.x + be.x), 0.5f * (al.y + be.y));
+    const float2 qm = make_float2(0.5f * (al.x - be.x), 0.5f * (al.y - be.y));
+    const float2 p = cmul(pp, X);
+    const float2 q0v = cmul(qm, X);
+    const float2 qv = make_float2(-q0v.y, q0v.x);
+    float e2 = 0.f;
 #pragma unroll
-            for (int j = 0; j < MMAX; ++j) {
-                if (j < M) {
-                    const float2 e = E[(size_t)j * kTPB + tid];
-                    float2 R;
-                    R.x = y[j].x - fmaf(e.x, p.x, e.y * q.x);
-                    R.y = y[j].y - fmaf(e.x, p.y, e.y * q.y);
-                    e2 = fmaf(R.x, R.x, fmaf(R.y, R.y, e2));
-                    T1.x = fmaf(e.x, R.x, T1.x);
-                    T1.y = fmaf(-e.x, R.y, T1.y);
-                    T2.x = fmaf(e.y, R.x, T2.x);
-                    T2.y = fmaf(-e.y, R.y, T2.y);
-                }
-            }
+    for (int m = 0; m < CPH; ++m) {
+        const float rx = y[m].x - fmaf(E[m].x, p.x, E[m].y * qv.x);
+        const float ry = y[m].y - fmaf(E[m].x, p.y, E[m].y * qv.y);
+        e2 = fmaf(rx, rx, fmaf(ry, ry, e2));
+    }
+    e2 = pair_sum(e2);
+    float contrib = 0.f;
+    __syncthreads();                                    // dw_s cleared
+    if (valid) {
+        if (hf == 0) {
             contrib = om * e2;
             if (a.Xhat) a.Xhat[(size_t)i * a.F + k] = X;
-
-            if (a.want_grad && fm > 0.f && D != 0.f) {
-                const float iD = 1.f / D;
-                const float2 Kc = make_float2(-om * X.x * iD, -om * X.y * iD);   // conj(K)
-                const float b2 = B + 2.f * eps;
-                const float2 abC2 = cmul(ab, C2);
-                const float2 xc = make_float2(X.x, -X.y);
+        }
+        if (a.want_grad && fm > 0.f && D != 0.f) {
+            const float Scc = 0.5f * (Mf + C2.x), Sss = 0.5f * (Mf - C2.x), Scs = 0.5f * C2.y;
+            const float iD = __frcp_rn(D);
+            const float kmag = kTwoPi * fm;
+            const float2 Kc = make_float2(-om * X.x * iD, -om * X.y * iD);   // conj(K)
+            const float b2 = B + 2.f * eps;
+            const float2 abC2 = cmul(ab, C2);
+            const float2 xc = make_float2(X.x, -X.y);
+            // T1 = sum cos conj(R), T2 = sum sin conj(R)
+            const float2 T1 = make_float2(S1.x - p.x * Scc - qv.x * Scs, -S1.y + p.y * Scc + qv.y * Scs);
+            const float2 T2 = make_float2(S2.x - p.x * Scs - qv.x * Sss, -S2.y + p.y * Scs + qv.y * Sss);
+            float gW;
+            if (hf == 0) {
                 const float2 hp = make_float2(0.5f * (Mf + abC2.x), 0.5f * abC2.y);
-                const float2 hq = make_float2(0.5f * (Mf + abC2.x), -0.5f * abC2.y);
                 const float2 tp = make_float2(T1.x - T2.y, T1.y + T2.x);
-                const float2 tq = make_float2(T1.x + T2.y, T1.y - T2.x);
-                const float2 ap = cmul(al, tp), bq = cmul(be, tq);
-                const float2 xhp = cmul(xc, hp), xhq = cmul(xc, hq);
+                const float2 ap = cmul(al, tp), xhp = cmul(xc, hp);
                 const float2 SP = make_float2(b2 * ap.x - eps * xhp.x, b2 * ap.y - eps * xhp.y);
+                gW = kmag * (Kc.x * SP.y + Kc.y * SP.x);
+            } else {
+                const float2 hq = make_float2(0.5f * (Mf + abC2.x), -0.5f * abC2.y);
+                const float2 tq = make_float2(T1.x + T2.y, T1.y - T2.x);
+                const float2 bq = cmul(be, tq), xhq = cmul(xc, hq);
                 const float2 SQ = make_float2(b2 * bq.x - eps * xhq.x, b2 * bq.y - eps * xhq.y);
-                const float gW1 = kmag * (Kc.x * SP.y + Kc.y * SP.x);
-                const float gW2 = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
-                float* dwr = dw_s + (size_t)g * n_t;
-                atomicAdd(dwr + h.n1a, (1.f - h.fa) * gW1);
-                atomicAdd(dwr + n2a, h.fa * gW1);
-                atomicAdd(dwr + h.n1b, (1.f - h.fb) * gW2);
-                atomicAdd(dwr + n2b, h.fb * gW2);
+                gW = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
             }
+            atomicAdd(dw_s + n1, (1.f - fr) * gW);
+            atomicAdd(dw_s + n2, fr * gW);
         }
-        contrib = warp_sum(contrib);
-        if ((tid & 31) == 0) atomicAdd(&lsum_s[g], contrib);
     }
+    contrib = warp_sum(contrib);
+    if (lane == 0) atomicAdd(&lsum_s, contrib);
     __syncthreads();
-    if (tid < ng) a.part_loss[(size_t)(i0 + tid) * a.KT + kt] = lsum_s[tid];
     if (a.want_grad) {
-        for (int q = tid; q < ng * n_t; q += kTPB) {
-            const int g = q / n_t, n = q - (q / n_t) * n_t;
-            a.part_dw[((size_t)(i0 + g) * a.KT + kt) * n_t + n] = dw_s[q];
-        }
+        float* dst = a.part_dw + ((size_t)i * a.KT + kt) * n_t;
+        for (int n = tid; n < n_t; n += 512) dst[n] = dw_s[n];
     }
+    if (tid == 0) a.part_loss[(size_t)i * a.KT + kt] = lsum_s;
 }
 
 struct FinArgs {
@@ -294,21 +349,26 @@ __global__ void __launch_bounds__(kTPB) mcd_finalize_kernel(const FinArgs a) {
 }
 
 struct Plan {
-    int KT, NG;
-    size_t smem, off_dw, total;
+    int KT;
+    size_t off_dw, off_lut, off_etab, off_btab, off_c2d, total;
 };
 
 Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     Plan p;
     const int F = pt->p * (pt->p / 2 + 1);
-    p.KT = (F + kTPB - 1) / kTPB;
-    const int sms = num_sms();
-    int ng = (int)((long long)p.KT * pt->n / (2LL * sms));
-    p.NG = std::max(1, std::min(8, ng));
-    p.smem = (size_t)m * kTPB * sizeof(float2) + 2 * (size_t)p.NG * g->n_t * sizeof(float);
-    const size_t n_loss = (size_t)pt->n * p.KT;
-    p.off_dw = align_up(n_loss * sizeof(float), 256);
-    p.total = p.off_dw + align_up((size_t)pt->n * p.KT * g->n_t * sizeof(float), 256);
+    p.KT = (F + 255) / 256;
+    size_t o = align_up((size_t)pt->n * p.KT * sizeof(float), 256);
+    p.off_dw = o;
+    o += align_up((size_t)pt->n * p.KT * g->n_t * sizeof(float), 256);
+    p.off_lut = o;
+    o += align_up((size_t)pt->n * F * sizeof(float2), 256);
+    p.off_etab = o;
+    o += align_up((size_t)m * F * sizeof(float2), 256);
+    p.off_btab = o;
+    o += align_up((size_t)F * sizeof(float4), 256);
+    p.off_c2d = o;
+    o += align_up((size_t)F * sizeof(double2), 256);
+    p.total = o;
     return p;
 }
 
@@ -322,11 +382,12 @@ pact_status check_delays(const float* d, int m) {
     return PACT_OK;
 }
 
-template <int MMAX>
-pact_status launch_mcd(const McdArgs& a, size_t smem, cudaStream_t st) {
-    PACT_TRY(ensure_smem((const void*)mcd_kernel<MMAX>, smem, "mc_deconv_loss: shared memory attribute"));
-    dim3 grid(a.KT, (a.N + a.NG - 1) / a.NG);
-    mcd_kernel<MMAX><<<grid, kTPB, smem, st>>>(a);
+template <int CPH, bool EXACT>
+pact_status launch_mcd(const McdArgs& a, cudaStream_t st) {
+    const size_t smem = (size_t)a.g.n_t * sizeof(float);
+    PACT_TRY(ensure_smem((const void*)mcd_kernel<CPH, EXACT>, smem, "mc_deconv_loss: shared memory attribute"));
+    dim3 grid(a.KT, a.N);
+    mcd_kernel<CPH, EXACT><<<grid, 512, smem, st>>>(a);
     return check_launch("mc_deconv_loss kernel");
 }
 
@@ -341,9 +402,9 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     if (!(eps >= 0.f) || !isfinite(eps)) return fail(PACT_ERR_INVALID_ARG, "eps must be finite and >= 0");
     if (!ws) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss: workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    if (reinterpret_cast<uintptr_t>(Y) % 8) return fail(PACT_ERR_INVALID_ARG, "Y must be 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(Y) % 16) return fail(PACT_ERR_INVALID_ARG, "Y must be 16-byte aligned");
     const Plan pl = make_plan(g, pt, m);
-    if (pl.smem > 220 * 1024) return fail(PACT_ERR_SHAPE, "mc_deconv_loss: n_t x channels too large for shared memory");
+    if ((size_t)g->n_t * sizeof(float) > 200 * 1024) return fail(PACT_ERR_SHAPE, "mc_deconv_loss: n_t too large");
     if (ws_bytes < pl.total)
         return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, pl.total);
     cudaStream_t st = as_stream(stream);
@@ -364,13 +425,31 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.fp64 = eps < 1e-6f;
     a.part_loss = reinterpret_cast<float*>(base);
     a.part_dw = reinterpret_cast<float*>(base + pl.off_dw);
+    a.lut = reinterpret_cast<const float2*>(base + pl.off_lut);
+    a.etab = reinterpret_cast<const float2*>(base + pl.off_etab);
+    a.btab = reinterpret_cast<const float4*>(base + pl.off_btab);
+    a.c2d = reinterpret_cast<const double2*>(base + pl.off_c2d);
     a.KT = pl.KT;
-    a.NG = pl.NG;
+    dim3 tg((a.F + 255) / 256, a.N + 1);
+    mcd_tables_kernel<<<tg, 256, 0, st>>>(a.g, a.N, a.P, a.F, m, a.dl, a.centres,
+                                         reinterpret_cast<float2*>(base + pl.off_lut),
+                                         reinterpret_cast<float2*>(base + pl.off_etab),
+                                         reinterpret_cast<float4*>(base + pl.off_btab));
+    PACT_TRY(check_launch("mc_deconv_loss: tables"));
+    if (a.fp64) {
+        mcd_c2d_kernel<<<(a.F + 255) / 256, 256, 0, st>>>(a.P, a.F, (double)g->dx, a.dl,
+                                                          reinterpret_cast<double2*>(base + pl.off_c2d));
+        PACT_TRY(check_launch("mc_deconv_loss: FP64 table"));
+    }
     pact_status s;
-    if (m <= 8) s = launch_mcd<8>(a, pl.smem, st);
-    else if (m <= 16) s = launch_mcd<16>(a, pl.smem, st);
-    else if (m <= 32) s = launch_mcd<32>(a, pl.smem, st);
-    else s = launch_mcd<64>(a, pl.smem, st);
+    if (m == 8) s = launch_mcd<4, true>(a, st);
+    else if (m == 16) s = launch_mcd<8, true>(a, st);
+    else if (m == 32) s = launch_mcd<16, true>(a, st);
+    else if (m == 64) s = launch_mcd<32, true>(a, st);
+    else if (m < 8) s = launch_mcd<4, false>(a, st);
+    else if (m < 16) s = launch_mcd<8, false>(a, st);
+    else if (m < 32) s = launch_mcd<16, false>(a, st);
+    else s = launch_mcd<32, false>(a, st);
     if (s != PACT_OK) return s;
     FinArgs f;
     f.N = a.N;

@@ -1,0 +1,463 @@
+// Neural-field SOS on fifth-generation tensor cores (sm_103a tcgen05, BF16
+// operands, FP32 accumulation in tensor memory).
+//
+// The field (the coordinate-based SOS representation of Sec. 3.3, here the
+// Fourier-feature MLP of the BF16 workload) maps every SOS node to
+//   f(x, y) = [sin 2pi f_l x, cos 2pi f_l x, sin 2pi f_l y, cos 2pi f_l y]_l  (64)
+//   h1..h4 = relu(W h + b)  (128 each),   z = w5 . h4 + b5,
+//   v = v_mid + v_half tanh z  inside the mask, v_bg outside,
+// with x, y the node position over the field of view and f_l = 64^(l/15).
+//
+// pact_nf_forward: one CTA per 128 nodes; the four hidden layers are four
+// 128 x 128 (x 64 / 128) GEMMs on the tensor cores with the accumulator in
+// TMEM; each thread owns one node (one TMEM lane) for the bias/ReLU epilogue,
+// which writes the next layer's operand straight into shared memory.  Each
+// layer's output tile is also copied (in its shared-memory layout) to the
+// workspace for the backward pass.
+// pact_nf_backward: per CTA and layer, dW = dz^T h (M = out, N = in, K = 128
+// nodes) and dh = dz W (M = nodes, N = in, K = out) on the tensor cores; the
+// per-CTA weight gradients go to the workspace and a second kernel sums them
+// in a fixed order.
+#include <math.h>
+
+#include <algorithm>
+
+#include "pact_internal.cuh"
+#include "umma.cuh"
+
+namespace pact {
+namespace {
+
+constexpr int kF = 64;      // Fourier features
+constexpr int kH = 128;     // hidden width
+constexpr int kL = 4;       // hidden layers
+constexpr int kRows = 128;  // nodes per CTA (one TMEM lane each)
+constexpr uint64_t kNfWaitNs = 200ull * 1000ull * 1000ull;
+
+__host__ __device__ constexpr int in_dim(int l) { return l == 1 ? kF : kH; }
+__host__ __device__ constexpr int off_w(int l) { return l == 1 ? 0 : kH * kF + kH + (l - 2) * (kH * kH + kH); }
+__host__ __device__ constexpr int off_b(int l) { return off_w(l) + kH * in_dim(l); }
+constexpr int kOffW5 = off_w(kL + 1);
+constexpr int kOffB5 = kOffW5 + kH;
+constexpr int kNParam = kOffB5 + 1;
+constexpr int kPartStride = (kNParam + 63) / 64 * 64;   // per-CTA gradient row, 256-byte aligned
+constexpr int kWbf = kOffW5 + kH;             // bf16 weight copy: W1..W4 with their biases' slots unused, w5
+constexpr int kTileBytes = kRows * kH * 2;    // one 128 x 128 bf16 operand tile
+
+struct NfArgs {
+    int G;                 // nodes per side
+    int rows;              // G * G
+    float freqs[16];       // cycles per field of view
+    float v_mid, v_half, v_bg;
+    const float* params;   // [kNParam] FP32 master parameters
+    const unsigned char* mask;   // [G*G] or NULL (all inside)
+    __nv_bfloat16* wbf;    // [kWbf] BF16 copy of the weights (workspace)
+    unsigned char* htiles; // [cta][kL][kTileBytes] layer outputs in operand layout (workspace)
+    float* t5;             // [rows] tanh of the output pre-activation (workspace)
+    float* sos;            // [G*G] forward output
+    const float* dL_dsos;  // backward input
+    float* part;           // [cta][kPartStride] per-CTA parameter gradients (workspace)
+    int* status;           // workspace word: set to 1 if a wait gave up
+};
+
+// Features of node `row` written as row `r` of a K-major [128 x 64] tile.
+__device__ __forceinline__ void features(const NfArgs& a, int row, float (&f)[kF]) {
+    const int p = row / a.G, q = row - (row / a.G) * a.G;
+    const float x = (q - 0.5f * (a.G - 1)) / a.G, y = (p - 0.5f * (a.G - 1)) / a.G;
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        float sx, cx, sy, cy;
+        sincospif(2.f * a.freqs[l] * x, &sx, &cx);
+        sincospif(2.f * a.freqs[l] * y, &sy, &cy);
+        f[4 * l + 0] = sx;
+        f[4 * l + 1] = cx;
+        f[4 * l + 2] = sy;
+        f[4 * l + 3] = cy;
+    }
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// 8 consecutive K elements (one 16-byte core-matrix row) of row r at column k0.
+__device__ __forceinline__ void st8(unsigned char* tile, int r, int k0, int K, const float* v) {
+    uint4 u;
+    u.x = pack2(v[0], v[1]);
+    u.y = pack2(v[2], v[3]);
+    u.z = pack2(v[4], v[5]);
+    u.w = pack2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(tile + umma::kmaj_off(r, k0, K)) = u;
+}
+
+__device__ __forceinline__ float bfv(const unsigned char* tile, int r, int k, int K) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + umma::kmaj_off(r, k, K)));
+}
+
+__device__ __forceinline__ void st1(unsigned char* tile, int r, int k, int K, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(tile + umma::kmaj_off(r, k, K)) = __float2bfloat16_rn(v);
+}
+
+// Weight W_l (bf16 [out][in]) into a K-major [out x in] tile (B operand of h W^T).
+__device__ __forceinline__ void load_w(unsigned char* tile, const __nv_bfloat16* w, int K) {
+    const int chunks = kH * K / 8;
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+        const int o = c / (K / 8), k8 = c - (c / (K / 8)) * (K / 8);
+        *reinterpret_cast<uint4*>(tile + umma::kmaj_off(o, 8 * k8, K)) = reinterpret_cast<const uint4*>(w)[c];
+    }
+}
+
+// W_l^T as a K-major [in x out] tile (B operand of dz W): element (n = in, k = out).
+__device__ __forceinline__ void load_wt(unsigned char* tile, const __nv_bfloat16* w, int in) {
+    for (int e = threadIdx.x; e < kH * in; e += blockDim.x) {
+        const int o = e / in, n = e - (e / in) * in;
+        *reinterpret_cast<__nv_bfloat16*>(tile + umma::kmaj_off(n, o, kH)) = w[e];
+    }
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status) {
+    const bool ok = mbar_wait_bounded(bar, parity, kNfWaitNs);
+    if (!ok) atomicExch(status, 1);
+    return ok;
+}
+
+// BF16 copy of the weights (W1..W4 in their own slots, w5).
+__global__ void nf_cast_kernel(const float* params, __nv_bfloat16* wbf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kWbf) return;
+    bool is_w = i >= kOffW5;
+    for (int l = 1; l <= kL; ++l) is_w = is_w || (i >= off_w(l) && i < off_b(l));
+    wbf[i] = __float2bfloat16_rn(is_w ? params[i] : 0.f);
+}
+
+__global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A0 = sm;                                 // features  [128 x 64]   16 KB
+    unsigned char* Hb[2] = {sm + 16384, sm + 16384 + kTileBytes};   // layer outputs  2 x 32 KB
+    unsigned char* Wt[kL];                                  // W1 (16 KB), W2..W4 (32 KB each)
+    Wt[0] = sm + 16384 + 2 * kTileBytes;
+    for (int l = 1; l < kL; ++l) Wt[l] = Wt[0] + 16384 + (l - 1) * kTileBytes;
+    __shared__ float bias_s[kL][kH];
+    __shared__ float w5_s[kH];
+    __shared__ uint32_t tmem_s;
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = blockIdx.x * kRows + tid;
+    const bool valid = row < a.rows;
+
+    for (int l = 1; l <= kL; ++l) load_w(Wt[l - 1], a.wbf + off_w(l), in_dim(l));
+    for (int c = tid; c < kL * kH; c += blockDim.x) bias_s[c / kH][c % kH] = a.params[off_b(c / kH + 1) + c % kH];
+    for (int c = tid; c < kH; c += blockDim.x) w5_s[c] = __bfloat162float(a.wbf[kOffW5 + c]);
+    {
+        float f[kF];
+        features(a, valid ? row : 0, f);
+#pragma unroll
+        for (int k0 = 0; k0 < kF; k0 += 8) st8(A0, tid, k0, kF, f + k0);
+    }
+    if (warp == 0) umma::tmem_alloc(&tmem_s, 128);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    umma::fence_smem_to_async();
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = tmem_s;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    bool ok = true;
+    float z5 = 0.f;
+    for (int l = 1; l <= kL; ++l) {
+        const unsigned char* in = l == 1 ? A0 : Hb[l % 2];
+        unsigned char* out = Hb[(l + 1) % 2];
+        const int K = in_dim(l);
+        if (tid == 0) {
+            for (int kk = 0; kk < K / 16; ++kk)
+                umma::mma(tmem, umma::kslice(in, K, kk), umma::kslice(Wt[l - 1], K, kk), umma::idesc_bf16(128, 128),
+                          kk > 0);
+            umma::commit(&bar);
+        }
+        ok = wait_bar(&bar, (uint32_t)((l - 1) & 1), a.status) && ok;
+        umma::fence_after();
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            umma::ld32(tmem + lane_base + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float h = fmaxf(v[j] + bias_s[l - 1][c0 + j], 0.f);
+                v[j] = __bfloat162float(__float2bfloat16_rn(h));
+                if (l == kL) z5 = fmaf(v[j], w5_s[c0 + j], z5);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) st8(out, tid, c0 + j, kH, v + j);
+        }
+        umma::fence_smem_to_async();
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+        // layer output tile (operand layout) to the workspace for the backward pass
+        const uint4* src = reinterpret_cast<const uint4*>(out);
+        uint4* dst = reinterpret_cast<uint4*>(a.htiles + ((size_t)blockIdx.x * kL + (l - 1)) * kTileBytes);
+        for (int c = tid; c < kTileBytes / 16; c += blockDim.x) dst[c] = src[c];
+    }
+    const float t = tanhf(z5 + a.params[kOffB5]);
+    if (valid) {
+        a.t5[row] = ok ? t : __int_as_float(0x7fc00000);
+        const bool inside = a.mask ? a.mask[row] != 0 : true;
+        a.sos[row] = inside ? (ok ? fmaf(a.v_half, t, a.v_mid) : __int_as_float(0x7fc00000)) : a.v_bg;
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, 128);
+}
+
+__global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* hT = sm;                       // h_{l-1}^T  [in x 128 nodes]     32 KB
+    unsigned char* dzA = sm + kTileBytes;         // dz         [128 nodes x out]    32 KB
+    unsigned char* dzT = sm + 2 * kTileBytes;     // dz^T       [out x 128 nodes]    32 KB
+    unsigned char* WT = sm + 3 * kTileBytes;      // W_l^T      [in x out]           32 KB
+    unsigned char* Hr = sm + 4 * kTileBytes;      // h_{l-1}    [128 nodes x in]     32 KB
+    __shared__ float col_s[kH];
+    __shared__ float red_s[4];
+    __shared__ uint32_t tmem_s;
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = blockIdx.x * kRows + tid;
+    const bool valid = row < a.rows;
+    float* part = a.part + (size_t)blockIdx.x * kPartStride;   // 16-byte aligned rows for float4 stores
+    const unsigned char* tiles = a.htiles + (size_t)blockIdx.x * kL * kTileBytes;
+
+    // output layer: g5 = dL/dv dv/dz = dL/dv v_half (1 - t^2), inside the mask
+    float g5 = 0.f;
+    if (valid && (a.mask ? a.mask[row] != 0 : true)) {
+        const float t = a.t5[row];
+        g5 = a.dL_dsos[row] * a.v_half * (1.f - t * t);
+    }
+    // h4 of this CTA (operand layout) -> Hr
+    for (int c = tid; c < kTileBytes / 16; c += blockDim.x)
+        reinterpret_cast<uint4*>(Hr)[c] = reinterpret_cast<const uint4*>(tiles + (size_t)(kL - 1) * kTileBytes)[c];
+    if (tid < kH) col_s[tid] = 0.f;
+    if (warp == 0) umma::tmem_alloc(&tmem_s, 256);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // dW5 = sum_nodes g5 h4, db5 = sum g5; dz4 = g5 w5 (h4 > 0)
+    for (int c = 0; c < kH; ++c) {
+        const float h = bfv(Hr, tid, c, kH);
+        float s = warp_sum(g5 * h);
+        if (lane == 0) atomicAdd(&col_s[c], s);
+        const float w5 = __bfloat162float(a.wbf[kOffW5 + c]);
+        const float dz = h > 0.f ? g5 * w5 : 0.f;
+        st1(dzA, tid, c, kH, dz);
+        st1(dzT, c, tid, kRows, dz);
+    }
+    {
+        const float s = warp_sum(g5);
+        if (lane == 0) red_s[warp] = s;
+    }
+    __syncthreads();
+    if (tid < kH) part[kOffW5 + tid] = col_s[tid];
+    if (tid == 0) part[kOffB5] = red_s[0] + red_s[1] + red_s[2] + red_s[3];
+
+    const uint32_t tmem = tmem_s;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t phase = 0;
+    for (int l = kL; l >= 1; --l) {
+        const int K_in = in_dim(l);
+        // db_l = column sums of dz_l (row `tid` of dz^T)
+        {
+            float s = 0.f;
+            for (int r = 0; r < kRows; ++r) s += bfv(dzT, tid, r, kRows);
+            part[off_b(l) + tid] = s;
+        }
+        // h_{l-1}^T (B operand of dW) and, for l > 1, W_l^T (B operand of dh)
+        if (l > 1) {
+            for (int c = tid; c < kTileBytes / 16; c += blockDim.x)
+                reinterpret_cast<uint4*>(Hr)[c] = reinterpret_cast<const uint4*>(tiles + (size_t)(l - 2) * kTileBytes)[c];
+            __syncthreads();
+            for (int c = 0; c < kH; ++c) st1(hT, c, tid, kRows, bfv(Hr, tid, c, kH));
+            load_wt(WT, a.wbf + off_w(l), kH);
+        } else {
+            float f[kF];
+            features(a, valid ? row : 0, f);
+            for (int c = 0; c < kF; ++c) st1(hT, c, tid, kRows, __bfloat162float(__float2bfloat16_rn(f[c])));
+        }
+        umma::fence_smem_to_async();
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+        if (tid == 0) {
+            // dW_l [out x in] = dz^T [out x nodes] * (h^T [in x nodes])^T
+            for (int kk = 0; kk < kRows / 16; ++kk)
+                umma::mma(tmem, umma::kslice(dzT, kRows, kk), umma::kslice(hT, kRows, kk),
+                          umma::idesc_bf16(128, K_in), kk > 0);
+            // dh_{l-1} [nodes x in] = dz [nodes x out] * (W^T [in x out])^T
+            if (l > 1)
+                for (int kk = 0; kk < kH / 16; ++kk)
+                    umma::mma(tmem + 128, umma::kslice(dzA, kH, kk), umma::kslice(WT, kH, kk),
+                              umma::idesc_bf16(128, kH), kk > 0);
+            umma::commit(&bar);
+        }
+        wait_bar(&bar, phase, a.status);
+        phase ^= 1u;
+        umma::fence_after();
+        // weight-gradient row `tid` (TMEM lane = output unit)
+        for (int c0 = 0; c0 < K_in; c0 += 32) {
+            float v[32];
+            umma::ld32(tmem + lane_base + c0, v);
+            float4* dst = reinterpret_cast<float4*>(part + off_w(l) + tid * K_in + c0);
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) dst[j / 4] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        if (l > 1) {
+            // dz_{l-1} = dh (h_{l-1} > 0), node `tid`
+            for (int c0 = 0; c0 < kH; c0 += 32) {
+                float v[32];
+                umma::ld32(tmem + 128 + lane_base + c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float h = bfv(Hr, tid, c0 + j, kH);
+                    const float dz = h > 0.f ? v[j] : 0.f;
+                    st1(dzA, tid, c0 + j, kH, dz);
+                    st1(dzT, c0 + j, tid, kRows, dz);
+                }
+            }
+        }
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, 256);
+}
+
+__global__ void nf_reduce_kernel(const float* part, int nct, float* out, int accumulate) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kNParam) return;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int c = 0;
+    for (; c + 8 <= nct; c += 8)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] += part[(size_t)(c + u) * kPartStride + p];
+    for (; c < nct; ++c) s[0] += part[(size_t)c * kPartStride + p];
+    const float t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    out[p] = accumulate ? out[p] + t : t;
+}
+
+struct NfPlan {
+    int rows, nct;
+    size_t off_htiles, off_t5, off_part, off_status, total;
+    size_t smem_fwd, smem_bwd;
+};
+
+NfPlan nf_plan(const pact_geometry* g) {
+    NfPlan p;
+    p.rows = g->sos_g * g->sos_g;
+    p.nct = (p.rows + kRows - 1) / kRows;
+    size_t o = align_up((size_t)kWbf * sizeof(__nv_bfloat16), 256);
+    p.off_htiles = o;
+    o += align_up((size_t)p.nct * kL * kTileBytes, 256);
+    p.off_t5 = o;
+    o += align_up((size_t)p.rows * sizeof(float), 256);
+    p.off_part = o;
+    o += align_up((size_t)p.nct * kPartStride * sizeof(float), 256);
+    p.off_status = o;
+    o += 256;
+    p.total = o;
+    p.smem_fwd = 16384 + 2 * kTileBytes + 16384 + (kL - 1) * kTileBytes;
+    p.smem_bwd = 5 * kTileBytes;
+    return p;
+}
+
+pact_status nf_args(const pact_geometry* g, const float* params, const unsigned char* mask, float v_mid,
+                    float v_half, void* ws, size_t ws_bytes, NfArgs& a, NfPlan& pl) {
+    PACT_TRY(check_geometry(g));
+    if (!params) return fail(PACT_ERR_INVALID_ARG, "nf: params is NULL");
+    if (!ws) return fail(PACT_ERR_INVALID_ARG, "nf: workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (reinterpret_cast<uintptr_t>(params) % 16) return fail(PACT_ERR_INVALID_ARG, "nf: params must be 16-byte aligned");
+    if (!(v_half > 0.f)) return fail(PACT_ERR_INVALID_ARG, "nf: v_half must be > 0");
+    pl = nf_plan(g);
+    if (ws_bytes < pl.total) return fail(PACT_ERR_INVALID_ARG, "nf: workspace too small: %zu < %zu bytes", ws_bytes, pl.total);
+    char* base = static_cast<char*>(ws);
+    a.G = g->sos_g;
+    a.rows = pl.rows;
+    for (int l = 0; l < 16; ++l) a.freqs[l] = (float)pow(64.0, l / 15.0);
+    a.v_mid = v_mid;
+    a.v_half = v_half;
+    a.v_bg = g->v_bg;
+    a.params = params;
+    a.mask = mask;
+    a.wbf = reinterpret_cast<__nv_bfloat16*>(base);
+    a.htiles = reinterpret_cast<unsigned char*>(base + pl.off_htiles);
+    a.t5 = reinterpret_cast<float*>(base + pl.off_t5);
+    a.part = reinterpret_cast<float*>(base + pl.off_part);
+    a.status = reinterpret_cast<int*>(base + pl.off_status);
+    a.sos = nullptr;
+    a.dL_dsos = nullptr;
+    return PACT_OK;
+}
+
+}  // namespace
+}  // namespace pact
+
+using namespace pact;
+
+extern "C" int pact_nf_param_count(void) { return kNParam; }
+
+extern "C" size_t pact_nf_workspace_size(const pact_geometry* g) {
+    if (check_geometry(g) != PACT_OK) return 0;
+    return nf_plan(g).total;
+}
+
+extern "C" pact_status pact_nf_forward(const pact_geometry* g, const float* params, const unsigned char* mask,
+                                       float v_mid, float v_half, float* sos, void* ws, size_t ws_bytes,
+                                       void* stream) {
+    NfArgs a;
+    NfPlan pl;
+    PACT_TRY(nf_args(g, params, mask, v_mid, v_half, ws, ws_bytes, a, pl));
+    if (!sos) return fail(PACT_ERR_INVALID_ARG, "nf_forward: sos is NULL");
+    a.sos = sos;
+    cudaStream_t st = as_stream(stream);
+    if (cudaMemsetAsync(a.status, 0, sizeof(int), st) != cudaSuccess) return check_launch("nf_forward: memset");
+    nf_cast_kernel<<<(kWbf + 255) / 256, 256, 0, st>>>(params, a.wbf);
+    PACT_TRY(check_launch("nf_forward: weight cast"));
+    PACT_TRY(ensure_smem((const void*)nf_fwd_kernel, pl.smem_fwd, "nf_forward: shared memory attribute"));
+    nf_fwd_kernel<<<pl.nct, kRows, pl.smem_fwd, st>>>(a);
+    return check_launch("nf_forward kernel");
+}
+
+extern "C" pact_status pact_nf_backward(const pact_geometry* g, const float* params, const unsigned char* mask,
+                                        float v_mid, float v_half, const float* dL_dsos, float* dL_dparams,
+                                        int accumulate, void* ws, size_t ws_bytes, void* stream) {
+    NfArgs a;
+    NfPlan pl;
+    PACT_TRY(nf_args(g, params, mask, v_mid, v_half, ws, ws_bytes, a, pl));
+    if (!dL_dsos || !dL_dparams) return fail(PACT_ERR_INVALID_ARG, "nf_backward: dL_dsos and dL_dparams must not be NULL");
+    a.dL_dsos = dL_dsos;
+    cudaStream_t st = as_stream(stream);
+    PACT_TRY(ensure_smem((const void*)nf_bwd_kernel, pl.smem_bwd, "nf_backward: shared memory attribute"));
+    nf_bwd_kernel<<<pl.nct, kRows, pl.smem_bwd, st>>>(a);
+    PACT_TRY(check_launch("nf_backward kernel"));
+    nf_reduce_kernel<<<(kNParam + 255) / 256, 256, 0, st>>>(a.part, pl.nct, dL_dparams, accumulate);
+    return check_launch("nf_backward reduction");
+}
+
+extern "C" pact_status pact_nf_status(const pact_geometry* g, const void* ws, size_t ws_bytes, int* host_status,
+                                      void* stream) {
+    PACT_TRY(check_geometry(g));
+    if (!ws || !host_status) return fail(PACT_ERR_INVALID_ARG, "nf_status: null pointer");
+    const NfPlan pl = nf_plan(g);
+    if (ws_bytes < pl.total) return fail(PACT_ERR_INVALID_ARG, "nf_status: workspace too small");
+    cudaStream_t st = as_stream(stream);
+    if (cudaMemcpyAsync(host_status, static_cast<const char*>(ws) + pl.off_status, sizeof(int),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return check_launch("nf_status: copy");
+    return *host_status ? fail(PACT_ERR_TIMEOUT, "nf: a tensor-core completion wait gave up") : PACT_OK;
+}

@@ -24,10 +24,13 @@ namespace pact {
 namespace {
 
 struct Ray {
-    float cx, cy, ex, ey, L, s_in, chord, rem;
-    int nfull, nsamp;
+    float ax, ay, bx, by;   // fractional node coords at the mask entry and per metre along the ray
+    float L, chord, rem;
+    int nfull;
 };
 
+// Ray r'_i -> r_n clipped to the mask disk, in node-grid coordinates
+// fx = x / sos_dx + (G-1)/2 (same for y).
 __device__ __forceinline__ Ray make_ray(const Geo& g, float2 c, int n) {
     Ray r;
     float sn, cs;
@@ -35,78 +38,68 @@ __device__ __forceinline__ Ray make_ray(const Geo& g, float2 c, int n) {
     sincospif(2.f * ((float)n / (float)g.n_t) + g.phase * 0.318309886183790672f, &sn, &cs);
     const float dx = g.R * cs - c.x, dy = g.R * sn - c.y;
     r.L = sqrtf(dx * dx + dy * dy);
-    r.ex = dx / r.L;
-    r.ey = dy / r.L;
-    r.cx = c.x;
-    r.cy = c.y;
-    const float ce = c.x * r.ex + c.y * r.ey;
+    const float ex = dx / r.L, ey = dy / r.L;
+    const float ce = c.x * ex + c.y * ey;
     const float disc = ce * ce - (c.x * c.x + c.y * c.y - g.mask_r * g.mask_r);
-    r.s_in = 0.f;
+    float s_in = 0.f;
     r.chord = 0.f;
     if (disc > 0.f) {
         const float sq = sqrtf(disc);
         const float s0 = fminf(fmaxf(-ce - sq, 0.f), r.L);
         const float s1 = fminf(fmaxf(-ce + sq, 0.f), r.L);
-        r.s_in = s0;
+        s_in = s0;
         r.chord = fmaxf(s1 - s0, 0.f);
     }
     r.nfull = (int)floorf(r.chord / g.h);
     r.rem = fmaxf(r.chord - r.nfull * g.h, 0.f);
-    r.nsamp = r.nfull + (r.rem > 0.f ? 1 : 0);
+    const float inv = 1.f / g.sos_dx, half = 0.5f * (g.G - 1);
+    r.ax = fmaf(fmaf(s_in, ex, c.x), inv, half);
+    r.ay = fmaf(fmaf(s_in, ey, c.y), inv, half);
+    r.bx = ex * inv;
+    r.by = ey * inv;
     return r;
 }
 
-// Node-grid coordinates of sample m: fx = (x / sos_dx + (G-1)/2), same for y;
-// returns the quadrature weight.
-struct Walk {
-    float ax, ay, bx, by;     // fractional node coords at s_in and per unit length
-    float h;
-};
-
-__device__ __forceinline__ Walk make_walk(const Geo& g, const Ray& r) {
-    const float inv = 1.f / g.sos_dx, half = 0.5f * (g.G - 1);
-    Walk w;
-    w.ax = fmaf(fmaf(r.s_in, r.ex, r.cx), inv, half);
-    w.ay = fmaf(fmaf(r.s_in, r.ey, r.cy), inv, half);
-    w.bx = r.ex * inv;
-    w.by = r.ey * inv;
-    w.h = g.h;
-    return w;
-}
-
-__device__ __forceinline__ float sample_xy(const Walk& w, const Ray& r, int m, float& fx, float& fy) {
-    float s, wgt;
-    if (m < r.nfull) {
-        s = (m + 0.5f) * w.h;
-        wgt = w.h;
-    } else {
-        s = r.nfull * w.h + 0.5f * r.rem;
-        wgt = r.rem;
-    }
-    fx = fmaf(s, w.bx, w.ax);
-    fy = fmaf(s, w.by, w.ay);
-    return wgt;
+// Broadcast lane `src`'s ray to the whole warp.
+__device__ __forceinline__ Ray shfl_ray(const Ray& r, int src) {
+    Ray o;
+    o.ax = __shfl_sync(0xffffffffu, r.ax, src);
+    o.ay = __shfl_sync(0xffffffffu, r.ay, src);
+    o.bx = __shfl_sync(0xffffffffu, r.bx, src);
+    o.by = __shfl_sync(0xffffffffu, r.by, src);
+    o.L = __shfl_sync(0xffffffffu, r.L, src);
+    o.chord = __shfl_sync(0xffffffffu, r.chord, src);
+    o.rem = __shfl_sync(0xffffffffu, r.rem, src);
+    o.nfull = __shfl_sync(0xffffffffu, r.nfull, src);
+    return o;
 }
 
 struct Bil {
-    int idx;
+    int idx;        // node (iy, ix) in the grid of row pitch `pitch`
     float tx, ty;
 };
 
-__device__ __forceinline__ Bil bil(int G, float fx, float fy) {
+__device__ __forceinline__ Bil bil(int G, int pitch, float fx, float fy) {
     fx = fminf(fmaxf(fx, 0.f), (float)(G - 1));
     fy = fminf(fmaxf(fy, 0.f), (float)(G - 1));
     const int ix = min((int)fx, G - 2);
     const int iy = min((int)fy, G - 2);
     Bil b;
-    b.idx = iy * G + ix;
+    b.idx = iy * pitch + ix;
     b.tx = fx - ix;
     b.ty = fy - iy;
     return b;
 }
 
-__device__ __forceinline__ float interp(const float* dv, int G, const Bil& b) {
-    const float d00 = dv[b.idx], d01 = dv[b.idx + 1], d10 = dv[b.idx + G], d11 = dv[b.idx + G + 1];
+__device__ __forceinline__ float interp(const float* dv, int pitch, const Bil& b) {
+    const float d00 = dv[b.idx], d01 = dv[b.idx + 1], d10 = dv[b.idx + pitch], d11 = dv[b.idx + pitch + 1];
+    const float top = fmaf(b.tx, d01 - d00, d00), bot = fmaf(b.tx, d11 - d10, d10);
+    return fmaf(b.ty, bot - top, top);
+}
+
+__device__ __forceinline__ float interp_global(const float* sos, int G, float v0, const Bil& b) {
+    const float d00 = __ldg(sos + b.idx) - v0, d01 = __ldg(sos + b.idx + 1) - v0;
+    const float d10 = __ldg(sos + b.idx + G) - v0, d11 = __ldg(sos + b.idx + G + 1) - v0;
     const float top = fmaf(b.tx, d01 - d00, d00), bot = fmaf(b.tx, d11 - d10, d10);
     return fmaf(b.ty, bot - top, top);
 }
@@ -133,15 +126,23 @@ __device__ __forceinline__ void cta_rays(const RayArgs& a, int& i, int& n0, int&
     n1 = min(a.g.n_t, n0 + per);
 }
 
-__global__ void __launch_bounds__(1024) rays_fwd_kernel(const RayArgs a) {
+// Shared-memory grid pitch: one extra column so that nodes of one grid column
+// fall into different banks.
+__host__ __device__ __forceinline__ int smem_pitch(int G) { return G + 1; }
+
+// Warp w of a CTA takes every nw-th ray of the CTA's run; it sets up 32 of its
+// rays at once (one per lane) and then integrates them one after the other
+// (lanes over samples), taking each ray's setup by shuffles.
+__global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
     extern __shared__ float dv_s[];
-    const int G = a.g.G, GG = G * G;
+    const int G = a.g.G, pitch = a.use_smem ? smem_pitch(G) : G;
     const float v0 = a.g.v0;
-    const float* dv = a.sos;
     if (a.use_smem) {
-        for (int q = threadIdx.x; q < GG; q += blockDim.x) dv_s[q] = a.sos[q] - v0;
+        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+            const int p = q / G, c = q - (q / G) * G;
+            dv_s[p * pitch + c] = a.sos[q] - v0;
+        }
         __syncthreads();
-        dv = dv_s;
     }
     int i, n0, n1;
     cta_rays(a, i, n0, n1);
@@ -149,42 +150,62 @@ __global__ void __launch_bounds__(1024) rays_fwd_kernel(const RayArgs a) {
     const int2 cc = a.centres[i];
     const float2 c = pixel_xy(a.g, cc.x, cc.y);
     const float out_coef = (a.g.v_bg - v0) / a.g.v_bg;
-    for (int n = n0 + warp; n < n1; n += nw) {
-        const Ray r = make_ray(a.g, c, n);
-        const Walk wk = make_walk(a.g, r);
-        const int per = (r.nsamp + 31) >> 5;
-        const int m0 = lane * per, m1 = min(r.nsamp, m0 + per);
-        float acc = 0.f;
-        for (int m = m0; m < m1; ++m) {
-            float fx, fy;
-            const float wgt = sample_xy(wk, r, m, fx, fy);
-            const Bil b = bil(G, fx, fy);
-            float d;
-            if (a.use_smem) {
-                d = interp(dv, G, b);
-            } else {
-                const float d00 = __ldg(a.sos + b.idx) - v0, d01 = __ldg(a.sos + b.idx + 1) - v0;
-                const float d10 = __ldg(a.sos + b.idx + G) - v0, d11 = __ldg(a.sos + b.idx + G + 1) - v0;
-                const float top = fmaf(b.tx, d01 - d00, d00), bot = fmaf(b.tx, d11 - d10, d10);
-                d = fmaf(b.ty, bot - top, top);
+    const float h = a.g.h;
+    // warp w takes rays n0 + w, n0 + w + nw, ... (neighbouring rays have similar
+    // lengths, so striding balances the warps), 32 at a time
+    const int nmine = n1 - n0 > warp ? (n1 - n0 - warp + nw - 1) / nw : 0;
+    for (int kb = 0; kb < nmine; kb += 32) {
+        const int cnt = min(32, nmine - kb);
+        const int nl = n0 + warp + (kb + min(lane, cnt - 1)) * nw;
+        const Ray mine = make_ray(a.g, c, nl);
+        float my_w = 0.f;
+        for (int r = 0; r < cnt; ++r) {
+            const Ray ry = shfl_ray(mine, r);
+            const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
+            const int per = (nsamp + 31) >> 5;
+            const int m0 = lane * per, m1 = min(nsamp, m0 + per);
+            const int mf = min(m1, ry.nfull);
+            float acc = 0.f;
+            for (int m = m0; m < mf; ++m) {
+                const float s = (m + 0.5f) * h;
+                const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
+                const float d = a.use_smem ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                acc += __fdividef(d, v0 + d);
             }
-            acc = fmaf(wgt, __fdividef(d, v0 + d), acc);
+            acc *= h;
+            if (m0 <= ry.nfull && ry.nfull < m1) {    // last partial step, weighted by its length
+                const float s = ry.nfull * h + 0.5f * ry.rem;
+                const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
+                const float d = a.use_smem ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                acc = fmaf(ry.rem, __fdividef(d, v0 + d), acc);
+            }
+            acc = warp_sum(acc);
+            if (lane == r) my_w = fmaf(ry.L - ry.chord, out_coef, acc);
         }
-        acc = warp_sum(acc);
-        if (lane == 0) a.w[(size_t)i * a.g.n_t + n] = fmaf(r.L - r.chord, out_coef, acc);
+        if (lane < cnt) a.w[(size_t)i * a.g.n_t + nl] = my_w;
     }
 }
 
-__global__ void __launch_bounds__(1024) rays_adj_kernel(const RayArgs a) {
+__device__ __forceinline__ void scatter4(float* acc, int pitch, const Bil& b, float coef) {
+    const float cy0 = coef * (1.f - b.ty), cy1 = coef * b.ty;
+    atomicAdd(acc + b.idx, cy0 * (1.f - b.tx));
+    atomicAdd(acc + b.idx + 1, cy0 * b.tx);
+    atomicAdd(acc + b.idx + pitch, cy1 * (1.f - b.tx));
+    atomicAdd(acc + b.idx + pitch + 1, cy1 * b.tx);
+}
+
+__global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
     extern __shared__ float sm[];
-    const int G = a.g.G, GG = G * G;
+    const int G = a.g.G, pitch = a.use_smem ? smem_pitch(G) : G;
+    const int GP = G * pitch;
     const float v0 = a.g.v0;
     float* dv_s = sm;
-    float* acc_s = sm + GG;
+    float* acc_s = sm + GP;
     if (a.use_smem) {
-        for (int q = threadIdx.x; q < GG; q += blockDim.x) {
-            dv_s[q] = a.sos[q] - v0;
-            acc_s[q] = 0.f;
+        for (int q = threadIdx.x; q < GP; q += blockDim.x) acc_s[q] = 0.f;
+        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+            const int p = q / G, c = q - (q / G) * G;
+            dv_s[p * pitch + c] = a.sos[q] - v0;
         }
         __syncthreads();
     }
@@ -194,40 +215,39 @@ __global__ void __launch_bounds__(1024) rays_adj_kernel(const RayArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int2 cc = a.centres[i];
     const float2 c = pixel_xy(a.g, cc.x, cc.y);
-    for (int n = n0 + warp; n < n1; n += nw) {
-        const float gr = a.dLdw[(size_t)i * a.g.n_t + n];
-        if (gr == 0.f) continue;
-        const Ray r = make_ray(a.g, c, n);
-        const Walk wk = make_walk(a.g, r);
-        const int per = (r.nsamp + 31) >> 5;
-        const int m0 = lane * per, m1 = min(r.nsamp, m0 + per);
-        const float gv0 = gr * v0;
-        for (int m = m0; m < m1; ++m) {
-            float fx, fy;
-            const float wgt = sample_xy(wk, r, m, fx, fy);
-            const Bil b = bil(G, fx, fy);
-            float d;
-            if (a.use_smem) {
-                d = interp(dv_s, G, b);
-            } else {
-                const float d00 = __ldg(a.sos + b.idx) - v0, d01 = __ldg(a.sos + b.idx + 1) - v0;
-                const float d10 = __ldg(a.sos + b.idx + G) - v0, d11 = __ldg(a.sos + b.idx + G + 1) - v0;
-                const float top = fmaf(b.tx, d01 - d00, d00), bot = fmaf(b.tx, d11 - d10, d10);
-                d = fmaf(b.ty, bot - top, top);
+    const float h = a.g.h;
+    const int nmine = n1 - n0 > warp ? (n1 - n0 - warp + nw - 1) / nw : 0;
+    for (int kb = 0; kb < nmine; kb += 32) {
+        const int cnt = min(32, nmine - kb);
+        const int nl = n0 + warp + (kb + min(lane, cnt - 1)) * nw;
+        const Ray mine = make_ray(a.g, c, nl);
+        const float my_g = lane < cnt ? a.dLdw[(size_t)i * a.g.n_t + nl] : 0.f;
+        for (int r = 0; r < cnt; ++r) {
+            const float gr = __shfl_sync(0xffffffffu, my_g, r);
+            if (gr == 0.f) continue;
+            const Ray ry = shfl_ray(mine, r);
+            const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
+            const int per = (nsamp + 31) >> 5;
+            const int m0 = lane * per, m1 = min(nsamp, m0 + per);
+            const float gv0 = gr * v0;
+            for (int m = m0; m < m1; ++m) {
+                const bool last = m >= ry.nfull;
+                const float s = last ? ry.nfull * h + 0.5f * ry.rem : (m + 0.5f) * h;
+                const float wgt = last ? ry.rem : h;
+                const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
+                const float d = a.use_smem ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                const float iv = __frcp_rn(v0 + d);
+                scatter4(acc, pitch, b, gv0 * wgt * iv * iv);
             }
-            const float iv = __frcp_rn(v0 + d);
-            const float coef = gv0 * wgt * iv * iv;
-            const float cy0 = coef * (1.f - b.ty), cy1 = coef * b.ty;
-            atomicAdd(acc + b.idx, cy0 * (1.f - b.tx));
-            atomicAdd(acc + b.idx + 1, cy0 * b.tx);
-            atomicAdd(acc + b.idx + G, cy1 * (1.f - b.tx));
-            atomicAdd(acc + b.idx + G + 1, cy1 * b.tx);
         }
     }
     if (a.use_smem) {
         __syncthreads();
-        float* dst = a.part + (size_t)blockIdx.x * GG;
-        for (int q = threadIdx.x; q < GG; q += blockDim.x) dst[q] = acc_s[q];
+        float* dst = a.part + (size_t)blockIdx.x * G * G;
+        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+            const int p = q / G, cq = q - (q / G) * G;
+            dst[q] = acc_s[p * pitch + cq];
+        }
     }
 }
 
@@ -260,34 +280,38 @@ __global__ void reduce_stage2_kernel(const float* stage1, int nr, int GG, float*
 constexpr size_t kMaxSmem = 200 * 1024;
 
 struct Plan {
-    int splits_fwd, splits_adj, nb_fwd, nb_adj, nr, use_smem, threads;
+    int splits_fwd, splits_adj, nb_fwd, nb_adj, nr, use_smem;
     size_t smem_fwd, smem_adj, off_stage1, ws;
 };
 
-// CTAs per patch so that the grid fills the SMs once at the occupancy the
-// shared-memory footprint allows (at least 64 rays per CTA).
-int splits_for(const pact_geometry* g, const pact_patches* pt, size_t smem, int threads) {
+// CTAs per patch so that the grid fills every SM once at the occupancy the
+// kernel's registers and shared memory allow (at least 32 rays per CTA).
+int splits_for(const pact_geometry* g, const pact_patches* pt, const void* fn, int threads, size_t smem) {
     const int sms = num_sms();
-    int per_sm = std::max(1, 2048 / threads);
-    if (smem > 0) per_sm = std::min(per_sm, std::max(1, (int)((227 * 1024) / (smem + 1024))));
-    int s = (sms * per_sm) / pt->n;
-    return std::max(1, std::min(s, std::max(1, g->n_t / 64)));
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int s = (sms * per_sm) / pt->n;
+    return std::max(1, std::min(s, std::max(1, g->n_t / 32)));
 }
 
 Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     Plan p;
-    const size_t gbytes = (size_t)g->sos_g * g->sos_g * sizeof(float);
+    const int G = g->sos_g;
+    const size_t gbytes = (size_t)G * smem_pitch(G) * sizeof(float);
     p.use_smem = 2 * gbytes <= kMaxSmem;
-    p.threads = 1024;
     p.smem_fwd = p.use_smem ? gbytes : 0;
     p.smem_adj = p.use_smem ? 2 * gbytes : 0;
-    p.splits_fwd = splits_for(g, pt, p.smem_fwd, p.threads);
-    p.splits_adj = splits_for(g, pt, p.smem_adj, p.threads);
+    p.splits_fwd = splits_for(g, pt, (const void*)rays_fwd_kernel, 512, p.smem_fwd);
+    p.splits_adj = splits_for(g, pt, (const void*)rays_adj_kernel, 1024, p.smem_adj);
     p.nb_fwd = pt->n * p.splits_fwd;
     p.nb_adj = pt->n * p.splits_adj;
     p.nr = (p.nb_adj + kGroup - 1) / kGroup;
-    p.off_stage1 = align_up((size_t)p.nb_adj * gbytes, 256);
-    p.ws = p.use_smem ? p.off_stage1 + align_up((size_t)p.nr * gbytes, 256) : 256;
+    const size_t plane = (size_t)G * G * sizeof(float);
+    p.off_stage1 = align_up((size_t)p.nb_adj * plane, 256);
+    p.ws = p.use_smem ? p.off_stage1 + align_up((size_t)p.nr * plane, 256) : 256;
     return p;
 }
 
@@ -320,7 +344,7 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
     RayArgs a = make_args(g, pt, pl, pl.splits_fwd, sos);
     a.w = w;
     PACT_TRY(ensure_smem((const void*)rays_fwd_kernel, pl.smem_fwd, "sos_to_delays: shared memory attribute"));
-    rays_fwd_kernel<<<pl.nb_fwd, pl.threads, pl.smem_fwd, as_stream(stream)>>>(a);
+    rays_fwd_kernel<<<pl.nb_fwd, 512, pl.smem_fwd, as_stream(stream)>>>(a);
     return check_launch("sos_to_delays kernel");
 }
 
@@ -348,7 +372,7 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.out = dL_dsos;
     if (pl.use_smem) {
         PACT_TRY(ensure_smem((const void*)rays_adj_kernel, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
-        rays_adj_kernel<<<pl.nb_adj, pl.threads, pl.smem_adj, st>>>(a);
+        rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a);
         PACT_TRY(check_launch("sos_to_delays_adj kernel"));
         float* stage1 = reinterpret_cast<float*>(static_cast<char*>(ws) + pl.off_stage1);
         dim3 g1((GG + 255) / 256, pl.nr);
@@ -359,6 +383,6 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     }
     if (!accumulate && cudaMemsetAsync(dL_dsos, 0, (size_t)GG * sizeof(float), st) != cudaSuccess)
         return check_launch("sos_to_delays_adj: memset");
-    rays_adj_kernel<<<pl.nb_adj, pl.threads, 0, st>>>(a);
+    rays_adj_kernel<<<pl.nb_adj, 1024, 0, st>>>(a);
     return check_launch("sos_to_delays_adj kernel");
 }

@@ -309,3 +309,50 @@ def random_spectra(shape: Tuple[int, ...], rng: np.random.Generator) -> np.ndarr
 
 def random_rf(n_t: int, n_s: int, rng: np.random.Generator) -> np.ndarray:
     return rng.standard_normal((n_t, n_s)).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# neural-field SOS parametrisation: sizes and seeded initial parameters
+# --------------------------------------------------------------------------
+
+NF_FREQS = 16          # log-spaced frequencies, 1 .. 64 cycles per field of view
+NF_FEATURES = 4 * NF_FREQS
+NF_HIDDEN = 128
+NF_LAYERS = 4          # hidden layers
+NF_V_MID, NF_V_HALF = 1525.0, 125.0      # v = 1525 + 125 tanh(z) spans 1400 .. 1650 m/s
+
+
+def nf_frequencies() -> np.ndarray:
+    """Fourier-feature frequencies f_l (cycles per field of view)."""
+    return np.logspace(0.0, np.log10(64.0), NF_FREQS)
+
+
+def nf_shapes():
+    """(name, shape) of the neural-field parameters in their flat order."""
+    sh = [("W1", (NF_HIDDEN, NF_FEATURES)), ("b1", (NF_HIDDEN,))]
+    for l in range(2, NF_LAYERS + 1):
+        sh += [(f"W{l}", (NF_HIDDEN, NF_HIDDEN)), (f"b{l}", (NF_HIDDEN,))]
+    sh += [("w5", (NF_HIDDEN,)), ("b5", (1,))]
+    return sh
+
+
+def nf_param_count() -> int:
+    return int(sum(np.prod(s) for _, s in nf_shapes()))
+
+
+def nf_init(seed: int, v_start: float = 1500.0) -> np.ndarray:
+    """Seeded flat float32 parameter vector: U(-1/sqrt(fan_in), 1/sqrt(fan_in))
+    for the hidden layers, a small output layer and an output bias that makes
+    the initial field about v_start."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for name, shape in nf_shapes():
+        if name == "b5":
+            parts.append(np.array([np.arctanh((v_start - NF_V_MID) / NF_V_HALF)]))
+            continue
+        fan_in = shape[1] if len(shape) == 2 else NF_HIDDEN
+        bound = 1.0 / np.sqrt(fan_in)
+        if name == "w5":
+            bound *= 0.05
+        parts.append(rng.uniform(-bound, bound, size=shape).ravel())
+    return np.concatenate(parts).astype(np.float32)

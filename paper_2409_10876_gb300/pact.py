@@ -59,6 +59,11 @@ _SIGS = {
     "pact_adam_step": ([_I, _VP, _VP, _VP, _VP, _I, _VP, _F, _F, _F, _F, _VP, _VP], _I),
     "pact_stitch_workspace_size": ([_GP, _PP], _SZ),
     "pact_stitch": ([_GP, _PP, _VP, _VP, _VP, _SZ, _VP], _I),
+    "pact_nf_param_count": ([], _I),
+    "pact_nf_workspace_size": ([_GP], _SZ),
+    "pact_nf_forward": ([_GP, _VP, _VP, _F, _F, _VP, _VP, _SZ, _VP], _I),
+    "pact_nf_backward": ([_GP, _VP, _VP, _F, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
+    "pact_nf_status": ([_GP, _VP, _SZ, ctypes.POINTER(ctypes.c_int), _VP], _I),
 }
 
 
@@ -382,3 +387,59 @@ def stitch(pb: Problem, Xhat, image=None, ws=None):
         ws = _ws(stitch_workspace_size(pb), Xhat.device)
     _check(L.pact_stitch(pb.gp(), pb.pp(), _ptr(Xhat), _ptr(image), _ptr(ws), ws.numel(), _stream()), "stitch")
     return image
+
+
+# ------------------------------------------------------------------ neural-field SOS (BF16 tensor cores)
+
+def nf_param_count() -> int:
+    return int(load().pact_nf_param_count())
+
+
+def nf_workspace_size(pb: Problem) -> int:
+    return int(load().pact_nf_workspace_size(pb.gp()))
+
+
+class NeuralField:
+    """Device state of the neural-field SOS: FP32 parameters and the workspace
+    that carries activations from forward to backward."""
+
+    def __init__(self, pb: Problem, params, mask=None, v_mid: float = 1525.0, v_half: float = 125.0):
+        self.pb = pb
+        self.params = torch.as_tensor(np.asarray(params, np.float32), device=pb.device).contiguous()
+        if self.params.numel() != nf_param_count():
+            raise PactError(f"neural field has {nf_param_count()} parameters, got {self.params.numel()}")
+        self.mask = None if mask is None else torch.as_tensor(np.asarray(mask, np.uint8), device=pb.device).contiguous()
+        self.v_mid, self.v_half = float(v_mid), float(v_half)
+        self.ws = _ws(nf_workspace_size(pb), pb.device)
+
+
+def nf_forward(nf: NeuralField, sos=None):
+    """SOS [G, G] from the neural field (activations kept for nf_backward)."""
+    L = load()
+    pb = nf.pb
+    if sos is None:
+        sos = _empty((pb.g, pb.g), torch.float32, pb.device)
+    _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    _check(L.pact_nf_forward(pb.gp(), _ptr(nf.params), _ptr(nf.mask), nf.v_mid, nf.v_half, _ptr(sos), _ptr(nf.ws),
+                             nf.ws.numel(), _stream()), "nf_forward")
+    return sos
+
+
+def nf_backward(nf: NeuralField, dL_dsos, dL_dparams=None, accumulate=False):
+    """dL/dparams from dL/dsos for the parameters of the last nf_forward."""
+    L = load()
+    pb = nf.pb
+    dL_dsos = _dev(dL_dsos, "dL_dsos", torch.float32, (pb.g, pb.g))
+    if dL_dparams is None:
+        dL_dparams = torch.zeros_like(nf.params)
+    _dev(dL_dparams, "dL_dparams", torch.float32, tuple(nf.params.shape))
+    _check(L.pact_nf_backward(pb.gp(), _ptr(nf.params), _ptr(nf.mask), nf.v_mid, nf.v_half, _ptr(dL_dsos),
+                              _ptr(dL_dparams), int(accumulate), _ptr(nf.ws), nf.ws.numel(), _stream()), "nf_backward")
+    return dL_dparams
+
+
+def nf_status(nf: NeuralField) -> None:
+    """Raises if a tensor-core wait of the neural-field kernels gave up (synchronises)."""
+    L = load()
+    st = ctypes.c_int(0)
+    _check(L.pact_nf_status(nf.pb.gp(), _ptr(nf.ws), nf.ws.numel(), ctypes.byref(st), _stream()), "nf_status")

@@ -1,0 +1,95 @@
+"""Neural-field SOS on BF16 tensor cores (pact_nf_forward / pact_nf_backward)
+vs the FP64 oracle.
+
+Tolerances: BF16 keeps 8 significant bits (relative rounding 2^-9); features,
+weights and the activations of 4 hidden layers of width 128 are rounded, so
+the field deviation v - v_bg and the gradients are compared at relative L2
+3e-2 / 5e-2 (the FP32 path of the pixel grid keeps its 1e-4 / 2e-3)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pact_oracle as O
+from paper_2409_10876_gb300 import inputs, pact
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 3e-2
+GRAD_TOL = 5e-2
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _params(seed, w5_scale=30.0):
+    p = inputs.nf_init(seed).astype(np.float32)
+    sh = dict((n, s) for n, s in inputs.nf_shapes())
+    off = 0
+    for name, shape in inputs.nf_shapes():
+        n = int(np.prod(shape))
+        if name == "w5":
+            p[off:off + n] *= w5_scale          # a field that varies by tens of m/s
+        off += n
+    return p
+
+
+def _oracle_args(cfg):
+    return (O.geom(cfg), inputs.nf_shapes(), inputs.nf_frequencies(), inputs.sos_mask(cfg),
+            inputs.NF_V_MID, inputs.NF_V_HALF)
+
+
+@pytest.mark.parametrize("cfg", [inputs.config_small(), inputs.config_full()], ids=["G32", "G128"])
+def test_nf_forward_matches_oracle(cfg):
+    pb = pact.Problem(cfg, "cuda")
+    prm = _params(1)
+    nf = pact.NeuralField(pb, prm, inputs.sos_mask(cfg))
+    v = pact.nf_forward(nf).cpu().numpy()
+    pact.nf_status(nf)
+    g, sh, f, mask, vm, vh = _oracle_args(cfg)
+    ref = O.nf_sos(g, O._t(prm), sh, f, mask, vm, vh).numpy()
+    assert np.all(v[mask == 0] == cfg.v_bg)
+    assert _rel(v - cfg.v_bg, ref - cfg.v_bg) <= FWD_TOL
+    assert np.abs(v - ref).max() <= 2.0           # m/s
+
+
+@pytest.mark.parametrize("cfg", [inputs.config_small(), inputs.config_full()], ids=["G32", "G128"])
+def test_nf_backward_matches_oracle_vjp(cfg):
+    pb = pact.Problem(cfg, "cuda")
+    prm = _params(2)
+    nf = pact.NeuralField(pb, prm, inputs.sos_mask(cfg))
+    pact.nf_forward(nf)
+    up = np.random.default_rng(3).standard_normal((cfg.sos_g, cfg.sos_g)).astype(np.float32)
+    gp = pact.nf_backward(nf, torch.as_tensor(up, device="cuda")).cpu().numpy()
+    pact.nf_status(nf)
+    g, sh, f, mask, vm, vh = _oracle_args(cfg)
+    p64 = O._t(prm).clone().requires_grad_(True)
+    (ref,) = torch.autograd.grad((O.nf_sos(g, p64, sh, f, mask, vm, vh) * O._t(up)).sum(), p64)
+    assert _rel(gp, ref.numpy()) <= GRAD_TOL
+    # accumulate adds
+    gp2 = pact.nf_backward(nf, torch.as_tensor(up, device="cuda"), torch.ones(prm.size, device="cuda"),
+                           accumulate=True).cpu().numpy()
+    assert _rel(gp2 - 1.0, gp) <= 1e-5
+
+
+def test_nf_objective_gradient_end_to_end():
+    """NF -> rays -> fused deconvolution/loss/adjoint -> ray adjoint -> NF
+    backward, all in libpact, vs the oracle's autograd gradient of Eq. 7."""
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 0)
+    g, sh, f, mask, vm, vh = _oracle_args(cfg)
+    Y64, _, _ = O.make_measurement(g, case)
+    pb = pact.Problem(cfg, "cuda")
+    prm = _params(4)
+    nf = pact.NeuralField(pb, prm, mask)
+    Y = torch.as_tensor(Y64.numpy().astype(np.complex64), device="cuda")
+    sos = pact.nf_forward(nf)
+    w = pact.sos_to_delays(pb, sos)
+    out = pact.mc_deconv_loss(pb, w, Y, case["d"], cfg.eps)
+    gs = pact.sos_to_delays_adj(pb, sos, out["dL_dw"])
+    gp = pact.nf_backward(nf, gs).cpu().numpy()
+    pact.nf_status(nf)
+    L, _, gref = O.nf_objective(g, prm, sh, f, mask, vm, vh, Y64, case["centres"], case["d"], cfg.eps)
+    assert abs(float(out["loss"].item()) - float(L)) <= FWD_TOL * float(L)
+    assert _rel(gp, gref.numpy()) <= GRAD_TOL
