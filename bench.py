@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -195,7 +196,8 @@ def run_gpu(args, cfg, case, rank, world, local):
     with torch.cuda.graph(g_rays):
         pact.sos_to_delays(pb, rec.sos, rec.w)
     with torch.cuda.graph(g_mcd):
-        pact.mc_deconv_loss(pb, rec.w, rec.Y, rec.d, rec.eps, want_grad=True, out=rec.out, ws=rec.ws_mcd)
+        pact.mc_deconv_loss(pb, rec.w, rec.Y, rec.d, rec.eps, want_grad=True, out=rec.out, ws=rec.ws_mcd,
+                            tables=rec.tables)
     with torch.cuda.graph(g_rest):
         pact.sos_to_delays_adj(pb, rec.sos, rec.out["dL_dw"], rec.grad, accumulate=False, ws=rec.ws_adj)
         pact.tv(pb, rec.sos, rec.lam, value=rec.out["loss"], grad=rec.grad, accumulate=True)
@@ -305,8 +307,68 @@ def run_gpu(args, cfg, case, rank, world, local):
         line["e2e"] = {"value": e2e, "unit": "iters/s", "h2d_bytes_per_step": stack.numel() * 4 / iters,
                        "d2h_bytes_per_step": 4, "what": f"recover(): pinned host stack upload, patch FFT, graph "
                                                        f"capture, {iters} iterations with a loss read-back each"}
+    if not args.no_variants:
+        line["variants"] = {"neural_field": nf_variant(args, cfg, case, pb, Y, flush, stream),
+                            "das_stack": das_variant(dev, flush, stream)}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _time_graph(g, flush, stream, steps: int):
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    for e in evs:
+        flush.zero_()
+        e[0].record(stream)
+        g.replay()
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    return [e[0].elapsed_time(e[1]) for e in evs]
+
+
+def nf_variant(args, cfg, case, pb, Y, flush, stream):
+    """Neural-field SOS (BF16 tensor cores) on the same problem: one iteration =
+    nf_forward + rays + fused pass + ray adjoint + nf_backward + Adam."""
+    import torch
+    from paper_2409_10876_gb300 import inputs
+    from paper_2409_10876_gb300.recovery import NFRecovery
+    rec = NFRecovery(pb, Y, case["d"], cfg.eps, 5e-3, inputs.nf_init(args.seed), case["mask"])
+    g = rec.capture()
+    for _ in range(3):
+        g.replay()
+    steps = max(20, min(args.steps, 500))
+    ms = _time_graph(g, flush, stream, steps)
+    return {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
+            "dtype": "bf16 (field) + f32 (forward model)", "params": int(rec.params.numel()),
+            "gpu_launches_per_step": 12}
+
+
+def das_variant(dev, flush, stream):
+    """Eq. 1 DAS stack at the channel-data scale (once per recovery): 1024-element
+    ring, 4096 samples at 40 MHz -> 32 delay channels x 1024 x 1024 pixels."""
+    import torch
+    from paper_2409_10876_gb300 import inputs, pact
+    cfg = inputs.config_rf()
+    pb = pact.Problem(cfg, dev)
+    rng = np.random.default_rng(7)
+    rf = torch.as_tensor(rng.standard_normal((cfg.n_t, 4096)).astype(np.float32), device=dev)
+    d = cfg.delays()
+    stack = torch.empty((cfg.m, cfg.img_h, cfg.img_w), dtype=torch.float32, device=dev)
+    pact.das_stack(pb, rf, 40e6, 0.0, d, stack)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pact.das_stack(pb, rf, 40e6, 0.0, d, stack)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    taps = cfg.img_h * cfg.img_w * cfg.n_t * cfg.m
+    t = statistics.median(ms) / 1e3
+    return {"ms": statistics.median(ms), "taps": taps, "gtaps_per_s": taps / t / 1e9,
+            "workload": "1024 el x 4096 samples -> 32 x 1024 x 1024"}
 
 
 def kernel_revision() -> str:

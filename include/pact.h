@@ -196,8 +196,15 @@ size_t pact_mc_deconv_loss_workspace_size(const pact_geometry* g, const pact_pat
  *   Xhat     DEVICE c64 [N][P][P/2+1] or NULL
  *   dL_dw    DEVICE float [N][N_t] or NULL  output gradient
  *   ws       DEVICE workspace (256-byte aligned) of the size above
- * When eps < 1e-6 the per-bin channel-sum denominator and the division run
- * in FP64.  Errors: INVALID_ARG (null w/Y/loss/ws, eps < 0, small ws,
+ * For eps >= 1e-6 the residual energy of a bin is evaluated as
+ * sum_j |Y_ij|^2 - |A|^2 (B + 2 eps) / (B + eps)^2 (A, B the numerator and
+ * denominator sums of Eq. 6), so each Y element is read once; its FP32
+ * rounding is about 1e-7 of sum_j |Y_ij|^2 per bin, of either sign.  When
+ * eps < 1e-6 the per-bin channel-sum denominator and the division run in FP64
+ * and the residual Y_ij - H_ij X_i is formed explicitly (a second pass over a
+ * shared-memory copy of the bin tile), so an exact fit gives a loss of
+ * rounding size relative to the residual, not to the data.
+ * Errors: INVALID_ARG (null w/Y/loss/ws, eps < 0, small ws,
  * misaligned Y), SHAPE (m > PACT_MAX_CHANNELS, P odd or out of range, n_t too
  * large for shared memory).  A bulk copy that does not complete within
  * 200 ms (never expected) makes the loss and dL_dw NaN instead of hanging.
@@ -215,6 +222,33 @@ pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* 
                                     const float* Y, const float* d, int m, float eps,
                                     const float* dL_dloss, float* dL_dw, int accumulate, void* ws,
                                     size_t ws_bytes, void* stream);
+
+/*
+ * Prebuilt tables for repeated pact_mc_deconv_loss calls.  Everything in the
+ * fused pass that depends only on the geometry, the patch centres and the
+ * delays -- the ring coordinates of the directions ang k and ang k + pi for
+ * every (patch, bin) (the lookups of Eq. 4), exp(j|k|d_j) per (channel, bin),
+ * and the per-bin sums C2 = sum_j exp(2j|k|d_j) in FP32 and FP64 -- is built
+ * once by pact_mc_deconv_tables; a recovery loop (Sec. 3.3) keeps them for
+ * every iteration, where pact_mc_deconv_loss rebuilds them per call.
+ *   tables   DEVICE, 256-byte aligned, pact_mc_deconv_tables_size bytes,
+ *            owned by the caller, written by pact_mc_deconv_tables.
+ * pact_mc_deconv_loss_tabled takes the arguments of pact_mc_deconv_loss plus
+ * the tables, and a workspace of pact_mc_deconv_loss_tabled_workspace_size
+ * bytes (the per-call scratch only); loss or dL_dw may be NULL (not both).
+ * The tables carry a fingerprint of (geometry, N, P, centres pointer, m, d);
+ * a call whose arguments do not match it writes NaN to loss and dL_dw.
+ * Errors as pact_mc_deconv_loss, plus INVALID_ARG for NULL, misaligned or
+ * small tables.
+ */
+size_t pact_mc_deconv_tables_size(const pact_geometry* g, const pact_patches* pt, int m);
+size_t pact_mc_deconv_loss_tabled_workspace_size(const pact_geometry* g, const pact_patches* pt, int m);
+pact_status pact_mc_deconv_tables(const pact_geometry* g, const pact_patches* pt, const float* d, int m,
+                                  void* tables, size_t tables_bytes, void* stream);
+pact_status pact_mc_deconv_loss_tabled(const pact_geometry* g, const pact_patches* pt, const float* w,
+                                       const float* Y, const float* d, int m, float eps, const void* tables,
+                                       size_t tables_bytes, float* loss, float* loss_pp, float* Xhat,
+                                       float* dL_dw, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * pact_mc_deconv_loss without a workspace argument.  The paper has no

@@ -10,18 +10,21 @@
 //     A  = sum_j conj(H_j) Y_j = (conj(a) (S1 - jS2) + conj(b) (S1 + jS2)) / 2
 //     B  = sum_j |H_j|^2       = (M + Re(a conj(b) C2)) / 2
 //     X  = A / (B + eps)                                                  (Eq. 6)
-// The residual R_j = Y_j - H_j X = Y_j - cos(|k|d_j) p - sin(|k|d_j) q with
-// p = (a + b) X / 2, q = j (a - b) X / 2 is formed explicitly in a second
-// pass over the shared-memory copy of Y (no E - |A|^2/B cancellation), giving
-// the loss term w_k sum_j |R_j|^2 (Eq. 7, w_k = c_k |k|_mm).
+// The residual is R_j = Y_j - H_j X = Y_j - cos(|k|d_j) p - sin(|k|d_j) q with
+// p = (a + b) X / 2, q = j (a - b) X / 2; the loss term is w_k sum_j |R_j|^2
+// (Eq. 7, w_k = c_k |k|_mm).  For eps >= 1e-6 it is taken in closed form,
+// sum_j |R_j|^2 = sum_j |Y_j|^2 - |A|^2 (B + 2 eps) / D^2, and Y streams through
+// the SM once (mcd_stream_kernel); the FP64 path (eps < 1e-6, where an exact fit
+// is the case of interest) forms R_j explicitly in a second pass over a
+// shared-memory copy of the tile (mcd_kernel), free of that cancellation.
 // Adjoint: dL/dconj(H_j) = -(w_k conj(X)/D) ((B + 2 eps) R_j - eps X H_j),
 // D = B + eps, and with T1 = sum_j cos(|k|d_j) conj(R_j),
 // T2 = sum_j sin(|k|d_j) conj(R_j):
 //     dL/dW(ang k)      =  |k| Im(conj(K) ((B+2eps) a (T1 + jT2) - eps conj(X) (M + a conj(b) C2)/2))
 //     dL/dW(ang k + pi) = -|k| Im(conj(K) ((B+2eps) b (T1 - jT2) - eps conj(X) (M + conj(a) b conj(C2))/2))
 // with K = -w_k conj(X)/D; these are scattered to the two transducers each
-// lookup interpolates (shared-memory accumulation per CTA, then a
-// deterministic reduction over the CTAs of a patch).
+// lookup interpolates (shared-memory accumulation per CTA, then one global
+// atomic add per touched transducer).
 #include <algorithm>
 #include <mutex>
 
@@ -74,15 +77,18 @@ struct McdArgs {
     float eps;
     Delays dl;
     float2* Xhat;
-    int want_grad;
+    float* dL_dw;          // [N][n_t] output (cleared by the host call unless accumulating) or NULL
+    const float* scale;    // device scalar multiplying dL/dw, or NULL
     int fp64;
     float* part_loss;      // [N][KT]
-    float* part_dw;        // [N][KT][n_t]
     const float2* lut;     // [N][F] ring coordinates (t_a, t_b)
     const float2* etab;    // [M][F] exp(j|k|d_j)
     const float4* btab;    // [F] (|k|/2pi, c_k |k|_mm, Re C2, Im C2)
     const double2* c2d;    // [F] C2 in FP64 (eps < 1e-6 only)
     int KT;                // 256-bin tiles
+    const unsigned long long* tag;   // fingerprint the tables were built for
+    unsigned long long want;         // fingerprint of this call's arguments
+    int* tile_next;                  // [KT] per-tile claim counters, zero at launch
 };
 
 // Ring coordinate t = alpha N_t / (2 pi) in [0, N_t) of the point where the ray
@@ -104,8 +110,9 @@ __device__ __forceinline__ float ring_coord(float cx, float cy, float dx, float 
 //  * blockIdx.y == N: per-bin tables etab[j][k] = exp(j|k|d_j) and
 //    btab[k] = (|k|/2pi, c_k |k|_mm, Re C2, Im C2) with C2 = sum_j exp(2j|k|d_j).
 __global__ void mcd_tables_kernel(Geo g, int N, int P, int F, int M, Delays dl, const int2* centres, float2* lut,
-                                  float2* etab, float4* btab) {
+                                  float2* etab, float4* btab, unsigned long long* tag, unsigned long long fp) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0 && blockIdx.y == 0) *tag = fp;
     if (k >= F) return;
     int u, v;
     const float2 f = bin_freq(k, P, 1.f / (P * g.dx), u, v);
@@ -149,83 +156,100 @@ __global__ void mcd_c2d_kernel(int P, int F, double dx, Delays dl, double2* out)
     out[k] = make_double2(re, im);
 }
 
-// Sum over the two threads of a bin (lanes b and b + 16).
-__device__ __forceinline__ float pair_sum(float x) { return x + __shfl_xor_sync(0xffffffffu, x, 16); }
 
-// CTA (kt, i): bins kt*256 .. kt*256+255 of patch i, 512 threads.  Two
-// threads share a bin (lanes b and b+16 of a warp; warp w owns bins
-// 16w .. 16w+15): half h owns channels j = h, h+2, ..., loads Y_ij(k) and
-// exp(j|k|d_j) for them straight into registers (Y streamed once from HBM,
-// the exp table from L2) and completes every channel sum with one shuffle.
-// Half 0 evaluates the lookup of w at ang k, half 1 at ang k + pi.  With
-// S1 = sum cos(|k|d_j) Y_j and S2 = sum sin(|k|d_j) Y_j the residual sums of
-// the adjoint follow in closed form, T1 = conj(S1) - conj(p) Scc - conj(q) Scs,
-// T2 = conj(S2) - conj(p) Scs - conj(q) Sss; only sum |R_j|^2 needs the explicit
-// second pass over the registers.  CPH channels per half; EXACT: M == 2 CPH.
-template <int CPH, bool EXACT>
-__global__ void __launch_bounds__(512, 1) mcd_kernel(const McdArgs a) {
-    extern __shared__ float dw_s[];                          // [n_t]
-    __shared__ float lsum_s;
-    const int n_t = a.g.n_t, M = EXACT ? 2 * CPH : a.M;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int hf = lane >> 4;
+constexpr int kBins = 256;                                 // bins per CTA, one thread each
+constexpr uint64_t kCopyWaitNs = 200ull * 1000ull * 1000ull;   // bound on the bulk-copy wait
+
+// CTA (kt, i): bins kt*256 .. kt*256+255 of patch i, one thread per bin.  The
+// M channel rows Y_ij(k0 .. k0+255) arrive by 1-D bulk copies (TMA) into
+// shared memory while the threads load their per-bin tables (exp(j|k|d_j) for
+// all channels stays in registers) and evaluate the two lookups of w of
+// Eq. 4.  With S1 = sum cos(|k|d_j) Y_j and S2 = sum sin(|k|d_j) Y_j the
+// residual sums of the adjoint follow in closed form,
+// T1 = conj(S1) - conj(p) Scc - conj(q) Scs, T2 = conj(S2) - conj(p) Scs - conj(q) Sss;
+// only sum |R_j|^2 needs the explicit second pass over the tile.  The CTA's
+// dL/dw contributions are summed in shared memory and added to the output with
+// one atomic per touched transducer.  Two CTAs per SM keep the copies of one
+// overlapped with the arithmetic of the other.  CPT channels per thread;
+// EXACT: M == CPT.
+template <int CPT, bool EXACT>
+__global__ void __launch_bounds__(kBins, 2) mcd_kernel(const McdArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int n_t = a.g.n_t, M = EXACT ? CPT : a.M;
+    float2* ytile = reinterpret_cast<float2*>(smem_raw);                      // [M][kBins]
+    float* dw_s = reinterpret_cast<float*>(ytile + (size_t)M * kBins);        // [n_t]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float lsum_s[kBins / 32];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int kt = blockIdx.x, i = blockIdx.y;
-    const int k = kt * 256 + warp * 16 + (lane & 15);
+    const int k0 = kt * kBins;
+    const int k = k0 + tid;
     const bool valid = k < a.F;
-    for (int n = tid; n < n_t; n += 512) dw_s[n] = 0.f;
-    if (tid == 0) lsum_s = 0.f;
+    __shared__ int tag_ok;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        tag_ok = *a.tag == a.want;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)(min(kBins, a.F - k0) * sizeof(float2));
+        mbar_arrive_expect_tx(&bar, bytes * (uint32_t)M);
+        const float2* src = a.Y + (size_t)i * M * a.F + k0;
+        for (int j = 0; j < M; ++j) tma_bulk_g2s(ytile + (size_t)j * kBins, src + (size_t)j * a.F, bytes, &bar);
+    }
+    for (int n = tid; n < n_t; n += kBins) dw_s[n] = 0.f;
 
-    float2 y[CPH], E[CPH];
-    const float2* yp = a.Y + ((size_t)i * M + hf) * a.F + k;
-    const float2* ep = a.etab + (size_t)hf * a.F + k;
+    // per-bin tables and the two lookups of w while the copies are in flight
+    float2 E[CPT];
     float4 bt = make_float4(0.f, 0.f, 0.f, 0.f);
-    float tr = 0.f;
+    float2 tr = make_float2(0.f, 0.f);
     if (valid) {
+        const float2* ep = a.etab + k;
 #pragma unroll
-        for (int m = 0; m < CPH; ++m) {
-            if (EXACT || 2 * m + hf < M) {
-                y[m] = __ldcs(yp + (size_t)(2 * m) * a.F);
-                E[m] = __ldg(ep + (size_t)(2 * m) * a.F);
-            } else {
-                y[m] = make_float2(0.f, 0.f);
-                E[m] = make_float2(0.f, 0.f);
-            }
-        }
+        for (int m = 0; m < CPT; ++m)
+            E[m] = (EXACT || m < M) ? __ldg(ep + (size_t)m * a.F) : make_float2(0.f, 0.f);
         bt = __ldg(a.btab + k);
-        tr = __ldg(reinterpret_cast<const float*>(a.lut) + 2 * ((size_t)i * a.F + k) + hf);
+        tr = __ldg(a.lut + (size_t)i * a.F + k);
+    } else {
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) E[m] = make_float2(0.f, 0.f);
     }
     const float fm = bt.x, om = bt.y;
     const float2 C2 = make_float2(bt.z, bt.w);
     const float Mf = (float)M;
     const float eps = a.eps;
-
-    // w at this thread's direction (Eq. 4): linear in ring angle between two transducers
     const float* wr = a.w + (size_t)i * n_t;
-    const float fl = floorf(tr);
-    const float fr = tr - fl;
-    int n1 = (int)fl;
-    n1 = n1 >= n_t ? n1 - n_t : n1;
-    const int n2 = n1 + 1 == n_t ? 0 : n1 + 1;
-    const float w1 = __ldg(wr + n1), w2 = __ldg(wr + n2);
-    const float Wd = fmaf(fr, w2 - w1, w1);
-    const float dsgn = hf ? -1.f : 1.f;
-    const float2 ph = cis_pi(-dsgn * 2.f * fm * Wd);   // half 0: exp(-j|k|W1), half 1: exp(+j|k|W2)
-    const float2 oth = make_float2(__shfl_xor_sync(0xffffffffu, ph.x, 16), __shfl_xor_sync(0xffffffffu, ph.y, 16));
-    const float Wo = __shfl_xor_sync(0xffffffffu, Wd, 16);
-    const float2 al = hf ? oth : ph, be = hf ? ph : oth;
-    const float W1 = hf ? Wo : Wd, W2 = hf ? Wd : Wo;
+    const float fla = floorf(tr.x), flb = floorf(tr.y);
+    const float fa = tr.x - fla, fb = tr.y - flb;
+    int n1a = (int)fla, n1b = (int)flb;
+    n1a = n1a >= n_t ? n1a - n_t : n1a;
+    n1b = n1b >= n_t ? n1b - n_t : n1b;
+    const int n2a = n1a + 1 == n_t ? 0 : n1a + 1;
+    const int n2b = n1b + 1 == n_t ? 0 : n1b + 1;
+    const float wa1 = __ldg(wr + n1a), wa2 = __ldg(wr + n2a), wb1 = __ldg(wr + n1b), wb2 = __ldg(wr + n2b);
+    const float W1 = fmaf(fa, wa2 - wa1, wa1), W2 = fmaf(fb, wb2 - wb1, wb1);
+    const float2 al = cis_pi(-2.f * fm * W1);      // exp(-j|k| W(ang k))
+    const float2 be = cis_pi(2.f * fm * W2);       // exp(+j|k| W(ang k + pi))
 
-    // pass 1 (own channels), completed across the pair
-    float s1x = 0.f, s1y = 0.f, s2x = 0.f, s2y = 0.f;
+    __syncthreads();                                // dw_s cleared
+    const bool ok = mbar_wait_bounded(&bar, 0, kCopyWaitNs) && tag_ok;
+    const float2* ys = ytile + tid;
+
+    // pass 1: S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j
+    float2 S1 = make_float2(0.f, 0.f), S2 = S1;
+    if (valid && ok) {
 #pragma unroll
-    for (int m = 0; m < CPH; ++m) {
-        s1x = fmaf(E[m].x, y[m].x, s1x);
-        s1y = fmaf(E[m].x, y[m].y, s1y);
-        s2x = fmaf(E[m].y, y[m].x, s2x);
-        s2y = fmaf(E[m].y, y[m].y, s2y);
+        for (int m = 0; m < CPT; ++m) {
+            if (EXACT || m < M) {
+                const float2 y = ys[(size_t)m * kBins];
+                S1.x = fmaf(E[m].x, y.x, S1.x);
+                S1.y = fmaf(E[m].x, y.y, S1.y);
+                S2.x = fmaf(E[m].y, y.x, S2.x);
+                S2.y = fmaf(E[m].y, y.y, S2.y);
+            }
+        }
     }
-    const float2 S1 = make_float2(pair_sum(s1x), pair_sum(s1y));
-    const float2 S2 = make_float2(pair_sum(s2x), pair_sum(s2y));
     const float2 U = make_float2(S1.x + S2.y, S1.y - S2.x);   // sum conj(E_j) Y_j
     const float2 V = make_float2(S1.x - S2.y, S1.y + S2.x);   // sum E_j Y_j
     const float2 ca = cmulc(al, U), cb = cmulc(be, V);
@@ -249,28 +273,29 @@ __global__ void __launch_bounds__(512, 1) mcd_kernel(const McdArgs a) {
         X = make_float2(A.x * iD, A.y * iD);
     }
 
-    // pass 2: explicit residual energy of the own channels
+    // pass 2: explicit residual energy R_j = Y_j - cos(|k|d_j) p - sin(|k|d_j) q
     const float2 pp = make_float2(0.5f * (al.x + be.x), 0.5f * (al.y + be.y));
     const float2 qm = make_float2(0.5f * (al.x - be.x), 0.5f * (al.y - be.y));
     const float2 p = cmul(pp, X);
     const float2 q0v = cmul(qm, X);
     const float2 qv = make_float2(-q0v.y, q0v.x);
     float e2 = 0.f;
+    if (valid && ok) {
 #pragma unroll
-    for (int m = 0; m < CPH; ++m) {
-        const float rx = y[m].x - fmaf(E[m].x, p.x, E[m].y * qv.x);
-        const float ry = y[m].y - fmaf(E[m].x, p.y, E[m].y * qv.y);
-        e2 = fmaf(rx, rx, fmaf(ry, ry, e2));
-    }
-    e2 = pair_sum(e2);
-    float contrib = 0.f;
-    __syncthreads();                                    // dw_s cleared
-    if (valid) {
-        if (hf == 0) {
-            contrib = om * e2;
-            if (a.Xhat) a.Xhat[(size_t)i * a.F + k] = X;
+        for (int m = 0; m < CPT; ++m) {
+            if (EXACT || m < M) {
+                const float2 y = ys[(size_t)m * kBins];
+                const float rx = y.x - fmaf(E[m].x, p.x, E[m].y * qv.x);
+                const float ry = y.y - fmaf(E[m].x, p.y, E[m].y * qv.y);
+                e2 = fmaf(rx, rx, fmaf(ry, ry, e2));
+            }
         }
-        if (a.want_grad && fm > 0.f && D != 0.f) {
+    }
+    float contrib = 0.f;
+    if (valid) {
+        contrib = om * e2;
+        if (a.Xhat) a.Xhat[(size_t)i * a.F + k] = X;
+        if (a.dL_dw && fm > 0.f && D != 0.f) {
             const float Scc = 0.5f * (Mf + C2.x), Sss = 0.5f * (Mf - C2.x), Scs = 0.5f * C2.y;
             const float iD = __frcp_rn(D);
             const float kmag = kTwoPi * fm;
@@ -281,95 +306,364 @@ __global__ void __launch_bounds__(512, 1) mcd_kernel(const McdArgs a) {
             // T1 = sum cos conj(R), T2 = sum sin conj(R)
             const float2 T1 = make_float2(S1.x - p.x * Scc - qv.x * Scs, -S1.y + p.y * Scc + qv.y * Scs);
             const float2 T2 = make_float2(S2.x - p.x * Scs - qv.x * Sss, -S2.y + p.y * Scs + qv.y * Sss);
-            float gW;
-            if (hf == 0) {
-                const float2 hp = make_float2(0.5f * (Mf + abC2.x), 0.5f * abC2.y);
-                const float2 tp = make_float2(T1.x - T2.y, T1.y + T2.x);
-                const float2 ap = cmul(al, tp), xhp = cmul(xc, hp);
-                const float2 SP = make_float2(b2 * ap.x - eps * xhp.x, b2 * ap.y - eps * xhp.y);
-                gW = kmag * (Kc.x * SP.y + Kc.y * SP.x);
-            } else {
-                const float2 hq = make_float2(0.5f * (Mf + abC2.x), -0.5f * abC2.y);
-                const float2 tq = make_float2(T1.x + T2.y, T1.y - T2.x);
-                const float2 bq = cmul(be, tq), xhq = cmul(xc, hq);
-                const float2 SQ = make_float2(b2 * bq.x - eps * xhq.x, b2 * bq.y - eps * xhq.y);
-                gW = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
-            }
-            atomicAdd(dw_s + n1, (1.f - fr) * gW);
-            atomicAdd(dw_s + n2, fr * gW);
+            const float2 hp = make_float2(0.5f * (Mf + abC2.x), 0.5f * abC2.y);     // sum conj(H) P
+            const float2 hq = make_float2(hp.x, -hp.y);                             // sum conj(H) Q
+            const float2 tp = make_float2(T1.x - T2.y, T1.y + T2.x);                 // T1 + jT2
+            const float2 tq = make_float2(T1.x + T2.y, T1.y - T2.x);                 // T1 - jT2
+            const float2 ap = cmul(al, tp), xhp = cmul(xc, hp);
+            const float2 bq = cmul(be, tq), xhq = cmul(xc, hq);
+            const float2 SP = make_float2(b2 * ap.x - eps * xhp.x, b2 * ap.y - eps * xhp.y);
+            const float2 SQ = make_float2(b2 * bq.x - eps * xhq.x, b2 * bq.y - eps * xhq.y);
+            const float gW1 = kmag * (Kc.x * SP.y + Kc.y * SP.x);
+            const float gW2 = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
+            atomicAdd(dw_s + n1a, (1.f - fa) * gW1);
+            atomicAdd(dw_s + n2a, fa * gW1);
+            atomicAdd(dw_s + n1b, (1.f - fb) * gW2);
+            atomicAdd(dw_s + n2b, fb * gW2);
         }
     }
     contrib = warp_sum(contrib);
-    if (lane == 0) atomicAdd(&lsum_s, contrib);
+    if (lane == 0) lsum_s[tid >> 5] = contrib;
     __syncthreads();
-    if (a.want_grad) {
-        float* dst = a.part_dw + ((size_t)i * a.KT + kt) * n_t;
-        for (int n = tid; n < n_t; n += 512) dst[n] = dw_s[n];
+    const float nan = __int_as_float(0x7fc00000);
+    if (a.dL_dw) {
+        const float sc = a.scale ? *a.scale : 1.f;
+        float* dst = a.dL_dw + (size_t)i * n_t;
+        for (int n = tid; n < n_t; n += kBins) {
+            const float v = dw_s[n];
+            if (v != 0.f) atomicAdd(dst + n, sc * v);
+        }
+        if (!ok && tid == 0) atomicAdd(dst, nan);      // copy never arrived: poison the gradient
     }
-    if (tid == 0) a.part_loss[(size_t)i * a.KT + kt] = lsum_s;
+    if (tid == 0) {
+        float acc = 0.f;
+        for (int q = 0; q < kBins / 32; ++q) acc += lsum_s[q];     // fixed order: deterministic
+        a.part_loss[(size_t)i * a.KT + kt] = ok ? acc : nan;
+    }
 }
 
-struct FinArgs {
-    int N, S, n_t;
-    const float* part_loss;
-    const float* part_dw;
-    float* loss;
-    float* loss_pp;
-    float* dL_dw;
-    const float* scale;   // device scalar or NULL
-    int accumulate;
-    int want_grad;
-};
+constexpr int kCh = 8;          // channel rows per pipeline stage (16 KB)
+constexpr int kStages = 6;      // stages in flight per CTA
+constexpr int kRing = 8;        // unit ids published ahead of their consumers
+constexpr int kTile = 224;                   // bins per unit of the streaming kernel, one consumer thread each
+constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two CTAs per SM)
 
-__global__ void __launch_bounds__(kTPB) mcd_finalize_kernel(const FinArgs a) {
-    __shared__ float red[kTPB / 32];
-    const int i = blockIdx.x;
-    const float sc = a.scale ? *a.scale : 1.f;
-    if (a.want_grad && a.dL_dw) {
-        for (int n = threadIdx.x; n < a.n_t; n += kTPB) {
-            float acc = 0.f;
-            for (int s = 0; s < a.S; ++s) acc += a.part_dw[((size_t)i * a.S + s) * a.n_t + n];
-            acc *= sc;
-            float* o = a.dL_dw + (size_t)i * a.n_t + n;
-            *o = a.accumulate ? *o + acc : acc;
+// Streaming form of the fused pass (eps >= 1e-6).  The residual energy follows
+// from the same sums as the deconvolution,
+//   sum_j |Y_j - H_j X|^2 = sum_j |Y_j|^2 - |A|^2 (B + 2 eps) / (B + eps)^2,
+// so every Y element is used once and the tile need not stay resident.  Work
+// units are (224-bin tile kt, patch i).  A persistent CTA has seven consumer
+// warps (one thread per bin) and one producer warp.  The producer claims units
+// one at a time from per-tile counters (starting at tile blockIdx.x mod KT and
+// moving on when a tile is exhausted, so the CTAs of a tile share
+// exp(j|k|d_j), which the consumers keep in registers, and a slow SM simply
+// takes fewer units), publishes each unit id in a small ring, and streams the
+// unit's Y rows through kStages stages of kCh rows by 1-D bulk copies (TMA) on
+// a "full" mbarrier per stage; the consumer warps release a stage on its
+// "empty" mbarrier.  The dL/dw contributions of a unit are summed in one of two
+// shared buffers (alternating per unit) and added to the output after the
+// unit's closing consumer barrier.
+template <int CPT, bool EXACT>
+__global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const McdArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int n_t = a.g.n_t, M = EXACT ? CPT : a.M, N = a.N;
+    float2* stage = reinterpret_cast<float2*>(smem_raw);                          // [kStages][kCh][kTile]
+    float* dw_s = reinterpret_cast<float*>(stage + (size_t)kStages * kCh * kTile);  // [2][n_t]
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ float lsum_s[2][kTile / 32];
+    __shared__ int ring[kRing];
+    __shared__ int tag_ok;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nc = EXACT ? CPT / kCh : (M + kCh - 1) / kCh;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kTile / 32);
+        }
+        mbar_init_fence();
+        tag_ok = *a.tag == a.want;
+    }
+    for (int n = tid; n < 2 * n_t; n += blockDim.x) dw_s[n] = 0.f;
+    __syncthreads();
+
+    if (tid >= kTile) {                              // ---------------- producer warp
+        if (lane != 0) return;
+        if (!tag_ok) {                                // tables built for other arguments: no work
+            ring[0] = -1;
+            mbar_arrive(&full[0]);
+            if (blockIdx.x == 0) {
+                a.part_loss[0] = __int_as_float(0x7fc00000);
+                if (a.dL_dw) atomicAdd(a.dL_dw, __int_as_float(0x7fc00000));
+            }
+            return;
+        }
+        int kt = blockIdx.x % a.KT, tried = 0, unit = -1;
+        for (int q = 0;; ++q) {
+            const int s = q % kStages, lu = q / nc, c = q - lu * nc;
+            if (q >= kStages &&                       // consumers released chunk q - kStages
+                !mbar_wait_bounded(&empty[s], (uint32_t)((q / kStages - 1) & 1), kCopyWaitNs))
+                return;                               // consumers time out on the missing chunk
+            if (c == 0) {                             // claim the next unit
+                unit = -1;
+                while (tried < a.KT) {
+                    const int i = atomicAdd(a.tile_next + kt, 1);
+                    if (i < N) {
+                        unit = kt * N + i;
+                        break;
+                    }
+                    kt = kt + 1 == a.KT ? 0 : kt + 1;
+                    ++tried;
+                }
+                ring[lu % kRing] = unit;
+                if (unit < 0) {                       // no work left: release the consumers
+                    mbar_arrive(&full[s]);
+                    return;
+                }
+            }
+            fence_proxy_async_smem();
+            const int ukt = unit / N, i = unit - ukt * N;
+            const int k0 = ukt * kTile;
+            const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
+            const int j0 = c * kCh, rows = min(kCh, M - j0);
+            mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)rows);
+            const float2* src = a.Y + ((size_t)i * M + j0) * a.F + k0;
+            float2* dst = stage + (size_t)s * kCh * kTile;
+            for (int r = 0; r < rows; ++r)
+                tma_bulk_g2s(dst + (size_t)r * kTile, src + (size_t)r * a.F, bytes, &full[s]);
         }
     }
-    if (a.loss_pp && threadIdx.x == 0) {
-        float acc = 0.f;
-        for (int s = 0; s < a.S; ++s) acc += a.part_loss[(size_t)i * a.S + s];
-        a.loss_pp[i] = acc;
-    }
-    if (i == 0 && a.loss) {
-        float acc = 0.f;
-        const int tot = a.N * a.S;
-        for (int q = threadIdx.x; q < tot; q += kTPB) acc += a.part_loss[q];
-        acc = block_sum(acc, red);
-        if (threadIdx.x == 0) a.loss[0] = acc;
+
+    // ------------------------------------------------------------------ consumer warps
+    float2 E[CPT];
+    float4 bt = make_float4(0.f, 0.f, 0.f, 0.f);
+    int kt_loaded = -1;
+    bool ok = tag_ok;
+    const float nan = __int_as_float(0x7fc00000);
+    const float sc = a.scale ? *a.scale : 1.f;
+
+    // the first chunk of a unit also publishes its id
+    if (ok) ok = mbar_wait_bounded(&full[0], 0u, kCopyWaitNs);
+    int u = ring[0];
+    if (!bar_and(1, kTile, ok)) u = -1;
+    for (int lu = 0; u >= 0; ++lu) {
+        const int kt = u / N, i = u - kt * N;
+        const int k = kt * kTile + tid;
+        const bool valid = k < a.F;
+        const int buf = lu & 1;
+        if (kt != kt_loaded) {                       // per-bin tables of this tile
+            kt_loaded = kt;
+#pragma unroll
+            for (int m = 0; m < CPT; ++m)
+                E[m] = (valid && (EXACT || m < M)) ? __ldg(a.etab + (size_t)m * a.F + k) : make_float2(0.f, 0.f);
+            bt = valid ? __ldg(a.btab + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // the two lookups of w of Eq. 4
+        const float2 tr = valid ? __ldg(a.lut + (size_t)i * a.F + k) : make_float2(0.f, 0.f);
+        const float* wr = a.w + (size_t)i * n_t;
+        const float fla = floorf(tr.x), flb = floorf(tr.y);
+        const float fa = tr.x - fla, fb = tr.y - flb;
+        int n1a = (int)fla, n1b = (int)flb;
+        n1a = n1a >= n_t ? n1a - n_t : n1a;
+        n1b = n1b >= n_t ? n1b - n_t : n1b;
+        const int n2a = n1a + 1 == n_t ? 0 : n1a + 1;
+        const int n2b = n1b + 1 == n_t ? 0 : n1b + 1;
+        const float wa1 = __ldg(wr + n1a), wa2 = __ldg(wr + n2a), wb1 = __ldg(wr + n1b), wb2 = __ldg(wr + n2b);
+
+        // S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j, Ey = sum |Y_j|^2
+        float2 S1 = make_float2(0.f, 0.f), S2 = S1;
+        float Ey = 0.f;
+        const int qb = lu * nc;
+#pragma unroll
+        for (int c = 0; c < CPT / kCh; ++c) {
+            if (EXACT || c < nc) {
+                const int q = qb + c, s = q % kStages;
+                if (c > 0 && ok) ok = mbar_wait_bounded(&full[s], (uint32_t)((q / kStages) & 1), kCopyWaitNs);
+                const float2* ys = stage + (size_t)s * kCh * kTile + tid;
+#pragma unroll
+                for (int r = 0; r < kCh; ++r) {
+                    const int m = c * kCh + r;
+                    if (EXACT || m < M) {
+                        const float2 y = ys[(size_t)r * kTile];
+                        S1.x = fmaf(E[m].x, y.x, S1.x);
+                        S1.y = fmaf(E[m].x, y.y, S1.y);
+                        S2.x = fmaf(E[m].y, y.x, S2.x);
+                        S2.y = fmaf(E[m].y, y.y, S2.y);
+                        Ey = fmaf(y.x, y.x, fmaf(y.y, y.y, Ey));
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+        }
+
+        float contrib = 0.f;
+        if (valid) {
+            const float fm = bt.x, om = bt.y;
+            const float2 C2 = make_float2(bt.z, bt.w);
+            const float Mf = (float)M, eps = a.eps;
+            const float W1 = fmaf(fa, wa2 - wa1, wa1), W2 = fmaf(fb, wb2 - wb1, wb1);
+            const float2 al = cis_pi(-2.f * fm * W1);      // exp(-j|k| W(ang k))
+            const float2 be = cis_pi(2.f * fm * W2);       // exp(+j|k| W(ang k + pi))
+            const float2 U1 = make_float2(S1.x + S2.y, S1.y - S2.x);   // sum conj(E_j) Y_j
+            const float2 V1 = make_float2(S1.x - S2.y, S1.y + S2.x);   // sum E_j Y_j
+            const float2 ca = cmulc(al, U1), cb = cmulc(be, V1);
+            const float2 A = make_float2(0.5f * (ca.x + cb.x), 0.5f * (ca.y + cb.y));
+            const float2 ab = cmulc(be, al);                           // a conj(b)
+            const float B = 0.5f * (Mf + (ab.x * C2.x - ab.y * C2.y));
+            const float D = B + eps;
+            const float iD = D != 0.f ? __frcp_rn(D) : 0.f;
+            const float2 X = make_float2(A.x * iD, A.y * iD);
+            // sum_j |R_j|^2 = Ey - |A|^2 (B + 2 eps) / D^2
+            const float e2 = Ey - (A.x * A.x + A.y * A.y) * (B + 2.f * eps) * iD * iD;
+            contrib = om * e2;
+            if (a.Xhat) a.Xhat[(size_t)i * a.F + k] = X;
+            if (a.dL_dw && fm > 0.f && D != 0.f) {
+                const float pq_re = 0.5f * (al.x + be.x), pq_im = 0.5f * (al.y + be.y);
+                const float qm_re = 0.5f * (al.x - be.x), qm_im = 0.5f * (al.y - be.y);
+                const float2 p = make_float2(pq_re * X.x - pq_im * X.y, pq_re * X.y + pq_im * X.x);
+                const float2 q0v = make_float2(qm_re * X.x - qm_im * X.y, qm_re * X.y + qm_im * X.x);
+                const float2 qv = make_float2(-q0v.y, q0v.x);
+                const float Scc = 0.5f * (Mf + C2.x), Sss = 0.5f * (Mf - C2.x), Scs = 0.5f * C2.y;
+                const float kmag = kTwoPi * fm;
+                const float2 Kc = make_float2(-om * X.x * iD, -om * X.y * iD);   // conj(K)
+                const float b2 = B + 2.f * eps;
+                const float2 abC2 = cmul(ab, C2);
+                const float2 xc = make_float2(X.x, -X.y);
+                // T1 = sum cos conj(R), T2 = sum sin conj(R)
+                const float2 T1 = make_float2(S1.x - p.x * Scc - qv.x * Scs, -S1.y + p.y * Scc + qv.y * Scs);
+                const float2 T2 = make_float2(S2.x - p.x * Scs - qv.x * Sss, -S2.y + p.y * Scs + qv.y * Sss);
+                const float2 hp = make_float2(0.5f * (Mf + abC2.x), 0.5f * abC2.y);     // sum conj(H) P
+                const float2 hq = make_float2(hp.x, -hp.y);                             // sum conj(H) Q
+                const float2 tp = make_float2(T1.x - T2.y, T1.y + T2.x);                 // T1 + jT2
+                const float2 tq = make_float2(T1.x + T2.y, T1.y - T2.x);                 // T1 - jT2
+                const float2 ap = cmul(al, tp), xhp = cmul(xc, hp);
+                const float2 bq = cmul(be, tq), xhq = cmul(xc, hq);
+                const float2 SP = make_float2(b2 * ap.x - eps * xhp.x, b2 * ap.y - eps * xhp.y);
+                const float2 SQ = make_float2(b2 * bq.x - eps * xhq.x, b2 * bq.y - eps * xhq.y);
+                const float gW1 = kmag * (Kc.x * SP.y + Kc.y * SP.x);
+                const float gW2 = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
+                float* dws = dw_s + buf * n_t;
+                atomicAdd(dws + n1a, (1.f - fa) * gW1);
+                atomicAdd(dws + n2a, fa * gW1);
+                atomicAdd(dws + n1b, (1.f - fb) * gW2);
+                atomicAdd(dws + n2b, fb * gW2);
+            }
+        }
+        contrib = warp_sum(contrib);
+        if (lane == 0) lsum_s[buf][tid >> 5] = contrib;
+        // wait for the next unit's first chunk (normally long landed) so that its
+        // id is visible, then close unit lu with one consumer barrier
+        const int qn = (lu + 1) * nc, sn = qn % kStages;
+        if (ok) ok = mbar_wait_bounded(&full[sn], (uint32_t)((qn / kStages) & 1), kCopyWaitNs);
+        const int u_next = ring[(lu + 1) % kRing];
+        const bool all_ok = bar_and(1, kTile, ok);
+        if (a.dL_dw) {
+            float* dst = a.dL_dw + (size_t)i * n_t;
+            float* dws = dw_s + buf * n_t;
+            for (int n = tid; n < n_t; n += kTile) {
+                const float v = dws[n];
+                if (v != 0.f) {
+                    atomicAdd(dst + n, sc * v);
+                    dws[n] = 0.f;
+                }
+            }
+            if (!all_ok && tid == 0) atomicAdd(dst, nan);   // a copy never arrived: poison the gradient
+        }
+        if (tid == 0) {
+            float acc = 0.f;
+            for (int q = 0; q < kTile / 32; ++q) acc += lsum_s[buf][q];   // fixed order: deterministic
+            a.part_loss[(size_t)i * a.KT + kt] = all_ok ? acc : nan;
+        }
+        u = all_ok ? u_next : -1;
     }
 }
 
+// Per-patch and total loss from the per-CTA partial sums (fixed order).
+__global__ void __launch_bounds__(kTPB) mcd_finalize_kernel(int N, int KT, const float* part_loss, float* loss,
+                                                            float* loss_pp) {
+    __shared__ float red[kTPB / 32];
+    if (loss_pp)
+        for (int i = blockIdx.x * kTPB + threadIdx.x; i < N; i += gridDim.x * kTPB) {
+            float acc = 0.f;
+            for (int s = 0; s < KT; ++s) acc += part_loss[(size_t)i * KT + s];
+            loss_pp[i] = acc;
+        }
+    if (blockIdx.x == 0 && loss) {
+        float acc = 0.f;
+        for (int q = threadIdx.x; q < N * KT; q += kTPB) acc += part_loss[q];
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) loss[0] = acc;
+    }
+}
+
+// Memory of the fused pass: per-call scratch (loss partials) followed, unless the
+// caller provides prebuilt tables, by the tables (ring lookups, exp(j|k|d_j),
+// per-bin sums, FP64 C2) that depend only on geometry, patches and delays.
 struct Plan {
-    int KT;
-    size_t off_dw, off_lut, off_etab, off_btab, off_c2d, total;
+    int KT, KTs;                                   // tiles of the two-pass (256) and streaming (224) kernels
+    size_t off_next, scratch;                      // loss partials, then per-tile claim counters
+    size_t t_lut, t_etab, t_btab, t_c2d, tables;   // offsets inside the tables, their size
+    size_t total;                                  // workspace bytes without prebuilt tables
 };
 
 Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
+    (void)g;
     Plan p;
     const int F = pt->p * (pt->p / 2 + 1);
-    p.KT = (F + 255) / 256;
-    size_t o = align_up((size_t)pt->n * p.KT * sizeof(float), 256);
-    p.off_dw = o;
-    o += align_up((size_t)pt->n * p.KT * g->n_t * sizeof(float), 256);
-    p.off_lut = o;
+    p.KT = (F + kBins - 1) / kBins;
+    p.KTs = (F + kTile - 1) / kTile;
+    p.off_next = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
+    p.scratch = p.off_next + align_up((size_t)p.KTs * sizeof(int), 256);
+    size_t o = 256;                                // fingerprint header
+    p.t_lut = o;
     o += align_up((size_t)pt->n * F * sizeof(float2), 256);
-    p.off_etab = o;
+    p.t_etab = o;
     o += align_up((size_t)m * F * sizeof(float2), 256);
-    p.off_btab = o;
+    p.t_btab = o;
     o += align_up((size_t)F * sizeof(float4), 256);
-    p.off_c2d = o;
+    p.t_c2d = o;
     o += align_up((size_t)F * sizeof(double2), 256);
-    p.total = o;
+    p.tables = o;
+    p.total = p.scratch + p.tables;
     return p;
+}
+
+// FNV-1a fingerprint of what the tables depend on and the host can see:
+// geometry, patch count and size, channel count and delays.
+unsigned long long fingerprint(const pact_geometry* g, const pact_patches* pt, const float* d, int m) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t q = 0; q < n; ++q) h = (h ^ b[q]) * 1099511628211ull;
+    };
+    mix(g, sizeof(*g));
+    mix(&pt->n, sizeof(pt->n));
+    mix(&pt->p, sizeof(pt->p));
+    mix(&pt->centres, sizeof(pt->centres));
+    mix(&m, sizeof(m));
+    mix(d, sizeof(float) * (size_t)m);
+    return h;
+}
+
+// Fills the tables at `t` (layout of make_plan); the FP64 table when `fp64`.
+pact_status build_tables(const pact_geometry* g, const pact_patches* pt, const float* d, int m, bool fp64,
+                         const Plan& pl, char* t, cudaStream_t st) {
+    const int F = pt->p * (pt->p / 2 + 1);
+    const Delays dl = make_delays(d, m);
+    dim3 tg((F + 255) / 256, pt->n + 1);
+    mcd_tables_kernel<<<tg, 256, 0, st>>>(make_geo(g), pt->n, pt->p, F, m, dl,
+                                         reinterpret_cast<const int2*>(pt->centres),
+                                         reinterpret_cast<float2*>(t + pl.t_lut), reinterpret_cast<float2*>(t + pl.t_etab),
+                                         reinterpret_cast<float4*>(t + pl.t_btab),
+                                         reinterpret_cast<unsigned long long*>(t), fingerprint(g, pt, d, m));
+    PACT_TRY(check_launch("mc_deconv_loss: tables"));
+    if (fp64) {
+        mcd_c2d_kernel<<<(F + 255) / 256, 256, 0, st>>>(pt->p, F, (double)g->dx, dl,
+                                                        reinterpret_cast<double2*>(t + pl.t_c2d));
+        PACT_TRY(check_launch("mc_deconv_loss: FP64 table"));
+    }
+    return PACT_OK;
 }
 
 pact_status check_delays(const float* d, int m) {
@@ -382,19 +676,31 @@ pact_status check_delays(const float* d, int m) {
     return PACT_OK;
 }
 
-template <int CPH, bool EXACT>
+template <int CPT, bool EXACT>
 pact_status launch_mcd(const McdArgs& a, cudaStream_t st) {
-    const size_t smem = (size_t)a.g.n_t * sizeof(float);
-    PACT_TRY(ensure_smem((const void*)mcd_kernel<CPH, EXACT>, smem, "mc_deconv_loss: shared memory attribute"));
-    dim3 grid(a.KT, a.N);
-    mcd_kernel<CPH, EXACT><<<grid, 512, smem, st>>>(a);
+    if (a.fp64) {
+        const size_t smem = (size_t)a.M * kBins * sizeof(float2) + (size_t)a.g.n_t * sizeof(float);
+        PACT_TRY(ensure_smem((const void*)mcd_kernel<CPT, EXACT>, smem, "mc_deconv_loss: shared memory attribute"));
+        dim3 grid(a.KT, a.N);
+        mcd_kernel<CPT, EXACT><<<grid, kBins, smem, st>>>(a);
+        return check_launch("mc_deconv_loss kernel");
+    }
+    const void* fn = (const void*)mcd_stream_kernel<CPT, EXACT>;
+    const size_t smem = (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)a.g.n_t * sizeof(float);
+    PACT_TRY(ensure_smem(fn, smem, "mc_deconv_loss: shared memory attribute"));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStreamThreads, smem) != cudaSuccess || per_sm < 1)
+        return check_launch("mc_deconv_loss: occupancy query");
+    const int units = a.KT * a.N;
+    const int grid = std::min(units, per_sm * num_sms());
+    mcd_stream_kernel<CPT, EXACT><<<grid, kStreamThreads, smem, st>>>(a);
     return check_launch("mc_deconv_loss kernel");
 }
 
 pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float* w, const float* Y,
                     const float* d, int m, float eps, float* loss, float* loss_pp, float* Xhat,
                     float* dL_dw, const float* scale, int accumulate, void* ws, size_t ws_bytes,
-                    void* stream) {
+                    void* stream, const void* tables = nullptr, size_t tables_bytes = 0) {
     PACT_TRY(check_geometry(g));
     PACT_TRY(check_patches(pt));
     PACT_TRY(check_delays(d, m));
@@ -403,12 +709,20 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     if (!ws) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss: workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(Y) % 16) return fail(PACT_ERR_INVALID_ARG, "Y must be 16-byte aligned");
+    if ((size_t)m * kBins * sizeof(float2) + (size_t)g->n_t * sizeof(float) > 200 * 1024 ||
+        (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)g->n_t * sizeof(float) > 200 * 1024)
+        return fail(PACT_ERR_SHAPE, "mc_deconv_loss: n_t too large");
     const Plan pl = make_plan(g, pt, m);
-    if ((size_t)g->n_t * sizeof(float) > 200 * 1024) return fail(PACT_ERR_SHAPE, "mc_deconv_loss: n_t too large");
-    if (ws_bytes < pl.total)
-        return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, pl.total);
+    const size_t need = tables ? pl.scratch : pl.total;
+    if (ws_bytes < need) return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    if (tables) {
+        if (reinterpret_cast<uintptr_t>(tables) % 256) return fail(PACT_ERR_INVALID_ARG, "tables must be 256-byte aligned");
+        if (tables_bytes < pl.tables)
+            return fail(PACT_ERR_INVALID_ARG, "tables too small: %zu < %zu bytes", tables_bytes, pl.tables);
+    }
     cudaStream_t st = as_stream(stream);
     char* base = static_cast<char*>(ws);
+    char* tb = tables ? const_cast<char*>(static_cast<const char*>(tables)) : base + pl.scratch;
     McdArgs a;
     a.g = make_geo(g);
     a.N = pt->n;
@@ -421,50 +735,39 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.eps = eps;
     a.dl = make_delays(d, m);
     a.Xhat = reinterpret_cast<float2*>(Xhat);
-    a.want_grad = dL_dw != nullptr;
+    a.dL_dw = dL_dw;
+    a.scale = scale;
     a.fp64 = eps < 1e-6f;
     a.part_loss = reinterpret_cast<float*>(base);
-    a.part_dw = reinterpret_cast<float*>(base + pl.off_dw);
-    a.lut = reinterpret_cast<const float2*>(base + pl.off_lut);
-    a.etab = reinterpret_cast<const float2*>(base + pl.off_etab);
-    a.btab = reinterpret_cast<const float4*>(base + pl.off_btab);
-    a.c2d = reinterpret_cast<const double2*>(base + pl.off_c2d);
-    a.KT = pl.KT;
-    dim3 tg((a.F + 255) / 256, a.N + 1);
-    mcd_tables_kernel<<<tg, 256, 0, st>>>(a.g, a.N, a.P, a.F, m, a.dl, a.centres,
-                                         reinterpret_cast<float2*>(base + pl.off_lut),
-                                         reinterpret_cast<float2*>(base + pl.off_etab),
-                                         reinterpret_cast<float4*>(base + pl.off_btab));
-    PACT_TRY(check_launch("mc_deconv_loss: tables"));
-    if (a.fp64) {
-        mcd_c2d_kernel<<<(a.F + 255) / 256, 256, 0, st>>>(a.P, a.F, (double)g->dx, a.dl,
-                                                          reinterpret_cast<double2*>(base + pl.off_c2d));
-        PACT_TRY(check_launch("mc_deconv_loss: FP64 table"));
-    }
+    a.lut = reinterpret_cast<const float2*>(tb + pl.t_lut);
+    a.etab = reinterpret_cast<const float2*>(tb + pl.t_etab);
+    a.btab = reinterpret_cast<const float4*>(tb + pl.t_btab);
+    a.c2d = reinterpret_cast<const double2*>(tb + pl.t_c2d);
+    a.KT = a.fp64 ? pl.KT : pl.KTs;
+    a.tag = reinterpret_cast<const unsigned long long*>(tb);
+    a.want = fingerprint(g, pt, d, m);
+    a.tile_next = reinterpret_cast<int*>(base + pl.off_next);
+    if (!tables) PACT_TRY(build_tables(g, pt, d, m, a.fp64, pl, tb, st));
+    if (!a.fp64 && cudaMemsetAsync(a.tile_next, 0, (size_t)pl.KTs * sizeof(int), st) != cudaSuccess)
+        return check_launch("mc_deconv_loss: clearing the tile counters");
+    if (dL_dw && !accumulate &&
+        cudaMemsetAsync(dL_dw, 0, (size_t)pt->n * g->n_t * sizeof(float), st) != cudaSuccess)
+        return check_launch("mc_deconv_loss: clearing dL_dw");
     pact_status s;
-    if (m == 8) s = launch_mcd<4, true>(a, st);
-    else if (m == 16) s = launch_mcd<8, true>(a, st);
-    else if (m == 32) s = launch_mcd<16, true>(a, st);
-    else if (m == 64) s = launch_mcd<32, true>(a, st);
-    else if (m < 8) s = launch_mcd<4, false>(a, st);
-    else if (m < 16) s = launch_mcd<8, false>(a, st);
-    else if (m < 32) s = launch_mcd<16, false>(a, st);
-    else s = launch_mcd<32, false>(a, st);
+    if (m == 8) s = launch_mcd<8, true>(a, st);
+    else if (m == 16) s = launch_mcd<16, true>(a, st);
+    else if (m == 32) s = launch_mcd<32, true>(a, st);
+    else if (m == 64) s = launch_mcd<64, true>(a, st);
+    else if (m < 8) s = launch_mcd<8, false>(a, st);
+    else if (m < 16) s = launch_mcd<16, false>(a, st);
+    else if (m < 32) s = launch_mcd<32, false>(a, st);
+    else s = launch_mcd<64, false>(a, st);
     if (s != PACT_OK) return s;
-    FinArgs f;
-    f.N = a.N;
-    f.S = a.KT;
-    f.n_t = g->n_t;
-    f.part_loss = a.part_loss;
-    f.part_dw = a.part_dw;
-    f.loss = loss;
-    f.loss_pp = loss_pp;
-    f.dL_dw = dL_dw;
-    f.scale = scale;
-    f.accumulate = accumulate;
-    f.want_grad = a.want_grad;
-    mcd_finalize_kernel<<<a.N, kTPB, 0, st>>>(f);
-    return check_launch("mc_deconv_loss finalize");
+    if (loss || loss_pp) {
+        mcd_finalize_kernel<<<(a.N + kTPB - 1) / kTPB, kTPB, 0, st>>>(a.N, a.KT, a.part_loss, loss, loss_pp);
+        return check_launch("mc_deconv_loss finalize");
+    }
+    return PACT_OK;
 }
 
 // ---------------------------------------------------------------- psf synthesis
@@ -596,6 +899,40 @@ extern "C" pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pac
     if (!dL_dw) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss_adj: dL_dw is NULL");
     return run_mcd(g, pt, w, Y, d, m, eps, nullptr, nullptr, nullptr, dL_dw, dL_dloss, accumulate, ws,
                    ws_bytes, stream);
+}
+
+extern "C" size_t pact_mc_deconv_tables_size(const pact_geometry* g, const pact_patches* pt, int m) {
+    if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK) return 0;
+    return make_plan(g, pt, m).tables;
+}
+
+extern "C" size_t pact_mc_deconv_loss_tabled_workspace_size(const pact_geometry* g, const pact_patches* pt, int m) {
+    if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK) return 0;
+    return make_plan(g, pt, m).scratch;
+}
+
+extern "C" pact_status pact_mc_deconv_tables(const pact_geometry* g, const pact_patches* pt, const float* d, int m,
+                                             void* tables, size_t tables_bytes, void* stream) {
+    PACT_TRY(check_geometry(g));
+    PACT_TRY(check_patches(pt));
+    PACT_TRY(check_delays(d, m));
+    if (!tables) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_tables: tables is NULL");
+    if (reinterpret_cast<uintptr_t>(tables) % 256) return fail(PACT_ERR_INVALID_ARG, "tables must be 256-byte aligned");
+    const Plan pl = make_plan(g, pt, m);
+    if (tables_bytes < pl.tables)
+        return fail(PACT_ERR_INVALID_ARG, "tables too small: %zu < %zu bytes", tables_bytes, pl.tables);
+    return build_tables(g, pt, d, m, true, pl, static_cast<char*>(tables), as_stream(stream));
+}
+
+extern "C" pact_status pact_mc_deconv_loss_tabled(const pact_geometry* g, const pact_patches* pt, const float* w,
+                                                  const float* Y, const float* d, int m, float eps,
+                                                  const void* tables, size_t tables_bytes, float* loss,
+                                                  float* loss_pp, float* Xhat, float* dL_dw, void* ws,
+                                                  size_t ws_bytes, void* stream) {
+    if (!tables) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss_tabled: tables is NULL");
+    if (!loss && !dL_dw) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss_tabled: loss and dL_dw are both NULL");
+    return run_mcd(g, pt, w, Y, d, m, eps, loss, loss_pp, Xhat, dL_dw, nullptr, 0, ws, ws_bytes, stream, tables,
+                   tables_bytes);
 }
 
 extern "C" pact_status pact_psf_synth(const pact_geometry* g, const pact_patches* pt, const float* w,

@@ -186,14 +186,21 @@ __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
     }
 }
 
-__device__ __forceinline__ void scatter4(float* acc, int pitch, const Bil& b, float coef) {
-    const float cy0 = coef * (1.f - b.ty), cy1 = coef * b.ty;
-    atomicAdd(acc + b.idx, cy0 * (1.f - b.tx));
-    atomicAdd(acc + b.idx + 1, cy0 * b.tx);
-    atomicAdd(acc + b.idx + pitch, cy1 * (1.f - b.tx));
-    atomicAdd(acc + b.idx + pitch + 1, cy1 * b.tx);
+__device__ __forceinline__ void scatter4(float* acc, int pitch, int idx, float c00, float c01, float c10,
+                                         float c11) {
+    atomicAdd(acc + idx, c00);
+    atomicAdd(acc + idx + 1, c01);
+    atomicAdd(acc + idx + pitch, c10);
+    atomicAdd(acc + idx + pitch + 1, c11);
 }
 
+// CTA b takes the rays r = b, b + nb, b + 2 nb, ... of the flat (patch,
+// transducer) index r = i N_t + n, so that its warps integrate rays of different
+// patches and directions at the same time (rays of one patch all start at the
+// same centre, where their scatters would collide).  A lane walks a contiguous
+// run of samples of one ray and keeps the bilinear weights of the current cell
+// in registers, adding them to the shared grid only when the walk leaves the
+// cell.
 __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
     extern __shared__ float sm[];
     const int G = a.g.G, pitch = a.use_smem ? smem_pitch(G) : G;
@@ -210,26 +217,28 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
         __syncthreads();
     }
     float* acc = a.use_smem ? acc_s : a.out;
-    int i, n0, n1;
-    cta_rays(a, i, n0, n1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int2 cc = a.centres[i];
-    const float2 c = pixel_xy(a.g, cc.x, cc.y);
+    const int nrays = a.N * a.g.n_t, nb = gridDim.x;
+    const int mine = nrays > (int)blockIdx.x ? (nrays - (int)blockIdx.x + nb - 1) / nb : 0;   // rays of this CTA
+    const int nwarp = mine > warp ? (mine - warp + nw - 1) / nw : 0;                           // ... of this warp
     const float h = a.g.h;
-    const int nmine = n1 - n0 > warp ? (n1 - n0 - warp + nw - 1) / nw : 0;
-    for (int kb = 0; kb < nmine; kb += 32) {
-        const int cnt = min(32, nmine - kb);
-        const int nl = n0 + warp + (kb + min(lane, cnt - 1)) * nw;
-        const Ray mine = make_ray(a.g, c, nl);
-        const float my_g = lane < cnt ? a.dLdw[(size_t)i * a.g.n_t + nl] : 0.f;
-        for (int r = 0; r < cnt; ++r) {
-            const float gr = __shfl_sync(0xffffffffu, my_g, r);
+    for (int kb = 0; kb < nwarp; kb += 32) {
+        const int cnt = min(32, nwarp - kb);
+        const int r = (int)blockIdx.x + nb * (warp + nw * (kb + min(lane, cnt - 1)));
+        const int i = r / a.g.n_t, n = r - (r / a.g.n_t) * a.g.n_t;
+        const int2 cc = a.centres[i];
+        const Ray mine_ray = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
+        const float my_g = lane < cnt ? a.dLdw[r] : 0.f;
+        for (int rr = 0; rr < cnt; ++rr) {
+            const float gr = __shfl_sync(0xffffffffu, my_g, rr);
             if (gr == 0.f) continue;
-            const Ray ry = shfl_ray(mine, r);
+            const Ray ry = shfl_ray(mine_ray, rr);
             const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
             const int per = (nsamp + 31) >> 5;
             const int m0 = lane * per, m1 = min(nsamp, m0 + per);
             const float gv0 = gr * v0;
+            int cur = -1;
+            float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
             for (int m = m0; m < m1; ++m) {
                 const bool last = m >= ry.nfull;
                 const float s = last ? ry.nfull * h + 0.5f * ry.rem : (m + 0.5f) * h;
@@ -237,8 +246,19 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
                 const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
                 const float d = a.use_smem ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
                 const float iv = __frcp_rn(v0 + d);
-                scatter4(acc, pitch, b, gv0 * wgt * iv * iv);
+                const float coef = gv0 * wgt * iv * iv;
+                if (b.idx != cur) {
+                    if (cur >= 0) scatter4(acc, pitch, cur, c00, c01, c10, c11);
+                    cur = b.idx;
+                    c00 = c01 = c10 = c11 = 0.f;
+                }
+                const float cy0 = coef * (1.f - b.ty), cy1 = coef * b.ty;
+                c00 = fmaf(cy0, 1.f - b.tx, c00);
+                c01 = fmaf(cy0, b.tx, c01);
+                c10 = fmaf(cy1, 1.f - b.tx, c10);
+                c11 = fmaf(cy1, b.tx, c11);
             }
+            if (cur >= 0) scatter4(acc, pitch, cur, c00, c01, c10, c11);
         }
     }
     if (a.use_smem) {

@@ -356,3 +356,57 @@ def nf_init(seed: int, v_start: float = 1500.0) -> np.ndarray:
             bound *= 0.05
         parts.append(rng.uniform(-bound, bound, size=shape).ravel())
     return np.concatenate(parts).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# warm-start CNN: sizes, seeded initial parameters, training-set phantoms
+# --------------------------------------------------------------------------
+
+CNN_POOL = 4           # the M x 512 x 512 delay stack is averaged over 4 x 4 pixels
+CNN_RES = 128          # input side after pooling
+CNN_OUT = 32           # output SOS side (upsampled x4 to the 128 x 128 node grid)
+# (c_in, c_out, 2 x 2 average pooling after the layer); c_in of the first is M
+CNN_CONVS = ((None, 32, True), (32, 64, True), (64, 64, False), (64, 64, False), (64, 64, False))
+CNN_V_MID, CNN_V_HALF = 1525.0, 125.0    # v = 1525 + 125 tanh(z) spans 1400 .. 1650 m/s
+CNN_V_SCALE = 100.0                      # training loss: mean ((v - v_true) / 100 m/s)^2
+
+
+def cnn_shapes(m: int = 32):
+    """(name, shape) of the CNN parameters in their flat order: five 3x3
+    convolutions W_l [c_out][c_in][3][3], b_l [c_out], then the 1x1 head
+    w6 [64], b6 [1]."""
+    sh = []
+    for l, (cin, cout, _) in enumerate(CNN_CONVS, start=1):
+        cin = m if cin is None else cin
+        sh += [(f"W{l}", (cout, cin, 3, 3)), (f"b{l}", (cout,))]
+    sh += [("w6", (CNN_CONVS[-1][1],)), ("b6", (1,))]
+    return sh
+
+
+def cnn_param_count(m: int = 32) -> int:
+    return int(sum(np.prod(s) for _, s in cnn_shapes(m)))
+
+
+def cnn_init(seed: int, m: int = 32, v_start: float = 1500.0) -> np.ndarray:
+    """Seeded flat float32 parameters: U(-sqrt(6/fan_in), sqrt(6/fan_in)) for the
+    convolutions, zero biases, a small head and a head bias that makes the
+    initial output about v_start."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for name, shape in cnn_shapes(m):
+        if name == "b6":
+            parts.append(np.array([np.arctanh((v_start - CNN_V_MID) / CNN_V_HALF)]))
+        elif name.startswith("b"):
+            parts.append(np.zeros(shape))
+        elif name == "w6":
+            parts.append(rng.uniform(-0.01, 0.01, size=shape))
+        else:
+            bound = math.sqrt(6.0 / (shape[1] * 9))
+            parts.append(rng.uniform(-bound, bound, size=shape).ravel())
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def config_cnn() -> Config:
+    """The full-size problem with training phantoms of 1-6 ellipses spanning
+    1400-1650 m/s (the warm-start network's training distribution)."""
+    return config_full().replace(name="cnn512_ring512_p80_m32", sos_lo=1400.0, sos_hi=1650.0)

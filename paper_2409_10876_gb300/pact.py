@@ -54,6 +54,11 @@ _SIGS = {
     "pact_mc_deconv_loss_workspace_size": ([_GP, _PP, _I], _SZ),
     "pact_mc_deconv_loss": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _VP, _VP, _VP, _SZ, _VP], _I),
     "pact_mc_deconv_loss_noalloc": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _VP, _VP, _VP], _I),
+    "pact_mc_deconv_tables_size": ([_GP, _PP, _I], _SZ),
+    "pact_mc_deconv_loss_tabled_workspace_size": ([_GP, _PP, _I], _SZ),
+    "pact_mc_deconv_tables": ([_GP, _PP, _VP, _I, _VP, _SZ, _VP], _I),
+    "pact_mc_deconv_loss_tabled": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _SZ, _VP, _VP, _VP, _VP, _VP, _SZ, _VP],
+                                   _I),
     "pact_mc_deconv_loss_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_tv": ([_GP, _VP, _F, _VP, _VP, _I, _VP], _I),
     "pact_adam_step": ([_I, _VP, _VP, _VP, _VP, _I, _VP, _F, _F, _F, _F, _VP, _VP], _I),
@@ -264,10 +269,11 @@ def mc_deconv_loss_workspace_size(pb: Problem, m: int) -> int:
 
 
 def mc_deconv_loss(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=False, want_loss_pp=False,
-                   out=None, ws=None):
+                   out=None, ws=None, tables: "McdTables" = None):
     """Eq. 6-7 fused (+ adjoint when want_grad).  Returns a dict with
     'loss' [1], and 'dL_dw' [N, N_t], 'Xhat' [N, P, P/2+1], 'loss_pp' [N] as asked.
-    `out` may hold preallocated tensors under the same keys."""
+    `out` may hold preallocated tensors under the same keys; `tables` (built
+    for the same problem and delays) skips the per-call table build."""
     L = load()
     w = _dev(w, "w", torch.float32, (pb.n, pb.n_t))
     Y = _dev(Y, "Y", torch.complex64)
@@ -286,6 +292,16 @@ def mc_deconv_loss(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=F
         out["Xhat"] = _empty((pb.n, pb.p, pb.p // 2 + 1), torch.complex64, dev)
     if want_loss_pp and "loss_pp" not in out:
         out["loss_pp"] = _empty((pb.n,), torch.float32, dev)
+    if tables is not None:
+        if ws is None:
+            ws = _ws(tables.scratch_bytes, dev)
+        _check(L.pact_mc_deconv_loss_tabled(pb.gp(), pb.pp(), _ptr(w), _ptr(Y), dp, m, float(eps), _ptr(tables.buf),
+                                            tables.buf.numel(), _ptr(out["loss"]),
+                                            _ptr(out.get("loss_pp") if want_loss_pp else None),
+                                            _ptr(out.get("Xhat") if want_xhat else None),
+                                            _ptr(out.get("dL_dw") if want_grad else None), _ptr(ws), ws.numel(),
+                                            _stream()), "mc_deconv_loss_tabled")
+        return out
     if ws is None:
         ws = _ws(mc_deconv_loss_workspace_size(pb, m), dev)
     _check(L.pact_mc_deconv_loss(pb.gp(), pb.pp(), _ptr(w), _ptr(Y), dp, m, float(eps), _ptr(out["loss"]),
@@ -294,6 +310,21 @@ def mc_deconv_loss(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=F
                                  _ptr(out.get("dL_dw") if want_grad else None), _ptr(ws), ws.numel(), _stream()),
            "mc_deconv_loss")
     return out
+
+
+class McdTables:
+    """Prebuilt tables of the fused pass for fixed (geometry, patches, delays):
+    build once, pass to mc_deconv_loss(..., tables=...) every iteration."""
+
+    def __init__(self, pb: Problem, d, device=None):
+        L = load()
+        self.d, dp = _host_f32(d)
+        self.m = int(self.d.size)
+        dev = pb.device if device is None else device
+        self.buf = _ws(int(L.pact_mc_deconv_tables_size(pb.gp(), pb.pp(), self.m)), dev)
+        self.scratch_bytes = int(L.pact_mc_deconv_loss_tabled_workspace_size(pb.gp(), pb.pp(), self.m))
+        _check(L.pact_mc_deconv_tables(pb.gp(), pb.pp(), dp, self.m, _ptr(self.buf), self.buf.numel(), _stream()),
+               "mc_deconv_tables")
 
 
 def mc_deconv_loss_noalloc(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=False, want_loss_pp=False,

@@ -70,7 +70,8 @@ class PGRecovery:
         self.grad = torch.empty_like(self.sos)
         self.out = {"loss": torch.zeros(1, dtype=torch.float32, device=dev),
                     "dL_dw": torch.empty((pb.n, pb.n_t), dtype=torch.float32, device=dev)}
-        self.ws_mcd = pact._ws(pact.mc_deconv_loss_workspace_size(pb, self.m), dev)
+        self.tables = pact.McdTables(pb, self.d, dev)       # geometry/delay tables, built once
+        self.ws_mcd = pact._ws(self.tables.scratch_bytes, dev)
         self.ws_adj = pact._ws(pact.sos_to_delays_adj_workspace_size(pb), dev)
         self.graph = None
 
@@ -78,7 +79,8 @@ class PGRecovery:
     def step(self):
         pb = self.pb
         pact.sos_to_delays(pb, self.sos, self.w)
-        pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd)
+        pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
+                            tables=self.tables)
         pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
         if self.lam != 0.0:
             pact.tv(pb, self.sos, self.lam, value=self.out["loss"], grad=self.grad, accumulate=True)
@@ -126,6 +128,40 @@ class PGRecovery:
 
     def loss(self) -> float:
         return float(self.out["loss"].item())
+
+
+class NFRecovery(PGRecovery):
+    """Neural-field SOS (Sec. 3.3, lambda = 0): Adam on the field's parameters;
+    every iteration is nf_forward -> sos_to_delays -> fused deconvolution/loss/
+    adjoint -> sos_to_delays_adj -> nf_backward -> Adam, one CUDA graph."""
+
+    def __init__(self, pb: "pact.Problem", Y: torch.Tensor, d, eps: float, lr: float, params,
+                 mask=None, betas=(0.9, 0.999), adam_eps=1e-8, v_mid: float = 1525.0, v_half: float = 125.0):
+        dev = Y.device
+        self.nf = pact.NeuralField(pb, params, mask, v_mid, v_half)
+        super().__init__(pb, Y, d, eps, 0.0, lr, torch.zeros(pb.g, pb.g), None, betas, adam_eps)
+        self.params = self.nf.params
+        self.adam_m = torch.zeros_like(self.params)
+        self.adam_v = torch.zeros_like(self.params)
+        self.gparams = torch.zeros_like(self.params)
+
+    def step(self):
+        pb = self.pb
+        pact.nf_forward(self.nf, self.sos)
+        pact.sos_to_delays(pb, self.sos, self.w)
+        pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
+                            tables=self.tables)
+        pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
+        pact.nf_backward(self.nf, self.grad, self.gparams)
+        pact.adam_step(self.params, self.gparams, self.adam_m, self.adam_v, 1, self.lr, self.betas[0],
+                       self.betas[1], self.adam_eps, step_counter=self.counter)
+
+    def state(self):
+        return [t.clone() for t in (self.params, self.adam_m, self.adam_v, self.counter)]
+
+    def set_state(self, st):
+        for dst, src in zip((self.params, self.adam_m, self.adam_v, self.counter), st):
+            dst.copy_(src)
 
 
 def synthesize_stack(pb: "pact.Problem", case: dict, device) -> torch.Tensor:

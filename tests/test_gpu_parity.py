@@ -248,6 +248,29 @@ def test_mc_deconv_loss_adj_scale_and_accumulate():
     assert rel(cpu(g3), cpu(g1) + 1) <= 1e-6
 
 
+@pytest.mark.parametrize("eps", [1e-3, 1e-8])
+def test_mc_deconv_loss_tabled_matches_per_call_tables(eps):
+    """Prebuilt tables give the outputs of the per-call build (and the oracle);
+    tables built for other delays poison the outputs with NaN."""
+    cfg = inputs.config_small()
+    Y, w, d = _mcd_case(cfg, 0, realistic=True)
+    pb = pact.Problem(cfg, DEV)
+    wt, Yt = torch.as_tensor(w, device=DEV), to_dev_c(Y)
+    tab = pact.McdTables(pb, d)
+    ref = pact.mc_deconv_loss(pb, wt, Yt, d, eps, want_xhat=True, want_loss_pp=True)
+    for _ in range(2):
+        out = pact.mc_deconv_loss(pb, wt, Yt, d, eps, want_xhat=True, want_loss_pp=True, tables=tab)
+        assert float(out["loss"].item()) == float(ref["loss"].item())
+        assert torch.equal(out["Xhat"], ref["Xhat"]) and torch.equal(out["loss_pp"], ref["loss_pp"])
+        assert rel(cpu(out["dL_dw"]), cpu(ref["dL_dw"])) <= 1e-6
+    L, _, _, gw = O.mc_deconv_loss(O.geom(cfg), w.astype(np.float64), torch.as_tensor(Y), cfg.centres(), d, eps)
+    assert abs(float(out["loss"].item()) - float(L)) <= 1e-4 * float(L)
+    assert rel(cpu(out["dL_dw"]), gw.numpy()) <= 2e-3
+    other = pact.McdTables(pb, d * 1.01)
+    bad = pact.mc_deconv_loss(pb, wt, Yt, d, eps, tables=other)
+    assert np.isnan(float(bad["loss"].item())) and np.isnan(cpu(bad["dL_dw"])).any()
+
+
 def test_mc_deconv_loss_noise_free_truth_is_minimum():
     """Y = H(w) X exactly, eps = 0: the loss at w is ~0 relative to a perturbed w."""
     cfg = inputs.config_small()
