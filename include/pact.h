@@ -353,6 +353,80 @@ size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt
 pact_status pact_stitch(const pact_geometry* g, const pact_patches* pt, const float* Xhat,
                         float* image, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * pact_stitch for every channel of a patch-spectrum set at once: the delay
+ * stack of the forward model (Eq. 5) in the image domain,
+ *   stack[j] = stitch of the patches Y[:, j]   (Sec. S1.4, window once at crop).
+ *   Y      DEVICE c64 [N][m][P][P/2+1];  stack DEVICE float [m][H][W] output
+ *   ws     DEVICE workspace of pact_stitch_channels_workspace_size bytes
+ */
+size_t pact_stitch_channels_workspace_size(const pact_geometry* g, const pact_patches* pt, int m);
+pact_status pact_stitch_channels(const pact_geometry* g, const pact_patches* pt, int m, const float* Y,
+                                 float* stack, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Warm-start CNN.  The paper has no counterpart: it recovers the SOS by
+ * test-time optimisation alone (Sec. 3.3).  This learned initialiser maps a
+ * delay stack (Eq. 1 / Eq. 5, the "focal stack" of Sec. 3.2) to an SOS map
+ * from which that optimisation starts; it is trained on stacks that the
+ * forward model of this library generates from random SOS fields, and the
+ * plain optimisation refines its output.  BF16 tensor-core arithmetic with
+ * FP32 accumulation; activations are stored in BF16.
+ *
+ * Geometry: a square image of 4 G pixels per side, G (the SOS grid) a
+ * multiple of 8.  Network, with R = G and Cp = 16, 32 or 64 (the stack's m
+ * channels zero-padded):
+ *   x  = 4x4 block means of the stack / their root-mean-square   [R][R][Cp] BF16
+ *   five 3x3 convolutions with ReLU (zero padding): Cp->32 at R, 2x2 mean,
+ *   32->64 at R/2, 2x2 mean, then three 64->64 at R/4;
+ *   z  = w6 . h5 + b6;  v = v_mid + v_half tanh(z) on the R/4 grid;
+ *   sos = bilinear x4 upsampling of v (sample (q + 0.5)/4 - 0.5, clamped),
+ *         v_bg outside the mask                                   [G][G]
+ * Parameters (FP32, flat, in this order): W_l [c_out][c_in][3][3], b_l [c_out]
+ * for l = 1..5 (c_in of W1 is m), then w6 [64], b6 [1];
+ * pact_cnn_param_count(m) gives the total.
+ *
+ *   pact_cnn_pool_stack   stack DEVICE float [m][4G][4G] -> x DEVICE BF16
+ *                         [G][G][Cp] (16-byte aligned), workspace of
+ *                         pact_cnn_pool_workspace_size bytes.
+ *   pact_cnn_forward      x DEVICE BF16 [batch][G][G][Cp] -> sos DEVICE float
+ *                         [batch][G][G]; mask DEVICE uint8 [G][G] or NULL.
+ *                         Keeps the activations in the workspace
+ *                         (pact_cnn_workspace_size(g, m, batch) bytes, 256-byte
+ *                         aligned) for pact_cnn_backward.
+ *   pact_cnn_backward     dL_dsos DEVICE float [batch][G][G] -> dL_dparams
+ *                         (accumulate = 1 adds); must follow pact_cnn_forward
+ *                         with the same g, m, batch, params, x, mask and
+ *                         workspace.
+ *   pact_cnn_mse          training loss mean over samples and mask nodes of
+ *                         ((sos - sos_true) / scale)^2 into loss DEVICE [1] and
+ *                         its gradient into dL_dsos (NULL to skip); mask_count
+ *                         = nonzero mask entries (G^2 when mask is NULL);
+ *                         scratch DEVICE float [batch].
+ *   pact_cnn_status       reads the workspace status word (synchronises the
+ *                         stream): PACT_ERR_TIMEOUT if a tensor-core
+ *                         completion wait gave up (the outputs are then NaN).
+ * Errors: SHAPE for an unsupported geometry or m, INVALID_ARG for null or
+ * misaligned pointers and small workspaces.
+ */
+int pact_cnn_param_count(int m);
+int pact_cnn_input_channels(int m);
+size_t pact_cnn_pool_workspace_size(const pact_geometry* g, int m);
+pact_status pact_cnn_pool_stack(const pact_geometry* g, const float* stack, int m, void* x, void* ws,
+                                size_t ws_bytes, void* stream);
+size_t pact_cnn_workspace_size(const pact_geometry* g, int m, int batch);
+pact_status pact_cnn_forward(const pact_geometry* g, int m, int batch, const float* params, const void* x,
+                             const unsigned char* mask, float v_mid, float v_half, float* sos, void* ws,
+                             size_t ws_bytes, void* stream);
+pact_status pact_cnn_backward(const pact_geometry* g, int m, int batch, const float* params, const void* x,
+                              const unsigned char* mask, float v_half, const float* dL_dsos, float* dL_dparams,
+                              int accumulate, void* ws, size_t ws_bytes, void* stream);
+pact_status pact_cnn_mse(const pact_geometry* g, int batch, const float* sos, const float* sos_true,
+                         const unsigned char* mask, int mask_count, float scale, float* loss, float* dL_dsos,
+                         float* scratch, void* stream);
+pact_status pact_cnn_status(const pact_geometry* g, int m, int batch, const void* ws, size_t ws_bytes,
+                            int* host_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

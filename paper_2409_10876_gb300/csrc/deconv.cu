@@ -88,7 +88,9 @@ struct McdArgs {
     int KT;                // 256-bin tiles
     const unsigned long long* tag;   // fingerprint the tables were built for
     unsigned long long want;         // fingerprint of this call's arguments
-    int* tile_next;                  // [KT] per-tile claim counters, zero at launch
+    int* tile_next;                  // [KT + 1] per-tile claim counters, then a CTA-done ticket; zero at launch
+    float* loss;                     // [1] or NULL (streaming kernel: summed by the last CTA)
+    float* loss_pp;                  // [N] or NULL
 };
 
 // Ring coordinate t = alpha N_t / (2 pi) in [0, N_t) of the point where the ray
@@ -577,6 +579,32 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
         }
         u = all_ok ? u_next : -1;
     }
+
+    // The last CTA to finish sums the per-unit partials (fixed order) into the
+    // per-patch and total loss.
+    if (!a.loss && !a.loss_pp) return;
+    __shared__ int last_s;
+    __shared__ float red_s[kTile / 32];
+    __threadfence();
+    if (tid == 0) last_s = atomicAdd(a.tile_next + a.KT, 1) == (int)gridDim.x - 1;
+    bar_and(1, kTile, true);
+    if (!last_s) return;
+    __threadfence();
+    float tot = 0.f;
+    for (int i = tid; i < N; i += kTile) {
+        float acc = 0.f;
+        for (int t = 0; t < a.KT; ++t) acc += __ldcg(a.part_loss + (size_t)i * a.KT + t);
+        if (a.loss_pp) a.loss_pp[i] = acc;
+        tot += acc;
+    }
+    tot = warp_sum(tot);
+    if (lane == 0) red_s[tid >> 5] = tot;
+    bar_and(1, kTile, true);
+    if (tid == 0 && a.loss) {
+        float acc = 0.f;
+        for (int q = 0; q < kTile / 32; ++q) acc += red_s[q];
+        a.loss[0] = acc;
+    }
 }
 
 // Per-patch and total loss from the per-CTA partial sums (fixed order).
@@ -614,7 +642,7 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     p.KT = (F + kBins - 1) / kBins;
     p.KTs = (F + kTile - 1) / kTile;
     p.off_next = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
-    p.scratch = p.off_next + align_up((size_t)p.KTs * sizeof(int), 256);
+    p.scratch = p.off_next + align_up((size_t)(p.KTs + 1) * sizeof(int), 256);
     size_t o = 256;                                // fingerprint header
     p.t_lut = o;
     o += align_up((size_t)pt->n * F * sizeof(float2), 256);
@@ -748,7 +776,9 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.want = fingerprint(g, pt, d, m);
     a.tile_next = reinterpret_cast<int*>(base + pl.off_next);
     if (!tables) PACT_TRY(build_tables(g, pt, d, m, a.fp64, pl, tb, st));
-    if (!a.fp64 && cudaMemsetAsync(a.tile_next, 0, (size_t)pl.KTs * sizeof(int), st) != cudaSuccess)
+    a.loss = loss;
+    a.loss_pp = loss_pp;
+    if (!a.fp64 && cudaMemsetAsync(a.tile_next, 0, (size_t)(pl.KTs + 1) * sizeof(int), st) != cudaSuccess)
         return check_launch("mc_deconv_loss: clearing the tile counters");
     if (dL_dw && !accumulate &&
         cudaMemsetAsync(dL_dw, 0, (size_t)pt->n * g->n_t * sizeof(float), st) != cudaSuccess)
@@ -763,7 +793,7 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     else if (m < 32) s = launch_mcd<32, false>(a, st);
     else s = launch_mcd<64, false>(a, st);
     if (s != PACT_OK) return s;
-    if (loss || loss_pp) {
+    if (a.fp64 && (loss || loss_pp)) {
         mcd_finalize_kernel<<<(a.N + kTPB - 1) / kTPB, kTPB, 0, st>>>(a.N, a.KT, a.part_loss, loss, loss_pp);
         return check_launch("mc_deconv_loss finalize");
     }

@@ -66,8 +66,9 @@ __global__ void __launch_bounds__(256) patch_fft_kernel(Geo g, int P, int M, con
     }
 }
 
-// Inverse half-spectrum DFT of patch i, then scatter-add into the numerator
-// and window-sum images.
+// Inverse half-spectrum DFT of patch i = blockIdx.x, channel j = blockIdx.y
+// (X [N][m][P][P/2+1]), then scatter-add into the channel's numerator image
+// and, for channel 0, into the window-sum image.
 __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* centres, float inv_2s2,
                                                      const float2* X, float* num, float* den) {
     extern __shared__ float sm[];
@@ -79,7 +80,9 @@ __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* c
     const int r0 = c.x - P / 2, c0 = c.y - P / 2;
     for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = cis_pi(2.f * t / P);
     __syncthreads();
-    const float2* Xi = X + (size_t)i * P * half;
+    const int j = blockIdx.y, m = gridDim.y;
+    const float2* Xi = X + ((size_t)i * m + j) * P * half;
+    num += (size_t)j * g.H * g.W;
     for (int q = threadIdx.x; q < P * half; q += blockDim.x) {
         const int a = q / half, v = q - (q / half) * half;
         float re = 0.f, im = 0.f;
@@ -113,15 +116,17 @@ __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* c
         s = fmaf(2.f, acc, s);
         const float oa = (a - P / 2) * g.dx, ob = (b - P / 2) * g.dx;
         atomicAdd(num + (size_t)row * g.W + col, s * inv_p);
-        atomicAdd(den + (size_t)row * g.W + col, expf(-(oa * oa + ob * ob) * inv_2s2));
+        if (j == 0) atomicAdd(den + (size_t)row * g.W + col, expf(-(oa * oa + ob * ob) * inv_2s2));
     }
 }
 
+// out[j][q] = num[j][q] / den[q] (0 where no window reaches), j = blockIdx.y.
 __global__ void stitch_divide_kernel(int n, const float* num, const float* den, float* out) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
+    const size_t o = (size_t)blockIdx.y * n + q;
     const float d = den[q];
-    out[q] = d > 0.f ? num[q] / d : 0.f;
+    out[o] = d > 0.f ? num[o] / d : 0.f;
 }
 
 float inv_two_sigma2(float fwhm) {
@@ -153,31 +158,54 @@ extern "C" pact_status pact_patch_fft(const pact_geometry* g, const pact_patches
     return check_launch("patch_fft kernel");
 }
 
+namespace pact {
+namespace {
+
+pact_status run_stitch(const pact_geometry* g, const pact_patches* pt, int m, const float* Xhat, float* image,
+                       void* ws, size_t ws_bytes, void* stream) {
+    PACT_TRY(check_geometry(g));
+    PACT_TRY(check_patches(pt));
+    if (!Xhat || !image || !ws) return fail(PACT_ERR_INVALID_ARG, "stitch: Xhat, image and ws must not be NULL");
+    if (m < 1 || m > 65535) return fail(PACT_ERR_INVALID_ARG, "stitch: channel count %d out of range", m);
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const size_t plane = (size_t)g->img_h * g->img_w * sizeof(float);
+    const size_t need = align_up((size_t)(m + 1) * plane, 256);
+    if (ws_bytes < need) return fail(PACT_ERR_INVALID_ARG, "stitch: workspace too small: %zu < %zu", ws_bytes, need);
+    cudaStream_t st = as_stream(stream);
+    float* num = static_cast<float*>(ws);
+    float* den = num + (size_t)m * g->img_h * g->img_w;
+    if (cudaMemsetAsync(ws, 0, (size_t)(m + 1) * plane, st) != cudaSuccess) return check_launch("stitch: memset");
+    const int P = pt->p, half = P / 2 + 1;
+    const size_t shm = (size_t)(P * half + P) * sizeof(float2);
+    PACT_TRY(ensure_smem((const void*)stitch_kernel, shm, "stitch: shared memory attribute"));
+    stitch_kernel<<<dim3(pt->n, m), 256, shm, st>>>(make_geo(g), P, reinterpret_cast<const int2*>(pt->centres),
+                                                    inv_two_sigma2(pt->window_fwhm),
+                                                    reinterpret_cast<const float2*>(Xhat), num, den);
+    PACT_TRY(check_launch("stitch kernel"));
+    const int n = g->img_h * g->img_w;
+    stitch_divide_kernel<<<dim3((n + 255) / 256, m), 256, 0, st>>>(n, num, den, image);
+    return check_launch("stitch divide");
+}
+
+}  // namespace
+}  // namespace pact
+
 extern "C" size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt) {
     if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK) return 0;
-    return 2 * align_up((size_t)g->img_h * g->img_w * sizeof(float), 256);
+    return align_up(2 * (size_t)g->img_h * g->img_w * sizeof(float), 256);
 }
 
 extern "C" pact_status pact_stitch(const pact_geometry* g, const pact_patches* pt, const float* Xhat,
                                    float* image, void* ws, size_t ws_bytes, void* stream) {
-    PACT_TRY(check_geometry(g));
-    PACT_TRY(check_patches(pt));
-    if (!Xhat || !image || !ws) return fail(PACT_ERR_INVALID_ARG, "stitch: Xhat, image and ws must not be NULL");
-    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    const size_t plane = align_up((size_t)g->img_h * g->img_w * sizeof(float), 256);
-    if (ws_bytes < 2 * plane) return fail(PACT_ERR_INVALID_ARG, "stitch: workspace too small");
-    cudaStream_t st = as_stream(stream);
-    float* num = static_cast<float*>(ws);
-    float* den = reinterpret_cast<float*>(static_cast<char*>(ws) + plane);
-    if (cudaMemsetAsync(ws, 0, 2 * plane, st) != cudaSuccess) return check_launch("stitch: memset");
-    const int P = pt->p, half = P / 2 + 1;
-    const size_t shm = (size_t)(P * half + P) * sizeof(float2);
-    PACT_TRY(ensure_smem((const void*)stitch_kernel, shm, "stitch: shared memory attribute"));
-    stitch_kernel<<<pt->n, 256, shm, st>>>(make_geo(g), P, reinterpret_cast<const int2*>(pt->centres),
-                                           inv_two_sigma2(pt->window_fwhm), reinterpret_cast<const float2*>(Xhat),
-                                           num, den);
-    PACT_TRY(check_launch("stitch kernel"));
-    const int n = g->img_h * g->img_w;
-    stitch_divide_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, num, den, image);
-    return check_launch("stitch divide");
+    return run_stitch(g, pt, 1, Xhat, image, ws, ws_bytes, stream);
+}
+
+extern "C" size_t pact_stitch_channels_workspace_size(const pact_geometry* g, const pact_patches* pt, int m) {
+    if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK || m < 1) return 0;
+    return align_up((size_t)(m + 1) * g->img_h * g->img_w * sizeof(float), 256);
+}
+
+extern "C" pact_status pact_stitch_channels(const pact_geometry* g, const pact_patches* pt, int m, const float* Y,
+                                            float* stack, void* ws, size_t ws_bytes, void* stream) {
+    return run_stitch(g, pt, m, Y, stack, ws, ws_bytes, stream);
 }

@@ -64,11 +64,22 @@ _SIGS = {
     "pact_adam_step": ([_I, _VP, _VP, _VP, _VP, _I, _VP, _F, _F, _F, _F, _VP, _VP], _I),
     "pact_stitch_workspace_size": ([_GP, _PP], _SZ),
     "pact_stitch": ([_GP, _PP, _VP, _VP, _VP, _SZ, _VP], _I),
+    "pact_stitch_channels_workspace_size": ([_GP, _PP, _I], _SZ),
+    "pact_stitch_channels": ([_GP, _PP, _I, _VP, _VP, _VP, _SZ, _VP], _I),
     "pact_nf_param_count": ([], _I),
     "pact_nf_workspace_size": ([_GP], _SZ),
     "pact_nf_forward": ([_GP, _VP, _VP, _F, _F, _VP, _VP, _SZ, _VP], _I),
     "pact_nf_backward": ([_GP, _VP, _VP, _F, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_nf_status": ([_GP, _VP, _SZ, ctypes.POINTER(ctypes.c_int), _VP], _I),
+    "pact_cnn_param_count": ([_I], _I),
+    "pact_cnn_input_channels": ([_I], _I),
+    "pact_cnn_pool_workspace_size": ([_GP, _I], _SZ),
+    "pact_cnn_pool_stack": ([_GP, _VP, _I, _VP, _VP, _SZ, _VP], _I),
+    "pact_cnn_workspace_size": ([_GP, _I, _I], _SZ),
+    "pact_cnn_forward": ([_GP, _I, _I, _VP, _VP, _VP, _F, _F, _VP, _VP, _SZ, _VP], _I),
+    "pact_cnn_backward": ([_GP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
+    "pact_cnn_mse": ([_GP, _I, _VP, _VP, _VP, _I, _F, _VP, _VP, _VP, _VP], _I),
+    "pact_cnn_status": ([_GP, _I, _I, _VP, _SZ, ctypes.POINTER(ctypes.c_int), _VP], _I),
 }
 
 
@@ -420,6 +431,23 @@ def stitch(pb: Problem, Xhat, image=None, ws=None):
     return image
 
 
+def stitch_channels(pb: Problem, Y, stack=None, ws=None):
+    """Sec. S1.4 for every channel: delay stack [M, H, W] from patch spectra
+    [N, M, P, P/2+1]."""
+    L = load()
+    Y = _dev(Y, "Y", torch.complex64)
+    m = int(Y.shape[1])
+    _dev(Y, "Y", torch.complex64, pb.spectra_shape(m))
+    if stack is None:
+        stack = _empty((m, pb.cfg.img_h, pb.cfg.img_w), torch.float32, Y.device)
+    _dev(stack, "stack", torch.float32, (m, pb.cfg.img_h, pb.cfg.img_w))
+    if ws is None:
+        ws = _ws(L.pact_stitch_channels_workspace_size(pb.gp(), pb.pp(), m), Y.device)
+    _check(L.pact_stitch_channels(pb.gp(), pb.pp(), m, _ptr(Y), _ptr(stack), _ptr(ws), ws.numel(), _stream()),
+           "stitch_channels")
+    return stack
+
+
 # ------------------------------------------------------------------ neural-field SOS (BF16 tensor cores)
 
 def nf_param_count() -> int:
@@ -474,3 +502,105 @@ def nf_status(nf: NeuralField) -> None:
     L = load()
     st = ctypes.c_int(0)
     _check(L.pact_nf_status(nf.pb.gp(), _ptr(nf.ws), nf.ws.numel(), ctypes.byref(st), _stream()), "nf_status")
+
+
+# ------------------------------------------------------------------ warm-start CNN
+
+def cnn_param_count(m: int) -> int:
+    return int(load().pact_cnn_param_count(int(m)))
+
+
+def cnn_input_channels(m: int) -> int:
+    return int(load().pact_cnn_input_channels(int(m)))
+
+
+def cnn_pool_stack(pb: Problem, stack, x=None, ws=None):
+    """Pooled, RMS-normalised BF16 network input [G, G, Cp] of one delay stack
+    [M, 4G, 4G]; `x` may be a slice of a larger BF16 dataset tensor."""
+    L = load()
+    stack = _dev(stack, "stack", torch.float32)
+    m = int(stack.shape[0])
+    _dev(stack, "stack", torch.float32, (m, pb.cfg.img_h, pb.cfg.img_w))
+    cp = cnn_input_channels(m)
+    if x is None:
+        x = _empty((pb.g, pb.g, cp), torch.bfloat16, pb.device)
+    _dev(x, "x", torch.bfloat16, (pb.g, pb.g, cp))
+    if ws is None:
+        ws = _ws(L.pact_cnn_pool_workspace_size(pb.gp(), m), pb.device)
+    _check(L.pact_cnn_pool_stack(pb.gp(), _ptr(stack), m, _ptr(x), _ptr(ws), ws.numel(), _stream()), "cnn_pool_stack")
+    return x
+
+
+class WarmStartCNN:
+    """Device state of the warm-start network for a fixed batch size: FP32
+    parameters and the workspace that carries activations from forward to
+    backward."""
+
+    def __init__(self, pb: Problem, m: int, batch: int, params, mask=None, v_mid: float = 1525.0,
+                 v_half: float = 125.0):
+        L = load()
+        self.pb, self.m, self.batch = pb, int(m), int(batch)
+        self.params = torch.as_tensor(np.asarray(params, np.float32), device=pb.device).contiguous()
+        if self.params.numel() != cnn_param_count(m):
+            raise PactError(f"the network has {cnn_param_count(m)} parameters, got {self.params.numel()}")
+        self.mask = None if mask is None else torch.as_tensor(np.asarray(mask, np.uint8), device=pb.device).contiguous()
+        self.mask_count = pb.g * pb.g if mask is None else int(np.count_nonzero(np.asarray(mask)))
+        self.v_mid, self.v_half = float(v_mid), float(v_half)
+        self.cp = cnn_input_channels(m)
+        self.ws = _ws(L.pact_cnn_workspace_size(pb.gp(), self.m, self.batch), pb.device)
+        self.scratch = torch.empty(max(self.batch, 64), dtype=torch.float32, device=pb.device)
+
+    def _x(self, x):
+        return _dev(x, "x", torch.bfloat16, (self.batch, self.pb.g, self.pb.g, self.cp))
+
+
+def cnn_forward(net: WarmStartCNN, x, sos=None):
+    """SOS maps [batch, G, G] predicted from pooled inputs x [batch, G, G, Cp]."""
+    L = load()
+    pb = net.pb
+    x = net._x(x)
+    if sos is None:
+        sos = _empty((net.batch, pb.g, pb.g), torch.float32, pb.device)
+    _dev(sos, "sos", torch.float32, (net.batch, pb.g, pb.g))
+    _check(L.pact_cnn_forward(pb.gp(), net.m, net.batch, _ptr(net.params), _ptr(x), _ptr(net.mask), net.v_mid,
+                              net.v_half, _ptr(sos), _ptr(net.ws), net.ws.numel(), _stream()), "cnn_forward")
+    return sos
+
+
+def cnn_backward(net: WarmStartCNN, x, dL_dsos, dL_dparams=None, accumulate=False):
+    """dL/dparams for the inputs of the last cnn_forward."""
+    L = load()
+    pb = net.pb
+    x = net._x(x)
+    dL_dsos = _dev(dL_dsos, "dL_dsos", torch.float32, (net.batch, pb.g, pb.g))
+    if dL_dparams is None:
+        dL_dparams = torch.zeros_like(net.params)
+    _dev(dL_dparams, "dL_dparams", torch.float32, tuple(net.params.shape))
+    _check(L.pact_cnn_backward(pb.gp(), net.m, net.batch, _ptr(net.params), _ptr(x), _ptr(net.mask), net.v_half,
+                               _ptr(dL_dsos), _ptr(dL_dparams), int(accumulate), _ptr(net.ws), net.ws.numel(),
+                               _stream()), "cnn_backward")
+    return dL_dparams
+
+
+def cnn_mse(net: WarmStartCNN, sos, sos_true, scale: float = 100.0, loss=None, dL_dsos=None, want_grad=True):
+    """Training loss mean ((sos - sos_true) / scale)^2 over samples and mask
+    nodes (device [1]) and, when asked, its gradient [batch, G, G]."""
+    L = load()
+    pb = net.pb
+    sos = _dev(sos, "sos", torch.float32, (net.batch, pb.g, pb.g))
+    sos_true = _dev(sos_true, "sos_true", torch.float32, (net.batch, pb.g, pb.g))
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=pb.device)
+    if want_grad and dL_dsos is None:
+        dL_dsos = _empty((net.batch, pb.g, pb.g), torch.float32, pb.device)
+    _check(L.pact_cnn_mse(pb.gp(), net.batch, _ptr(sos), _ptr(sos_true), _ptr(net.mask), net.mask_count, float(scale),
+                          _ptr(loss), _ptr(dL_dsos if want_grad else None), _ptr(net.scratch), _stream()), "cnn_mse")
+    return loss, dL_dsos
+
+
+def cnn_status(net: WarmStartCNN) -> None:
+    """Raises if a tensor-core wait of the network kernels gave up (synchronises)."""
+    L = load()
+    st = ctypes.c_int(0)
+    _check(L.pact_cnn_status(net.pb.gp(), net.m, net.batch, _ptr(net.ws), net.ws.numel(), ctypes.byref(st), _stream()),
+           "cnn_status")
