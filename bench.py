@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true")
+    ap.add_argument("--ws-samples", type=int, default=8192, help="training stacks for the warm-start CNN")
+    ap.add_argument("--ws-epochs", type=int, default=8)
     return ap.parse_args()
 
 
@@ -277,7 +280,7 @@ def run_gpu(args, cfg, case, rank, world, local):
                        "seed": args.seed, "eps": cfg.eps, "tv_lambda": cfg.tv_lambda},
             "breakdown_ms": {"sos_to_delays": statistics.mean(rays_ms), "mc_deconv_loss": statistics.mean(mcd_ms),
                              "adj_tv_adam": statistics.mean(rest_ms)},
-            "roofline": {"bound": "hbm", "kernel": "mc_deconv_loss (fused Eq. 4-7 + adjoint, 2 launches)",
+            "roofline": {"bound": "hbm", "kernel": "mc_deconv_loss (fused Eq. 4-7 + adjoint: 1 kernel, 2 memsets)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "measured" if peaks else "fallback",
                          "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},
@@ -310,6 +313,8 @@ def run_gpu(args, cfg, case, rank, world, local):
     if not args.no_variants:
         line["variants"] = {"neural_field": nf_variant(args, cfg, case, pb, Y, flush, stream),
                             "das_stack": das_variant(dev, flush, stream)}
+    if rank == 0 and not args.no_warm_start:
+        line["warm_start"] = warm_start_run(args, cfg, pb, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -369,6 +374,89 @@ def das_variant(dev, flush, stream):
     t = statistics.median(ms) / 1e3
     return {"ms": statistics.median(ms), "taps": taps, "gtaps_per_s": taps / t / 1e9,
             "workload": "1024 el x 4096 samples -> 32 x 1024 x 1024"}
+
+
+def warm_start_run(args, cfg, pb, dev):
+    """Learned warm start on the full-size problem: the CNN is trained on the GPU
+    (library kernels) on stacks the forward model generates from random SOS
+    fields; on a held-out problem the plain recovery is timed from the CNN's SOS
+    and from uniform 1500 m/s until the loss is within 1 % of L*_cold, the best
+    loss of a 1000-iteration cold run.  The FP64 oracle re-evaluates the data
+    loss at both end points."""
+    import torch
+    from paper_2409_10876_gb300 import inputs, pact, warmstart
+    from paper_2409_10876_gb300.recovery import measurement_spectra, synthesize_stack
+    mask = inputs.sos_mask(cfg)
+    t0 = time.perf_counter()
+    gen = warmstart.StackGenerator(pb, cfg, n_ip=4, n_noise=2, seed=args.seed + 7)
+    S = args.ws_samples
+    X = torch.empty((S, cfg.sos_g, cfg.sos_g, pact.cnn_input_channels(cfg.m)), dtype=torch.bfloat16, device=dev)
+    V = torch.empty((S, cfg.sos_g, cfg.sos_g), dtype=torch.float32, device=dev)
+    gen.fill(X, V)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    B = 32
+    net = pact.WarmStartCNN(pb, cfg.m, B, inputs.cnn_init(args.seed, cfg.m), mask)
+    t0 = time.perf_counter()
+    hist = warmstart.train(net, X, V, args.ws_epochs, lr=1e-3, seed=args.seed)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    steps = args.ws_epochs * (S // B)
+    # algorithmic FLOPs of one training sample: forward of every conv, dgrad of layers 2-5, wgrad of all
+    R, fl, res = cfg.sos_g, 0.0, cfg.sos_g
+    cin = pact.cnn_input_channels(cfg.m)
+    for l, (_, cout, pool) in enumerate(inputs.CNN_CONVS):
+        f = 2.0 * res * res * cin * cout * 9
+        fl += f * (3 if l > 0 else 2)
+        cin = cout
+        res = res // 2 if pool else res
+    train_tflops = fl * B * steps / t_train / 1e12
+    del X, V
+    net1 = pact.WarmStartCNN(pb, cfg.m, 1, net.params.cpu().numpy(), mask)
+    mask_d = torch.as_tensor(mask.astype(np.uint8), device=dev)
+    held = cfg.replace(sos_kind="ellipses", sos_lo=1400.0, sos_hi=1650.0)
+    case = inputs.make_case(held, args.seed + 1000)
+    Y = measurement_spectra(pb, case, dev)
+    stack = synthesize_stack(pb, case, dev)
+    v_true = torch.as_tensor(case["sos_true"], device=dev)
+    v_cold = torch.full_like(v_true, cfg.v_bg)
+    _, _, h_cold, rec_cold = warmstart.time_to_target(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, v_cold,
+                                                      mask_d, -1.0, 1000)
+    L_star = min(h_cold)
+    target = 1.01 * L_star
+    it_c, s_c, _, _ = warmstart.time_to_target(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, v_cold, mask_d,
+                                               target, 1000)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    warmstart.predict(net1, pb, stack)
+    torch.cuda.synchronize()
+    e0.record()
+    v_warm = warmstart.predict(net1, pb, stack)
+    e1.record()
+    torch.cuda.synchronize()
+    s_pred = e0.elapsed_time(e1) * 1e-3
+    it_w, s_w, h_w, rec_w = warmstart.time_to_target(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr,
+                                                     v_warm.clone(), mask_d, target, 1000)
+    m = mask_d > 0
+    out = {"train_samples": S, "epochs": args.ws_epochs, "batch": B, "generate_s": t_gen, "train_s": t_train,
+           "train_step_ms": 1e3 * t_train / steps, "train_tflops_bf16": train_tflops,
+           "train_loss": {"first_epoch": hist[0], "last_epoch": hist[-1]},
+           "sos_mae_mps": {"cnn": float((v_warm - v_true)[m].abs().mean()),
+                           "uniform_1500": float((v_cold - v_true)[m].abs().mean())},
+           "L_star_cold_1000": L_star, "target": target,
+           "cold": {"iters": it_c, "s": s_c}, "warm": {"iters": it_w, "s": s_w + s_pred, "cnn_s": s_pred},
+           "speedup": (s_c / (s_w + s_pred)) if (it_c and it_w) else None,
+           "held_out_seed": args.seed + 1000}
+    if not args.no_cpu_baseline:
+        from oracle import pact_oracle as O
+        g = O.geom(held)
+        Y64, _, _ = O.make_measurement(g, case)           # the oracle's own measurement of the seeded case
+        for name, rec in (("cold_end", rec_cold), ("warm_end", rec_w)):
+            w64 = O.wavefront_errors(g, rec.sos.cpu().numpy().astype(np.float64), case["centres"])
+            L64 = O.mc_deconv_loss(g, w64, Y64, case["centres"], case["d"], cfg.eps, want_grad=False)[0]
+            out[f"oracle_data_loss_{name}"] = float(L64)
+            out[f"gpu_data_loss_{name}"] = float(pact.mc_deconv_loss(pb, pact.sos_to_delays(pb, rec.sos), Y,
+                                                                     case["d"], cfg.eps, want_grad=False)["loss"])
+    return out
 
 
 def kernel_revision() -> str:

@@ -1,0 +1,48 @@
+"""What the trained warm-start network gains over the plain method alone.
+
+A CNN is trained on the GPU (library kernels only) on stacks that the forward
+model generates from random SOS fields; on held-out problems the plain
+pixel-grid recovery started from its prediction reaches 1.01 times the cold
+run's best loss in far fewer iterations than the cold start from uniform
+1500 m/s."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2409_10876_gb300 import inputs, pact, warmstart
+from paper_2409_10876_gb300.recovery import measurement_spectra, synthesize_stack
+
+pytestmark = pytest.mark.gpu
+
+
+def test_warm_start_reaches_the_cold_optimum_sooner():
+    cfg = inputs.config_small()
+    pb = pact.Problem(cfg, "cuda")
+    mask = inputs.sos_mask(cfg)
+    gen = warmstart.StackGenerator(pb, cfg, n_ip=2, n_noise=2, seed=1)
+    S = 2048
+    X = torch.empty((S, cfg.sos_g, cfg.sos_g, pact.cnn_input_channels(cfg.m)), dtype=torch.bfloat16, device="cuda")
+    V = torch.empty((S, cfg.sos_g, cfg.sos_g), dtype=torch.float32, device="cuda")
+    gen.fill(X, V)
+    net = pact.WarmStartCNN(pb, cfg.m, 32, inputs.cnn_init(0, cfg.m), mask)
+    hist = warmstart.train(net, X, V, epochs=12, lr=1e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    net1 = pact.WarmStartCNN(pb, cfg.m, 1, net.params.cpu().numpy(), mask)
+    mask_d = torch.as_tensor(mask.astype(np.uint8), device="cuda")
+    held_out = cfg.replace(sos_kind="ellipses", sos_lo=1400.0, sos_hi=1650.0)
+    gains = []
+    for seed in (100, 101, 102):
+        case = inputs.make_case(held_out, seed)
+        Y = measurement_spectra(pb, case, "cuda")
+        v_warm = warmstart.predict(net1, pb, synthesize_stack(pb, case, "cuda"))
+        v_cold = torch.full((cfg.sos_g, cfg.sos_g), cfg.v_bg, dtype=torch.float32, device="cuda")
+        _, _, h_cold, _ = warmstart.time_to_target(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, v_cold, mask_d,
+                                                   -1.0, 1000)
+        target = 1.01 * min(h_cold)
+        it_cold, _, _, _ = warmstart.time_to_target(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, v_cold, mask_d,
+                                                    target, 1000)
+        it_warm, _, _, _ = warmstart.time_to_target(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, v_warm, mask_d,
+                                                    target, 1000)
+        assert it_cold is not None and it_warm is not None
+        gains.append(it_cold / it_warm)
+    assert min(gains) >= 2.0 and np.median(gains) >= 4.0, gains
