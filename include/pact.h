@@ -196,7 +196,8 @@ size_t pact_mc_deconv_loss_workspace_size(const pact_geometry* g, const pact_pat
  *   Xhat     DEVICE c64 [N][P][P/2+1] or NULL
  *   dL_dw    DEVICE float [N][N_t] or NULL  output gradient
  *   ws       DEVICE workspace (256-byte aligned) of the size above
- * For eps >= 1e-6 the residual energy of a bin is evaluated as
+ * For eps >= 1e-6 (with N_t a multiple of 4 and w 16-byte aligned, else as
+ * for small eps but in FP32) the residual energy of a bin is evaluated as
  * sum_j |Y_ij|^2 - |A|^2 (B + 2 eps) / (B + eps)^2 (A, B the numerator and
  * denominator sums of Eq. 6), so each Y element is read once; its FP32
  * rounding is about 1e-7 of sum_j |Y_ij|^2 per bin, of either sign.  When

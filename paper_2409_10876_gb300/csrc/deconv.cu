@@ -80,6 +80,7 @@ struct McdArgs {
     float* dL_dw;          // [N][n_t] output (cleared by the host call unless accumulating) or NULL
     const float* scale;    // device scalar multiplying dL/dw, or NULL
     int fp64;
+    int stream;            // 1: streaming kernel (eps >= 1e-6 and its layout needs met), 0: two-pass kernel
     float* part_loss;      // [N][KT]
     const float2* lut;     // [N][F] ring coordinates (t_a, t_b)
     const float2* etab;    // [M][F] exp(j|k|d_j)
@@ -345,8 +346,9 @@ __global__ void __launch_bounds__(kBins, 2) mcd_kernel(const McdArgs a) {
 }
 
 constexpr int kCh = 8;          // channel rows per pipeline stage (16 KB)
-constexpr int kStages = 6;      // stages in flight per CTA
+constexpr int kStages = 4;      // stages in flight per CTA (about one unit of look-ahead: a short tail)
 constexpr int kRing = 8;        // unit ids published ahead of their consumers
+constexpr int kSlots = 4;       // per-unit lookup rows (ring coordinates, w) staged ahead
 constexpr int kTile = 224;                   // bins per unit of the streaming kernel, one consumer thread each
 constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two CTAs per SM)
 
@@ -362,7 +364,9 @@ constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer wa
 // takes fewer units), publishes each unit id in a small ring, and streams the
 // unit's Y rows through kStages stages of kCh rows by 1-D bulk copies (TMA) on
 // a "full" mbarrier per stage; the consumer warps release a stage on its
-// "empty" mbarrier.  The dL/dw contributions of a unit are summed in one of two
+// "empty" mbarrier.  With the first chunk of a unit the producer also copies
+// the unit's ring-coordinate row and its patch's w row into one of kSlots
+// shared slots, so the consumers' lookups of Eq. 4 hit shared memory.  The dL/dw contributions of a unit are summed in one of two
 // shared buffers (alternating per unit) and added to the output after the
 // unit's closing consumer barrier.
 template <int CPT, bool EXACT>
@@ -371,7 +375,9 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
     const int n_t = a.g.n_t, M = EXACT ? CPT : a.M, N = a.N;
     float2* stage = reinterpret_cast<float2*>(smem_raw);                          // [kStages][kCh][kTile]
     float* dw_s = reinterpret_cast<float*>(stage + (size_t)kStages * kCh * kTile);  // [2][n_t]
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    float2* slot_lut = reinterpret_cast<float2*>(dw_s + 2 * n_t);                    // [kSlots][kTile]
+    float* slot_w = reinterpret_cast<float*>(slot_lut + (size_t)kSlots * kTile);     // [kSlots][n_t]
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], slot_free[kSlots];
     __shared__ float lsum_s[2][kTile / 32];
     __shared__ int ring[kRing];
     __shared__ int tag_ok;
@@ -383,6 +389,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kTile / 32);
         }
+        for (int s = 0; s < kSlots; ++s) mbar_init(&slot_free[s], kTile / 32);
         mbar_init_fence();
         tag_ok = *a.tag == a.want;
     }
@@ -423,16 +430,25 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
                     return;
                 }
             }
-            fence_proxy_async_smem();
             const int ukt = unit / N, i = unit - ukt * N;
             const int k0 = ukt * kTile;
             const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
             const int j0 = c * kCh, rows = min(kCh, M - j0);
-            mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)rows);
+            const int slot = lu % kSlots;
+            if (c == 0 && lu >= kSlots &&             // consumers read the slot's previous unit
+                !mbar_wait_bounded(&slot_free[slot], (uint32_t)((lu / kSlots - 1) & 1), kCopyWaitNs))
+                return;
+            const uint32_t wbytes = (uint32_t)n_t * 4u;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)rows + (c == 0 ? bytes + wbytes : 0u));
             const float2* src = a.Y + ((size_t)i * M + j0) * a.F + k0;
             float2* dst = stage + (size_t)s * kCh * kTile;
             for (int r = 0; r < rows; ++r)
                 tma_bulk_g2s(dst + (size_t)r * kTile, src + (size_t)r * a.F, bytes, &full[s]);
+            if (c == 0) {
+                tma_bulk_g2s(slot_lut + (size_t)slot * kTile, a.lut + (size_t)i * a.F + k0, bytes, &full[s]);
+                tma_bulk_g2s(slot_w + (size_t)slot * n_t, a.w + (size_t)i * n_t, wbytes, &full[s]);
+            }
         }
     }
 
@@ -460,9 +476,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
                 E[m] = (valid && (EXACT || m < M)) ? __ldg(a.etab + (size_t)m * a.F + k) : make_float2(0.f, 0.f);
             bt = valid ? __ldg(a.btab + k) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        // the two lookups of w of Eq. 4
-        const float2 tr = valid ? __ldg(a.lut + (size_t)i * a.F + k) : make_float2(0.f, 0.f);
-        const float* wr = a.w + (size_t)i * n_t;
+        // the two lookups of w of Eq. 4, from the unit's shared slot (landed with its first chunk)
+        const int slot = lu % kSlots;
+        const float2 tr = valid ? slot_lut[slot * kTile + tid] : make_float2(0.f, 0.f);
+        const float* wr = slot_w + (size_t)slot * n_t;
         const float fla = floorf(tr.x), flb = floorf(tr.y);
         const float fa = tr.x - fla, fb = tr.y - flb;
         int n1a = (int)fla, n1b = (int)flb;
@@ -470,11 +487,14 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
         n1b = n1b >= n_t ? n1b - n_t : n1b;
         const int n2a = n1a + 1 == n_t ? 0 : n1a + 1;
         const int n2b = n1b + 1 == n_t ? 0 : n1b + 1;
-        const float wa1 = __ldg(wr + n1a), wa2 = __ldg(wr + n2a), wb1 = __ldg(wr + n1b), wb2 = __ldg(wr + n2b);
+        const float wa1 = wr[n1a], wa2 = wr[n2a], wb1 = wr[n1b], wb2 = wr[n2b];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&slot_free[slot]);   // this warp is done with the slot
 
-        // S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j, Ey = sum |Y_j|^2
-        float2 S1 = make_float2(0.f, 0.f), S2 = S1;
-        float Ey = 0.f;
+        // S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j, Ey = sum |Y_j|^2, each as
+        // two partial sums over even and odd channels (shorter dependency chains)
+        float2 S1 = make_float2(0.f, 0.f), S2 = S1, S1o = S1, S2o = S1;
+        float Ey = 0.f, Eyo = 0.f;
         const int qb = lu * nc;
 #pragma unroll
         for (int c = 0; c < CPT / kCh; ++c) {
@@ -487,17 +507,25 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
                     const int m = c * kCh + r;
                     if (EXACT || m < M) {
                         const float2 y = ys[(size_t)r * kTile];
-                        S1.x = fmaf(E[m].x, y.x, S1.x);
-                        S1.y = fmaf(E[m].x, y.y, S1.y);
-                        S2.x = fmaf(E[m].y, y.x, S2.x);
-                        S2.y = fmaf(E[m].y, y.y, S2.y);
-                        Ey = fmaf(y.x, y.x, fmaf(y.y, y.y, Ey));
+                        float2& s1 = (r & 1) ? S1o : S1;
+                        float2& s2 = (r & 1) ? S2o : S2;
+                        s1.x = fmaf(E[m].x, y.x, s1.x);
+                        s1.y = fmaf(E[m].x, y.y, s1.y);
+                        s2.x = fmaf(E[m].y, y.x, s2.x);
+                        s2.y = fmaf(E[m].y, y.y, s2.y);
+                        Ey = fmaf(y.x, y.x, Ey);
+                        Eyo = fmaf(y.y, y.y, Eyo);
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
         }
+        S1.x += S1o.x;
+        S1.y += S1o.y;
+        S2.x += S2o.x;
+        S2.y += S2o.y;
+        Ey += Eyo;
 
         float contrib = 0.f;
         if (valid) {
@@ -706,7 +734,7 @@ pact_status check_delays(const float* d, int m) {
 
 template <int CPT, bool EXACT>
 pact_status launch_mcd(const McdArgs& a, cudaStream_t st) {
-    if (a.fp64) {
+    if (!a.stream) {
         const size_t smem = (size_t)a.M * kBins * sizeof(float2) + (size_t)a.g.n_t * sizeof(float);
         PACT_TRY(ensure_smem((const void*)mcd_kernel<CPT, EXACT>, smem, "mc_deconv_loss: shared memory attribute"));
         dim3 grid(a.KT, a.N);
@@ -714,7 +742,8 @@ pact_status launch_mcd(const McdArgs& a, cudaStream_t st) {
         return check_launch("mc_deconv_loss kernel");
     }
     const void* fn = (const void*)mcd_stream_kernel<CPT, EXACT>;
-    const size_t smem = (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)a.g.n_t * sizeof(float);
+    const size_t smem = (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)a.g.n_t * sizeof(float) +
+                        (size_t)kSlots * (kTile * sizeof(float2) + (size_t)a.g.n_t * sizeof(float));
     PACT_TRY(ensure_smem(fn, smem, "mc_deconv_loss: shared memory attribute"));
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStreamThreads, smem) != cudaSuccess || per_sm < 1)
@@ -737,8 +766,7 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     if (!ws) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss: workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(Y) % 16) return fail(PACT_ERR_INVALID_ARG, "Y must be 16-byte aligned");
-    if ((size_t)m * kBins * sizeof(float2) + (size_t)g->n_t * sizeof(float) > 200 * 1024 ||
-        (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)g->n_t * sizeof(float) > 200 * 1024)
+    if ((size_t)m * kBins * sizeof(float2) + (size_t)g->n_t * sizeof(float) > 200 * 1024)
         return fail(PACT_ERR_SHAPE, "mc_deconv_loss: n_t too large");
     const Plan pl = make_plan(g, pt, m);
     const size_t need = tables ? pl.scratch : pl.total;
@@ -766,19 +794,23 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.dL_dw = dL_dw;
     a.scale = scale;
     a.fp64 = eps < 1e-6f;
+    // the streaming kernel copies w rows with bulk copies (16-byte granularity)
+    a.stream = !a.fp64 && g->n_t % 4 == 0 && reinterpret_cast<uintptr_t>(w) % 16 == 0 &&
+               (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)g->n_t * sizeof(float) +
+                       (size_t)kSlots * (kTile * sizeof(float2) + (size_t)g->n_t * sizeof(float)) <= 220 * 1024;
     a.part_loss = reinterpret_cast<float*>(base);
     a.lut = reinterpret_cast<const float2*>(tb + pl.t_lut);
     a.etab = reinterpret_cast<const float2*>(tb + pl.t_etab);
     a.btab = reinterpret_cast<const float4*>(tb + pl.t_btab);
     a.c2d = reinterpret_cast<const double2*>(tb + pl.t_c2d);
-    a.KT = a.fp64 ? pl.KT : pl.KTs;
+    a.KT = a.stream ? pl.KTs : pl.KT;
     a.tag = reinterpret_cast<const unsigned long long*>(tb);
     a.want = fingerprint(g, pt, d, m);
     a.tile_next = reinterpret_cast<int*>(base + pl.off_next);
     if (!tables) PACT_TRY(build_tables(g, pt, d, m, a.fp64, pl, tb, st));
     a.loss = loss;
     a.loss_pp = loss_pp;
-    if (!a.fp64 && cudaMemsetAsync(a.tile_next, 0, (size_t)(pl.KTs + 1) * sizeof(int), st) != cudaSuccess)
+    if (a.stream && cudaMemsetAsync(a.tile_next, 0, (size_t)(pl.KTs + 1) * sizeof(int), st) != cudaSuccess)
         return check_launch("mc_deconv_loss: clearing the tile counters");
     if (dL_dw && !accumulate &&
         cudaMemsetAsync(dL_dw, 0, (size_t)pt->n * g->n_t * sizeof(float), st) != cudaSuccess)
@@ -793,7 +825,7 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     else if (m < 32) s = launch_mcd<32, false>(a, st);
     else s = launch_mcd<64, false>(a, st);
     if (s != PACT_OK) return s;
-    if (a.fp64 && (loss || loss_pp)) {
+    if (!a.stream && (loss || loss_pp)) {
         mcd_finalize_kernel<<<(a.N + kTPB - 1) / kTPB, kTPB, 0, st>>>(a.N, a.KT, a.part_loss, loss, loss_pp);
         return check_launch("mc_deconv_loss finalize");
     }

@@ -45,6 +45,7 @@ CASES = {
     "tiny_p8_m1": lambda: inputs.config_tiny(p=8, m=1),
     "tiny_p12_m3": lambda: inputs.config_tiny(p=12, m=3, grid=3),
     "small_p32_m8": inputs.config_small,
+    "tiny_nt48": lambda: inputs.config_tiny(p=16, m=4, n_t=48),     # N_t not a multiple of 32: warp-per-ray kernels
 }
 
 
@@ -84,7 +85,7 @@ def test_sos_to_delays_full_size_sampled():
     assert rel(w[idx], ref) <= 1e-4
 
 
-@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8"])
+@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8", "tiny_nt48"])
 def test_sos_to_delays_adj(name):
     cfg = CASES[name]()
     case = inputs.make_case(cfg, 2)
@@ -269,6 +270,24 @@ def test_mc_deconv_loss_tabled_matches_per_call_tables(eps):
     other = pact.McdTables(pb, d * 1.01)
     bad = pact.mc_deconv_loss(pb, wt, Yt, d, eps, tables=other)
     assert np.isnan(float(bad["loss"].item())) and np.isnan(cpu(bad["dL_dw"])).any()
+
+
+def test_mc_deconv_loss_misaligned_w_takes_the_general_path():
+    """w not 16-byte aligned (the streaming kernel copies w rows in bulk): the
+    two-pass kernel serves the call with the same results."""
+    cfg = inputs.config_small()
+    Y, w, d = _mcd_case(cfg, 0, realistic=True)
+    pb = pact.Problem(cfg, DEV)
+    big = torch.zeros(w.size + 1, dtype=torch.float32, device=DEV)
+    big[1:] = torch.as_tensor(w.ravel(), device=DEV)
+    w_odd = big[1:].view(w.shape)
+    assert w_odd.data_ptr() % 16 != 0
+    Yt = to_dev_c(Y)
+    a = pact.mc_deconv_loss(pb, torch.as_tensor(w, device=DEV), Yt, d, cfg.eps, want_xhat=True)
+    b = pact.mc_deconv_loss(pb, w_odd, Yt, d, cfg.eps, want_xhat=True)
+    assert abs(float(a["loss"].item()) - float(b["loss"].item())) <= 1e-5 * float(a["loss"].item())
+    assert rel(cpu(b["Xhat"]), cpu(a["Xhat"])) <= 1e-6
+    assert rel(cpu(b["dL_dw"]), cpu(a["dL_dw"])) <= 1e-5
 
 
 def test_mc_deconv_loss_noise_free_truth_is_minimum():
