@@ -84,6 +84,8 @@ struct McdArgs {
     float* part_loss;      // [N][KT]
     const float2* lut;     // [N][F] ring coordinates (t_a, t_b)
     const float2* etab;    // [M][F] exp(j|k|d_j)
+    const float2* estep;   // [8][F] exp(j|k| r delta), r = 0..7, for uniformly spaced delays
+    int fact;              // 1: delays uniform with step delta (factorised phases in the streaming kernel)
     const float4* btab;    // [F] (|k|/2pi, c_k |k|_mm, Re C2, Im C2)
     const double2* c2d;    // [F] C2 in FP64 (eps < 1e-6 only)
     int KT;                // 256-bin tiles
@@ -110,10 +112,13 @@ __device__ __forceinline__ float ring_coord(float cx, float cy, float dx, float 
 //  * blockIdx.y < N: geometry-only part of Eq. 4 for patch i = blockIdx.y, the
 //    ring coordinates of the directions ang k and ang k + pi,
 //    lut[i][k] = (t_a, t_b);
-//  * blockIdx.y == N: per-bin tables etab[j][k] = exp(j|k|d_j) and
-//    btab[k] = (|k|/2pi, c_k |k|_mm, Re C2, Im C2) with C2 = sum_j exp(2j|k|d_j).
+//  * blockIdx.y == N: per-bin tables etab[j][k] = exp(j|k|d_j),
+//    btab[k] = (|k|/2pi, c_k |k|_mm, Re C2, Im C2) with C2 = sum_j exp(2j|k|d_j),
+//    and estep[r][k] = exp(j|k| r step) (r = 0..7; used when the delays are
+//    uniformly spaced by `step`).
 __global__ void mcd_tables_kernel(Geo g, int N, int P, int F, int M, Delays dl, const int2* centres, float2* lut,
-                                  float2* etab, float4* btab, unsigned long long* tag, unsigned long long fp) {
+                                  float2* etab, float4* btab, float2* estep, float step,
+                                  unsigned long long* tag, unsigned long long fp) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0 && blockIdx.y == 0) *tag = fp;
     if (k >= F) return;
@@ -138,6 +143,7 @@ __global__ void mcd_tables_kernel(Geo g, int N, int P, int F, int M, Delays dl, 
     }
     const float om = ((v == 0 || v == P / 2) ? 1.f : 2.f) * kTwoPi * fm * 1e-3f;
     btab[k] = make_float4(fm, om, c2x, c2y);
+    for (int r = 0; r < 8; ++r) estep[(size_t)r * F + k] = cis_pi(2.f * fm * (r * step));
 }
 
 // FP64 C2(k) = sum_j exp(2j|k|d_j) for the eps < 1e-6 path.
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(kBins, 2) mcd_kernel(const McdArgs a) {
 constexpr int kCh = 8;          // channel rows per pipeline stage (16 KB)
 constexpr int kStages = 4;      // stages in flight per CTA (about one unit of look-ahead: a short tail)
 constexpr int kRing = 8;        // unit ids published ahead of their consumers
-constexpr int kSlots = 4;       // per-unit lookup rows (ring coordinates, w) staged ahead
+constexpr int kSlots = 3;       // per-unit lookup rows (ring coordinates, w) staged ahead
 constexpr int kTile = 224;                   // bins per unit of the streaming kernel, one consumer thread each
 constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two CTAs per SM)
 
@@ -369,8 +375,14 @@ constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer wa
 // shared slots, so the consumers' lookups of Eq. 4 hit shared memory.  The dL/dw contributions of a unit are summed in one of two
 // shared buffers (alternating per unit) and added to the output after the
 // unit's closing consumer barrier.
-template <int CPT, bool EXACT>
-__global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const McdArgs a) {
+// FACT (uniformly spaced delays, M a multiple of 8): with d_{8c+r} = d_{8c} + r
+// delta the phase factors split as exp(j|k|d_{8c}) exp(j|k| r delta); the
+// consumers keep the M/8 + 8 factors (not all M) in registers, form the
+// chunk sums P = sum_r cos(|k| r delta) Y, Q = sum_r sin(|k| r delta) Y and
+// rotate them by the chunk's base phase, which frees registers for a third CTA
+// per SM.
+template <int CPT, bool EXACT, bool FACT>
+__global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kernel(const McdArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int n_t = a.g.n_t, M = EXACT ? CPT : a.M, N = a.N;
     float2* stage = reinterpret_cast<float2*>(smem_raw);                          // [kStages][kCh][kTile]
@@ -453,7 +465,8 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
     }
 
     // ------------------------------------------------------------------ consumer warps
-    float2 E[CPT];
+    constexpr int NE = FACT ? CPT / kCh + kCh : CPT;   // registers of phase factors
+    float2 E[NE];
     float4 bt = make_float4(0.f, 0.f, 0.f, 0.f);
     int kt_loaded = -1;
     bool ok = tag_ok;
@@ -471,9 +484,18 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
         const int buf = lu & 1;
         if (kt != kt_loaded) {                       // per-bin tables of this tile
             kt_loaded = kt;
+            if (FACT) {                              // E[c]: exp(j|k|d_{8c}); E[CPT/8 + r]: exp(j|k| r delta)
 #pragma unroll
-            for (int m = 0; m < CPT; ++m)
-                E[m] = (valid && (EXACT || m < M)) ? __ldg(a.etab + (size_t)m * a.F + k) : make_float2(0.f, 0.f);
+                for (int c = 0; c < CPT / kCh; ++c)
+                    E[c] = valid ? __ldg(a.etab + (size_t)(c * kCh) * a.F + k) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < kCh; ++r)
+                    E[CPT / kCh + r] = valid ? __ldg(a.estep + (size_t)r * a.F + k) : make_float2(0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int m = 0; m < NE; ++m)
+                    E[m] = (valid && (EXACT || m < M)) ? __ldg(a.etab + (size_t)m * a.F + k) : make_float2(0.f, 0.f);
+            }
             bt = valid ? __ldg(a.btab + k) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // the two lookups of w of Eq. 4, from the unit's shared slot (landed with its first chunk)
@@ -502,23 +524,52 @@ __global__ void __launch_bounds__(kStreamThreads, 2) mcd_stream_kernel(const Mcd
                 const int q = qb + c, s = q % kStages;
                 if (c > 0 && ok) ok = mbar_wait_bounded(&full[s], (uint32_t)((q / kStages) & 1), kCopyWaitNs);
                 const float2* ys = stage + (size_t)s * kCh * kTile + tid;
+                if (FACT) {
+                    float2 P = make_float2(0.f, 0.f), Q = P, Po = P, Qo = P;
 #pragma unroll
-                for (int r = 0; r < kCh; ++r) {
-                    const int m = c * kCh + r;
-                    if (EXACT || m < M) {
+                    for (int r = 0; r < kCh; ++r) {
                         const float2 y = ys[(size_t)r * kTile];
-                        float2& s1 = (r & 1) ? S1o : S1;
-                        float2& s2 = (r & 1) ? S2o : S2;
-                        s1.x = fmaf(E[m].x, y.x, s1.x);
-                        s1.y = fmaf(E[m].x, y.y, s1.y);
-                        s2.x = fmaf(E[m].y, y.x, s2.x);
-                        s2.y = fmaf(E[m].y, y.y, s2.y);
+                        const float2 es = E[CPT / kCh + r];
+                        float2& pp = (r & 1) ? Po : P;
+                        float2& qq = (r & 1) ? Qo : Q;
+                        pp.x = fmaf(es.x, y.x, pp.x);
+                        pp.y = fmaf(es.x, y.y, pp.y);
+                        qq.x = fmaf(es.y, y.x, qq.x);
+                        qq.y = fmaf(es.y, y.y, qq.y);
                         Ey = fmaf(y.x, y.x, Ey);
                         Eyo = fmaf(y.y, y.y, Eyo);
                     }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                    P.x += Po.x;
+                    P.y += Po.y;
+                    Q.x += Qo.x;
+                    Q.y += Qo.y;
+                    // cos(a + b) = cos a cos b - sin a sin b, sin(a + b) = sin a cos b + cos a sin b
+                    const float2 eb = E[c];
+                    S1.x = fmaf(eb.x, P.x, fmaf(-eb.y, Q.x, S1.x));
+                    S1.y = fmaf(eb.x, P.y, fmaf(-eb.y, Q.y, S1.y));
+                    S2.x = fmaf(eb.y, P.x, fmaf(eb.x, Q.x, S2.x));
+                    S2.y = fmaf(eb.y, P.y, fmaf(eb.x, Q.y, S2.y));
+                } else {
+#pragma unroll
+                    for (int r = 0; r < kCh; ++r) {
+                        const int m = c * kCh + r;
+                        if (EXACT || m < M) {
+                            const float2 y = ys[(size_t)r * kTile];
+                            float2& s1 = (r & 1) ? S1o : S1;
+                            float2& s2 = (r & 1) ? S2o : S2;
+                            s1.x = fmaf(E[m].x, y.x, s1.x);
+                            s1.y = fmaf(E[m].x, y.y, s1.y);
+                            s2.x = fmaf(E[m].y, y.x, s2.x);
+                            s2.y = fmaf(E[m].y, y.y, s2.y);
+                            Ey = fmaf(y.x, y.x, Ey);
+                            Eyo = fmaf(y.y, y.y, Eyo);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);
             }
         }
         S1.x += S1o.x;
@@ -659,7 +710,7 @@ __global__ void __launch_bounds__(kTPB) mcd_finalize_kernel(int N, int KT, const
 struct Plan {
     int KT, KTs;                                   // tiles of the two-pass (256) and streaming (224) kernels
     size_t off_next, scratch;                      // loss partials, then per-tile claim counters
-    size_t t_lut, t_etab, t_btab, t_c2d, tables;   // offsets inside the tables, their size
+    size_t t_lut, t_etab, t_btab, t_c2d, t_estep, tables;   // offsets inside the tables, their size
     size_t total;                                  // workspace bytes without prebuilt tables
 };
 
@@ -680,6 +731,8 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     o += align_up((size_t)F * sizeof(float4), 256);
     p.t_c2d = o;
     o += align_up((size_t)F * sizeof(double2), 256);
+    p.t_estep = o;
+    o += align_up((size_t)8 * F * sizeof(float2), 256);
     p.tables = o;
     p.total = p.scratch + p.tables;
     return p;
@@ -703,6 +756,16 @@ unsigned long long fingerprint(const pact_geometry* g, const pact_patches* pt, c
 }
 
 // Fills the tables at `t` (layout of make_plan); the FP64 table when `fp64`.
+// Step of uniformly spaced delays (every d_j within 1e-10 m of d_0 + j step, and m
+// a multiple of 8), else 0.
+float uniform_step(const float* d, int m) {
+    if (m < 8 || m % 8) return 0.f;
+    const double step = ((double)d[m - 1] - (double)d[0]) / (m - 1);
+    for (int j = 0; j < m; ++j)
+        if (fabs((double)d[j] - ((double)d[0] + j * step)) > 1e-10) return 0.f;
+    return (float)step;
+}
+
 pact_status build_tables(const pact_geometry* g, const pact_patches* pt, const float* d, int m, bool fp64,
                          const Plan& pl, char* t, cudaStream_t st) {
     const int F = pt->p * (pt->p / 2 + 1);
@@ -712,6 +775,7 @@ pact_status build_tables(const pact_geometry* g, const pact_patches* pt, const f
                                          reinterpret_cast<const int2*>(pt->centres),
                                          reinterpret_cast<float2*>(t + pl.t_lut), reinterpret_cast<float2*>(t + pl.t_etab),
                                          reinterpret_cast<float4*>(t + pl.t_btab),
+                                         reinterpret_cast<float2*>(t + pl.t_estep), uniform_step(d, m),
                                          reinterpret_cast<unsigned long long*>(t), fingerprint(g, pt, d, m));
     PACT_TRY(check_launch("mc_deconv_loss: tables"));
     if (fp64) {
@@ -732,6 +796,21 @@ pact_status check_delays(const float* d, int m) {
     return PACT_OK;
 }
 
+template <int CPT, bool EXACT, bool FACT>
+pact_status launch_stream(const McdArgs& a, cudaStream_t st) {
+    const void* fn = (const void*)mcd_stream_kernel<CPT, EXACT, FACT>;
+    const size_t smem = (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)a.g.n_t * sizeof(float) +
+                        (size_t)kSlots * (kTile * sizeof(float2) + (size_t)a.g.n_t * sizeof(float));
+    PACT_TRY(ensure_smem(fn, smem, "mc_deconv_loss: shared memory attribute"));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStreamThreads, smem) != cudaSuccess || per_sm < 1)
+        return check_launch("mc_deconv_loss: occupancy query");
+    const int units = a.KT * a.N;
+    const int grid = std::min(units, per_sm * num_sms());
+    mcd_stream_kernel<CPT, EXACT, FACT><<<grid, kStreamThreads, smem, st>>>(a);
+    return check_launch("mc_deconv_loss kernel");
+}
+
 template <int CPT, bool EXACT>
 pact_status launch_mcd(const McdArgs& a, cudaStream_t st) {
     if (!a.stream) {
@@ -741,17 +820,8 @@ pact_status launch_mcd(const McdArgs& a, cudaStream_t st) {
         mcd_kernel<CPT, EXACT><<<grid, kBins, smem, st>>>(a);
         return check_launch("mc_deconv_loss kernel");
     }
-    const void* fn = (const void*)mcd_stream_kernel<CPT, EXACT>;
-    const size_t smem = (size_t)kStages * kCh * kTile * sizeof(float2) + 2 * (size_t)a.g.n_t * sizeof(float) +
-                        (size_t)kSlots * (kTile * sizeof(float2) + (size_t)a.g.n_t * sizeof(float));
-    PACT_TRY(ensure_smem(fn, smem, "mc_deconv_loss: shared memory attribute"));
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStreamThreads, smem) != cudaSuccess || per_sm < 1)
-        return check_launch("mc_deconv_loss: occupancy query");
-    const int units = a.KT * a.N;
-    const int grid = std::min(units, per_sm * num_sms());
-    mcd_stream_kernel<CPT, EXACT><<<grid, kStreamThreads, smem, st>>>(a);
-    return check_launch("mc_deconv_loss kernel");
+    if (EXACT && CPT >= 16 && a.fact) return launch_stream<CPT, EXACT, EXACT && CPT >= 16>(a, st);
+    return launch_stream<CPT, EXACT, false>(a, st);
 }
 
 pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float* w, const float* Y,
@@ -802,6 +872,8 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.lut = reinterpret_cast<const float2*>(tb + pl.t_lut);
     a.etab = reinterpret_cast<const float2*>(tb + pl.t_etab);
     a.btab = reinterpret_cast<const float4*>(tb + pl.t_btab);
+    a.estep = reinterpret_cast<const float2*>(tb + pl.t_estep);
+    a.fact = uniform_step(d, m) != 0.f;
     a.c2d = reinterpret_cast<const double2*>(tb + pl.t_c2d);
     a.KT = a.stream ? pl.KTs : pl.KT;
     a.tag = reinterpret_cast<const unsigned long long*>(tb);

@@ -226,6 +226,12 @@ def test_mc_deconv_loss_nonuniform_delays_and_wide_channels():
     cfg40 = inputs.config_tiny(p=10, m=40)
     Y, w, d = _mcd_case(cfg40, 14)
     _check_mcd(cfg40, Y, w, d, 1e-3)
+    cfg16 = inputs.config_tiny(p=12, m=16)             # uniform delays: factorised phases
+    Y, w, d = _mcd_case(cfg16, 22)
+    _check_mcd(cfg16, Y, w, d, 1e-3)
+    d16 = d.copy()
+    d16[5] += 3e-6                                     # no longer uniform: one phase factor per channel
+    _check_mcd(cfg16, Y, w, d16, 1e-3)
 
 
 def test_mc_deconv_loss_full_size_sampled():

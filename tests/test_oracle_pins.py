@@ -506,3 +506,15 @@ def test_stitch_of_windowed_patches_is_identity():
     assert np.abs(out - x)[cov].max() < 1e-10
     assert np.abs(ones - 1)[cov].max() < 1e-12
     assert np.abs(out[~cov]).max() == 0.0
+
+
+def test_quality_metrics_closed_forms():
+    """PSNR/SSIM helpers used for the recovered images: known values."""
+    from paper_2409_10876_gb300 import quality
+    rng = np.random.default_rng(30)
+    ref = rng.uniform(0, 1, (40, 40))
+    assert quality.psnr(ref + 0.1, ref) == pytest.approx(20.0, abs=1e-9)        # MSE 0.01
+    assert quality.ssim(ref, ref) == pytest.approx(1.0, abs=1e-12)
+    assert quality.ssim(0.5 * ref, ref) < 0.95
+    noisy = ref + 0.3 * rng.standard_normal(ref.shape)
+    assert quality.ssim(noisy, ref) < quality.ssim(ref + 0.05 * rng.standard_normal(ref.shape), ref)
