@@ -312,7 +312,8 @@ def run_gpu(args, cfg, case, rank, world, local):
                                                        f"capture, {iters} iterations with a loss read-back each"}
     if not args.no_variants:
         line["variants"] = {"neural_field": nf_variant(args, cfg, case, pb, Y, flush, stream),
-                            "das_stack": das_variant(dev, flush, stream)}
+                            "das_stack": das_variant(dev, flush, stream),
+                            "channels": channels_variant(args, cfg, dev, flush, stream)}
     if rank == 0 and not args.no_warm_start:
         line["warm_start"] = warm_start_run(args, cfg, pb, dev)
     if rank == 0:
@@ -346,6 +347,28 @@ def nf_variant(args, cfg, case, pb, Y, flush, stream):
     return {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
             "dtype": "bf16 (field) + f32 (forward model)", "params": int(rec.params.numel()),
             "gpu_launches_per_step": 12}
+
+
+def channels_variant(args, cfg, dev, flush, stream):
+    """Iterations/s against the number of delay channels M at the same delay
+    range (the trade-off behind the paper's channel-count ablation, Sec. S3.1)."""
+    import torch
+    from paper_2409_10876_gb300 import inputs, pact
+    from paper_2409_10876_gb300.recovery import PGRecovery, measurement_spectra
+    out = {}
+    for m in (4, 8, 16, 32):
+        c = cfg.replace(m=m)
+        case = inputs.make_case(c, args.seed)
+        pb = pact.Problem(c, dev)
+        Y = measurement_spectra(pb, case, dev)
+        rec = PGRecovery(pb, Y, case["d"], c.eps, c.tv_lambda, c.lr, torch.as_tensor(case["sos_init"]),
+                         torch.as_tensor(case["mask"]))
+        g = rec.capture()
+        for _ in range(3):
+            g.replay()
+        ms = _time_graph(g, flush, stream, 200)
+        out[str(m)] = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_iter": statistics.mean(ms)}
+    return out
 
 
 def das_variant(dev, flush, stream):
@@ -437,7 +460,15 @@ def warm_start_run(args, cfg, pb, dev):
     it_w, s_w, h_w, rec_w = warmstart.time_to_target(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr,
                                                      v_warm.clone(), mask_d, target, 1000)
     m = mask_d > 0
-    out = {"train_samples": S, "epochs": args.ws_epochs, "batch": B, "generate_s": t_gen, "train_s": t_train,
+    from paper_2409_10876_gb300 import quality
+    ip = case["ip"]
+    pm = quality.image_mask(cfg)
+    iq = {}
+    for name, v in (("uniform_1500", v_cold), ("cold_end", rec_cold.sos), ("warm_end", rec_w.sos),
+                    ("true_sos", v_true)):
+        img = quality.recovered_image(pb, Y, case["d"], cfg.eps, v)
+        iq[name] = {"psnr_db": quality.psnr(img, ip, 1.0, pm), "ssim": quality.ssim(img, ip, 1.0, pm)}
+    out = {"image_quality": iq, "train_samples": S, "epochs": args.ws_epochs, "batch": B, "generate_s": t_gen, "train_s": t_train,
            "train_step_ms": 1e3 * t_train / steps, "train_tflops_bf16": train_tflops,
            "train_loss": {"first_epoch": hist[0], "last_epoch": hist[-1]},
            "sos_mae_mps": {"cnn": float((v_warm - v_true)[m].abs().mean()),

@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         S2.y += S2o.y;
         Ey += Eyo;
 
-        float contrib = 0.f;
+        float contrib = 0.f, gW1 = 0.f, gW2 = 0.f;
         if (valid) {
             const float fm = bt.x, om = bt.y;
             const float2 C2 = make_float2(bt.z, bt.w);
@@ -622,14 +622,16 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                 const float2 bq = cmul(be, tq), xhq = cmul(xc, hq);
                 const float2 SP = make_float2(b2 * ap.x - eps * xhp.x, b2 * ap.y - eps * xhp.y);
                 const float2 SQ = make_float2(b2 * bq.x - eps * xhq.x, b2 * bq.y - eps * xhq.y);
-                const float gW1 = kmag * (Kc.x * SP.y + Kc.y * SP.x);
-                const float gW2 = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
-                float* dws = dw_s + buf * n_t;
-                atomicAdd(dws + n1a, (1.f - fa) * gW1);
-                atomicAdd(dws + n2a, fa * gW1);
-                atomicAdd(dws + n1b, (1.f - fb) * gW2);
-                atomicAdd(dws + n2b, fb * gW2);
+                gW1 = kmag * (Kc.x * SP.y + Kc.y * SP.x);
+                gW2 = -kmag * (Kc.x * SQ.y + Kc.y * SQ.x);
             }
+        }
+        if (a.dL_dw) {                               // whole warps: lanes without a term add 0
+            float* dws = dw_s + buf * n_t;
+            warp_seg_add(dws, n1a, (1.f - fa) * gW1);
+            warp_seg_add(dws, n2a, fa * gW1);
+            warp_seg_add(dws, n1b, (1.f - fb) * gW2);
+            warp_seg_add(dws, n2b, fb * gW2);
         }
         contrib = warp_sum(contrib);
         if (lane == 0) lsum_s[buf][tid >> 5] = contrib;

@@ -149,6 +149,25 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
+// Adds v to dst[idx] (shared memory) for every lane of a converged warp with one
+// atomic per run of consecutive lanes holding the same idx: the run's values
+// are summed by a segmented shuffle scan and the run's last lane adds the sum.
+// (Shared-memory float atomics are compare-and-swap loops, which neighbouring
+// lanes aiming at one address would serialise.)
+__device__ __forceinline__ void warp_seg_add(float* dst, int idx, float v) {
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, idx, 1);
+    const int next = __shfl_down_sync(0xffffffffu, idx, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != idx);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // head of this lane's run
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float x = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane - d >= start) v += x;
+    }
+    if (lane == 31 || next != idx) atomicAdd(dst + idx, v);
+}
+
 // Block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
 __device__ __forceinline__ float block_sum(float x, float* red) {
     x = warp_sum(x);

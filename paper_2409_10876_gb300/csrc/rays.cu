@@ -130,18 +130,41 @@ __device__ __forceinline__ void cta_rays(const RayArgs& a, int& i, int& n0, int&
 // fall into different banks.
 __host__ __device__ __forceinline__ int smem_pitch(int G) { return G + 1; }
 
+// dv[p][c] = sos[p][c] - v0 into the padded shared grid, with 16-byte loads
+// (several in flight per thread) when the layout allows.
+__device__ __forceinline__ void load_excess(float* dv, const float* sos, int G, int pitch, float v0) {
+    if ((G & 3) == 0 && (reinterpret_cast<uintptr_t>(sos) & 15) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(sos);
+        const int G4 = G >> 2, n4 = G * G4;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+            const float4 v = __ldg(s4 + q);
+            const int p = q / G4, c = (q - (q / G4) * G4) << 2;
+            float* d = dv + p * pitch + c;
+            d[0] = v.x - v0;
+            d[1] = v.y - v0;
+            d[2] = v.z - v0;
+            d[3] = v.w - v0;
+        }
+    } else {
+        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+            const int p = q / G, c = q - (q / G) * G;
+            dv[p * pitch + c] = sos[q] - v0;
+        }
+    }
+}
+
 // Warp w of a CTA takes every nw-th ray of the CTA's run; it sets up 32 of its
 // rays at once (one per lane) and then integrates them one after the other
 // (lanes over samples), taking each ray's setup by shuffles.
+// SMEM: the SOS excess grid is staged in shared memory (else read from global).
+template <bool SMEM>
 __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
     extern __shared__ float dv_s[];
-    const int G = a.g.G, pitch = a.use_smem ? smem_pitch(G) : G;
+    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
     const float v0 = a.g.v0;
-    if (a.use_smem) {
-        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
-            const int p = q / G, c = q - (q / G) * G;
-            dv_s[p * pitch + c] = a.sos[q] - v0;
-        }
+    if (SMEM) {
+        load_excess(dv_s, a.sos, G, pitch, v0);
         __syncthreads();
     }
     int i, n0, n1;
@@ -169,14 +192,14 @@ __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
             for (int m = m0; m < mf; ++m) {
                 const float s = (m + 0.5f) * h;
                 const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = a.use_smem ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                const float d = SMEM ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
                 acc += __fdividef(d, v0 + d);
             }
             acc *= h;
             if (m0 <= ry.nfull && ry.nfull < m1) {    // last partial step, weighted by its length
                 const float s = ry.nfull * h + 0.5f * ry.rem;
                 const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = a.use_smem ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                const float d = SMEM ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
                 acc = fmaf(ry.rem, __fdividef(d, v0 + d), acc);
             }
             acc = warp_sum(acc);
@@ -195,36 +218,38 @@ __device__ __forceinline__ void scatter4(float* acc, int pitch, int idx, float c
 }
 
 // CTA b takes the rays r = b, b + nb, b + 2 nb, ... of the flat (patch,
-// transducer) index r = i N_t + n, so that its warps integrate rays of different
-// patches and directions at the same time (rays of one patch all start at the
-// same centre, where their scatters would collide).  A lane walks a contiguous
+// transducer) index r = i N_t + n, and each warp a contiguous block of them, so
+// that its warps integrate rays of different patches and directions at the same
+// time (rays of one patch all start at the same centre, where their scatters
+// would collide).  A lane walks a contiguous
 // run of samples of one ray and keeps the bilinear weights of the current cell
 // in registers, adding them to the shared grid only when the walk leaves the
 // cell.
+template <bool SMEM>
 __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
     extern __shared__ float sm[];
-    const int G = a.g.G, pitch = a.use_smem ? smem_pitch(G) : G;
+    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
     const int GP = G * pitch;
     const float v0 = a.g.v0;
     float* dv_s = sm;
     float* acc_s = sm + GP;
-    if (a.use_smem) {
+    if (SMEM) {
         for (int q = threadIdx.x; q < GP; q += blockDim.x) acc_s[q] = 0.f;
-        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
-            const int p = q / G, c = q - (q / G) * G;
-            dv_s[p * pitch + c] = a.sos[q] - v0;
-        }
-        __syncthreads();
+        load_excess(dv_s, a.sos, G, pitch, v0);
     }
-    float* acc = a.use_smem ? acc_s : a.out;
+    __syncthreads();
+    float* acc = SMEM ? acc_s : a.out;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nrays = a.N * a.g.n_t, nb = gridDim.x;
     const int mine = nrays > (int)blockIdx.x ? (nrays - (int)blockIdx.x + nb - 1) / nb : 0;   // rays of this CTA
-    const int nwarp = mine > warp ? (mine - warp + nw - 1) / nw : 0;                           // ... of this warp
+    // warp w takes the contiguous block t0 <= t < t1 of the CTA's rays t (r = b + nb t), so that the
+    // warps work on rays of different patches at any moment (rays of one patch share their start)
+    const int t0 = (int)((long long)mine * warp / nw), t1 = (int)((long long)mine * (warp + 1) / nw);
+    const int nwarp = t1 - t0;
     const float h = a.g.h;
     for (int kb = 0; kb < nwarp; kb += 32) {
         const int cnt = min(32, nwarp - kb);
-        const int r = (int)blockIdx.x + nb * (warp + nw * (kb + min(lane, cnt - 1)));
+        const int r = (int)blockIdx.x + nb * (t0 + kb + min(lane, cnt - 1));
         const int i = r / a.g.n_t, n = r - (r / a.g.n_t) * a.g.n_t;
         const int2 cc = a.centres[i];
         const Ray mine_ray = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
@@ -244,7 +269,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
                 const float s = last ? ry.nfull * h + 0.5f * ry.rem : (m + 0.5f) * h;
                 const float wgt = last ? ry.rem : h;
                 const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = a.use_smem ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                const float d = SMEM ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
                 const float iv = __frcp_rn(v0 + d);
                 const float coef = gv0 * wgt * iv * iv;
                 if (b.idx != cur) {
@@ -261,7 +286,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
             if (cur >= 0) scatter4(acc, pitch, cur, c00, c01, c10, c11);
         }
     }
-    if (a.use_smem) {
+    if (SMEM) {
         __syncthreads();
         float* dst = a.part + (size_t)blockIdx.x * G * G;
         for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
@@ -324,8 +349,10 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     p.use_smem = 2 * gbytes <= kMaxSmem;
     p.smem_fwd = p.use_smem ? gbytes : 0;
     p.smem_adj = p.use_smem ? 2 * gbytes : 0;
-    p.splits_fwd = splits_for(g, pt, (const void*)rays_fwd_kernel, 512, p.smem_fwd);
-    p.splits_adj = splits_for(g, pt, (const void*)rays_adj_kernel, 1024, p.smem_adj);
+    p.splits_fwd = splits_for(g, pt, p.use_smem ? (const void*)rays_fwd_kernel<true> : (const void*)rays_fwd_kernel<false>,
+                              512, p.smem_fwd);
+    p.splits_adj = splits_for(g, pt, p.use_smem ? (const void*)rays_adj_kernel<true> : (const void*)rays_adj_kernel<false>,
+                              1024, p.smem_adj);
     p.nb_fwd = pt->n * p.splits_fwd;
     p.nb_adj = pt->n * p.splits_adj;
     p.nr = (p.nb_adj + kGroup - 1) / kGroup;
@@ -363,8 +390,12 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
     const Plan pl = make_plan(g, pt);
     RayArgs a = make_args(g, pt, pl, pl.splits_fwd, sos);
     a.w = w;
-    PACT_TRY(ensure_smem((const void*)rays_fwd_kernel, pl.smem_fwd, "sos_to_delays: shared memory attribute"));
-    rays_fwd_kernel<<<pl.nb_fwd, 512, pl.smem_fwd, as_stream(stream)>>>(a);
+    if (pl.use_smem) {
+        PACT_TRY(ensure_smem((const void*)rays_fwd_kernel<true>, pl.smem_fwd, "sos_to_delays: shared memory attribute"));
+        rays_fwd_kernel<true><<<pl.nb_fwd, 512, pl.smem_fwd, as_stream(stream)>>>(a);
+    } else {
+        rays_fwd_kernel<false><<<pl.nb_fwd, 512, 0, as_stream(stream)>>>(a);
+    }
     return check_launch("sos_to_delays kernel");
 }
 
@@ -391,8 +422,9 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
     if (pl.use_smem) {
-        PACT_TRY(ensure_smem((const void*)rays_adj_kernel, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
-        rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a);
+        PACT_TRY(ensure_smem((const void*)rays_adj_kernel<true>, pl.smem_adj,
+                             "sos_to_delays_adj: shared memory attribute"));
+        rays_adj_kernel<true><<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a);
         PACT_TRY(check_launch("sos_to_delays_adj kernel"));
         float* stage1 = reinterpret_cast<float*>(static_cast<char*>(ws) + pl.off_stage1);
         dim3 g1((GG + 255) / 256, pl.nr);
@@ -403,6 +435,6 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     }
     if (!accumulate && cudaMemsetAsync(dL_dsos, 0, (size_t)GG * sizeof(float), st) != cudaSuccess)
         return check_launch("sos_to_delays_adj: memset");
-    rays_adj_kernel<<<pl.nb_adj, 1024, 0, st>>>(a);
+    rays_adj_kernel<false><<<pl.nb_adj, 1024, 0, st>>>(a);
     return check_launch("sos_to_delays_adj kernel");
 }
