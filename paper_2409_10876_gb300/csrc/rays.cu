@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
                 const float wgt = last ? ry.rem : h;
                 const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
                 const float d = SMEM ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
-                const float iv = __frcp_rn(v0 + d);
+                const float iv = __fdividef(1.f, v0 + d);
                 const float coef = gv0 * wgt * iv * iv;
                 if (b.idx != cur) {
                     if (cur >= 0) scatter4(acc, pitch, cur, c00, c01, c10, c11);
