@@ -312,6 +312,7 @@ def run_gpu(args, cfg, case, rank, world, local):
                                                        f"capture, {iters} iterations with a loss read-back each"}
     if not args.no_variants:
         line["variants"] = {"neural_field": nf_variant(args, cfg, case, pb, Y, flush, stream),
+                            "siren_field": siren_variant(args, cfg, case, pb, Y, flush, stream),
                             "das_stack": das_variant(dev, flush, stream),
                             "channels": channels_variant(args, cfg, dev, flush, stream)}
     if rank == 0 and not args.no_warm_start:
@@ -369,6 +370,21 @@ def channels_variant(args, cfg, dev, flush, stream):
         ms = _time_graph(g, flush, stream, 200)
         out[str(m)] = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_iter": statistics.mean(ms)}
     return out
+
+
+def siren_variant(args, cfg, case, pb, Y, flush, stream):
+    """The paper's neural field (SIREN, 1027 parameters, FP32) on the same
+    problem: siren_forward + rays + fused pass + ray adjoint + siren_backward + Adam."""
+    from paper_2409_10876_gb300 import inputs
+    from paper_2409_10876_gb300.recovery import SirenRecovery
+    rec = SirenRecovery(pb, Y, case["d"], cfg.eps, inputs.SIREN_LR, inputs.siren_init(args.seed), case["mask"])
+    g = rec.capture()
+    for _ in range(3):
+        g.replay()
+    steps = max(20, min(args.steps, 500))
+    ms = _time_graph(g, flush, stream, steps)
+    return {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
+            "dtype": "f32", "params": int(rec.params.numel()), "gpu_launches_per_step": 11}
 
 
 def das_variant(dev, flush, stream):

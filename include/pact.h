@@ -341,6 +341,30 @@ pact_status pact_nf_backward(const pact_geometry* g, const float* params, const 
 pact_status pact_nf_status(const pact_geometry* g, const void* ws, size_t ws_bytes, int* host_status,
                            void* stream);
 
+/*
+ * The paper's neural field (Sec. 3.3): a SIREN without hidden layers, 256
+ * sine features of the node coordinates and a linear output, plus an output
+ * scale and offset -- 1027 parameters:
+ *   v(x) = offset + scale (sum_f w2_f sin(omega0 (W1_f . x + b1_f)) + b2)
+ * on the mask (v_bg outside), x = ((col - (G-1)/2), (row - (G-1)/2)) / ((G-1)/2).
+ * Parameters (FP32, flat): W1 [256][2], b1 [256], w2 [256], b2, scale, offset.
+ * FP32 on the CUDA cores (two inputs: no contraction worth a tensor core).
+ *   params    DEVICE float [1027];  mask DEVICE uint8 [G][G] or NULL
+ *   sos       DEVICE float [G][G] output of pact_siren_forward
+ *   dL_dsos   DEVICE float [G][G];  dL_dparams DEVICE float [1027] (accumulate = 1 adds)
+ *   ws        DEVICE workspace of pact_siren_workspace_size bytes; it carries the
+ *             network output from forward to backward, so pact_siren_backward must
+ *             follow a pact_siren_forward with the same arguments and workspace.
+ * The backward pass is deterministic (per-chunk partial sums, fixed-order reduction).
+ */
+int pact_siren_param_count(void);
+size_t pact_siren_workspace_size(const pact_geometry* g);
+pact_status pact_siren_forward(const pact_geometry* g, const float* params, const unsigned char* mask, float omega0,
+                               float* sos, void* ws, size_t ws_bytes, void* stream);
+pact_status pact_siren_backward(const pact_geometry* g, const float* params, const unsigned char* mask, float omega0,
+                                const float* dL_dsos, float* dL_dparams, int accumulate, void* ws, size_t ws_bytes,
+                                void* stream);
+
 /* Workspace bytes of pact_stitch. */
 size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt);
 

@@ -17,6 +17,8 @@ Everything here is a literal FP64 evaluation of the paper's definitions:
 * Eq. 7   |k|-weighted aberrated-image-matching loss + TV      -> data_loss, tv, objective
 * Sec. 3.3 Adam on the SOS parameters                          -> adam_step
 * Sec. S1.4 stitching: place patches, divide by summed windows  -> stitch
+* Sec. 3.3 neural fields: the Fourier-feature MLP               -> nf_sos
+  and the paper's SIREN (256 sine features, no hidden layer)    -> siren_sos
 
 The DFT is an explicit matrix product (no FFT routine).  The gradients of
 the objective come from PyTorch autograd through these FP64 definitions,
@@ -518,6 +520,47 @@ def nf_objective(g, params, shapes, freqs, mask, v_mid, v_half, Y, centres, d, e
     the neural-field parameters; gradient by autograd."""
     prm = _t(params).clone().requires_grad_(want_grad)
     sos = nf_sos(g, prm, shapes, freqs, mask, v_mid, v_half)
+    w = wavefront_errors(g, sos, centres)
+    Yc = Y.to(CT) if isinstance(Y, torch.Tensor) else torch.as_tensor(Y).to(CT)
+    H = transfer_functions(g, w, centres, d)
+    Xh = deconvolve(H, Yc, eps)
+    L = data_loss(g, H, Yc, Xh)
+    gp = None
+    if want_grad:
+        (gp,) = torch.autograd.grad(L, prm)
+    return L.detach(), sos.detach(), gp
+
+
+# ----------------------------------------------------------------------------
+# the paper's neural field (Sec. 3.3): SIREN without hidden layers, 256 sine
+# features, a linear output and two extra scalars (output scale and offset)
+# ----------------------------------------------------------------------------
+
+def siren_coords(g) -> torch.Tensor:
+    """[G*G, 2] node coordinates (x = column, y = row) scaled to [-1, 1]."""
+    G = g.sos_g
+    c = (torch.arange(G, dtype=DT) - (G - 1) / 2.0) / ((G - 1) / 2.0)
+    yy, xx = torch.meshgrid(c, c, indexing="ij")
+    return torch.stack([xx.reshape(-1), yy.reshape(-1)], 1)
+
+
+def siren_sos(g, params, shapes, mask, omega0: float) -> torch.Tensor:
+    """SOS [G, G]: v = offset + scale (sum_f w2_f sin(omega0 (W1_f . x + b1_f)) + b2)
+    on the mask, v_bg elsewhere; params may require grad."""
+    p = nf_unflatten(params if isinstance(params, torch.Tensor) else _t(params), shapes)
+    x = siren_coords(g)
+    h = torch.sin(omega0 * (x @ p["W1"].T + p["b1"]))
+    z = h @ p["w2"] + p["b2"]
+    v = p["offset"] + p["scale"] * z
+    keep = _t(mask).reshape(-1) > 0
+    v = torch.where(keep, v, torch.full_like(v, g.v_bg))
+    return v.reshape(g.sos_g, g.sos_g)
+
+
+def siren_objective(g, params, shapes, mask, omega0, Y, centres, d, eps: float, want_grad: bool = True):
+    """Eq. 7 (lambda = 0) as a function of the SIREN parameters; gradient by autograd."""
+    prm = _t(params).clone().requires_grad_(want_grad)
+    sos = siren_sos(g, prm, shapes, mask, omega0)
     w = wavefront_errors(g, sos, centres)
     Yc = Y.to(CT) if isinstance(Y, torch.Tensor) else torch.as_tensor(Y).to(CT)
     H = transfer_functions(g, w, centres, d)

@@ -410,3 +410,37 @@ def config_cnn() -> Config:
     """The full-size problem with training phantoms of 1-6 ellipses spanning
     1400-1650 m/s (the warm-start network's training distribution)."""
     return config_full().replace(name="cnn512_ring512_p80_m32", sos_lo=1400.0, sos_hi=1650.0)
+
+
+# --------------------------------------------------------------------------
+# the paper's neural field: SIREN without hidden layers, 256 sine features
+# --------------------------------------------------------------------------
+
+SIREN_FEATURES = 256
+SIREN_OMEGA0 = 30.0    # sine frequency factor of the SIREN first layer
+SIREN_LR = 5e-3        # Adam learning rate for the neural field (Sec. 3.3)
+
+
+def siren_shapes():
+    """(name, shape) of the SIREN parameters in their flat order: W1 [256][2],
+    b1 [256], w2 [256], b2 [1], then the output scale and offset (1027 in all)."""
+    f = SIREN_FEATURES
+    return [("W1", (f, 2)), ("b1", (f,)), ("w2", (f,)), ("b2", (1,)), ("scale", (1,)), ("offset", (1,))]
+
+
+def siren_param_count() -> int:
+    return int(sum(np.prod(s) for _, s in siren_shapes()))
+
+
+def siren_init(seed: int, v_start: float = 1500.0, scale: float = 50.0) -> np.ndarray:
+    """Seeded flat float32 parameters with the SIREN initialisation: first
+    layer U(-1/2, 1/2) (fan-in 2), biases U(-1/sqrt 2, 1/sqrt 2), output layer
+    U(-sqrt(6/256)/omega0, +sqrt(6/256)/omega0), b2 = 0; output scale `scale` m/s
+    and offset v_start."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f = SIREN_FEATURES
+    W1 = rng.uniform(-0.5, 0.5, (f, 2))
+    b1 = rng.uniform(-1 / np.sqrt(2.0), 1 / np.sqrt(2.0), f)
+    bw = np.sqrt(6.0 / f) / SIREN_OMEGA0
+    w2 = rng.uniform(-bw, bw, f)
+    return np.concatenate([W1.ravel(), b1, w2, [0.0], [scale], [v_start]]).astype(np.float32)

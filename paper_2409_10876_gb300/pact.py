@@ -71,6 +71,10 @@ _SIGS = {
     "pact_nf_forward": ([_GP, _VP, _VP, _F, _F, _VP, _VP, _SZ, _VP], _I),
     "pact_nf_backward": ([_GP, _VP, _VP, _F, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_nf_status": ([_GP, _VP, _SZ, ctypes.POINTER(ctypes.c_int), _VP], _I),
+    "pact_siren_param_count": ([], _I),
+    "pact_siren_workspace_size": ([_GP], _SZ),
+    "pact_siren_forward": ([_GP, _VP, _VP, _F, _VP, _VP, _SZ, _VP], _I),
+    "pact_siren_backward": ([_GP, _VP, _VP, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_cnn_param_count": ([_I], _I),
     "pact_cnn_input_channels": ([_I], _I),
     "pact_cnn_pool_workspace_size": ([_GP, _I], _SZ),
@@ -502,6 +506,47 @@ def nf_status(nf: NeuralField) -> None:
     L = load()
     st = ctypes.c_int(0)
     _check(L.pact_nf_status(nf.pb.gp(), _ptr(nf.ws), nf.ws.numel(), ctypes.byref(st), _stream()), "nf_status")
+
+
+# ------------------------------------------------------------------ the paper's SIREN field
+
+class SirenField:
+    """Device state of the paper's neural field (SIREN, 1027 parameters)."""
+
+    def __init__(self, pb: Problem, params, mask=None, omega0: float = 30.0):
+        L = load()
+        self.pb = pb
+        self.params = torch.as_tensor(np.asarray(params, np.float32), device=pb.device).contiguous()
+        if self.params.numel() != int(L.pact_siren_param_count()):
+            raise PactError(f"the field has {int(L.pact_siren_param_count())} parameters, got {self.params.numel()}")
+        self.mask = None if mask is None else torch.as_tensor(np.asarray(mask, np.uint8), device=pb.device).contiguous()
+        self.omega0 = float(omega0)
+        self.ws = _ws(L.pact_siren_workspace_size(pb.gp()), pb.device)
+
+
+def siren_forward(sf: SirenField, sos=None):
+    """SOS [G, G] from the SIREN field (its output kept for siren_backward)."""
+    L = load()
+    pb = sf.pb
+    if sos is None:
+        sos = _empty((pb.g, pb.g), torch.float32, pb.device)
+    _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    _check(L.pact_siren_forward(pb.gp(), _ptr(sf.params), _ptr(sf.mask), sf.omega0, _ptr(sos), _ptr(sf.ws),
+                                sf.ws.numel(), _stream()), "siren_forward")
+    return sos
+
+
+def siren_backward(sf: SirenField, dL_dsos, dL_dparams=None, accumulate=False):
+    """dL/dparams from dL/dsos for the parameters of the last siren_forward."""
+    L = load()
+    pb = sf.pb
+    dL_dsos = _dev(dL_dsos, "dL_dsos", torch.float32, (pb.g, pb.g))
+    if dL_dparams is None:
+        dL_dparams = torch.zeros_like(sf.params)
+    _dev(dL_dparams, "dL_dparams", torch.float32, tuple(sf.params.shape))
+    _check(L.pact_siren_backward(pb.gp(), _ptr(sf.params), _ptr(sf.mask), sf.omega0, _ptr(dL_dsos), _ptr(dL_dparams),
+                                 int(accumulate), _ptr(sf.ws), sf.ws.numel(), _stream()), "siren_backward")
+    return dL_dparams
 
 
 # ------------------------------------------------------------------ warm-start CNN

@@ -164,6 +164,40 @@ class NFRecovery(PGRecovery):
             dst.copy_(src)
 
 
+class SirenRecovery(PGRecovery):
+    """The paper's neural field (SIREN, Sec. 3.3, lambda = 0): Adam on its 1027
+    parameters; every iteration is siren_forward -> sos_to_delays -> fused
+    deconvolution/loss/adjoint -> sos_to_delays_adj -> siren_backward -> Adam,
+    one CUDA graph."""
+
+    def __init__(self, pb: "pact.Problem", Y: torch.Tensor, d, eps: float, lr: float, params, mask=None,
+                 betas=(0.9, 0.999), adam_eps=1e-8, omega0: float = 30.0):
+        self.sf = pact.SirenField(pb, params, mask, omega0)
+        super().__init__(pb, Y, d, eps, 0.0, lr, torch.zeros(pb.g, pb.g), None, betas, adam_eps)
+        self.params = self.sf.params
+        self.adam_m = torch.zeros_like(self.params)
+        self.adam_v = torch.zeros_like(self.params)
+        self.gparams = torch.zeros_like(self.params)
+
+    def step(self):
+        pb = self.pb
+        pact.siren_forward(self.sf, self.sos)
+        pact.sos_to_delays(pb, self.sos, self.w)
+        pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
+                            tables=self.tables)
+        pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
+        pact.siren_backward(self.sf, self.grad, self.gparams)
+        pact.adam_step(self.params, self.gparams, self.adam_m, self.adam_v, 1, self.lr, self.betas[0],
+                       self.betas[1], self.adam_eps, step_counter=self.counter)
+
+    def state(self):
+        return [t.clone() for t in (self.params, self.adam_m, self.adam_v, self.counter)]
+
+    def set_state(self, st):
+        for dst, src in zip((self.params, self.adam_m, self.adam_v, self.counter), st):
+            dst.copy_(src)
+
+
 def synthesize_stack(pb: "pact.Problem", case: dict, device) -> torch.Tensor:
     """Delay stack [M, H, W] made by the forward model (Eq. 5) from the
     ground-truth SOS and IP: every channel j is the stitch of the patches
