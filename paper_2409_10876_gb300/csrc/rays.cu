@@ -16,6 +16,8 @@
 // partial grid to the workspace and two small kernels sum the partials in a
 // fixed order (deterministic).  Grids too large for shared memory read the SOS
 // from global memory and scatter with global atomics instead.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "pact_internal.cuh"
@@ -115,6 +117,7 @@ struct RayArgs {
     float* out;           // adjoint output (global-atomic variant)
     int splits;           // CTAs per patch
     int use_smem;
+    int cluster;          // adjoint: CTAs per thread-block cluster that pool their grids (0: none)
 };
 
 // CTA b handles patch b / splits, rays [n0, n1) of it.
@@ -286,7 +289,25 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
             if (cur >= 0) scatter4(acc, pitch, cur, c00, c01, c10, c11);
         }
     }
-    if (SMEM) {
+    if (SMEM && a.cluster) {
+        // the CTAs of a cluster sum their shared grids through distributed shared
+        // memory (CTA rank r takes a band of rows, in a fixed order of ranks) and
+        // write one partial grid per cluster
+        namespace cg = cooperative_groups;
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+        const int rows = (G + csize - 1) / csize;
+        const int r0 = min(G, rank * rows), r1 = min(G, r0 + rows);
+        float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G;
+        for (int q = threadIdx.x; q < (r1 - r0) * G; q += blockDim.x) {
+            const int p = r0 + q / G, cq = q - (q / G) * G;
+            float sum = 0.f;
+            for (int r = 0; r < csize; ++r) sum += cl.map_shared_rank(acc_s, r)[p * pitch + cq];
+            dst[p * G + cq] = sum;
+        }
+        cl.sync();                                   // remote reads end before any CTA exits
+    } else if (SMEM) {
         __syncthreads();
         float* dst = a.part + (size_t)blockIdx.x * G * G;
         for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
@@ -324,8 +345,10 @@ __global__ void reduce_stage2_kernel(const float* stage1, int nr, int GG, float*
 
 constexpr size_t kMaxSmem = 200 * 1024;
 
+constexpr int kCluster = 4;   // CTAs per cluster in the ray adjoint (8 would not fit in one wave)
+
 struct Plan {
-    int splits_fwd, splits_adj, nb_fwd, nb_adj, nr, use_smem;
+    int splits_fwd, splits_adj, nb_fwd, nb_adj, nr, use_smem, cluster, nparts;
     size_t smem_fwd, smem_adj, off_stage1, ws;
 };
 
@@ -342,6 +365,36 @@ int splits_for(const pact_geometry* g, const pact_patches* pt, const void* fn, i
     return std::max(1, std::min(s, std::max(1, g->n_t / 32)));
 }
 
+// Whether clusters of kCluster adjoint CTAs (1024 threads, `smem` bytes each) can
+// be resident on this device (queried once per device).
+bool cluster_fits(size_t smem) {
+    static int cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (cached[dev] == 0) {
+        int ok = -1;
+        const void* fn = (const void*)rays_adj_kernel<true>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(kCluster);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeClusterDimension;
+            attr.val.clusterDim.x = kCluster;
+            attr.val.clusterDim.y = 1;
+            attr.val.clusterDim.z = 1;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) ok = 1;
+        }
+        cudaGetLastError();
+        cached[dev] = ok;
+    }
+    return cached[dev] > 0;
+}
+
 Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     Plan p;
     const int G = g->sos_g;
@@ -355,9 +408,15 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
                               1024, p.smem_adj);
     p.nb_fwd = pt->n * p.splits_fwd;
     p.nb_adj = pt->n * p.splits_adj;
-    p.nr = (p.nb_adj + kGroup - 1) / kGroup;
+    p.cluster = 0;
+    if (p.use_smem && cluster_fits(p.smem_adj)) {
+        p.cluster = kCluster;
+        p.nb_adj = (p.nb_adj + kCluster - 1) / kCluster * kCluster;
+    }
+    p.nparts = p.cluster ? p.nb_adj / p.cluster : p.nb_adj;
+    p.nr = (p.nparts + kGroup - 1) / kGroup;
     const size_t plane = (size_t)G * G * sizeof(float);
-    p.off_stage1 = align_up((size_t)p.nb_adj * plane, 256);
+    p.off_stage1 = align_up((size_t)p.nparts * plane, 256);
     p.ws = p.use_smem ? p.off_stage1 + align_up((size_t)p.nr * plane, 256) : 256;
     return p;
 }
@@ -374,6 +433,7 @@ RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl
     a.out = nullptr;
     a.splits = splits;
     a.use_smem = pl.use_smem;
+    a.cluster = pl.cluster;
     return a;
 }
 
@@ -424,6 +484,26 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     if (pl.use_smem) {
         PACT_TRY(ensure_smem((const void*)rays_adj_kernel<true>, pl.smem_adj,
                              "sos_to_delays_adj: shared memory attribute"));
+        if (pl.cluster) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(pl.nb_adj);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = pl.smem_adj;
+            cfg.stream = st;
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeClusterDimension;
+            attr.val.clusterDim.x = pl.cluster;
+            attr.val.clusterDim.y = 1;
+            attr.val.clusterDim.z = 1;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, rays_adj_kernel<true>, a) != cudaSuccess)
+                return check_launch("sos_to_delays_adj kernel (cluster launch)");
+            PACT_TRY(check_launch("sos_to_delays_adj kernel"));
+            // one partial grid per cluster: a single fixed-order sum
+            reduce_stage2_kernel<<<(GG + 255) / 256, 256, 0, st>>>(a.part, pl.nparts, GG, dL_dsos, accumulate);
+            return check_launch("sos_to_delays_adj reduction");
+        }
         rays_adj_kernel<true><<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a);
         PACT_TRY(check_launch("sos_to_delays_adj kernel"));
         float* stage1 = reinterpret_cast<float*>(static_cast<char*>(ws) + pl.off_stage1);
