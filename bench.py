@@ -280,7 +280,7 @@ def run_gpu(args, cfg, case, rank, world, local):
                        "seed": args.seed, "eps": cfg.eps, "tv_lambda": cfg.tv_lambda},
             "breakdown_ms": {"sos_to_delays": statistics.mean(rays_ms), "mc_deconv_loss": statistics.mean(mcd_ms),
                              "adj_tv_adam": statistics.mean(rest_ms)},
-            "roofline": {"bound": "hbm", "kernel": "mc_deconv_loss (fused Eq. 4-7 + adjoint: 1 kernel, 2 memsets)",
+            "roofline": {"bound": "hbm", "kernel": "mc_deconv_loss (fused Eq. 4-7 + adjoint: one kernel + the dL/dw memset)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "measured" if peaks else "fallback",
                          "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},

@@ -238,7 +238,10 @@ pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* 
  * the tables, and a workspace of pact_mc_deconv_loss_tabled_workspace_size
  * bytes (the per-call scratch only); loss or dL_dw may be NULL (not both).
  * The tables carry a fingerprint of (geometry, N, P, centres pointer, m, d);
- * a call whose arguments do not match it writes NaN to loss and dL_dw.
+ * a call whose arguments do not match it writes NaN to loss and dL_dw.  They
+ * also hold the work-claim counters of the streaming kernel, which every call
+ * leaves at zero: calls that share one table set must be ordered (one stream),
+ * and after a call that reported a timeout the tables must be rebuilt.
  * Errors as pact_mc_deconv_loss, plus INVALID_ARG for NULL, misaligned or
  * small tables.
  */

@@ -91,7 +91,8 @@ struct McdArgs {
     int KT;                // 256-bin tiles
     const unsigned long long* tag;   // fingerprint the tables were built for
     unsigned long long want;         // fingerprint of this call's arguments
-    int* tile_next;                  // [KT + 1] per-tile claim counters, then a CTA-done ticket; zero at launch
+    int* sync;                       // [KT] tile claim counters, [1] CTA-done ticket: zero at launch and left
+                                     // zero by the launch (they live in the tables)
     float* loss;                     // [1] or NULL (streaming kernel: summed by the last CTA)
     float* loss_pp;                  // [N] or NULL
 };
@@ -118,9 +119,11 @@ __device__ __forceinline__ float ring_coord(float cx, float cy, float dx, float 
 //    uniformly spaced by `step`).
 __global__ void mcd_tables_kernel(Geo g, int N, int P, int F, int M, Delays dl, const int2* centres, float2* lut,
                                   float2* etab, float4* btab, float2* estep, float step,
-                                  unsigned long long* tag, unsigned long long fp) {
+                                  unsigned long long* tag, unsigned long long fp, int* sync, int nsync) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0 && blockIdx.y == 0) *tag = fp;
+    if (blockIdx.y == 0)
+        for (int q = k; q < nsync; q += gridDim.x * blockDim.x) sync[q] = 0;
     if (k >= F) return;
     int u, v;
     const float2 f = bin_freq(k, P, 1.f / (P * g.dx), u, v);
@@ -395,6 +398,8 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     __shared__ int tag_ok;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nc = EXACT ? CPT / kCh : (M + kCh - 1) / kCh;
+    int* tile_next = a.sync;                      // [KT]
+    int* done_ticket = a.sync + a.KT;             // [1]
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             if (c == 0) {                             // claim the next unit
                 unit = -1;
                 while (tried < a.KT) {
-                    const int i = atomicAdd(a.tile_next + kt, 1);
+                    const int i = atomicAdd(tile_next + kt, 1);
                     if (i < N) {
                         unit = kt * N + i;
                         break;
@@ -662,15 +667,17 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     }
 
     // The last CTA to finish sums the per-unit partials (fixed order) into the
-    // per-patch and total loss.
-    if (!a.loss && !a.loss_pp) return;
+    // per-patch and total loss and leaves the claim counters at zero.
     __shared__ int last_s;
     __shared__ float red_s[kTile / 32];
     __threadfence();
-    if (tid == 0) last_s = atomicAdd(a.tile_next + a.KT, 1) == (int)gridDim.x - 1;
+    bar_and(1, kTile, true);
+    if (tid == 0) last_s = atomicAdd(done_ticket, 1) == (int)gridDim.x - 1;
     bar_and(1, kTile, true);
     if (!last_s) return;
     __threadfence();
+    for (int t = tid; t <= a.KT; t += kTile) a.sync[t] = 0;   // tile counters and the done ticket
+    if (!a.loss && !a.loss_pp) return;
     float tot = 0.f;
     for (int i = tid; i < N; i += kTile) {
         float acc = 0.f;
@@ -711,8 +718,9 @@ __global__ void __launch_bounds__(kTPB) mcd_finalize_kernel(int N, int KT, const
 // per-bin sums, FP64 C2) that depend only on geometry, patches and delays.
 struct Plan {
     int KT, KTs;                                   // tiles of the two-pass (256) and streaming (224) kernels
-    size_t off_next, scratch;                      // loss partials, then per-tile claim counters
-    size_t t_lut, t_etab, t_btab, t_c2d, t_estep, tables;   // offsets inside the tables, their size
+    size_t scratch;                                // loss partials
+    size_t t_sync, t_lut, t_etab, t_btab, t_c2d, t_estep, tables;   // offsets inside the tables, their size
+    int nsync;                                     // ints in the sync block
     size_t total;                                  // workspace bytes without prebuilt tables
 };
 
@@ -722,9 +730,11 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     const int F = pt->p * (pt->p / 2 + 1);
     p.KT = (F + kBins - 1) / kBins;
     p.KTs = (F + kTile - 1) / kTile;
-    p.off_next = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
-    p.scratch = p.off_next + align_up((size_t)(p.KTs + 1) * sizeof(int), 256);
+    p.scratch = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
+    p.nsync = p.KTs + 1;
     size_t o = 256;                                // fingerprint header
+    p.t_sync = o;
+    o += align_up((size_t)p.nsync * sizeof(int), 256);
     p.t_lut = o;
     o += align_up((size_t)pt->n * F * sizeof(float2), 256);
     p.t_etab = o;
@@ -778,7 +788,8 @@ pact_status build_tables(const pact_geometry* g, const pact_patches* pt, const f
                                          reinterpret_cast<float2*>(t + pl.t_lut), reinterpret_cast<float2*>(t + pl.t_etab),
                                          reinterpret_cast<float4*>(t + pl.t_btab),
                                          reinterpret_cast<float2*>(t + pl.t_estep), uniform_step(d, m),
-                                         reinterpret_cast<unsigned long long*>(t), fingerprint(g, pt, d, m));
+                                         reinterpret_cast<unsigned long long*>(t), fingerprint(g, pt, d, m),
+                                         reinterpret_cast<int*>(t + pl.t_sync), pl.nsync);
     PACT_TRY(check_launch("mc_deconv_loss: tables"));
     if (fp64) {
         mcd_c2d_kernel<<<(F + 255) / 256, 256, 0, st>>>(pt->p, F, (double)g->dx, dl,
@@ -880,12 +891,11 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.KT = a.stream ? pl.KTs : pl.KT;
     a.tag = reinterpret_cast<const unsigned long long*>(tb);
     a.want = fingerprint(g, pt, d, m);
-    a.tile_next = reinterpret_cast<int*>(base + pl.off_next);
+    a.sync = reinterpret_cast<int*>(tb + pl.t_sync);
     if (!tables) PACT_TRY(build_tables(g, pt, d, m, a.fp64, pl, tb, st));
     a.loss = loss;
     a.loss_pp = loss_pp;
-    if (a.stream && cudaMemsetAsync(a.tile_next, 0, (size_t)(pl.KTs + 1) * sizeof(int), st) != cudaSuccess)
-        return check_launch("mc_deconv_loss: clearing the tile counters");
+
     if (dL_dw && !accumulate &&
         cudaMemsetAsync(dL_dw, 0, (size_t)pt->n * g->n_t * sizeof(float), st) != cudaSuccess)
         return check_launch("mc_deconv_loss: clearing dL_dw");
