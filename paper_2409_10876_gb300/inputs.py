@@ -49,6 +49,11 @@ class Config:
     ip_kind: str              # "disks_lines" | "vessels"
     sos_lo: float = 1450.0
     sos_hi: float = 1600.0
+    # ring channel data (the input of Eq. 1 for end-to-end runs)
+    rf_fs: float = 40e6                 # sample rate [Hz]
+    rf_ns: int = 4096                   # samples per transducer
+    rf_t0: float = 0.0                  # time of sample 0 [s]
+    rf_sigma: float = 3.9788735773e-8   # pulse width [s]: spectrum peak 4 MHz, half-amplitude band 1.3-7.7 MHz
 
     # ---- derived geometry (configuration readings, not method arithmetic) ----
     @property

@@ -1,0 +1,163 @@
+"""Pins of the FP64 channel-data oracle (the input of Eq. 1) against closed
+forms that do not come from the oracle: the pulse's extremes and spectrum
+(numpy FFT), straight-line times of flight in uniform media, chord lengths of
+a constant-SOS disk, the spreading and ring-offset factors, linearity, and the
+DAS value at a source whose wavefront error is the same for all transducers."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import pact_oracle as O
+from oracle import rf_oracle as R
+from paper_2409_10876_gb300 import inputs
+
+
+def _tiny(**kw):
+    return inputs.config_tiny(p=16, m=2).replace(img_h=33, img_w=33, dx=0.2e-3, n_t=24, **kw)
+
+
+def _ring(cfg, radius=None):
+    a = 2 * np.pi * np.arange(cfg.n_t) / cfg.n_t + cfg.ring_phase
+    r = cfg.ring_radius if radius is None else radius
+    return np.stack([r * np.cos(a), r * np.sin(a)], 1)
+
+
+def _pix(cfg, row, col):
+    return np.array([(col - (cfg.img_w - 1) / 2) * cfg.dx, (row - (cfg.img_h - 1) / 2) * cfg.dx])
+
+
+def _psi(t, sigma):
+    u = t / sigma
+    return u * np.exp(0.5 - 0.5 * u * u)
+
+
+def test_pulse_extremes_and_spectrum_peak():
+    sig = inputs.config_rf().rf_sigma
+    assert float(R.pulse(-sig, sig)) == pytest.approx(-1.0, abs=1e-15)
+    assert float(R.pulse(sig, sig)) == pytest.approx(1.0, abs=1e-15)
+    # extremes: the derivative vanishes at +-sigma only (central differences)
+    t = np.linspace(-6 * sig, 6 * sig, 120001)
+    y = R.pulse(t, sig).numpy()
+    assert abs(t[np.argmax(y)] - sig) < 2 * (t[1] - t[0])
+    # amplitude spectrum by numpy's FFT: peak at 1 / (2 pi sigma) and the
+    # half-amplitude band of the closed form
+    dt = sig / 200
+    tt = (np.arange(1 << 18) - (1 << 17)) * dt
+    spec = np.abs(np.fft.rfft(R.pulse(tt, sig).numpy()))
+    f = np.fft.rfftfreq(tt.size, dt)
+    assert abs(f[np.argmax(spec)] - 1 / (2 * np.pi * sig)) <= f[1]
+    lo, hi = R.pulse_band(sig)
+    above = f[spec >= 0.5 * spec.max()]
+    assert abs(above.min() - lo) <= 2 * f[1] and abs(above.max() - hi) <= 2 * f[1]
+    assert 1.0e6 < lo < 1.5e6 and 7.0e6 < hi < 8.0e6
+
+
+def test_uniform_sos_is_straight_line_time_of_flight():
+    cfg = _tiny()
+    g = O.geom(cfg)
+    sos = np.full((cfg.sos_g, cfg.sos_g), cfg.v0)
+    p0 = np.zeros((cfg.img_h, cfg.img_w))
+    p0[7, 21] = 0.8
+    fs, t0, n_s, sig = 100e6, 2e-6, 900, 3e-8
+    S = R.rf_synth(g, p0, sos, fs, t0, n_s, sig).numpy()
+    L = np.linalg.norm(_ring(cfg) - _pix(cfg, 7, 21)[None], axis=1)
+    t = t0 + np.arange(n_s) / fs
+    ref = 0.8 * _psi(t[None] - L[:, None] / cfg.v0, sig)
+    assert np.abs(S - ref).max() < 1e-12
+
+
+def test_constant_sos_disk_delays_by_the_chord():
+    """v = c inside the mask disk, v_bg = v0 outside: tau = (L - (1 - v0/c) chord)/v0
+    with the chord of the segment pixel -> transducer through the disk."""
+    c = 1580.0
+    cfg = _tiny()
+    g = O.geom(cfg)
+    sos = np.full((cfg.sos_g, cfg.sos_g), c)
+    p0 = np.zeros((cfg.img_h, cfg.img_w))
+    p0[3, 2] = 1.0                       # a corner pixel outside the disk: some rays miss it
+    p0[20, 14] = -0.5
+    fs, t0, n_s, sig = 80e6, 4e-6, 900, 4e-8
+    S = R.rf_synth(g, p0, sos, fs, t0, n_s, sig).numpy()
+    rn = _ring(cfg)
+    t = t0 + np.arange(n_s) / fs
+    ref = np.zeros_like(S)
+    for (row, col), amp in (((3, 2), 1.0), ((20, 14), -0.5)):
+        a = _pix(cfg, row, col)
+        for n in range(cfg.n_t):
+            e = rn[n] - a
+            L = np.linalg.norm(e)
+            u = e / L
+            b = a @ u
+            disc = b * b - (a @ a - cfg.mask_radius ** 2)
+            chord = 0.0
+            if disc > 0:
+                s0, s1 = np.clip([-b - math.sqrt(disc), -b + math.sqrt(disc)], 0.0, L)
+                chord = s1 - s0
+            tau = (L - (1 - cfg.v0 / c) * chord) / cfg.v0
+            ref[n] += amp * _psi(t - tau, sig)
+    assert np.abs(S - ref).max() < 1e-9
+
+
+def test_linear_in_the_source_image():
+    cfg = _tiny()
+    g = O.geom(cfg)
+    case = inputs.make_case(cfg.replace(sos_kind="blobs"), 4)
+    rng = np.random.default_rng(3)
+    p1 = (rng.uniform(size=(cfg.img_h, cfg.img_w)) < 0.03) * rng.uniform(0.2, 1.0, (cfg.img_h, cfg.img_w))
+    p2 = (rng.uniform(size=(cfg.img_h, cfg.img_w)) < 0.03) * rng.uniform(0.2, 1.0, (cfg.img_h, cfg.img_w))
+    args = (case["sos_true"], 60e6, 3e-6, 700, 4e-8)
+    s1 = R.rf_synth(g, p1, *args)
+    s2 = R.rf_synth(g, p2, *args)
+    s12 = R.rf_synth(g, 2 * p1 - 0.5 * p2, *args)
+    assert float((s12 - (2 * s1 - 0.5 * s2)).abs().max()) < 1e-10 * float(s1.abs().max())
+
+
+def test_spreading_and_ring_offset():
+    cfg = _tiny()
+    g = O.geom(cfg)
+    sos = np.full((cfg.sos_g, cfg.sos_g), cfg.v0)
+    p0 = np.zeros((cfg.img_h, cfg.img_w))
+    p0[11, 26] = 1.0
+    fs, t0, n_s, sig, dr = 100e6, 2e-6, 1000, 3e-8, 0.3e-3
+    S = R.rf_synth(g, p0, sos, fs, t0, n_s, sig, spread=0.5, ring_dr=dr).numpy()
+    Rs = cfg.ring_radius + dr
+    L = np.linalg.norm(_ring(cfg, Rs) - _pix(cfg, 11, 26)[None], axis=1)
+    t = t0 + np.arange(n_s) / fs
+    ref = np.sqrt(Rs / L)[:, None] * _psi(t[None] - L[:, None] / cfg.v0, sig)
+    assert np.abs(S - ref).max() < 1e-12
+    # a channel subset gives those rows of the full record
+    sub = R.rf_synth(g, p0, sos, fs, t0, n_s, sig, spread=0.5, ring_dr=dr, channels=[0, 5, 23]).numpy()
+    assert np.array_equal(sub, S[[0, 5, 23]])
+
+
+def test_das_of_a_centred_source_follows_the_pulse():
+    """A source at the disk centre in a constant-SOS disk has the same wavefront
+    error w = (1 - v0/c) R_mask on every ray, so Eq. 1 at the source gives
+    y(d) = N_t psi((w - d)/v0) (up to the linear interpolation of S)."""
+    c = 1560.0
+    cfg = _tiny()
+    g = O.geom(cfg)
+    sos = np.full((cfg.sos_g, cfg.sos_g), c)
+    p0 = np.zeros((cfg.img_h, cfg.img_w))
+    p0[16, 16] = 1.0                     # 33 x 33 image: pixel (16, 16) is the origin
+    fs, t0, n_s, sig = 2e9, 4e-6, 14000, 4e-8
+    S = R.rf_synth(g, p0, sos, fs, t0, n_s, sig)
+    w = (1 - cfg.v0 / c) * cfg.mask_radius
+    d = np.array([w - 2 * sig * cfg.v0, w - sig * cfg.v0, w, w + 0.5 * sig * cfg.v0])
+    y = R.das_at(g, S, fs, t0, d, torch.tensor([16]), torch.tensor([16])).numpy()[:, 0]
+    ref = cfg.n_t * _psi((w - d) / cfg.v0, sig)
+    assert np.abs(y - ref).max() < 1e-3 * cfg.n_t
+
+
+def test_das_at_equals_the_full_stack():
+    cfg = _tiny()
+    g = O.geom(cfg)
+    rng = np.random.default_rng(8)
+    rf = rng.standard_normal((cfg.n_t, 300))
+    d = np.array([-2e-4, 1e-4])
+    full = O.das_stack(g, rf, 40e6, 1e-6, d).numpy()
+    rows, cols = np.array([0, 5, 16, 32]), np.array([32, 7, 16, 0])
+    part = R.das_at(g, rf, 40e6, 1e-6, d, torch.tensor(rows), torch.tensor(cols)).numpy()
+    assert np.abs(part - full[:, rows, cols]).max() < 1e-12
