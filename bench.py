@@ -369,7 +369,8 @@ def run_gpu(args, cfg, case, rank, world, local):
         line["variants"] = {"neural_field": nf_variant(args, cfg, case, pb, Y, flush, stream),
                             "siren_field": siren_variant(args, cfg, case, pb, Y, flush, stream),
                             "das_stack": das_variant(dev, flush, stream),
-                            "channels": channels_variant(args, cfg, dev, flush, stream)}
+                            "channels": channels_variant(args, cfg, dev, flush, stream),
+                            "channel_data": channel_data_variant(args, dev, flush, stream)}
     if rank == 0 and not args.no_warm_start:
         line["warm_start"] = warm_start_run(args, cfg, pb, dev)
     if rank == 0:
@@ -440,6 +441,82 @@ def siren_variant(args, cfg, case, pb, Y, flush, stream):
     ms = _time_graph(g, flush, stream, steps)
     return {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
             "dtype": "f32", "params": int(rec.params.numel()), "gpu_launches_per_step": 11}
+
+
+def channel_data_variant(args, dev, flush, stream):
+    """End to end from channel data on the 1024 x 1024 / 1024-element workload:
+    synthetic ring RF (4096 samples at 40 MHz, straight-ray times of flight
+    through a 256 x 256 SOS map, vessel-tree sources) -> DAS stack (32 x
+    1024 x 1024) -> patch spectra (3721 patches of 64 x 64: 2.0 GB) ->
+    recovery iterations with the pixel-grid and the neural-field SOS.  The
+    fused pass is also timed alone: its spectra are 16x the L2, so it is the
+    HBM-bound figure."""
+    import torch
+    from paper_2409_10876_gb300 import inputs, pact
+    from paper_2409_10876_gb300.recovery import NFRecovery, PGRecovery
+    cfg = inputs.config_rf()
+    case = inputs.make_case(cfg, args.seed)
+    pb = pact.Problem(cfg, dev)
+    ip = torch.as_tensor(case["ip"], device=dev)
+    sos_t = torch.as_tensor(case["sos_true"], device=dev)
+    rf = torch.empty((cfg.n_t, cfg.rf_ns), dtype=torch.float32, device=dev)
+    ws = pact._ws(pact.rf_synth_workspace_size(pb, 65536), dev)
+    stack = torch.empty((cfg.m, cfg.img_h, cfg.img_w), dtype=torch.float32, device=dev)
+    Y = torch.empty(pb.spectra_shape(cfg.m), dtype=torch.complex64, device=dev)
+
+    def timed(fn, reps):
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    def synth():
+        pact.rf_synth(pb, ip, sos_t, cfg.rf_fs, cfg.rf_t0, cfg.rf_ns, cfg.rf_sigma, rf=rf, ws=ws)
+
+    synth()
+    t_rf = timed(synth, 2)
+    t_das = timed(lambda: pact.das_stack(pb, rf, cfg.rf_fs, cfg.rf_t0, case["d"], stack), 2)
+    t_fft = timed(lambda: pact.patch_fft(pb, stack, Y), 3)
+    emitting = int((ip != 0).sum().item())
+    out = {"workload": "rf1024_ring1024_p64_m32: 1024x1024 @0.05mm, 1024-el ring R=40mm, 4096 samples @40 MHz, "
+                       "3721 patches 64x64, M=32, SOS 256x256",
+           "rf_synth_ms": t_rf, "emitting_pixels": emitting,
+           "das_stack_ms": t_das, "patch_fft_ms": t_fft}
+    rec = PGRecovery(pb, Y, case["d"], cfg.eps, 1e-4, cfg.lr, torch.as_tensor(case["sos_init"]),
+                     torch.as_tensor(case["mask"]))
+    g = rec.capture()
+    for _ in range(3):
+        g.replay()
+    ms = _time_graph(g, flush, stream, 20)
+    out["pixel_grid"] = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_iter": statistics.mean(ms),
+                         "loss_after_23": rec.loss()}
+    gm = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gm):
+        pact.mc_deconv_loss(pb, rec.w, rec.Y, rec.d, rec.eps, want_grad=True, out=rec.out, ws=rec.ws_mcd,
+                            tables=rec.tables)
+    for _ in range(3):
+        gm.replay()
+    ms = _time_graph(gm, flush, stream, 20)
+    alg = 8 * pb.n * cfg.m * pb.f + 8 * pb.n * pb.n_t
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else None
+    peak, src = (peaks["hbm_gbs"], "measured") if peaks else (6800.0, "fallback")
+    ach = alg / (statistics.mean(ms) * 1e-3) / 1e9
+    out["mc_deconv_loss"] = {"ms": statistics.mean(ms), "algorithmic_bytes": alg, "achieved_gbs": ach,
+                             "peak_gbs": peak, "peak_source": src, "frac": ach / peak}
+    del rec, g, gm
+    nf = NFRecovery(pb, Y, case["d"], cfg.eps, 5e-3, inputs.nf_init(args.seed), case["mask"])
+    g = nf.capture()
+    for _ in range(3):
+        g.replay()
+    ms = _time_graph(g, flush, stream, 20)
+    out["neural_field"] = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_iter": statistics.mean(ms)}
+    return out
 
 
 def das_variant(dev, flush, stream):

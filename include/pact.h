@@ -106,6 +106,58 @@ pact_status pact_das_stack(const pact_geometry* g, const float* rf, int n_s, flo
                            const float* d, int m, float* stack, void* stream);
 
 /*
+ * Synthetic ring channel data: the input of Eq. 1 for end-to-end runs.
+ * The paper's data are the time derivative of the photoacoustic pressure,
+ * S = -2 dp/dt (Sec. S1.1); here every pixel p of the initial-pressure image
+ * p0 emits one pulse that reaches transducer n after the straight-ray time
+ * of flight of Eq. 2-3,
+ *   tau(p, n) = int dl / v = (|r_p - r_n| - w(p, n)) / v0,
+ * with w the wavefront error of pact_sos_to_delays on the segment r_p -> r_n
+ * (same quadrature, mask and background), and
+ *   rf[n][q] = sum_p p0_p (R_s / |r_p - r_n|)^spread psi(t0 + q/fs - tau(p, n)),
+ *   psi(t) = (t / sigma) exp(1/2 - t^2 / (2 sigma^2)),
+ * minus the derivative of a Gaussian pressure pulse, extremes -+1 at
+ * t = -+sigma, amplitude spectrum peaking at 1 / (2 pi sigma).  psi is
+ * evaluated within 6 sigma of each arrival (|psi| < 2e-7 beyond).
+ * Model mismatches for robustness runs: spread = 1/2 adds cylindrical
+ * spreading; ring_dr moves the receiving ring to radius R_s = R + ring_dr
+ * while the geometry (and DAS) keep R.  spread = ring_dr = 0 is the model
+ * the method assumes.
+ */
+typedef struct pact_rf_params {
+    float fs;        /* sample rate [Hz] > 0 */
+    float t0;        /* time of sample 0 [s] */
+    int   n_s;       /* samples per transducer, 1 <= n_s <= 49152 */
+    float sigma;     /* pulse width [s] > 0, 6 sigma fs <= 1024 */
+    float spread;    /* amplitude exponent (0: none, 0.5: cylindrical) */
+    float ring_dr;   /* receiving-ring radius offset [m], R + ring_dr > 0 */
+} pact_rf_params;
+
+/*
+ * Workspace bytes for pact_rf_synth processing up to `pixels_per_pass`
+ * pixels per pass (N_t floats per pixel: the transposed wavefront errors of
+ * one pass).  Any workspace of at least pact_rf_synth_workspace_size(g, 1)
+ * bytes works; larger ones take fewer passes.  0 for an invalid geometry.
+ */
+size_t pact_rf_synth_workspace_size(const pact_geometry* g, int pixels_per_pass);
+
+/*
+ * rf = channel data of p0 (see above), overwritten.
+ *   p0   DEVICE float [H][W]    initial pressure (pixels equal to 0 emit nothing)
+ *   sos  DEVICE float [G][G]    node SOS [m/s]
+ *   rp   HOST                   sampling, pulse and mismatch parameters
+ *   rf   DEVICE float [N_t][n_s] output
+ *   ws   DEVICE workspace, 256-byte aligned, ws_bytes >= pact_rf_synth_workspace_size(g, 1)
+ * The passes over pixel blocks sum into rf in a fixed order; within a pass
+ * the pulses of one transducer are summed with shared-memory atomics (the
+ * rounding order can vary from run to run).
+ * Errors: INVALID_ARG for null pointers, bad parameters or a small or
+ * misaligned workspace; SHAPE for n_s or pulse widths beyond the limits.
+ */
+pact_status pact_rf_synth(const pact_geometry* g, const float* p0, const float* sos, const pact_rf_params* rp,
+                          float* rf, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Patch spectra (Sec. S1.4, the Y_i(k; d_j) of Eq. 5): crop each of the m
  * channels around every patch centre, multiply by the Gaussian window
  * exp(-|rho|^2 / (2 sigma^2)), FWHM = 2 sqrt(2 ln 2) sigma, rho measured from

@@ -32,6 +32,12 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 pact_status check_geometry(const pact_geometry* g);
 pact_status check_patches(const pact_patches* pt);
 
+// Eq. 3 wavefront errors from the image pixels pix0 .. pix0 + npix - 1 with
+// p0 != 0 to every transducer of g (rays.cu), written transposed:
+// wT[n * ld + (pix - pix0)]; entries of pixels with p0 == 0 are not written.
+pact_status launch_pixel_rays(const pact_geometry* g, const float* sos, const float* p0, int pix0, int npix,
+                              float* wT, int ld, cudaStream_t st);
+
 #define PACT_TRY(expr)                       \
     do {                                     \
         pact_status _s = (expr);             \

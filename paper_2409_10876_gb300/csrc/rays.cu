@@ -157,28 +157,19 @@ __device__ __forceinline__ void load_excess(float* dv, const float* sos, int G, 
     }
 }
 
-// Warp w of a CTA takes every nw-th ray of the CTA's run; it sets up 32 of its
-// rays at once (one per lane) and then integrates them one after the other
-// (lanes over samples), taking each ray's setup by shuffles.
-// SMEM: the SOS excess grid is staged in shared memory (else read from global).
-template <bool SMEM>
-__global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
-    extern __shared__ float dv_s[];
-    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
+// Warp `warp` of `nw` integrates the rays r'_c -> r_n, n = n0 + warp, n0 + warp
+// + nw, ... < n1 (neighbouring rays have similar lengths, so striding balances
+// the warps): it sets up 32 of its rays at once (one per lane) and then
+// integrates them one after the other (lanes over samples), taking each ray's
+// setup by shuffles; out(n, w) runs on the lane that owns ray n.
+// SMEM: the SOS excess grid dv is staged in shared memory (else read from global).
+template <bool SMEM, class Out>
+__device__ __forceinline__ void warp_rays(const RayArgs& a, const float* dv, int pitch, float2 c, int n0, int n1,
+                                          int warp, int nw, Out out) {
+    const int G = a.g.G, lane = threadIdx.x & 31;
     const float v0 = a.g.v0;
-    if (SMEM) {
-        load_excess(dv_s, a.sos, G, pitch, v0);
-        __syncthreads();
-    }
-    int i, n0, n1;
-    cta_rays(a, i, n0, n1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int2 cc = a.centres[i];
-    const float2 c = pixel_xy(a.g, cc.x, cc.y);
     const float out_coef = (a.g.v_bg - v0) / a.g.v_bg;
     const float h = a.g.h;
-    // warp w takes rays n0 + w, n0 + w + nw, ... (neighbouring rays have similar
-    // lengths, so striding balances the warps), 32 at a time
     const int nmine = n1 - n0 > warp ? (n1 - n0 - warp + nw - 1) / nw : 0;
     for (int kb = 0; kb < nmine; kb += 32) {
         const int cnt = min(32, nmine - kb);
@@ -195,20 +186,58 @@ __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
             for (int m = m0; m < mf; ++m) {
                 const float s = (m + 0.5f) * h;
                 const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = SMEM ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                const float d = SMEM ? interp(dv, pitch, b) : interp_global(a.sos, G, v0, b);
                 acc += __fdividef(d, v0 + d);
             }
             acc *= h;
             if (m0 <= ry.nfull && ry.nfull < m1) {    // last partial step, weighted by its length
                 const float s = ry.nfull * h + 0.5f * ry.rem;
                 const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = SMEM ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
+                const float d = SMEM ? interp(dv, pitch, b) : interp_global(a.sos, G, v0, b);
                 acc = fmaf(ry.rem, __fdividef(d, v0 + d), acc);
             }
             acc = warp_sum(acc);
             if (lane == r) my_w = fmaf(ry.L - ry.chord, out_coef, acc);
         }
-        if (lane < cnt) a.w[(size_t)i * a.g.n_t + nl] = my_w;
+        if (lane < cnt) out(nl, my_w);
+    }
+}
+
+// CTA b: rays [n0, n1) of patch b / splits.
+template <bool SMEM>
+__global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
+    extern __shared__ float dv_s[];
+    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
+    if (SMEM) {
+        load_excess(dv_s, a.sos, G, pitch, a.g.v0);
+        __syncthreads();
+    }
+    int i, n0, n1;
+    cta_rays(a, i, n0, n1);
+    const int2 cc = a.centres[i];
+    float* w = a.w + (size_t)i * a.g.n_t;
+    warp_rays<SMEM>(a, dv_s, pitch, pixel_xy(a.g, cc.x, cc.y), n0, n1, threadIdx.x >> 5, blockDim.x >> 5,
+                    [&](int n, float wn) { w[n] = wn; });
+}
+
+// Rays from image pixels (sources of channel data): the CTAs take the pixels
+// pix0 + q, q = blockIdx.x, blockIdx.x + gridDim.x, ... < npix, skip those with
+// p0 == 0, and write w from pixel q to every transducer n at wT[n * ld + q].
+template <bool SMEM>
+__global__ void __launch_bounds__(512) rays_pix_kernel(const RayArgs a, const float* p0, int pix0, int npix,
+                                                       float* wT, int ld) {
+    extern __shared__ float dv_s[];
+    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
+    if (SMEM) {
+        load_excess(dv_s, a.sos, G, pitch, a.g.v0);
+        __syncthreads();
+    }
+    for (int q = blockIdx.x; q < npix; q += gridDim.x) {
+        const int pix = pix0 + q;
+        if (p0[pix] == 0.f) continue;                 // the same for the whole CTA
+        const int row = pix / a.g.W, col = pix - (pix / a.g.W) * a.g.W;
+        warp_rays<SMEM>(a, dv_s, pitch, pixel_xy(a.g, row, col), 0, a.g.n_t, threadIdx.x >> 5, blockDim.x >> 5,
+                        [&](int n, float wn) { wT[(size_t)n * ld + q] = wn; });
     }
 }
 
@@ -438,6 +467,34 @@ RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl
 }
 
 }  // namespace
+
+pact_status launch_pixel_rays(const pact_geometry* g, const float* sos, const float* p0, int pix0, int npix,
+                              float* wT, int ld, cudaStream_t st) {
+    if (npix <= 0) return PACT_OK;
+    const int G = g->sos_g;
+    const size_t gbytes = (size_t)G * smem_pitch(G) * sizeof(float);
+    const bool smem = gbytes <= kMaxSmem;
+    const void* fn = smem ? (const void*)rays_pix_kernel<true> : (const void*)rays_pix_kernel<false>;
+    if (smem) PACT_TRY(ensure_smem(fn, gbytes, "rf_synth: shared memory attribute"));
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, smem ? gbytes : 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int grid = std::min(npix, num_sms() * per_sm);
+    RayArgs a = {};
+    a.g = make_geo(g);
+    a.N = 0;
+    a.sos = sos;
+    a.use_smem = smem;
+    if (smem)
+        rays_pix_kernel<true><<<grid, 512, gbytes, st>>>(a, p0, pix0, npix, wT, ld);
+    else
+        rays_pix_kernel<false><<<grid, 512, 0, st>>>(a, p0, pix0, npix, wT, ld);
+    return check_launch("rf_synth: ray kernel");
+}
+
 }  // namespace pact
 
 using namespace pact;

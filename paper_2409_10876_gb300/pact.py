@@ -36,6 +36,11 @@ class _PatchesC(ctypes.Structure):
                 ("window_fwhm", ctypes.c_float)]
 
 
+class RfParams(ctypes.Structure):
+    _fields_ = [("fs", ctypes.c_float), ("t0", ctypes.c_float), ("n_s", ctypes.c_int),
+                ("sigma", ctypes.c_float), ("spread", ctypes.c_float), ("ring_dr", ctypes.c_float)]
+
+
 _VP, _I, _F, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
 _GP = ctypes.POINTER(Geometry)
 _PP = ctypes.POINTER(_PatchesC)
@@ -44,6 +49,8 @@ _SIGS = {
     "pact_version": ([], ctypes.c_char_p),
     "pact_last_error_message": ([], ctypes.c_char_p),
     "pact_das_stack": ([_GP, _VP, _I, _F, _F, _VP, _I, _VP, _VP], _I),
+    "pact_rf_synth_workspace_size": ([_GP, _I], _SZ),
+    "pact_rf_synth": ([_GP, _VP, _VP, ctypes.POINTER(RfParams), _VP, _VP, _SZ, _VP], _I),
     "pact_patch_fft": ([_GP, _PP, _VP, _I, _VP, _VP], _I),
     "pact_sos_to_delays": ([_GP, _PP, _VP, _VP, _VP], _I),
     "pact_sos_to_delays_adj_workspace_size": ([_GP, _PP], _SZ),
@@ -194,6 +201,30 @@ def das_stack(pb: Problem, rf, fs: float, t0: float, d, stack=None):
     _dev(stack, "stack", torch.float32, (m, pb.cfg.img_h, pb.cfg.img_w))
     _check(L.pact_das_stack(pb.gp(), _ptr(rf), rf.shape[1], fs, t0, dp, m, _ptr(stack), _stream()), "das_stack")
     return stack
+
+
+def rf_synth_workspace_size(pb: Problem, pixels_per_pass: int) -> int:
+    return int(load().pact_rf_synth_workspace_size(pb.gp(), int(pixels_per_pass)))
+
+
+def rf_synth(pb: Problem, p0, sos, fs: float, t0: float, n_s: int, sigma: float, spread: float = 0.0,
+             ring_dr: float = 0.0, rf=None, ws=None, pixels_per_pass: int = 65536):
+    """Synthetic ring channel data rf [N_t, n_s] of the initial pressure p0 [H, W]
+    with straight-ray times of flight through the SOS grid [G, G] (the input of
+    Eq. 1).  The workspace (made if None) sets the pixels per pass."""
+    L = load()
+    cfg = pb.cfg
+    p0 = _dev(p0, "p0", torch.float32, (cfg.img_h, cfg.img_w))
+    sos = _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    if rf is None:
+        rf = _empty((pb.n_t, int(n_s)), torch.float32, p0.device)
+    _dev(rf, "rf", torch.float32, (pb.n_t, int(n_s)))
+    if ws is None:
+        ws = _ws(rf_synth_workspace_size(pb, min(int(pixels_per_pass), cfg.img_h * cfg.img_w)), p0.device)
+    rp = RfParams(float(fs), float(t0), int(n_s), float(sigma), float(spread), float(ring_dr))
+    _check(L.pact_rf_synth(pb.gp(), _ptr(p0), _ptr(sos), ctypes.byref(rp), _ptr(rf), _ptr(ws), ws.numel(),
+                           _stream()), "rf_synth")
+    return rf
 
 
 def patch_fft(pb: Problem, stack, Y=None):

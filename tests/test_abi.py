@@ -102,3 +102,26 @@ def test_workspace_sizes_positive(lib):
     assert lib.pact_mc_deconv_loss_workspace_size(ctypes.byref(g), ctypes.byref(pt), 32) > cfg.n_patches * 4
     assert lib.pact_sos_to_delays_adj_workspace_size(ctypes.byref(g), ctypes.byref(pt)) >= cfg.sos_g ** 2 * 4
     assert lib.pact_stitch_workspace_size(ctypes.byref(g), ctypes.byref(pt)) >= 2 * 512 * 512 * 4
+
+
+def test_rf_synth_rejects_bad_parameters(lib):
+    cfg = inputs.config_tiny()
+    g = _geom(cfg)
+    ws_ok = lib.pact_rf_synth_workspace_size(ctypes.byref(g), 1)
+    assert ws_ok >= cfg.n_t * 4
+    assert lib.pact_rf_synth_workspace_size(ctypes.byref(g), 0) == 0
+    fake = 4096                                      # never dereferenced: the calls fail on the host
+    for rp, ws, code, msg in [
+        (pact.RfParams(0.0, 0.0, 100, 4e-8, 0.0, 0.0), fake, 1, b"fs"),
+        (pact.RfParams(40e6, 0.0, 100, -1.0, 0.0, 0.0), fake, 1, b"sigma"),
+        (pact.RfParams(40e6, 0.0, 100, 4e-8, 0.0, -1.0), fake, 1, b"ring"),
+        (pact.RfParams(40e6, 0.0, 1 << 20, 4e-8, 0.0, 0.0), fake, 2, b"n_s"),
+        (pact.RfParams(40e6, 0.0, 100, 1e-3, 0.0, 0.0), fake, 2, b"sigma"),
+        (pact.RfParams(40e6, 0.0, 100, 4e-8, 0.0, 0.0), fake + 8, 1, b"aligned"),
+        (pact.RfParams(40e6, 0.0, 100, 4e-8, 0.0, 0.0), None, 1, b"workspace"),
+    ]:
+        st = lib.pact_rf_synth(ctypes.byref(g), fake, fake, ctypes.byref(rp), fake, ws, ws_ok, None)
+        assert st == code, (rp.fs, rp.n_s, st)
+        assert msg in lib.pact_last_error_message()
+    rp = pact.RfParams(40e6, 0.0, 100, 4e-8, 0.0, 0.0)
+    assert lib.pact_rf_synth(ctypes.byref(g), fake, fake, ctypes.byref(rp), fake, fake, 16, None) == 1

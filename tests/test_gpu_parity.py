@@ -115,6 +115,27 @@ def test_sos_to_delays_adj_full_size():
     assert rel(g, ref) <= 2e-3
 
 
+def test_sos_to_delays_and_adj_channel_data_size_sampled():
+    """1024 x 1024 image, 3721 patches, 1024 transducers, 256 x 256 SOS grid
+    (too large to stage in shared memory: the kernels read the grid from
+    global memory and the adjoint scatters with global atomics)."""
+    cfg = inputs.config_rf()
+    case = inputs.make_case(cfg.replace(m=1), 6)
+    pb = pact.Problem(cfg, DEV)
+    sos = torch.as_tensor(case["sos_true"], device=DEV)
+    w = cpu(pact.sos_to_delays(pb, sos))
+    idx = [0, 61, 1860, 2999, 3720]
+    ref = O.wavefront_errors(O.geom(cfg), case["sos_true"], case["centres"][idx]).numpy()
+    assert rel(w[idx], ref) <= 1e-4
+    rng = np.random.default_rng(7)
+    r = np.zeros((cfg.n_patches, cfg.n_t), np.float32)
+    idx = [100, 1900, 3600]
+    r[idx] = rng.standard_normal((len(idx), cfg.n_t))
+    g = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV)))
+    ref = O.sos_to_delays_adj(O.geom(cfg), case["sos_true"], case["centres"][idx], r[idx]).numpy()
+    assert rel(g, ref) <= 2e-3
+
+
 # ------------------------------------------------------------------ Eq. 4-5
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -240,6 +261,18 @@ def test_mc_deconv_loss_full_size_sampled():
     cfg = inputs.config_full()
     Y, w, d = _mcd_case(cfg, 15)
     _check_mcd(cfg, Y, w, d, cfg.eps, idx=[0, 11, 72, 100, 143])
+
+
+def test_mc_deconv_loss_channel_data_size_sampled():
+    """3721 patches of 64 x 64, 32 channels, 1024 transducers: 2.0 GB of
+    spectra, far beyond L2; the oracle checks a sample of patches."""
+    cfg = inputs.config_rf()
+    rng = np.random.default_rng(31)
+    z = rng.standard_normal((cfg.n_patches, cfg.m, cfg.p, cfg.p // 2 + 1, 2), dtype=np.float32)
+    Y = z.view(np.complex64)[..., 0]
+    del z
+    w = inputs.random_wavefronts(cfg.n_patches, cfg.n_t, rng)
+    _check_mcd(cfg, Y, w, cfg.delays(), cfg.eps, idx=[0, 60, 1234, 1860, 3720])
 
 
 def test_mc_deconv_loss_adj_scale_and_accumulate():
