@@ -241,134 +241,203 @@ __global__ void __launch_bounds__(512) rays_pix_kernel(const RayArgs a, const fl
     }
 }
 
-__device__ __forceinline__ void scatter4(float* acc, int pitch, int idx, float c00, float c01, float c10,
+__device__ __forceinline__ void scatter4(int* acc, int pitch, int idx, float S, float c00, float c01, float c10,
                                          float c11) {
-    atomicAdd(acc + idx, c00);
-    atomicAdd(acc + idx + 1, c01);
-    atomicAdd(acc + idx + pitch, c10);
-    atomicAdd(acc + idx + pitch + 1, c11);
+    atomicAdd(acc + idx, __float2int_rn(c00 * S));
+    atomicAdd(acc + idx + 1, __float2int_rn(c01 * S));
+    atomicAdd(acc + idx + pitch, __float2int_rn(c10 * S));
+    atomicAdd(acc + idx + pitch + 1, __float2int_rn(c11 * S));
 }
 
-// CTA b takes the rays r = b, b + nb, b + 2 nb, ... of the flat (patch,
-// transducer) index r = i N_t + n, and each warp a contiguous block of them, so
-// that its warps integrate rays of different patches and directions at the same
-// time (rays of one patch all start at the same centre, where their scatters
-// would collide).  A lane walks a contiguous
-// run of samples of one ray and keeps the bilinear weights of the current cell
-// in registers, adding them to the shared grid only when the walk leaves the
-// cell.
-template <bool SMEM>
-__global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a) {
-    extern __shared__ float sm[];
-    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
-    const int GP = G * pitch;
-    const float v0 = a.g.v0;
-    float* dv_s = sm;
-    float* acc_s = sm + GP;
-    if (SMEM) {
-        for (int q = threadIdx.x; q < GP; q += blockDim.x) acc_s[q] = 0.f;
-        load_excess(dv_s, a.sos, G, pitch, v0);
-    }
+__device__ __forceinline__ float block_min(float x, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = x;
     __syncthreads();
-    float* acc = SMEM ? acc_s : a.out;
+    x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : INFINITY;
+    if (wid == 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    __syncthreads();
+    return x;
+}
+
+// Ray adjoint.  CTA b takes the rays r = b, b + nb, b + 2 nb, ... of the flat
+// (patch, transducer) index r = i N_t + n, and each warp a contiguous block of
+// them, so that its warps integrate rays of different patches and directions
+// at the same time (rays of one patch all start at the same centre, where their
+// scatters would collide).  A lane walks a contiguous run of samples of one ray
+// and keeps the bilinear weights of the current cell in registers, adding them
+// to the shared grid only when the walk leaves the cell.
+//
+// The shared grid holds 32-bit fixed-point sums (shared-memory integer atomics
+// are single instructions; float ones are compare-and-swap loops), which also
+// makes the result independent of the order of the additions.  Every
+// contribution is g h_s v0 / v^2 times a bilinear weight; v is a convex
+// combination of node values, so v >= vmin, and the weights h_s of a ray add up
+// to its chord <= 2 mask_r.  The absolute sum of all contributions of the CTA
+// is therefore at most  Mb = sum_r |g_r| 2 mask_r v0 / vmin^2 , and with the
+// scale S = 2^30 / Mb no partial sum of a node can leave the int32 range
+// (each flush rounds by at most 1/2).  A non-finite bound (NaN in dL/dw or the
+// SOS, or SOS <= 0) turns the CTA's partial grid into NaN.
+//
+// Grids are processed in bands of R cell rows (node rows r0 .. r0 + R), so
+// that the SOS excess rows and the accumulator of a band fit in shared memory
+// for every G <= 512; a ray visits each band with the samples whose cell row
+// lies in it.  Node row r0 + R is shared with the next band: its sums move to
+// that band's first row.  With clusters, the CTAs of a cluster sum each band of
+// their grids through distributed shared memory in a fixed order of ranks and
+// write one partial grid per cluster; otherwise every CTA writes its own.
+__global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int R, int nbands) {
+    extern __shared__ float sm[];
+    __shared__ float red_s[32];
+    __shared__ float scale_s[2];      // S and 1/S (NaN: poisoned)
+    const int G = a.g.G, pitch = smem_pitch(G);
+    float* dv_s = sm;                                              // [R + 1][pitch]
+    int* acc_s = reinterpret_cast<int*>(sm + (R + 1) * pitch);      // [R + 1][pitch]
+    const float v0 = a.g.v0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nrays = a.N * a.g.n_t, nb = gridDim.x;
     const int mine = nrays > (int)blockIdx.x ? (nrays - (int)blockIdx.x + nb - 1) / nb : 0;   // rays of this CTA
-    // warp w takes the contiguous block t0 <= t < t1 of the CTA's rays t (r = b + nb t), so that the
-    // warps work on rays of different patches at any moment (rays of one patch share their start)
+
+    // fixed-point scale of this CTA
+    float gsum = 0.f, vmin = INFINITY, bad = 0.f;
+    for (int t = threadIdx.x; t < mine; t += blockDim.x) gsum += fabsf(a.dLdw[(size_t)blockIdx.x + (size_t)nb * t]);
+    for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+        const float v = __ldg(a.sos + q);
+        if (!(v > 0.f) || !isfinite(v)) bad = 1.f;
+        vmin = fminf(vmin, v);
+    }
+    gsum = block_sum(gsum, red_s);
+    bad = block_sum(bad, red_s);
+    vmin = block_min(vmin, red_s);
+    if (threadIdx.x == 0) {
+        const float vm = vmin * (1.f - 1e-5f);
+        const float Mb = gsum * (2.f * a.g.mask_r) * (v0 / (vm * vm));
+        const bool poison = bad > 0.f || !isfinite(Mb);
+        const float S = Mb > 0.f ? fminf(1073741824.f / Mb, 1e30f) : 0.f;
+        scale_s[0] = poison ? 0.f : S;
+        scale_s[1] = poison ? __int_as_float(0x7fc00000) : (S > 0.f ? 1.f / S : 0.f);
+    }
+    __syncthreads();
+    const float S = scale_s[0];
+
+    // warp w takes the contiguous block t0 <= t < t1 of the CTA's rays t (r = b + nb t)
     const int t0 = (int)((long long)mine * warp / nw), t1 = (int)((long long)mine * (warp + 1) / nw);
     const int nwarp = t1 - t0;
     const float h = a.g.h;
-    for (int kb = 0; kb < nwarp; kb += 32) {
-        const int cnt = min(32, nwarp - kb);
-        const int r = (int)blockIdx.x + nb * (t0 + kb + min(lane, cnt - 1));
-        const int i = r / a.g.n_t, n = r - (r / a.g.n_t) * a.g.n_t;
-        const int2 cc = a.centres[i];
-        const Ray mine_ray = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
-        const float my_g = lane < cnt ? a.dLdw[r] : 0.f;
-        for (int rr = 0; rr < cnt; ++rr) {
-            const float gr = __shfl_sync(0xffffffffu, my_g, rr);
-            if (gr == 0.f) continue;
-            const Ray ry = shfl_ray(mine_ray, rr);
-            const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
-            const int per = (nsamp + 31) >> 5;
-            const int m0 = lane * per, m1 = min(nsamp, m0 + per);
-            const float gv0 = gr * v0;
-            int cur = -1;
-            float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
-            for (int m = m0; m < m1; ++m) {
-                const bool last = m >= ry.nfull;
-                const float s = last ? ry.nfull * h + 0.5f * ry.rem : (m + 0.5f) * h;
-                const float wgt = last ? ry.rem : h;
-                const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = SMEM ? interp(dv_s, pitch, b) : interp_global(a.sos, G, v0, b);
-                const float iv = __fdividef(1.f, v0 + d);
-                const float coef = gv0 * wgt * iv * iv;
-                if (b.idx != cur) {
-                    if (cur >= 0) scatter4(acc, pitch, cur, c00, c01, c10, c11);
-                    cur = b.idx;
-                    c00 = c01 = c10 = c11 = 0.f;
-                }
-                const float cy0 = coef * (1.f - b.ty), cy1 = coef * b.ty;
-                c00 = fmaf(cy0, 1.f - b.tx, c00);
-                c01 = fmaf(cy0, b.tx, c01);
-                c10 = fmaf(cy1, 1.f - b.tx, c10);
-                c11 = fmaf(cy1, b.tx, c11);
-            }
-            if (cur >= 0) scatter4(acc, pitch, cur, c00, c01, c10, c11);
+    namespace cg = cooperative_groups;
+    for (int band = 0; band < nbands; ++band) {
+        const bool last_band = band == nbands - 1;
+        const int r0 = band * R;
+        const int r1 = last_band ? G - 1 : r0 + R;        // cell rows r0 <= iy < r1
+        const int rows = min(R + 1, G - r0);              // node rows r0 .. r0 + rows - 1 of the band
+        for (int q = threadIdx.x; q < rows * G; q += blockDim.x) {
+            const int p = q / G, c = q - (q / G) * G;
+            dv_s[p * pitch + c] = __ldg(a.sos + (size_t)(r0 + p) * G + c) - v0;
         }
-    }
-    if (SMEM && a.cluster) {
-        // the CTAs of a cluster sum their shared grids through distributed shared
-        // memory (CTA rank r takes a band of rows, in a fixed order of ranks) and
-        // write one partial grid per cluster
-        namespace cg = cooperative_groups;
-        cg::cluster_group cl = cg::this_cluster();
-        cl.sync();
-        const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-        const int rows = (G + csize - 1) / csize;
-        const int r0 = min(G, rank * rows), r1 = min(G, r0 + rows);
-        float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G;
-        for (int q = threadIdx.x; q < (r1 - r0) * G; q += blockDim.x) {
-            const int p = r0 + q / G, cq = q - (q / G) * G;
-            float sum = 0.f;
-            for (int r = 0; r < csize; ++r) sum += cl.map_shared_rank(acc_s, r)[p * pitch + cq];
-            dst[p * G + cq] = sum;
-        }
-        cl.sync();                                   // remote reads end before any CTA exits
-    } else if (SMEM) {
+        for (int q = threadIdx.x + (band > 0 ? pitch : 0); q < rows * pitch; q += blockDim.x) acc_s[q] = 0;
         __syncthreads();
-        float* dst = a.part + (size_t)blockIdx.x * G * G;
-        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
-            const int p = q / G, cq = q - (q / G) * G;
-            dst[q] = acc_s[p * pitch + cq];
+        for (int kb = 0; kb < nwarp; kb += 32) {
+            const int cnt = min(32, nwarp - kb);
+            const int r = (int)blockIdx.x + nb * (t0 + kb + min(lane, cnt - 1));
+            const int i = r / a.g.n_t, n = r - (r / a.g.n_t) * a.g.n_t;
+            const int2 cc = a.centres[i];
+            const Ray mine_ray = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
+            const float my_g = lane < cnt ? a.dLdw[r] : 0.f;
+            for (int rr = 0; rr < cnt; ++rr) {
+                const float gr = __shfl_sync(0xffffffffu, my_g, rr);
+                if (gr == 0.f) continue;
+                const Ray ry = shfl_ray(mine_ray, rr);
+                const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
+                // samples whose cell row can lie in the band (the test below is exact;
+                // this range only needs to contain them)
+                int mlo = 0, mhi = nsamp;
+                if (nbands > 1 && ry.by != 0.f) {
+                    const float inv = 1.f / (ry.by * h);
+                    float ma = ((float)r0 - ry.ay) * inv - 0.5f, mb = ((float)r1 - ry.ay) * inv - 0.5f;
+                    if (r0 == 0) ma = ry.by > 0.f ? -INFINITY : INFINITY;          // clamped rows below 0
+                    if (r1 == G - 1) mb = ry.by > 0.f ? INFINITY : -INFINITY;      // clamped rows above G - 2
+                    const float lo = fmaxf(fminf(ma, mb), -1e9f), hi = fminf(fmaxf(ma, mb), 1e9f);
+                    mlo = max(0, (int)floorf(lo) - 2);
+                    mhi = min(nsamp, (int)ceilf(hi) + 2);
+                }
+                if (mhi <= mlo) continue;
+                const int per = (mhi - mlo + 31) >> 5;
+                const int m0 = mlo + lane * per, m1 = min(mhi, m0 + per);
+                const float gv0 = gr * v0;
+                int cur = -1;
+                float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+                for (int m = m0; m < m1; ++m) {
+                    const bool last = m >= ry.nfull;
+                    const float s = last ? ry.nfull * h + 0.5f * ry.rem : (m + 0.5f) * h;
+                    const float fx = fminf(fmaxf(fmaf(s, ry.bx, ry.ax), 0.f), (float)(G - 1));
+                    const float fy = fminf(fmaxf(fmaf(s, ry.by, ry.ay), 0.f), (float)(G - 1));
+                    const int iy = min((int)fy, G - 2);
+                    if (iy < r0 || iy >= r1) continue;
+                    const int ix = min((int)fx, G - 2);
+                    Bil b;
+                    b.idx = (iy - r0) * pitch + ix;
+                    b.tx = fx - ix;
+                    b.ty = fy - iy;
+                    const float d = interp(dv_s, pitch, b);
+                    const float iv = __fdividef(1.f, v0 + d);
+                    const float coef = gv0 * (last ? ry.rem : h) * iv * iv;
+                    if (b.idx != cur) {
+                        if (cur >= 0) scatter4(acc_s, pitch, cur, S, c00, c01, c10, c11);
+                        cur = b.idx;
+                        c00 = c01 = c10 = c11 = 0.f;
+                    }
+                    const float cy0 = coef * (1.f - b.ty), cy1 = coef * b.ty;
+                    c00 = fmaf(cy0, 1.f - b.tx, c00);
+                    c01 = fmaf(cy0, b.tx, c01);
+                    c10 = fmaf(cy1, 1.f - b.tx, c10);
+                    c11 = fmaf(cy1, b.tx, c11);
+                }
+                if (cur >= 0) scatter4(acc_s, pitch, cur, S, c00, c01, c10, c11);
+            }
+        }
+        // node rows written by this band: r0 .. r0 + R - 1 (its last row moves to the next band)
+        const int out_rows = last_band ? rows : R;
+        if (a.cluster) {
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+            const int share = (out_rows + csize - 1) / csize;
+            const int p0 = min(out_rows, rank * share), p1 = min(out_rows, p0 + share);
+            float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G + (size_t)r0 * G;
+            for (int q = threadIdx.x; q < (p1 - p0) * G; q += blockDim.x) {
+                const int p = p0 + q / G, c = q - (q / G) * G;
+                float sum = 0.f;
+                for (int k = 0; k < csize; ++k)
+                    sum += (float)cl.map_shared_rank(acc_s, k)[p * pitch + c] * *cl.map_shared_rank(scale_s + 1, k);
+                dst[p * G + c] = sum;
+            }
+            cl.sync();                               // remote reads end before any CTA changes its grid
+        } else {
+            __syncthreads();
+            const float invS = scale_s[1];
+            float* dst = a.part + (size_t)blockIdx.x * G * G + (size_t)r0 * G;
+            for (int q = threadIdx.x; q < out_rows * G; q += blockDim.x) {
+                const int p = q / G, c = q - (q / G) * G;
+                dst[p * G + c] = (float)acc_s[p * pitch + c] * invS;
+            }
+            __syncthreads();
+        }
+        if (!last_band) {
+            for (int c = threadIdx.x; c < pitch; c += blockDim.x) acc_s[c] = acc_s[R * pitch + c];
+            __syncthreads();
         }
     }
 }
 
-constexpr int kGroup = 16;   // partials summed per thread in the first reduction stage
-
-// stage 1: stage1[r][q] = sum of partials r*kGroup .. r*kGroup + kGroup - 1 at node q
-__global__ void reduce_stage1_kernel(const float* part, int nb, int GG, float* stage1) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    if (q >= GG) return;
-    const int b0 = r * kGroup;
-    float s[kGroup];
-#pragma unroll
-    for (int k = 0; k < kGroup; ++k) s[k] = (b0 + k < nb) ? part[(size_t)(b0 + k) * GG + q] : 0.f;
-#pragma unroll
-    for (int k = kGroup / 2; k > 0; k >>= 1)
-#pragma unroll
-        for (int t = 0; t < k; ++t) s[t] += s[t + k];
-    stage1[(size_t)r * GG + q] = s[0];
-}
-
-__global__ void reduce_stage2_kernel(const float* stage1, int nr, int GG, float* out, int accumulate) {
+// out[q] (+)= sum of the partial grids part[0 .. np)[q], in order.
+__global__ void reduce_parts_kernel(const float* part, int np, int GG, float* out, int accumulate) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= GG) return;
     float s = 0.f;
-    for (int r = 0; r < nr; ++r) s += stage1[(size_t)r * GG + q];
+    for (int r = 0; r < np; ++r) s += part[(size_t)r * GG + q];
     out[q] = accumulate ? out[q] + s : s;
 }
 
@@ -377,8 +446,9 @@ constexpr size_t kMaxSmem = 200 * 1024;
 constexpr int kCluster = 4;   // CTAs per cluster in the ray adjoint (8 would not fit in one wave)
 
 struct Plan {
-    int splits_fwd, splits_adj, nb_fwd, nb_adj, nr, use_smem, cluster, nparts;
-    size_t smem_fwd, smem_adj, off_stage1, ws;
+    int splits_fwd, nb_fwd, use_smem_fwd;
+    int R, nbands, nb_adj, cluster, nparts;
+    size_t smem_fwd, smem_adj, ws;
 };
 
 // CTAs per patch so that the grid fills every SM once at the occupancy the
@@ -394,59 +464,69 @@ int splits_for(const pact_geometry* g, const pact_patches* pt, const void* fn, i
     return std::max(1, std::min(s, std::max(1, g->n_t / 32)));
 }
 
-// Whether clusters of kCluster adjoint CTAs (1024 threads, `smem` bytes each) can
-// be resident on this device (queried once per device).
-bool cluster_fits(size_t smem) {
-    static int cached[64];
+// How many clusters of kCluster adjoint CTAs (1024 threads, `smem` bytes each)
+// can be resident at once on this device (0: clusters unavailable); cached
+// per device and shared-memory size.
+int max_clusters(size_t smem) {
+    struct Entry {
+        int dev;
+        size_t smem;
+        int n;
+    };
+    static Entry cache[16];
+    static int used = 0;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    if (cached[dev] == 0) {
-        int ok = -1;
-        const void* fn = (const void*)rays_adj_kernel<true>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(kCluster);
-            cfg.blockDim = dim3(1024);
-            cfg.dynamicSmemBytes = smem;
-            cudaLaunchAttribute attr;
-            attr.id = cudaLaunchAttributeClusterDimension;
-            attr.val.clusterDim.x = kCluster;
-            attr.val.clusterDim.y = 1;
-            attr.val.clusterDim.z = 1;
-            cfg.attrs = &attr;
-            cfg.numAttrs = 1;
-            int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) ok = 1;
-        }
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
-        cached[dev] = ok;
+        return 0;
     }
-    return cached[dev] > 0;
+    for (int k = 0; k < used; ++k)
+        if (cache[k].dev == dev && cache[k].smem == smem) return cache[k].n;
+    int n = 0;
+    const void* fn = (const void*)rays_adj_kernel;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kCluster);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = kCluster;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();
+    if (used < 16) cache[used++] = Entry{dev, smem, n};
+    return n;
 }
 
 Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     Plan p;
-    const int G = g->sos_g;
-    const size_t gbytes = (size_t)G * smem_pitch(G) * sizeof(float);
-    p.use_smem = 2 * gbytes <= kMaxSmem;
-    p.smem_fwd = p.use_smem ? gbytes : 0;
-    p.smem_adj = p.use_smem ? 2 * gbytes : 0;
-    p.splits_fwd = splits_for(g, pt, p.use_smem ? (const void*)rays_fwd_kernel<true> : (const void*)rays_fwd_kernel<false>,
-                              512, p.smem_fwd);
-    p.splits_adj = splits_for(g, pt, p.use_smem ? (const void*)rays_adj_kernel<true> : (const void*)rays_adj_kernel<false>,
-                              1024, p.smem_adj);
+    const int G = g->sos_g, pitch = smem_pitch(G);
+    const size_t gbytes = (size_t)G * pitch * sizeof(float);
+    p.use_smem_fwd = gbytes <= kMaxSmem;
+    p.smem_fwd = p.use_smem_fwd ? gbytes : 0;
+    p.splits_fwd = splits_for(g, pt, p.use_smem_fwd ? (const void*)rays_fwd_kernel<true>
+                                                    : (const void*)rays_fwd_kernel<false>, 512, p.smem_fwd);
     p.nb_fwd = pt->n * p.splits_fwd;
-    p.nb_adj = pt->n * p.splits_adj;
+    // adjoint: bands of R cell rows, excess rows and accumulator of a band in shared memory
+    p.R = std::max(1, std::min(G - 1, (int)(kMaxSmem / (2 * sizeof(float) * (size_t)pitch)) - 1));
+    p.nbands = (G - 1 + p.R - 1) / p.R;
+    p.smem_adj = 2 * sizeof(float) * (size_t)(p.R + 1) * pitch;
+    const int nrays = pt->n * g->n_t;
+    const int want = std::max(1, std::min(num_sms(), (nrays + 31) / 32));   // one persistent CTA per SM
+    const int nc = max_clusters(p.smem_adj);
     p.cluster = 0;
-    if (p.use_smem && cluster_fits(p.smem_adj)) {
+    p.nb_adj = want;
+    if (nc > 0 && want >= kCluster) {
         p.cluster = kCluster;
-        p.nb_adj = (p.nb_adj + kCluster - 1) / kCluster * kCluster;
+        p.nb_adj = std::min(nc, want / kCluster) * kCluster;
     }
     p.nparts = p.cluster ? p.nb_adj / p.cluster : p.nb_adj;
-    p.nr = (p.nparts + kGroup - 1) / kGroup;
-    const size_t plane = (size_t)G * G * sizeof(float);
-    p.off_stage1 = align_up((size_t)p.nparts * plane, 256);
-    p.ws = p.use_smem ? p.off_stage1 + align_up((size_t)p.nr * plane, 256) : 256;
+    p.ws = align_up((size_t)p.nparts * G * G * sizeof(float), 256);
     return p;
 }
 
@@ -461,7 +541,7 @@ RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl
     a.part = nullptr;
     a.out = nullptr;
     a.splits = splits;
-    a.use_smem = pl.use_smem;
+    a.use_smem = pl.use_smem_fwd;
     a.cluster = pl.cluster;
     return a;
 }
@@ -507,7 +587,7 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
     const Plan pl = make_plan(g, pt);
     RayArgs a = make_args(g, pt, pl, pl.splits_fwd, sos);
     a.w = w;
-    if (pl.use_smem) {
+    if (pl.use_smem_fwd) {
         PACT_TRY(ensure_smem((const void*)rays_fwd_kernel<true>, pl.smem_fwd, "sos_to_delays: shared memory attribute"));
         rays_fwd_kernel<true><<<pl.nb_fwd, 512, pl.smem_fwd, as_stream(stream)>>>(a);
     } else {
@@ -534,44 +614,31 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     if (ws_bytes < pl.ws) return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, pl.ws);
     cudaStream_t st = as_stream(stream);
     const int GG = g->sos_g * g->sos_g;
-    RayArgs a = make_args(g, pt, pl, pl.splits_adj, sos);
+    RayArgs a = make_args(g, pt, pl, 1, sos);
     a.dLdw = dL_dw;
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
-    if (pl.use_smem) {
-        PACT_TRY(ensure_smem((const void*)rays_adj_kernel<true>, pl.smem_adj,
-                             "sos_to_delays_adj: shared memory attribute"));
-        if (pl.cluster) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(pl.nb_adj);
-            cfg.blockDim = dim3(1024);
-            cfg.dynamicSmemBytes = pl.smem_adj;
-            cfg.stream = st;
-            cudaLaunchAttribute attr;
-            attr.id = cudaLaunchAttributeClusterDimension;
-            attr.val.clusterDim.x = pl.cluster;
-            attr.val.clusterDim.y = 1;
-            attr.val.clusterDim.z = 1;
-            cfg.attrs = &attr;
-            cfg.numAttrs = 1;
-            if (cudaLaunchKernelEx(&cfg, rays_adj_kernel<true>, a) != cudaSuccess)
-                return check_launch("sos_to_delays_adj kernel (cluster launch)");
-            PACT_TRY(check_launch("sos_to_delays_adj kernel"));
-            // one partial grid per cluster: a single fixed-order sum
-            reduce_stage2_kernel<<<(GG + 255) / 256, 256, 0, st>>>(a.part, pl.nparts, GG, dL_dsos, accumulate);
-            return check_launch("sos_to_delays_adj reduction");
-        }
-        rays_adj_kernel<true><<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a);
-        PACT_TRY(check_launch("sos_to_delays_adj kernel"));
-        float* stage1 = reinterpret_cast<float*>(static_cast<char*>(ws) + pl.off_stage1);
-        dim3 g1((GG + 255) / 256, pl.nr);
-        reduce_stage1_kernel<<<g1, 256, 0, st>>>(a.part, pl.nb_adj, GG, stage1);
-        PACT_TRY(check_launch("sos_to_delays_adj reduction (1)"));
-        reduce_stage2_kernel<<<(GG + 255) / 256, 256, 0, st>>>(stage1, pl.nr, GG, dL_dsos, accumulate);
-        return check_launch("sos_to_delays_adj reduction (2)");
+    PACT_TRY(ensure_smem((const void*)rays_adj_kernel, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
+    if (pl.cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(pl.nb_adj);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = pl.smem_adj;
+        cfg.stream = st;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = pl.cluster;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, rays_adj_kernel, a, pl.R, pl.nbands) != cudaSuccess)
+            return check_launch("sos_to_delays_adj kernel (cluster launch)");
+    } else {
+        rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a, pl.R, pl.nbands);
     }
-    if (!accumulate && cudaMemsetAsync(dL_dsos, 0, (size_t)GG * sizeof(float), st) != cudaSuccess)
-        return check_launch("sos_to_delays_adj: memset");
-    rays_adj_kernel<false><<<pl.nb_adj, 1024, 0, st>>>(a);
-    return check_launch("sos_to_delays_adj kernel");
+    PACT_TRY(check_launch("sos_to_delays_adj kernel"));
+    // one partial grid per cluster (or CTA): a single fixed-order sum
+    reduce_parts_kernel<<<(GG + 255) / 256, 256, 0, st>>>(a.part, pl.nparts, GG, dL_dsos, accumulate);
+    return check_launch("sos_to_delays_adj reduction");
 }

@@ -51,9 +51,9 @@ CASES = {
 
 # ------------------------------------------------------------------ Eq. 3 and its adjoint
 
-@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("name", list(CASES) + ["tiny_g200", "tiny_g512"])
 def test_sos_to_delays(name):
-    cfg = CASES[name]()
+    cfg = ADJ_CASES[name]() if name in ADJ_CASES else CASES[name]()
     for seed in (0, 1):
         case = inputs.make_case(cfg, seed)
         pb = pact.Problem(cfg, DEV)
@@ -85,9 +85,19 @@ def test_sos_to_delays_full_size_sampled():
     assert rel(w[idx], ref) <= 1e-4
 
 
-@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8", "tiny_nt48"])
+ADJ_CASES = {
+    "tiny_p16_m4": CASES["tiny_p16_m4"],
+    "small_p32_m8": CASES["small_p32_m8"],
+    "tiny_nt48": CASES["tiny_nt48"],
+    # grids whose excess rows and accumulator take several shared-memory bands
+    "tiny_g200": lambda: inputs.config_tiny(p=16, m=4).replace(sos_g=200),
+    "tiny_g512": lambda: inputs.config_tiny(p=16, m=4).replace(sos_g=512),
+}
+
+
+@pytest.mark.parametrize("name", list(ADJ_CASES))
 def test_sos_to_delays_adj(name):
-    cfg = CASES[name]()
+    cfg = ADJ_CASES[name]()
     case = inputs.make_case(cfg, 2)
     pb = pact.Problem(cfg, DEV)
     r = np.random.default_rng(5).standard_normal((cfg.n_patches, cfg.n_t)).astype(np.float32)
@@ -95,6 +105,9 @@ def test_sos_to_delays_adj(name):
     g = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV)))
     ref = O.sos_to_delays_adj(O.geom(cfg), case["sos_true"], case["centres"], r).numpy()
     assert rel(g, ref) <= 2e-3
+    # fixed-point shared sums: the same bits on every call
+    g_again = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV)))
+    assert np.array_equal(g, g_again)
     # accumulate adds
     base = torch.ones((cfg.sos_g, cfg.sos_g), device=DEV)
     g2 = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV), base, accumulate=True))
