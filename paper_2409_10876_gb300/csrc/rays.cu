@@ -115,19 +115,9 @@ struct RayArgs {
     const float* dLdw;    // adjoint input
     float* part;          // adjoint partial grids [gridDim.x][G*G] (smem variant)
     float* out;           // adjoint output (global-atomic variant)
-    int splits;           // CTAs per patch
     int use_smem;
     int cluster;          // adjoint: CTAs per thread-block cluster that pool their grids (0: none)
 };
-
-// CTA b handles patch b / splits, rays [n0, n1) of it.
-__device__ __forceinline__ void cta_rays(const RayArgs& a, int& i, int& n0, int& n1) {
-    i = blockIdx.x / a.splits;
-    const int s = blockIdx.x - i * a.splits;
-    const int per = (a.g.n_t + a.splits - 1) / a.splits;
-    n0 = s * per;
-    n1 = min(a.g.n_t, n0 + per);
-}
 
 // Shared-memory grid pitch: one extra column so that nodes of one grid column
 // fall into different banks.
@@ -157,96 +147,184 @@ __device__ __forceinline__ void load_excess(float* dv, const float* sos, int G, 
     }
 }
 
-// Warp `warp` of `nw` integrates the rays r'_c -> r_n, n = n0 + warp, n0 + warp
-// + nw, ... < n1 (neighbouring rays have similar lengths, so striding balances
-// the warps): it sets up 32 of its rays at once (one per lane) and then
-// integrates them one after the other (lanes over samples), taking each ray's
-// setup by shuffles; out(n, w) runs on the lane that owns ray n.
-// SMEM: the SOS excess grid dv is staged in shared memory (else read from global).
-template <bool SMEM, class Out>
-__device__ __forceinline__ void warp_rays(const RayArgs& a, const float* dv, int pitch, float2 c, int n0, int n1,
-                                          int warp, int nw, Out out) {
-    const int G = a.g.G, lane = threadIdx.x & 31;
-    const float v0 = a.g.v0;
-    const float out_coef = (a.g.v_bg - v0) / a.g.v_bg;
-    const float h = a.g.h;
-    const int nmine = n1 - n0 > warp ? (n1 - n0 - warp + nw - 1) / nw : 0;
-    for (int kb = 0; kb < nmine; kb += 32) {
-        const int cnt = min(32, nmine - kb);
-        const int nl = n0 + warp + (kb + min(lane, cnt - 1)) * nw;
-        const Ray mine = make_ray(a.g, c, nl);
-        float my_w = 0.f;
-        for (int r = 0; r < cnt; ++r) {
-            const Ray ry = shfl_ray(mine, r);
-            const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
-            const int per = (nsamp + 31) >> 5;
-            const int m0 = lane * per, m1 = min(nsamp, m0 + per);
-            const int mf = min(m1, ry.nfull);
-            float acc = 0.f;
-            for (int m = m0; m < mf; ++m) {
-                const float s = (m + 0.5f) * h;
-                const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = SMEM ? interp(dv, pitch, b) : interp_global(a.sos, G, v0, b);
-                acc += __fdividef(d, v0 + d);
-            }
-            acc *= h;
-            if (m0 <= ry.nfull && ry.nfull < m1) {    // last partial step, weighted by its length
-                const float s = ry.nfull * h + 0.5f * ry.rem;
-                const Bil b = bil(G, pitch, fmaf(s, ry.bx, ry.ax), fmaf(s, ry.by, ry.ay));
-                const float d = SMEM ? interp(dv, pitch, b) : interp_global(a.sos, G, v0, b);
-                acc = fmaf(ry.rem, __fdividef(d, v0 + d), acc);
-            }
-            acc = warp_sum(acc);
-            if (lane == r) my_w = fmaf(ry.L - ry.chord, out_coef, acc);
+// Padded staging for the forward integrals: node (p, c) of the excess grid at
+// (p + 2, c + 2) of a (G + 4) x (G + 4) array of row pitch G + 5, the two outer
+// rings replicating the edge nodes, so that bilinear interpolation on the
+// padded array equals the edge-clamped interpolation of the grid for node
+// coordinates in [-2, G + 1] and needs no clamps.
+__host__ __device__ __forceinline__ int pad_pitch(int G) { return G + 5; }
+__host__ __device__ __forceinline__ size_t pad_bytes(int G) { return (size_t)(G + 4) * pad_pitch(G) * sizeof(float); }
+
+__device__ __forceinline__ void load_excess_padded(float* dv, const float* sos, int G, float v0) {
+    const int pitch = pad_pitch(G), P = G + 4;
+    if ((G & 3) == 0 && (reinterpret_cast<uintptr_t>(sos) & 15) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(sos);
+        const int G4 = G >> 2, n4 = G * G4;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+            const float4 v = __ldg(s4 + q);
+            const int p = q / G4, c = (q - (q / G4) * G4) << 2;
+            float* d = dv + (p + 2) * pitch + c + 2;
+            d[0] = v.x - v0;
+            d[1] = v.y - v0;
+            d[2] = v.z - v0;
+            d[3] = v.w - v0;
         }
-        if (lane < cnt) out(nl, my_w);
+    } else {
+        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+            const int p = q / G, c = q - (q / G) * G;
+            dv[(p + 2) * pitch + c + 2] = __ldg(sos + q) - v0;
+        }
+    }
+    // the two outer rings, replicated from the edge nodes (corners are written twice, with the same value)
+    for (int q = threadIdx.x; q < 4 * P; q += blockDim.x) {
+        const int side = q / P, k = q - (q / P) * P;        // k along the side
+        const int kk = min(max(k - 2, 0), G - 1);
+        for (int ring = 0; ring < 2; ++ring) {
+            int pp, cc, p, c;
+            if (side == 0) { pp = ring; cc = k; p = 0; c = kk; }                 // top rows
+            else if (side == 1) { pp = P - 1 - ring; cc = k; p = G - 1; c = kk; } // bottom rows
+            else if (side == 2) { pp = k; cc = ring; p = kk; c = 0; }            // left columns
+            else { pp = k; cc = P - 1 - ring; p = kk; c = G - 1; }               // right columns
+            dv[pp * pitch + cc] = __ldg(sos + p * G + c) - v0;
+        }
     }
 }
 
-// CTA b: rays [n0, n1) of patch b / splits.
-template <bool SMEM>
+// Slowness excess (v - v0)/v = dv / (v0 + dv) at padded node coordinates
+// (x, y) in [1, G + 2] (node coordinate + 2): bilinear dv on the padded grid.
+// floor() without conversions: adding 2^23 - 1/2 to x >= 1/2 rounds x - 1/2 to
+// an integer in the low mantissa bits of the sum, which is floor(x) (or x - 1
+// for integral x, where the weight 1 on the upper node gives the same value).
+__device__ __forceinline__ float excess_padded(const float* dv, int pitch, float x, float y, float v0) {
+    const float tX = x + 8388607.5f, tY = y + 8388607.5f;
+    const int ix = __float_as_int(tX) - 0x4B000000, iy = __float_as_int(tY) - 0x4B000000;
+    const float tx = x - (tX - 8388608.f), ty = y - (tY - 8388608.f);
+    const float* q = dv + iy * pitch + ix;
+    const float d00 = q[0], d01 = q[1], d10 = q[pitch], d11 = q[pitch + 1];
+    const float top = fmaf(tx, d01 - d00, d00), bot = fmaf(tx, d11 - d10, d10);
+    const float d = fmaf(ty, bot - top, top);
+    return __fdividef(d, v0 + d);
+}
+
+// The part of ray `ry` that lane `sub` of a group of L lanes integrates: a
+// contiguous run of its midpoint samples (the last one, of length rem, at
+// nfull h + rem/2), weighted by their lengths.
+// PAD: padded shared grid (see above); else SMEM: clamped shared grid of row
+// pitch `pitch`; else the SOS grid in global memory.
+template <int L, bool SMEM, bool PAD>
+__device__ __forceinline__ float ray_part(const RayArgs& a, const float* dv, int pitch, const Ray& ry, int sub) {
+    const int G = a.g.G;
+    const float h = a.g.h, v0 = a.g.v0;
+    const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
+    const int per = (nsamp + L - 1) / L;
+    const int m0 = sub * per, m1 = min(nsamp, m0 + per);
+    const float hbx = h * ry.bx, hby = h * ry.by;
+    const float ulast = ry.nfull + 0.5f * (ry.rem / h);
+    const float ax = PAD ? ry.ax + 2.f : ry.ax, ay = PAD ? ry.ay + 2.f : ry.ay;
+    float acc = 0.f, uf = m0 + 0.5f;
+    for (int m = m0; m < m1; ++m, uf += 1.f) {
+        const bool last = m >= ry.nfull;
+        const float u = last ? ulast : uf;
+        const float x = fmaf(u, hbx, ax), y = fmaf(u, hby, ay);
+        float e;
+        if (PAD) {
+            e = excess_padded(dv, pitch, x, y, v0);
+        } else {
+            const Bil b = bil(G, pitch, x, y);
+            const float d = SMEM ? interp(dv, pitch, b) : interp_global(a.sos, G, v0, b);
+            e = __fdividef(d, v0 + d);
+        }
+        acc = fmaf(last ? ry.rem : h, e, acc);
+    }
+    return acc;
+}
+
+// Forward rays.  Work item t = (patch i, block of 32/L consecutive
+// transducers); warp-strided over the grid (persistent CTAs), a warp's lanes
+// form 32/L groups of L lanes, one ray per group (neighbouring transducers:
+// similar directions and lengths), each lane a contiguous run of samples;
+// the group's partial sums meet in a fixed butterfly order.
+template <int L, bool SMEM, bool PAD>
 __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
     extern __shared__ float dv_s[];
-    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
+    const int G = a.g.G;
+    const int pitch = PAD ? pad_pitch(G) : (SMEM ? smem_pitch(G) : G);
     if (SMEM) {
-        load_excess(dv_s, a.sos, G, pitch, a.g.v0);
+        if (PAD)
+            load_excess_padded(dv_s, a.sos, G, a.g.v0);
+        else
+            load_excess(dv_s, a.sos, G, pitch, a.g.v0);
         __syncthreads();
     }
-    int i, n0, n1;
-    cta_rays(a, i, n0, n1);
-    const int2 cc = a.centres[i];
-    float* w = a.w + (size_t)i * a.g.n_t;
-    warp_rays<SMEM>(a, dv_s, pitch, pixel_xy(a.g, cc.x, cc.y), n0, n1, threadIdx.x >> 5, blockDim.x >> 5,
-                    [&](int n, float wn) { w[n] = wn; });
+    constexpr int RB = 32 / L;
+    const int n_t = a.g.n_t;
+    const int lane = threadIdx.x & 31, sub = lane % L, grp = lane / L;
+    const int nblk = (n_t + RB - 1) / RB, items = a.N * nblk;
+    const int wpb = blockDim.x >> 5, W = gridDim.x * wpb;
+    const float out_coef = (a.g.v_bg - a.g.v0) / a.g.v_bg;
+    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < items; t += W) {
+        const int i = t / nblk;
+        const int n = (t - i * nblk) * RB + grp;
+        const bool valid = n < n_t;
+        const int2 cc = a.centres[i];
+        const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), valid ? n : 0);
+        float acc = valid ? ray_part<L, SMEM, PAD>(a, dv_s, pitch, ry, sub) : 0.f;
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (valid && sub == 0) a.w[(size_t)i * n_t + n] = fmaf(ry.L - ry.chord, out_coef, acc);
+    }
 }
 
 // Rays from image pixels (sources of channel data): the CTAs take the pixels
 // pix0 + q, q = blockIdx.x, blockIdx.x + gridDim.x, ... < npix, skip those with
-// p0 == 0, and write w from pixel q to every transducer n at wT[n * ld + q].
-template <bool SMEM>
+// p0 == 0, and write w from pixel q to every transducer n at wT[n * ld + q]
+// (warps over blocks of 32/L transducers, groups of L lanes per ray).
+template <int L, bool SMEM, bool PAD>
 __global__ void __launch_bounds__(512) rays_pix_kernel(const RayArgs a, const float* p0, int pix0, int npix,
                                                        float* wT, int ld) {
     extern __shared__ float dv_s[];
-    const int G = a.g.G, pitch = SMEM ? smem_pitch(G) : G;
+    const int G = a.g.G;
+    const int pitch = PAD ? pad_pitch(G) : (SMEM ? smem_pitch(G) : G);
     if (SMEM) {
-        load_excess(dv_s, a.sos, G, pitch, a.g.v0);
+        if (PAD)
+            load_excess_padded(dv_s, a.sos, G, a.g.v0);
+        else
+            load_excess(dv_s, a.sos, G, pitch, a.g.v0);
         __syncthreads();
     }
+    constexpr int RB = 32 / L;
+    const int n_t = a.g.n_t;
+    const int lane = threadIdx.x & 31, sub = lane % L, grp = lane / L;
+    const int nblk = (n_t + RB - 1) / RB, wpb = blockDim.x >> 5;
+    const float out_coef = (a.g.v_bg - a.g.v0) / a.g.v_bg;
     for (int q = blockIdx.x; q < npix; q += gridDim.x) {
         const int pix = pix0 + q;
         if (p0[pix] == 0.f) continue;                 // the same for the whole CTA
         const int row = pix / a.g.W, col = pix - (pix / a.g.W) * a.g.W;
-        warp_rays<SMEM>(a, dv_s, pitch, pixel_xy(a.g, row, col), 0, a.g.n_t, threadIdx.x >> 5, blockDim.x >> 5,
-                        [&](int n, float wn) { wT[(size_t)n * ld + q] = wn; });
+        const float2 c = pixel_xy(a.g, row, col);
+        for (int blk = threadIdx.x >> 5; blk < nblk; blk += wpb) {
+            const int n = blk * RB + grp;
+            const bool valid = n < n_t;
+            const Ray ry = make_ray(a.g, c, valid ? n : 0);
+            float acc = valid ? ray_part<L, SMEM, PAD>(a, dv_s, pitch, ry, sub) : 0.f;
+#pragma unroll
+            for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (valid && sub == 0) wT[(size_t)n * ld + q] = fmaf(ry.L - ry.chord, out_coef, acc);
+        }
     }
 }
 
+// Round-to-nearest int of |x| < 2^22 without a conversion instruction: adding
+// 1.5 * 2^23 leaves round(x) in the low mantissa bits of the sum.
+__device__ __forceinline__ int fixed_round(float x) { return __float_as_int(x + 12582912.f) - 0x4B400000; }
+
 __device__ __forceinline__ void scatter4(int* acc, int pitch, int idx, float S, float c00, float c01, float c10,
                                          float c11) {
-    atomicAdd(acc + idx, __float2int_rn(c00 * S));
-    atomicAdd(acc + idx + 1, __float2int_rn(c01 * S));
-    atomicAdd(acc + idx + pitch, __float2int_rn(c10 * S));
-    atomicAdd(acc + idx + pitch + 1, __float2int_rn(c11 * S));
+    atomicAdd(acc + idx, fixed_round(c00 * S));
+    atomicAdd(acc + idx + 1, fixed_round(c01 * S));
+    atomicAdd(acc + idx + pitch, fixed_round(c10 * S));
+    atomicAdd(acc + idx + pitch + 1, fixed_round(c11 * S));
 }
 
 __device__ __forceinline__ float block_min(float x, float* red) {
@@ -263,13 +341,43 @@ __device__ __forceinline__ float block_min(float x, float* red) {
     return x;
 }
 
+__device__ __forceinline__ float block_max(float x, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -INFINITY;
+    if (wid == 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    __syncthreads();
+    return x;
+}
+
+// Node column c of a padded row: the padded columns that clamp to it.
+template <class T>
+__device__ __forceinline__ T fold_col(const T* row, int c, int G) {
+    T v = row[c + 2];
+    if (c == 0) v += row[0] + row[1];
+    if (c == G - 1) v += row[G + 2] + row[G + 3];
+    return v;
+}
+
 // Ray adjoint.  CTA b takes the rays r = b, b + nb, b + 2 nb, ... of the flat
 // (patch, transducer) index r = i N_t + n, and each warp a contiguous block of
 // them, so that its warps integrate rays of different patches and directions
 // at the same time (rays of one patch all start at the same centre, where their
-// scatters would collide).  A lane walks a contiguous run of samples of one ray
-// and keeps the bilinear weights of the current cell in registers, adding them
-// to the shared grid only when the walk leaves the cell.
+// scatters would collide).  A warp takes one ray at a time (its rays differ in
+// length, so lanes on different rays would wait for the longest); a lane walks
+// a contiguous run of samples of the ray and keeps the bilinear weights of the
+// current cell in registers, adding them to the shared grid only when the walk
+// leaves the cell.
+//
+// Coordinates are those of the padded grid (node (p, c) at (p + 2, c + 2), see
+// load_excess_padded), clamped to [1, G + 2]; floor() takes no conversion
+// (see excess_padded); the sums that land on the two outer rings belong to the
+// edge nodes they replicate and are folded onto them when the grid is written.
 //
 // The shared grid holds 32-bit fixed-point sums (shared-memory integer atomics
 // are single instructions; float ones are compare-and-swap loops), which also
@@ -277,46 +385,59 @@ __device__ __forceinline__ float block_min(float x, float* red) {
 // contribution is g h_s v0 / v^2 times a bilinear weight; v is a convex
 // combination of node values, so v >= vmin, and the weights h_s of a ray add up
 // to its chord <= 2 mask_r.  The absolute sum of all contributions of the CTA
-// is therefore at most  Mb = sum_r |g_r| 2 mask_r v0 / vmin^2 , and with the
-// scale S = 2^30 / Mb no partial sum of a node can leave the int32 range
-// (each flush rounds by at most 1/2).  A non-finite bound (NaN in dL/dw or the
-// SOS, or SOS <= 0) turns the CTA's partial grid into NaN.
+// is therefore at most  Mb = sum_r |g_r| 2 mask_r v0 / vmin^2 , and one
+// register flush (the samples of a ray inside one cell, a segment of length
+// <= sqrt(2) sos_dx + h) at most  F = max|g| (sqrt(2) sos_dx + h) v0 / vmin^2.
+// The scale S = 0.99 min(2^30 / Mb, 2^22 / F) keeps every node's sum inside the
+// int32 range (each flush rounds by at most 1/2) and every flushed value below
+// 2^22 (rounded without a conversion instruction).  A non-finite bound (NaN in
+// dL/dw or the SOS, or SOS <= 0) turns the CTA's partial grid into NaN.
 //
-// Grids are processed in bands of R cell rows (node rows r0 .. r0 + R), so
-// that the SOS excess rows and the accumulator of a band fit in shared memory
-// for every G <= 512; a ray visits each band with the samples whose cell row
-// lies in it.  Node row r0 + R is shared with the next band: its sums move to
-// that band's first row.  With clusters, the CTAs of a cluster sum each band of
-// their grids through distributed shared memory in a fixed order of ranks and
-// write one partial grid per cluster; otherwise every CTA writes its own.
-__global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int R, int nbands) {
+// The padded grid is processed in bands of R cell rows (padded node rows
+// r0 .. r0 + R), so that the excess rows and the accumulator of a band fit in
+// shared memory for every G <= 512; a ray visits each band with the samples
+// whose cell row lies in it.  Node row r0 + R is shared with the next band: its
+// sums move to that band's first row.  With clusters, the CTAs of a cluster sum
+// each band of their grids through distributed shared memory in a fixed order
+// of ranks and write one partial grid per cluster; otherwise every CTA writes
+// its own.
+__global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int R, int nbands, int narrow) {
     extern __shared__ float sm[];
     __shared__ float red_s[32];
     __shared__ float scale_s[2];      // S and 1/S (NaN: poisoned)
-    const int G = a.g.G, pitch = smem_pitch(G);
-    float* dv_s = sm;                                              // [R + 1][pitch]
-    int* acc_s = reinterpret_cast<int*>(sm + (R + 1) * pitch);      // [R + 1][pitch]
-    const float v0 = a.g.v0;
+    const int G = a.g.G, pitch = pad_pitch(G), PG = G + 4;
+    float* dv_s = sm;                                              // [R + 1][pitch] padded excess rows
+    int* acc_s = reinterpret_cast<int*>(sm + (R + 1) * pitch);      // [R + 1][pitch] padded sums
+    int* edge_s = acc_s + (R + 1) * pitch;                          // [2][G] sums of the first / last node row
+    const float v0 = a.g.v0, h = a.g.h;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nrays = a.N * a.g.n_t, nb = gridDim.x;
     const int mine = nrays > (int)blockIdx.x ? (nrays - (int)blockIdx.x + nb - 1) / nb : 0;   // rays of this CTA
 
     // fixed-point scale of this CTA
-    float gsum = 0.f, vmin = INFINITY, bad = 0.f;
-    for (int t = threadIdx.x; t < mine; t += blockDim.x) gsum += fabsf(a.dLdw[(size_t)blockIdx.x + (size_t)nb * t]);
+    float gsum = 0.f, gmax = 0.f, vmin = INFINITY, bad = 0.f;
+    for (int t = threadIdx.x; t < mine; t += blockDim.x) {
+        const float gv = fabsf(a.dLdw[(size_t)blockIdx.x + (size_t)nb * t]);
+        gsum += gv;
+        gmax = fmaxf(gmax, gv);
+    }
     for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
         const float v = __ldg(a.sos + q);
         if (!(v > 0.f) || !isfinite(v)) bad = 1.f;
         vmin = fminf(vmin, v);
     }
+    for (int q = threadIdx.x; q < 2 * G; q += blockDim.x) edge_s[q] = 0;
     gsum = block_sum(gsum, red_s);
+    gmax = block_max(gmax, red_s);
     bad = block_sum(bad, red_s);
     vmin = block_min(vmin, red_s);
     if (threadIdx.x == 0) {
         const float vm = vmin * (1.f - 1e-5f);
-        const float Mb = gsum * (2.f * a.g.mask_r) * (v0 / (vm * vm));
-        const bool poison = bad > 0.f || !isfinite(Mb);
-        const float S = Mb > 0.f ? fminf(1073741824.f / Mb, 1e30f) : 0.f;
+        const float k = v0 / (vm * vm);
+        const float Mb = gsum * (2.f * a.g.mask_r) * k;
+        const float F = gmax * (1.41421356f * a.g.sos_dx + h) * k;
+        const bool poison = bad > 0.f || !isfinite(Mb) || !isfinite(F) || !isfinite(gsum);
+        const float S = (Mb > 0.f && F > 0.f) ? 0.99f * fminf(fminf(1073741824.f / Mb, 4194304.f / F), 1e30f) : 0.f;
         scale_s[0] = poison ? 0.f : S;
         scale_s[1] = poison ? __int_as_float(0x7fc00000) : (S > 0.f ? 1.f / S : 0.f);
     }
@@ -326,20 +447,21 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     // warp w takes the contiguous block t0 <= t < t1 of the CTA's rays t (r = b + nb t)
     const int t0 = (int)((long long)mine * warp / nw), t1 = (int)((long long)mine * (warp + 1) / nw);
     const int nwarp = t1 - t0;
-    const float h = a.g.h;
     namespace cg = cooperative_groups;
     for (int band = 0; band < nbands; ++band) {
         const bool last_band = band == nbands - 1;
         const int r0 = band * R;
-        const int r1 = last_band ? G - 1 : r0 + R;        // cell rows r0 <= iy < r1
-        const int rows = min(R + 1, G - r0);              // node rows r0 .. r0 + rows - 1 of the band
-        for (int q = threadIdx.x; q < rows * G; q += blockDim.x) {
-            const int p = q / G, c = q - (q / G) * G;
-            dv_s[p * pitch + c] = __ldg(a.sos + (size_t)(r0 + p) * G + c) - v0;
+        const int r1 = last_band ? G + 3 : r0 + R;        // padded cell rows r0 <= iy < r1
+        const int rows = min(R + 1, PG - r0);             // padded node rows r0 .. r0 + rows - 1
+        for (int pl = warp; pl < rows; pl += nw) {
+            const float* src = a.sos + (size_t)min(max(r0 + pl - 2, 0), G - 1) * G;
+            for (int cc = lane; cc < PG; cc += 32) dv_s[pl * pitch + cc] = __ldg(src + min(max(cc - 2, 0), G - 1)) - v0;
         }
         for (int q = threadIdx.x + (band > 0 ? pitch : 0); q < rows * pitch; q += blockDim.x) acc_s[q] = 0;
         __syncthreads();
         for (int kb = 0; kb < nwarp; kb += 32) {
+            // 32 rays set up at once (one per lane), then integrated one after the
+            // other by the whole warp (lanes over samples: all lanes on one ray)
             const int cnt = min(32, nwarp - kb);
             const int r = (int)blockIdx.x + nb * (t0 + kb + min(lane, cnt - 1));
             const int i = r / a.g.n_t, n = r - (r / a.g.n_t) * a.g.n_t;
@@ -351,84 +473,125 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                 if (gr == 0.f) continue;
                 const Ray ry = shfl_ray(mine_ray, rr);
                 const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
+                const float hbx = h * ry.bx, hby = h * ry.by;
+                const float ax = ry.ax + 2.f, ay = ry.ay + 2.f;
                 // samples whose cell row can lie in the band (the test below is exact;
-                // this range only needs to contain them)
+                // this range only needs to contain them; `narrow` = no sample of any
+                // ray leaves the padded grid, so that the clamp below changes nothing)
                 int mlo = 0, mhi = nsamp;
-                if (nbands > 1 && ry.by != 0.f) {
-                    const float inv = 1.f / (ry.by * h);
-                    float ma = ((float)r0 - ry.ay) * inv - 0.5f, mb = ((float)r1 - ry.ay) * inv - 0.5f;
-                    if (r0 == 0) ma = ry.by > 0.f ? -INFINITY : INFINITY;          // clamped rows below 0
-                    if (r1 == G - 1) mb = ry.by > 0.f ? INFINITY : -INFINITY;      // clamped rows above G - 2
+                if (narrow && nbands > 1 && hby != 0.f) {
+                    const float inv = 1.f / hby;
+                    float ma = ((float)r0 - ay) * inv - 0.5f, mb = ((float)r1 - ay) * inv - 0.5f;
+                    if (r0 == 0) ma = hby > 0.f ? -INFINITY : INFINITY;
+                    if (last_band) mb = hby > 0.f ? INFINITY : -INFINITY;
                     const float lo = fmaxf(fminf(ma, mb), -1e9f), hi = fminf(fmaxf(ma, mb), 1e9f);
                     mlo = max(0, (int)floorf(lo) - 2);
                     mhi = min(nsamp, (int)ceilf(hi) + 2);
                 }
-                if (mhi <= mlo) continue;
-                const int per = (mhi - mlo + 31) >> 5;
+                const int per = (max(mhi - mlo, 0) + 31) >> 5;
                 const int m0 = mlo + lane * per, m1 = min(mhi, m0 + per);
+                const float ulast = ry.nfull + 0.5f * (ry.rem / h);
                 const float gv0 = gr * v0;
                 int cur = -1;
                 float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
-                for (int m = m0; m < m1; ++m) {
+                float uf = m0 + 0.5f;
+                for (int m = m0; m < m1; ++m, uf += 1.f) {
                     const bool last = m >= ry.nfull;
-                    const float s = last ? ry.nfull * h + 0.5f * ry.rem : (m + 0.5f) * h;
-                    const float fx = fminf(fmaxf(fmaf(s, ry.bx, ry.ax), 0.f), (float)(G - 1));
-                    const float fy = fminf(fmaxf(fmaf(s, ry.by, ry.ay), 0.f), (float)(G - 1));
-                    const int iy = min((int)fy, G - 2);
+                    const float u = last ? ulast : uf;
+                    // clamped to the padded grid: the same value as the edge-clamped
+                    // interpolation, and every access in bounds for any geometry
+                    const float x = fminf(fmaxf(fmaf(u, hbx, ax), 1.f), (float)(G + 2));
+                    const float y = fminf(fmaxf(fmaf(u, hby, ay), 1.f), (float)(G + 2));
+                    const float tY = y + 8388607.5f;
+                    const int iy = __float_as_int(tY) - 0x4B000000;
                     if (iy < r0 || iy >= r1) continue;
-                    const int ix = min((int)fx, G - 2);
-                    Bil b;
-                    b.idx = (iy - r0) * pitch + ix;
-                    b.tx = fx - ix;
-                    b.ty = fy - iy;
-                    const float d = interp(dv_s, pitch, b);
+                    const float tX = x + 8388607.5f;
+                    const int ix = __float_as_int(tX) - 0x4B000000;
+                    const float tx = x - (tX - 8388608.f), ty = y - (tY - 8388608.f);
+                    const int idx = (iy - r0) * pitch + ix;
+                    const float* q = dv_s + idx;
+                    const float d00 = q[0], d01 = q[1], d10 = q[pitch], d11 = q[pitch + 1];
+                    const float top = fmaf(tx, d01 - d00, d00), bot = fmaf(tx, d11 - d10, d10);
+                    const float d = fmaf(ty, bot - top, top);
                     const float iv = __fdividef(1.f, v0 + d);
                     const float coef = gv0 * (last ? ry.rem : h) * iv * iv;
-                    if (b.idx != cur) {
+                    if (idx != cur) {
                         if (cur >= 0) scatter4(acc_s, pitch, cur, S, c00, c01, c10, c11);
-                        cur = b.idx;
+                        cur = idx;
                         c00 = c01 = c10 = c11 = 0.f;
                     }
-                    const float cy0 = coef * (1.f - b.ty), cy1 = coef * b.ty;
-                    c00 = fmaf(cy0, 1.f - b.tx, c00);
-                    c01 = fmaf(cy0, b.tx, c01);
-                    c10 = fmaf(cy1, 1.f - b.tx, c10);
-                    c11 = fmaf(cy1, b.tx, c11);
+                    const float cy0 = coef * (1.f - ty), cy1 = coef * ty;
+                    c00 = fmaf(cy0, 1.f - tx, c00);
+                    c01 = fmaf(cy0, tx, c01);
+                    c10 = fmaf(cy1, 1.f - tx, c10);
+                    c11 = fmaf(cy1, tx, c11);
                 }
                 if (cur >= 0) scatter4(acc_s, pitch, cur, S, c00, c01, c10, c11);
             }
         }
-        // node rows written by this band: r0 .. r0 + R - 1 (its last row moves to the next band)
+        // padded rows written by this band: r0 .. r0 + out_rows - 1 (its last row moves to the next band);
+        // rows 3 .. G are node rows 1 .. G - 2, the rest fold onto node rows 0 and G - 1
         const int out_rows = last_band ? rows : R;
-        if (a.cluster) {
-            cg::cluster_group cl = cg::this_cluster();
+        cg::cluster_group cl = cg::this_cluster();
+        if (a.cluster)
             cl.sync();
-            const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-            const int share = (out_rows + csize - 1) / csize;
-            const int p0 = min(out_rows, rank * share), p1 = min(out_rows, p0 + share);
-            float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G + (size_t)r0 * G;
-            for (int q = threadIdx.x; q < (p1 - p0) * G; q += blockDim.x) {
-                const int p = p0 + q / G, c = q - (q / G) * G;
-                float sum = 0.f;
-                for (int k = 0; k < csize; ++k)
-                    sum += (float)cl.map_shared_rank(acc_s, k)[p * pitch + c] * *cl.map_shared_rank(scale_s + 1, k);
-                dst[p * G + c] = sum;
+        else
+            __syncthreads();
+        {
+            const int t_end = min(3, r0 + out_rows), b_beg = max(G + 1, r0);      // padded rows [r0, t_end), [b_beg, r0 + out_rows)
+            for (int c = threadIdx.x; c < G; c += blockDim.x) {
+                int top = 0, bottom = 0;
+                for (int pp = r0; pp < t_end; ++pp) top += fold_col(acc_s + (pp - r0) * pitch, c, G);
+                for (int pp = b_beg; pp < r0 + out_rows; ++pp) bottom += fold_col(acc_s + (pp - r0) * pitch, c, G);
+                edge_s[c] += top;
+                edge_s[G + c] += bottom;
             }
+        }
+        const int i0 = max(3, r0), i1 = min(G + 1, r0 + out_rows);    // interior padded rows [i0, i1)
+        if (a.cluster) {
+            const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+            const int nrow = max(0, i1 - i0), share = (nrow + csize - 1) / csize;
+            const int p0 = i0 + min(nrow, rank * share), p1 = i0 + min(nrow, rank * share + share);
+            float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G;
+            for (int pp = p0 + warp; pp < p1; pp += nw)
+                for (int c = lane; c < G; c += 32) {
+                    float sum = 0.f;
+                    for (int k = 0; k < csize; ++k)
+                        sum += (float)fold_col(cl.map_shared_rank(acc_s, k) + (pp - r0) * pitch, c, G) *
+                               *cl.map_shared_rank(scale_s + 1, k);
+                    dst[(pp - 2) * G + c] = sum;
+                }
             cl.sync();                               // remote reads end before any CTA changes its grid
         } else {
-            __syncthreads();
             const float invS = scale_s[1];
-            float* dst = a.part + (size_t)blockIdx.x * G * G + (size_t)r0 * G;
-            for (int q = threadIdx.x; q < out_rows * G; q += blockDim.x) {
-                const int p = q / G, c = q - (q / G) * G;
-                dst[p * G + c] = (float)acc_s[p * pitch + c] * invS;
-            }
+            float* dst = a.part + (size_t)blockIdx.x * G * G;
+            for (int pp = i0 + warp; pp < i1; pp += nw)
+                for (int c = lane; c < G; c += 32)
+                    dst[(pp - 2) * G + c] = (float)fold_col(acc_s + (pp - r0) * pitch, c, G) * invS;
             __syncthreads();
         }
         if (!last_band) {
             for (int c = threadIdx.x; c < pitch; c += blockDim.x) acc_s[c] = acc_s[R * pitch + c];
             __syncthreads();
         }
+    }
+    // node rows 0 and G - 1
+    if (a.cluster) {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+        float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G;
+        for (int q = rank * blockDim.x + threadIdx.x; q < 2 * G; q += csize * blockDim.x) {
+            float sum = 0.f;
+            for (int k = 0; k < csize; ++k) sum += (float)cl.map_shared_rank(edge_s, k)[q] * *cl.map_shared_rank(scale_s + 1, k);
+            dst[q < G ? q : (G - 1) * G + (q - G)] = sum;
+        }
+        cl.sync();
+    } else {
+        const float invS = scale_s[1];
+        float* dst = a.part + (size_t)blockIdx.x * G * G;
+        for (int q = threadIdx.x; q < 2 * G; q += blockDim.x)
+            dst[q < G ? q : (G - 1) * G + (q - G)] = (float)edge_s[q] * invS;
     }
 }
 
@@ -445,24 +608,53 @@ constexpr size_t kMaxSmem = 200 * 1024;
 
 constexpr int kCluster = 4;   // CTAs per cluster in the ray adjoint (8 would not fit in one wave)
 
-struct Plan {
-    int splits_fwd, nb_fwd, use_smem_fwd;
-    int R, nbands, nb_adj, cluster, nparts;
-    size_t smem_fwd, smem_adj, ws;
-};
+constexpr int kRayLanes = 1;   // lanes per ray in the forward integrals
 
-// CTAs per patch so that the grid fills every SM once at the occupancy the
-// kernel's registers and shared memory allow (at least 32 rays per CTA).
-int splits_for(const pact_geometry* g, const pact_patches* pt, const void* fn, int threads, size_t smem) {
-    const int sms = num_sms();
+enum FwdMode { kFwdGlobal = 0, kFwdShared = 1, kFwdPadded = 2 };
+
+// Staging of the SOS excess for the forward integrals: padded (no clamps) when
+// every sample inside the mask disk has node coordinates in [-1, G] and the
+// padded grid fits, else the plain shared grid, else global memory.
+// Every sample inside the mask disk has node coordinates in [-1, G] (padded
+// coordinates in [1, G + 2]).
+bool hull_ok(const pact_geometry* g) { return g->mask_radius <= (0.5f * g->sos_g + 0.5f) * g->sos_dx; }
+
+int fwd_mode(const pact_geometry* g, size_t* bytes) {
+    const int G = g->sos_g;
+    if (hull_ok(g) && pad_bytes(G) <= kMaxSmem) {
+        *bytes = pad_bytes(G);
+        return kFwdPadded;
+    }
+    const size_t plain = (size_t)G * smem_pitch(G) * sizeof(float);
+    if (plain <= kMaxSmem) {
+        *bytes = plain;
+        return kFwdShared;
+    }
+    *bytes = 0;
+    return kFwdGlobal;
+}
+
+const void* fwd_fn(int mode) {
+    return mode == kFwdPadded   ? (const void*)rays_fwd_kernel<kRayLanes, true, true>
+           : mode == kFwdShared ? (const void*)rays_fwd_kernel<kRayLanes, true, false>
+                                : (const void*)rays_fwd_kernel<kRayLanes, false, false>;
+}
+
+// Persistent grid: as many CTAs of `threads` as fit on the device at once.
+int persistent_grid(const void* fn, int threads, size_t smem) {
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const int s = (sms * per_sm) / pt->n;
-    return std::max(1, std::min(s, std::max(1, g->n_t / 32)));
+    return num_sms() * per_sm;
 }
+
+struct Plan {
+    int fwd_mode, nb_fwd;
+    int R, nbands, nb_adj, cluster, nparts, narrow;
+    size_t smem_fwd, smem_adj, ws;
+};
 
 // How many clusters of kCluster adjoint CTAs (1024 threads, `smem` bytes each)
 // can be resident at once on this device (0: clusters unavailable); cached
@@ -505,17 +697,21 @@ int max_clusters(size_t smem) {
 
 Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     Plan p;
-    const int G = g->sos_g, pitch = smem_pitch(G);
-    const size_t gbytes = (size_t)G * pitch * sizeof(float);
-    p.use_smem_fwd = gbytes <= kMaxSmem;
-    p.smem_fwd = p.use_smem_fwd ? gbytes : 0;
-    p.splits_fwd = splits_for(g, pt, p.use_smem_fwd ? (const void*)rays_fwd_kernel<true>
-                                                    : (const void*)rays_fwd_kernel<false>, 512, p.smem_fwd);
-    p.nb_fwd = pt->n * p.splits_fwd;
-    // adjoint: bands of R cell rows, excess rows and accumulator of a band in shared memory
-    p.R = std::max(1, std::min(G - 1, (int)(kMaxSmem / (2 * sizeof(float) * (size_t)pitch)) - 1));
-    p.nbands = (G - 1 + p.R - 1) / p.R;
-    p.smem_adj = 2 * sizeof(float) * (size_t)(p.R + 1) * pitch;
+    const int G = g->sos_g;
+    p.fwd_mode = fwd_mode(g, &p.smem_fwd);
+    {
+        constexpr int RB = 32 / kRayLanes;
+        const int items = pt->n * ((g->n_t + RB - 1) / RB);          // warp work items
+        p.nb_fwd = std::max(1, std::min(persistent_grid(fwd_fn(p.fwd_mode), 512, p.smem_fwd), (items + 15) / 16));
+    }
+    // adjoint: bands of R cell rows of the padded grid (G + 3 cell rows, row pitch
+    // pad_pitch(G)); excess rows, accumulator and the two edge rows in shared memory
+    const int pp = pad_pitch(G);
+    const size_t edge = 2 * sizeof(int) * (size_t)G;
+    p.R = std::max(1, std::min(G + 3, (int)((kMaxSmem - edge) / (2 * sizeof(float) * (size_t)pp)) - 1));
+    p.nbands = (G + 3 + p.R - 1) / p.R;
+    p.smem_adj = 2 * sizeof(float) * (size_t)(p.R + 1) * pp + edge;
+    p.narrow = hull_ok(g);
     const int nrays = pt->n * g->n_t;
     const int want = std::max(1, std::min(num_sms(), (nrays + 31) / 32));   // one persistent CTA per SM
     const int nc = max_clusters(p.smem_adj);
@@ -530,7 +726,7 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     return p;
 }
 
-RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl, int splits, const float* sos) {
+RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl, const float* sos) {
     RayArgs a;
     a.g = make_geo(g);
     a.N = pt->n;
@@ -540,8 +736,7 @@ RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl
     a.dLdw = nullptr;
     a.part = nullptr;
     a.out = nullptr;
-    a.splits = splits;
-    a.use_smem = pl.use_smem_fwd;
+    a.use_smem = pl.fwd_mode != kFwdGlobal;
     a.cluster = pl.cluster;
     return a;
 }
@@ -551,27 +746,24 @@ RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl
 pact_status launch_pixel_rays(const pact_geometry* g, const float* sos, const float* p0, int pix0, int npix,
                               float* wT, int ld, cudaStream_t st) {
     if (npix <= 0) return PACT_OK;
-    const int G = g->sos_g;
-    const size_t gbytes = (size_t)G * smem_pitch(G) * sizeof(float);
-    const bool smem = gbytes <= kMaxSmem;
-    const void* fn = smem ? (const void*)rays_pix_kernel<true> : (const void*)rays_pix_kernel<false>;
-    if (smem) PACT_TRY(ensure_smem(fn, gbytes, "rf_synth: shared memory attribute"));
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, smem ? gbytes : 0) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    const int grid = std::min(npix, num_sms() * per_sm);
+    size_t smem = 0;
+    const int mode = fwd_mode(g, &smem);
+    const void* fn = mode == kFwdPadded   ? (const void*)rays_pix_kernel<kRayLanes, true, true>
+                     : mode == kFwdShared ? (const void*)rays_pix_kernel<kRayLanes, true, false>
+                                          : (const void*)rays_pix_kernel<kRayLanes, false, false>;
+    if (smem) PACT_TRY(ensure_smem(fn, smem, "rf_synth: shared memory attribute"));
+    const int grid = std::min(npix, persistent_grid(fn, 512, smem));
     RayArgs a = {};
     a.g = make_geo(g);
     a.N = 0;
     a.sos = sos;
-    a.use_smem = smem;
-    if (smem)
-        rays_pix_kernel<true><<<grid, 512, gbytes, st>>>(a, p0, pix0, npix, wT, ld);
+    a.use_smem = mode != kFwdGlobal;
+    if (mode == kFwdPadded)
+        rays_pix_kernel<kRayLanes, true, true><<<grid, 512, smem, st>>>(a, p0, pix0, npix, wT, ld);
+    else if (mode == kFwdShared)
+        rays_pix_kernel<kRayLanes, true, false><<<grid, 512, smem, st>>>(a, p0, pix0, npix, wT, ld);
     else
-        rays_pix_kernel<false><<<grid, 512, 0, st>>>(a, p0, pix0, npix, wT, ld);
+        rays_pix_kernel<kRayLanes, false, false><<<grid, 512, 0, st>>>(a, p0, pix0, npix, wT, ld);
     return check_launch("rf_synth: ray kernel");
 }
 
@@ -585,14 +777,17 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
     PACT_TRY(check_patches(pt));
     if (!sos || !w) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays: sos and w must not be NULL");
     const Plan pl = make_plan(g, pt);
-    RayArgs a = make_args(g, pt, pl, pl.splits_fwd, sos);
+    RayArgs a = make_args(g, pt, pl, sos);
     a.w = w;
-    if (pl.use_smem_fwd) {
-        PACT_TRY(ensure_smem((const void*)rays_fwd_kernel<true>, pl.smem_fwd, "sos_to_delays: shared memory attribute"));
-        rays_fwd_kernel<true><<<pl.nb_fwd, 512, pl.smem_fwd, as_stream(stream)>>>(a);
-    } else {
-        rays_fwd_kernel<false><<<pl.nb_fwd, 512, 0, as_stream(stream)>>>(a);
-    }
+    cudaStream_t st = as_stream(stream);
+    if (pl.smem_fwd)
+        PACT_TRY(ensure_smem(fwd_fn(pl.fwd_mode), pl.smem_fwd, "sos_to_delays: shared memory attribute"));
+    if (pl.fwd_mode == kFwdPadded)
+        rays_fwd_kernel<kRayLanes, true, true><<<pl.nb_fwd, 512, pl.smem_fwd, st>>>(a);
+    else if (pl.fwd_mode == kFwdShared)
+        rays_fwd_kernel<kRayLanes, true, false><<<pl.nb_fwd, 512, pl.smem_fwd, st>>>(a);
+    else
+        rays_fwd_kernel<kRayLanes, false, false><<<pl.nb_fwd, 512, 0, st>>>(a);
     return check_launch("sos_to_delays kernel");
 }
 
@@ -614,7 +809,7 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     if (ws_bytes < pl.ws) return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, pl.ws);
     cudaStream_t st = as_stream(stream);
     const int GG = g->sos_g * g->sos_g;
-    RayArgs a = make_args(g, pt, pl, 1, sos);
+    RayArgs a = make_args(g, pt, pl, sos);
     a.dLdw = dL_dw;
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
@@ -632,10 +827,10 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
         attr.val.clusterDim.z = 1;
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, rays_adj_kernel, a, pl.R, pl.nbands) != cudaSuccess)
+        if (cudaLaunchKernelEx(&cfg, rays_adj_kernel, a, pl.R, pl.nbands, pl.narrow) != cudaSuccess)
             return check_launch("sos_to_delays_adj kernel (cluster launch)");
     } else {
-        rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a, pl.R, pl.nbands);
+        rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a, pl.R, pl.nbands, pl.narrow);
     }
     PACT_TRY(check_launch("sos_to_delays_adj kernel"));
     // one partial grid per cluster (or CTA): a single fixed-order sum

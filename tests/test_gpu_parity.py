@@ -114,6 +114,28 @@ def test_sos_to_delays_adj(name):
     assert rel(g2, ref + 1.0) <= 2e-3
 
 
+def test_rays_with_mask_beyond_the_node_hull():
+    """A mask disk larger than the SOS grid's field of view: samples beyond the
+    node hull take the edge-clamped SOS (the kernels' clamped paths)."""
+    cfg = inputs.config_tiny(p=16, m=4)
+    gd = cfg.geometry_dict()
+    gd["mask_radius"] = 0.7 * cfg.fov
+    pb = pact.Problem(cfg, DEV)
+    pb.geom.mask_radius = gd["mask_radius"]
+    case = inputs.make_case(cfg, 9)
+    sos_np = case["sos_true"].copy()
+    sos_np[0, :] += 30.0                              # the edge rows matter now
+    sos_np[:, -1] -= 25.0
+    sos = torch.as_tensor(sos_np, device=DEV)
+    w = cpu(pact.sos_to_delays(pb, sos))
+    ref = O.wavefront_errors(O.geom(gd), sos_np, case["centres"]).numpy()
+    assert rel(w, ref) <= 1e-4
+    r = np.random.default_rng(12).standard_normal((cfg.n_patches, cfg.n_t)).astype(np.float32)
+    g = cpu(pact.sos_to_delays_adj(pb, sos, torch.as_tensor(r, device=DEV)))
+    ref = O.sos_to_delays_adj(O.geom(gd), sos_np, case["centres"], r).numpy()
+    assert rel(g, ref) <= 2e-3
+
+
 def test_sos_to_delays_adj_full_size():
     cfg = inputs.config_full()
     case = inputs.make_case(cfg, 1)
