@@ -52,6 +52,7 @@ struct Geo {
     float dx;
     int G;
     float sos_dx, mask_r, h;
+    float inv_h;        // 1 / h
 };
 
 inline Geo make_geo(const pact_geometry* g) {
@@ -68,6 +69,7 @@ inline Geo make_geo(const pact_geometry* g) {
     o.sos_dx = g->sos_dx;
     o.mask_r = g->mask_radius;
     o.h = g->ray_step;
+    o.inv_h = 1.f / g->ray_step;
     return o;
 }
 

@@ -16,8 +16,6 @@
 // partial grid to the workspace and two small kernels sum the partials in a
 // fixed order (deterministic).  Grids too large for shared memory read the SOS
 // from global memory and scatter with global atomics instead.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
 #include "pact_internal.cuh"
@@ -62,20 +60,6 @@ __device__ __forceinline__ Ray make_ray(const Geo& g, float2 c, int n) {
     return r;
 }
 
-// Broadcast lane `src`'s ray to the whole warp.
-__device__ __forceinline__ Ray shfl_ray(const Ray& r, int src) {
-    Ray o;
-    o.ax = __shfl_sync(0xffffffffu, r.ax, src);
-    o.ay = __shfl_sync(0xffffffffu, r.ay, src);
-    o.bx = __shfl_sync(0xffffffffu, r.bx, src);
-    o.by = __shfl_sync(0xffffffffu, r.by, src);
-    o.L = __shfl_sync(0xffffffffu, r.L, src);
-    o.chord = __shfl_sync(0xffffffffu, r.chord, src);
-    o.rem = __shfl_sync(0xffffffffu, r.rem, src);
-    o.nfull = __shfl_sync(0xffffffffu, r.nfull, src);
-    return o;
-}
-
 struct Bil {
     int idx;        // node (iy, ix) in the grid of row pitch `pitch`
     float tx, ty;
@@ -116,7 +100,6 @@ struct RayArgs {
     float* part;          // adjoint partial grids [gridDim.x][G*G] (smem variant)
     float* out;           // adjoint output (global-atomic variant)
     int use_smem;
-    int cluster;          // adjoint: CTAs per thread-block cluster that pool their grids (0: none)
 };
 
 // Shared-memory grid pitch: one extra column so that nodes of one grid column
@@ -155,40 +138,33 @@ __device__ __forceinline__ void load_excess(float* dv, const float* sos, int G, 
 __host__ __device__ __forceinline__ int pad_pitch(int G) { return G + 5; }
 __host__ __device__ __forceinline__ size_t pad_bytes(int G) { return (size_t)(G + 4) * pad_pitch(G) * sizeof(float); }
 
+// Padded rows r0 .. r0 + rows - 1 of the SOS grid (raw values, edge-clamped
+// sources) into dv[row - r0][.] with 4-byte asynchronous copies, all in flight
+// at once (the grid comes from L2, whose latency would otherwise be paid per
+// load); the caller waits with cp_async_wait_all and a barrier.
+__device__ __forceinline__ void stage_padded_async(float* dv, const float* sos, int G, int r0, int rows) {
+    const int pitch = pad_pitch(G), P = G + 4;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int pl = threadIdx.x >> 5; pl < rows; pl += nw) {
+        const float* row = sos + (size_t)min(max(r0 + pl - 2, 0), G - 1) * G;
+        for (int cc = lane; cc < P; cc += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dv + pl * pitch + cc)),
+                         "l"(row + min(max(cc - 2, 0), G - 1))
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The whole padded excess grid dv = sos - v0 (see pad_pitch).
 __device__ __forceinline__ void load_excess_padded(float* dv, const float* sos, int G, float v0) {
     const int pitch = pad_pitch(G), P = G + 4;
-    if ((G & 3) == 0 && (reinterpret_cast<uintptr_t>(sos) & 15) == 0) {
-        const float4* s4 = reinterpret_cast<const float4*>(sos);
-        const int G4 = G >> 2, n4 = G * G4;
-#pragma unroll 4
-        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
-            const float4 v = __ldg(s4 + q);
-            const int p = q / G4, c = (q - (q / G4) * G4) << 2;
-            float* d = dv + (p + 2) * pitch + c + 2;
-            d[0] = v.x - v0;
-            d[1] = v.y - v0;
-            d[2] = v.z - v0;
-            d[3] = v.w - v0;
-        }
-    } else {
-        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
-            const int p = q / G, c = q - (q / G) * G;
-            dv[(p + 2) * pitch + c + 2] = __ldg(sos + q) - v0;
-        }
-    }
-    // the two outer rings, replicated from the edge nodes (corners are written twice, with the same value)
-    for (int q = threadIdx.x; q < 4 * P; q += blockDim.x) {
-        const int side = q / P, k = q - (q / P) * P;        // k along the side
-        const int kk = min(max(k - 2, 0), G - 1);
-        for (int ring = 0; ring < 2; ++ring) {
-            int pp, cc, p, c;
-            if (side == 0) { pp = ring; cc = k; p = 0; c = kk; }                 // top rows
-            else if (side == 1) { pp = P - 1 - ring; cc = k; p = G - 1; c = kk; } // bottom rows
-            else if (side == 2) { pp = k; cc = ring; p = kk; c = 0; }            // left columns
-            else { pp = k; cc = P - 1 - ring; p = kk; c = G - 1; }               // right columns
-            dv[pp * pitch + cc] = __ldg(sos + p * G + c) - v0;
-        }
-    }
+    stage_padded_async(dv, sos, G, 0, P);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int pl = threadIdx.x >> 5; pl < P; pl += blockDim.x >> 5)
+        for (int cc = threadIdx.x & 31; cc < P; cc += 32) dv[pl * pitch + cc] -= v0;
 }
 
 // Slowness excess (v - v0)/v = dv / (v0 + dv) at padded node coordinates
@@ -315,6 +291,8 @@ __global__ void __launch_bounds__(512) rays_pix_kernel(const RayArgs a, const fl
     }
 }
 
+constexpr int kAdjLanes = 4;   // lanes per ray in the adjoint
+
 // Round-to-nearest int of |x| < 2^22 without a conversion instruction: adding
 // 1.5 * 2^23 leaves round(x) in the low mantissa bits of the sum.
 __device__ __forceinline__ int fixed_round(float x) { return __float_as_int(x + 12582912.f) - 0x4B400000; }
@@ -364,15 +342,15 @@ __device__ __forceinline__ T fold_col(const T* row, int c, int G) {
     return v;
 }
 
-// Ray adjoint.  CTA b takes the rays r = b, b + nb, b + 2 nb, ... of the flat
-// (patch, transducer) index r = i N_t + n, and each warp a contiguous block of
-// them, so that its warps integrate rays of different patches and directions
-// at the same time (rays of one patch all start at the same centre, where their
-// scatters would collide).  A warp takes one ray at a time (its rays differ in
-// length, so lanes on different rays would wait for the longest); a lane walks
-// a contiguous run of samples of the ray and keeps the bilinear weights of the
-// current cell in registers, adding them to the shared grid only when the walk
-// leaves the cell.
+// Ray adjoint.  CTA b takes the work items t = b, b + nb, b + 2 nb, ... (item =
+// a patch and a block of 32 / kAdjLanes consecutive transducers), its warps
+// items of different patches at the same time (rays of one patch all start at
+// the same centre, where their
+// scatters would collide).  Within a warp, groups of kAdjLanes lanes take the
+// rays to consecutive transducers of one patch (similar lengths, so the lanes
+// finish together); a lane walks a contiguous run of samples of its ray, from a
+// staggered start, and keeps the bilinear weights of the current cell in
+// registers, adding them to the shared grid only when the walk leaves the cell.
 //
 // Coordinates are those of the padded grid (node (p, c) at (p + 2, c + 2), see
 // load_excess_padded), clamped to [1, G + 2]; floor() takes no conversion
@@ -397,35 +375,58 @@ __device__ __forceinline__ T fold_col(const T* row, int c, int G) {
 // r0 .. r0 + R), so that the excess rows and the accumulator of a band fit in
 // shared memory for every G <= 512; a ray visits each band with the samples
 // whose cell row lies in it.  Node row r0 + R is shared with the next band: its
-// sums move to that band's first row.  With clusters, the CTAs of a cluster sum
-// each band of their grids through distributed shared memory in a fixed order
-// of ranks and write one partial grid per cluster; otherwise every CTA writes
-// its own.
+// sums move to that band's first row.  Every CTA writes its own partial grid;
+// one fixed-order kernel sums them.  (Clusters of four CTAs summing their grids
+// through distributed shared memory were measured slower: fewer SMs in use and
+// the cluster barriers per band.)
 __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int R, int nbands, int narrow) {
     extern __shared__ float sm[];
     __shared__ float red_s[32];
     __shared__ float scale_s[2];      // S and 1/S (NaN: poisoned)
+    __shared__ int next_s;            // next unclaimed item of the band
     const int G = a.g.G, pitch = pad_pitch(G), PG = G + 4;
     float* dv_s = sm;                                              // [R + 1][pitch] padded excess rows
     int* acc_s = reinterpret_cast<int*>(sm + (R + 1) * pitch);      // [R + 1][pitch] padded sums
     int* edge_s = acc_s + (R + 1) * pitch;                          // [2][G] sums of the first / last node row
     const float v0 = a.g.v0, h = a.g.h;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nrays = a.N * a.g.n_t, nb = gridDim.x;
-    const int mine = nrays > (int)blockIdx.x ? (nrays - (int)blockIdx.x + nb - 1) / nb : 0;   // rays of this CTA
+    constexpr int L = kAdjLanes, RB = 32 / L;
+    const int n_t = a.g.n_t, nblk = (n_t + RB - 1) / RB, nb = gridDim.x;
+    const int items = a.N * nblk;                                  // (patch, block of RB transducers)
+    const int mine = items > (int)blockIdx.x ? (items - (int)blockIdx.x + nb - 1) / nb : 0;   // items of this CTA
 
     // fixed-point scale of this CTA
     float gsum = 0.f, gmax = 0.f, vmin = INFINITY, bad = 0.f;
-    for (int t = threadIdx.x; t < mine; t += blockDim.x) {
-        const float gv = fabsf(a.dLdw[(size_t)blockIdx.x + (size_t)nb * t]);
+    for (int q = threadIdx.x; q < mine * RB; q += blockDim.x) {
+        const int t = (int)blockIdx.x + nb * (q / RB), i = t / nblk, n = (t - i * nblk) * RB + q % RB;
+        const float gv = n < n_t ? fabsf(a.dLdw[(size_t)i * n_t + n]) : 0.f;
         gsum += gv;
         gmax = fmaxf(gmax, gv);
     }
-    for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
-        const float v = __ldg(a.sos + q);
-        if (!(v > 0.f) || !isfinite(v)) bad = 1.f;
-        vmin = fminf(vmin, v);
-    }
+    // band b's padded excess rows r0 .. r0 + rows - 1 into dv_s (raw values by
+    // asynchronous copies, then v - v0 in place); those of a one-band grid also
+    // give the minimum SOS
+    auto stage = [&](int r0, int rows, bool track) {
+        stage_padded_async(dv_s, a.sos, G, r0, rows);
+        cp_async_wait_all();
+        __syncthreads();
+        for (int pl = warp; pl < rows; pl += nw)
+            for (int cc = lane; cc < PG; cc += 32) {
+                const float v = dv_s[pl * pitch + cc];
+                if (track) {
+                    if (!(v > 0.f) || !isfinite(v)) bad = 1.f;
+                    vmin = fminf(vmin, v);
+                }
+                dv_s[pl * pitch + cc] = v - v0;
+            }
+    };
+    stage(0, min(R + 1, PG), nbands == 1);
+    if (nbands > 1)
+        for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+            const float v = __ldg(a.sos + q);
+            if (!(v > 0.f) || !isfinite(v)) bad = 1.f;
+            vmin = fminf(vmin, v);
+        }
     for (int q = threadIdx.x; q < 2 * G; q += blockDim.x) edge_s[q] = 0;
     gsum = block_sum(gsum, red_s);
     gmax = block_max(gmax, red_s);
@@ -444,34 +445,29 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     __syncthreads();
     const float S = scale_s[0];
 
-    // warp w takes the contiguous block t0 <= t < t1 of the CTA's rays t (r = b + nb t)
-    const int t0 = (int)((long long)mine * warp / nw), t1 = (int)((long long)mine * (warp + 1) / nw);
-    const int nwarp = t1 - t0;
-    namespace cg = cooperative_groups;
+    const int sub = lane % L, grp = lane / L;
     for (int band = 0; band < nbands; ++band) {
         const bool last_band = band == nbands - 1;
         const int r0 = band * R;
         const int r1 = last_band ? G + 3 : r0 + R;        // padded cell rows r0 <= iy < r1
         const int rows = min(R + 1, PG - r0);             // padded node rows r0 .. r0 + rows - 1
-        for (int pl = warp; pl < rows; pl += nw) {
-            const float* src = a.sos + (size_t)min(max(r0 + pl - 2, 0), G - 1) * G;
-            for (int cc = lane; cc < PG; cc += 32) dv_s[pl * pitch + cc] = __ldg(src + min(max(cc - 2, 0), G - 1)) - v0;
-        }
+        if (band > 0) stage(r0, rows, false);
         for (int q = threadIdx.x + (band > 0 ? pitch : 0); q < rows * pitch; q += blockDim.x) acc_s[q] = 0;
+        if (threadIdx.x == 0) next_s = nw;
         __syncthreads();
-        for (int kb = 0; kb < nwarp; kb += 32) {
-            // 32 rays set up at once (one per lane), then integrated one after the
-            // other by the whole warp (lanes over samples: all lanes on one ray)
-            const int cnt = min(32, nwarp - kb);
-            const int r = (int)blockIdx.x + nb * (t0 + kb + min(lane, cnt - 1));
-            const int i = r / a.g.n_t, n = r - (r / a.g.n_t) * a.g.n_t;
-            const int2 cc = a.centres[i];
-            const Ray mine_ray = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
-            const float my_g = lane < cnt ? a.dLdw[r] : 0.f;
-            for (int rr = 0; rr < cnt; ++rr) {
-                const float gr = __shfl_sync(0xffffffffu, my_g, rr);
-                if (gr == 0.f) continue;
-                const Ray ry = shfl_ray(mine_ray, rr);
+        // warp w starts on the CTA's item j = w and then claims the next free one
+        // (item t = b + nb j: the concurrent warps of a CTA work on different
+        // patches); group grp of L
+        // lanes takes transducer blk RB + grp, each lane a contiguous run of the
+        // ray's samples in this band, started at an offset that grows with grp
+        // (the RB rays of a warp leave the same centre in neighbouring directions:
+        // staggered, their lanes are never at the same place at the same time)
+        for (int j = warp; j < mine;) {
+            const int t = (int)blockIdx.x + nb * j, i = t / nblk, n = (t - i * nblk) * RB + grp;
+            const float gr = n < n_t ? a.dLdw[(size_t)i * n_t + n] : 0.f;
+            if (gr != 0.f) {
+                const int2 cc = a.centres[i];
+                const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
                 const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
                 const float hbx = h * ry.bx, hby = h * ry.by;
                 const float ax = ry.ax + 2.f, ay = ry.ay + 2.f;
@@ -488,20 +484,28 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                     mlo = max(0, (int)floorf(lo) - 2);
                     mhi = min(nsamp, (int)ceilf(hi) + 2);
                 }
-                const int per = (max(mhi - mlo, 0) + 31) >> 5;
-                const int m0 = mlo + lane * per, m1 = min(mhi, m0 + per);
-                const float ulast = ry.nfull + 0.5f * (ry.rem / h);
+                const int per = (max(mhi - mlo, 0) + L - 1) / L;
+                const int m0 = mlo + sub * per, len = max(0, min(mhi, m0 + per) - m0);
+                const int off = len * grp / RB;                   // staggered start within the run
+                const float ulast = ry.nfull + 0.5f * (ry.rem * a.g.inv_h);
                 const float gv0 = gr * v0;
                 int cur = -1;
                 float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
-                float uf = m0 + 0.5f;
-                for (int m = m0; m < m1; ++m, uf += 1.f) {
+                int m = m0 + off;
+                float uf = m + 0.5f;
+                for (int k = 0; k < len; ++k) {
                     const bool last = m >= ry.nfull;
                     const float u = last ? ulast : uf;
                     // clamped to the padded grid: the same value as the edge-clamped
                     // interpolation, and every access in bounds for any geometry
                     const float x = fminf(fmaxf(fmaf(u, hbx, ax), 1.f), (float)(G + 2));
                     const float y = fminf(fmaxf(fmaf(u, hby, ay), 1.f), (float)(G + 2));
+                    if (++m == m0 + len) {                        // wrap to the start of the run
+                        m = m0;
+                        uf = m0 + 0.5f;
+                    } else {
+                        uf += 1.f;
+                    }
                     const float tY = y + 8388607.5f;
                     const int iy = __float_as_int(tY) - 0x4B000000;
                     if (iy < r0 || iy >= r1) continue;
@@ -528,15 +532,16 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                 }
                 if (cur >= 0) scatter4(acc_s, pitch, cur, S, c00, c01, c10, c11);
             }
+            // next item of this CTA: claimed dynamically, so that warps whose
+            // items were short take more
+            int nj = 0;
+            if (lane == 0) nj = atomicAdd(&next_s, 1);
+            j = __shfl_sync(0xffffffffu, nj, 0);
         }
         // padded rows written by this band: r0 .. r0 + out_rows - 1 (its last row moves to the next band);
         // rows 3 .. G are node rows 1 .. G - 2, the rest fold onto node rows 0 and G - 1
         const int out_rows = last_band ? rows : R;
-        cg::cluster_group cl = cg::this_cluster();
-        if (a.cluster)
-            cl.sync();
-        else
-            __syncthreads();
+        __syncthreads();
         {
             const int t_end = min(3, r0 + out_rows), b_beg = max(G + 1, r0);      // padded rows [r0, t_end), [b_beg, r0 + out_rows)
             for (int c = threadIdx.x; c < G; c += blockDim.x) {
@@ -548,21 +553,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
             }
         }
         const int i0 = max(3, r0), i1 = min(G + 1, r0 + out_rows);    // interior padded rows [i0, i1)
-        if (a.cluster) {
-            const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-            const int nrow = max(0, i1 - i0), share = (nrow + csize - 1) / csize;
-            const int p0 = i0 + min(nrow, rank * share), p1 = i0 + min(nrow, rank * share + share);
-            float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G;
-            for (int pp = p0 + warp; pp < p1; pp += nw)
-                for (int c = lane; c < G; c += 32) {
-                    float sum = 0.f;
-                    for (int k = 0; k < csize; ++k)
-                        sum += (float)fold_col(cl.map_shared_rank(acc_s, k) + (pp - r0) * pitch, c, G) *
-                               *cl.map_shared_rank(scale_s + 1, k);
-                    dst[(pp - 2) * G + c] = sum;
-                }
-            cl.sync();                               // remote reads end before any CTA changes its grid
-        } else {
+        {
             const float invS = scale_s[1];
             float* dst = a.part + (size_t)blockIdx.x * G * G;
             for (int pp = i0 + warp; pp < i1; pp += nw)
@@ -576,18 +567,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
         }
     }
     // node rows 0 and G - 1
-    if (a.cluster) {
-        cg::cluster_group cl = cg::this_cluster();
-        cl.sync();
-        const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-        float* dst = a.part + (size_t)(blockIdx.x / csize) * G * G;
-        for (int q = rank * blockDim.x + threadIdx.x; q < 2 * G; q += csize * blockDim.x) {
-            float sum = 0.f;
-            for (int k = 0; k < csize; ++k) sum += (float)cl.map_shared_rank(edge_s, k)[q] * *cl.map_shared_rank(scale_s + 1, k);
-            dst[q < G ? q : (G - 1) * G + (q - G)] = sum;
-        }
-        cl.sync();
-    } else {
+    {
         const float invS = scale_s[1];
         float* dst = a.part + (size_t)blockIdx.x * G * G;
         for (int q = threadIdx.x; q < 2 * G; q += blockDim.x)
@@ -606,7 +586,6 @@ __global__ void reduce_parts_kernel(const float* part, int np, int GG, float* ou
 
 constexpr size_t kMaxSmem = 200 * 1024;
 
-constexpr int kCluster = 4;   // CTAs per cluster in the ray adjoint (8 would not fit in one wave)
 
 constexpr int kRayLanes = 1;   // lanes per ray in the forward integrals
 
@@ -652,48 +631,9 @@ int persistent_grid(const void* fn, int threads, size_t smem) {
 
 struct Plan {
     int fwd_mode, nb_fwd;
-    int R, nbands, nb_adj, cluster, nparts, narrow;
+    int R, nbands, nb_adj, nparts, narrow;
     size_t smem_fwd, smem_adj, ws;
 };
-
-// How many clusters of kCluster adjoint CTAs (1024 threads, `smem` bytes each)
-// can be resident at once on this device (0: clusters unavailable); cached
-// per device and shared-memory size.
-int max_clusters(size_t smem) {
-    struct Entry {
-        int dev;
-        size_t smem;
-        int n;
-    };
-    static Entry cache[16];
-    static int used = 0;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    for (int k = 0; k < used; ++k)
-        if (cache[k].dev == dev && cache[k].smem == smem) return cache[k].n;
-    int n = 0;
-    const void* fn = (const void*)rays_adj_kernel;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(kCluster);
-        cfg.blockDim = dim3(1024);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = kCluster;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) n = 0;
-    }
-    cudaGetLastError();
-    if (used < 16) cache[used++] = Entry{dev, smem, n};
-    return n;
-}
 
 Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     Plan p;
@@ -714,14 +654,8 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     p.narrow = hull_ok(g);
     const int nrays = pt->n * g->n_t;
     const int want = std::max(1, std::min(num_sms(), (nrays + 31) / 32));   // one persistent CTA per SM
-    const int nc = max_clusters(p.smem_adj);
-    p.cluster = 0;
     p.nb_adj = want;
-    if (nc > 0 && want >= kCluster) {
-        p.cluster = kCluster;
-        p.nb_adj = std::min(nc, want / kCluster) * kCluster;
-    }
-    p.nparts = p.cluster ? p.nb_adj / p.cluster : p.nb_adj;
+    p.nparts = p.nb_adj;
     p.ws = align_up((size_t)p.nparts * G * G * sizeof(float), 256);
     return p;
 }
@@ -737,7 +671,6 @@ RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl
     a.part = nullptr;
     a.out = nullptr;
     a.use_smem = pl.fwd_mode != kFwdGlobal;
-    a.cluster = pl.cluster;
     return a;
 }
 
@@ -814,26 +747,9 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
     PACT_TRY(ensure_smem((const void*)rays_adj_kernel, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
-    if (pl.cluster) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(pl.nb_adj);
-        cfg.blockDim = dim3(1024);
-        cfg.dynamicSmemBytes = pl.smem_adj;
-        cfg.stream = st;
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = pl.cluster;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, rays_adj_kernel, a, pl.R, pl.nbands, pl.narrow) != cudaSuccess)
-            return check_launch("sos_to_delays_adj kernel (cluster launch)");
-    } else {
-        rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a, pl.R, pl.nbands, pl.narrow);
-    }
+    rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a, pl.R, pl.nbands, pl.narrow);
     PACT_TRY(check_launch("sos_to_delays_adj kernel"));
-    // one partial grid per cluster (or CTA): a single fixed-order sum
+    // one partial grid per CTA: a single fixed-order sum
     reduce_parts_kernel<<<(GG + 255) / 256, 256, 0, st>>>(a.part, pl.nparts, GG, dL_dsos, accumulate);
     return check_launch("sos_to_delays_adj reduction");
 }
