@@ -575,13 +575,32 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     }
 }
 
-// out[q] (+)= sum of the partial grids part[0 .. np)[q], in order.
-__global__ void reduce_parts_kernel(const float* part, int np, int GG, float* out, int accumulate) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= GG) return;
+// Sum of the partial grids part[0 .. np) at the 32 consecutive nodes q0 + lane
+// of this block: warp w adds the partials of its chunk [np w / nw, np (w+1) / nw)
+// in order, warp 0 then adds the chunk sums in order (a fixed order, with
+// np / nw loads in flight per lane instead of np).  Valid in warp 0.
+__device__ __forceinline__ float sum_parts32(const float* part, int np, int GG, int q0, float* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int q = q0 + lane;
+    const int r0 = np * w / nw, r1 = np * (w + 1) / nw;
     float s = 0.f;
-    for (int r = 0; r < np; ++r) s += part[(size_t)r * GG + q];
-    out[q] = accumulate ? out[q] + s : s;
+    if (q < GG)
+        for (int r = r0; r < r1; ++r) s += part[(size_t)r * GG + q];
+    red[w * 32 + lane] = s;
+    __syncthreads();
+    float tot = 0.f;
+    if (w == 0)
+        for (int k = 0; k < nw; ++k) tot += red[k * 32 + lane];
+    return tot;
+}
+
+// out[q] (+)= sum of the partial grids part[0 .. np)[q] (block: 32 nodes).
+__global__ void __launch_bounds__(256) reduce_parts_kernel(const float* part, int np, int GG, float* out,
+                                                           int accumulate) {
+    __shared__ float red[256];
+    const int q = blockIdx.x * 32 + (threadIdx.x & 31);
+    const float g = sum_parts32(part, np, GG, blockIdx.x * 32, red);
+    if (threadIdx.x < 32 && q < GG) out[q] = accumulate ? out[q] + g : g;
 }
 
 constexpr size_t kMaxSmem = 200 * 1024;
@@ -661,7 +680,7 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
 }
 
 RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl, const float* sos) {
-    RayArgs a;
+    RayArgs a = {};
     a.g = make_geo(g);
     a.N = pt->n;
     a.centres = reinterpret_cast<const int2*>(pt->centres);
@@ -750,6 +769,6 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a, pl.R, pl.nbands, pl.narrow);
     PACT_TRY(check_launch("sos_to_delays_adj kernel"));
     // one partial grid per CTA: a single fixed-order sum
-    reduce_parts_kernel<<<(GG + 255) / 256, 256, 0, st>>>(a.part, pl.nparts, GG, dL_dsos, accumulate);
+    reduce_parts_kernel<<<(GG + 31) / 32, 256, 0, st>>>(a.part, pl.nparts, GG, dL_dsos, accumulate);
     return check_launch("sos_to_delays_adj reduction");
 }
