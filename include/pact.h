@@ -115,10 +115,11 @@ pact_status pact_das_stack(const pact_geometry* g, const float* rf, int n_s, flo
  * with w the wavefront error of pact_sos_to_delays on the segment r_p -> r_n
  * (same quadrature, mask and background), and
  *   rf[n][q] = sum_p p0_p (R_s / |r_p - r_n|)^spread psi(t0 + q/fs - tau(p, n)),
- *   psi(t) = (t / sigma) exp(1/2 - t^2 / (2 sigma^2)),
- * minus the derivative of a Gaussian pressure pulse, extremes -+1 at
- * t = -+sigma, amplitude spectrum peaking at 1 / (2 pi sigma).  psi is
- * evaluated within 6 sigma of each arrival (|psi| < 2e-7 beyond).
+ *   psi(t) = (1 - t^2 / sigma^2) exp(-t^2 / (2 sigma^2)),
+ * -2 dp/dt of an N-shaped pressure pulse p (the time derivative of a
+ * Gaussian): even, psi(0) = 1, amplitude spectrum peaking at
+ * 1 / (sqrt(2) pi sigma).  psi is evaluated within 6 sigma of each arrival
+ * (|psi| < 6e-7 beyond).
  * Model mismatches for robustness runs: spread = 1/2 adds cylindrical
  * spreading; ring_dr moves the receiving ring to radius R_s = R + ring_dr
  * while the geometry (and DAS) keep R.  spread = ring_dr = 0 is the model

@@ -20,14 +20,18 @@ Every pixel p of the initial-pressure image p0 emits one band-limited pulse:
     S(t_q, n) = sum_p p0_p a(p, n) psi(t_q - tau(p, n)),   t_q = t0 + q / fs,
 
 Readings (the paper's data come from a full-wave simulator; here the
-pressure pulse at the transducer is a Gaussian in time, a 1-8 MHz band after
-the derivative, and the path is the straight ray of Eq. 2-3):
+pressure at the transducer is the N-shaped pulse of a small absorber, the
+time derivative of a Gaussian, and the path is the straight ray of Eq. 2-3):
 
-* psi is minus the time derivative of a Gaussian, scaled so that its
-  extremes are -+1 at t = -+sigma:  psi(t) = (t / sigma) exp(1/2 - t^2 / (2 sigma^2)).
-  Its amplitude spectrum is proportional to f exp(-2 pi^2 sigma^2 f^2), which
-  peaks at 1 / (2 pi sigma); sigma = 1 / (2 pi 4 MHz) puts the half-amplitude
-  band at 1.3-7.7 MHz.
+* psi = -2 dp/dt of p(t) = -sigma t exp(-t^2 / (2 sigma^2)) / 2, i.e. minus the
+  second derivative of a Gaussian, scaled to psi(0) = 1:
+      psi(t) = (1 - t^2 / sigma^2) exp(-t^2 / (2 sigma^2)).
+  It is even, so the DAS image of a point source has the real, even
+  spectrum that the transfer functions of Eq. 4 assume (an odd pulse would
+  give the two ring directions of Eq. 4 opposite signs).  Its amplitude
+  spectrum is proportional to f^2 exp(-2 pi^2 sigma^2 f^2), peaking at
+  1 / (sqrt(2) pi sigma); sigma = 1 / (sqrt(2) pi 4 MHz) puts the
+  half-amplitude band at 1.9-6.5 MHz and the -20 dB band at 0.8-8.8 MHz.
 * a(p, n) = (R_s / |r_p - r_n|)^gamma: gamma = 0 (the default) is the model
   the method assumes; gamma = 1/2 adds cylindrical spreading, a model
   mismatch for robustness studies.
@@ -48,10 +52,10 @@ DT = torch.float64
 
 
 def pulse(t, sigma: float) -> torch.Tensor:
-    """psi(t) = (t / sigma) exp(1/2 - t^2 / (2 sigma^2))."""
+    """psi(t) = (1 - t^2 / sigma^2) exp(-t^2 / (2 sigma^2))."""
     t = O._t(t)
     u = t / sigma
-    return u * torch.exp(0.5 - 0.5 * u * u)
+    return (1.0 - u * u) * torch.exp(-0.5 * u * u)
 
 
 def synthesis_geometry(g, ring_dr: float = 0.0) -> SimpleNamespace:
@@ -124,9 +128,9 @@ def das_at(g, rf, fs: float, t0: float, d, rows, cols) -> torch.Tensor:
 
 def pulse_band(sigma: float, level: float = 0.5):
     """Frequencies [Hz] where the amplitude spectrum of psi falls to `level`
-    of its peak, from the closed form x exp((1 - x^2)/2) = level with
-    x = f / f_peak, f_peak = 1 / (2 pi sigma)."""
+    of its peak, from the closed form x^2 exp(1 - x^2) = level with
+    x = f / f_peak, f_peak = 1 / (sqrt(2) pi sigma)."""
     from scipy.optimize import brentq
-    fp = 1.0 / (2.0 * math.pi * sigma)
-    fn = lambda x: x * math.exp(0.5 * (1.0 - x * x)) - level
+    fp = 1.0 / (math.sqrt(2.0) * math.pi * sigma)
+    fn = lambda x: x * x * math.exp(1.0 - x * x) - level
     return fp * brentq(fn, 1e-9, 1.0), fp * brentq(fn, 1.0, 50.0)

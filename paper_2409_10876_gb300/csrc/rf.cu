@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kThreads) rf_scatter_kernel(const RfArgs a) {
                 const int k = kk + j;
                 if (k >= 0 && k < a.n_s) {
                     const float u = ((float)(j - a.half) - f) * a.inv_sig;
-                    atomicAdd(rec + k, am * u * __expf(0.5f - 0.5f * u * u));
+                    atomicAdd(rec + k, am * (1.f - u * u) * __expf(-0.5f * u * u));
                 }
             }
         }

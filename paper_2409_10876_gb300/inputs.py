@@ -53,7 +53,7 @@ class Config:
     rf_fs: float = 40e6                 # sample rate [Hz]
     rf_ns: int = 4096                   # samples per transducer
     rf_t0: float = 0.0                  # time of sample 0 [s]
-    rf_sigma: float = 3.9788735773e-8   # pulse width [s]: spectrum peak 4 MHz, half-amplitude band 1.3-7.7 MHz
+    rf_sigma: float = 5.6269769760e-8   # pulse width [s]: spectrum peak 4 MHz, half-amplitude band 1.9-6.5 MHz
 
     # ---- derived geometry (configuration readings, not method arithmetic) ----
     @property

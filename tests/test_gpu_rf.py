@@ -118,5 +118,5 @@ def test_rf_to_das_centred_source_closed_form():
     chord = -b + np.sqrt(b * b - (x @ x - cfg.mask_radius ** 2))
     wn = (1 - cfg.v0 / c) * chord
     uu = (wn[None, :] - d[:, None].astype(np.float64)) / cfg.v0 / sig
-    ref = (uu * np.exp(0.5 - 0.5 * uu * uu)).sum(1)
+    ref = ((1.0 - uu * uu) * np.exp(-0.5 * uu * uu)).sum(1)
     assert np.abs(st - ref).max() <= 2e-3 * cfg.n_t

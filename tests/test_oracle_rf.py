@@ -30,28 +30,39 @@ def _pix(cfg, row, col):
 
 def _psi(t, sigma):
     u = t / sigma
-    return u * np.exp(0.5 - 0.5 * u * u)
+    return (1.0 - u * u) * np.exp(-0.5 * u * u)
 
 
-def test_pulse_extremes_and_spectrum_peak():
+def test_pulse_shape_and_spectrum():
+    """psi = -2 dp/dt (Sec. S1.1) of the N-shaped pressure pulse
+    p(t) = -sigma t exp(-t^2/(2 sigma^2)) / 2 (compression, then rarefaction),
+    by central differences of p;
+    psi is even with psi(0) = 1 and minima -2 exp(-3/2) at +-sqrt(3) sigma; its
+    amplitude spectrum (numpy's FFT) peaks at 1 / (sqrt(2) pi sigma)."""
     sig = inputs.config_rf().rf_sigma
-    assert float(R.pulse(-sig, sig)) == pytest.approx(-1.0, abs=1e-15)
-    assert float(R.pulse(sig, sig)) == pytest.approx(1.0, abs=1e-15)
-    # extremes: the derivative vanishes at +-sigma only (central differences)
     t = np.linspace(-6 * sig, 6 * sig, 120001)
+    dt = t[1] - t[0]
+    p = lambda tt: -sig * tt * np.exp(-tt * tt / (2 * sig * sig)) / 2
+    psi_fd = -2 * (p(t + dt) - p(t - dt)) / (2 * dt) / sig          # psi is scaled by 1/sigma
     y = R.pulse(t, sig).numpy()
-    assert abs(t[np.argmax(y)] - sig) < 2 * (t[1] - t[0])
-    # amplitude spectrum by numpy's FFT: peak at 1 / (2 pi sigma) and the
-    # half-amplitude band of the closed form
-    dt = sig / 200
-    tt = (np.arange(1 << 18) - (1 << 17)) * dt
+    assert np.abs(y - psi_fd).max() < 1e-6
+    assert np.array_equal(R.pulse(-t, sig).numpy(), y)
+    assert float(R.pulse(0.0, sig)) == 1.0
+    assert abs(t[np.argmin(y)] ** 2 - 3 * sig * sig) < 4 * sig * dt
+    assert y.min() == pytest.approx(-2 * np.exp(-1.5), rel=1e-8)
+    ds = sig / 200
+    tt = (np.arange(1 << 18) - (1 << 17)) * ds
     spec = np.abs(np.fft.rfft(R.pulse(tt, sig).numpy()))
-    f = np.fft.rfftfreq(tt.size, dt)
-    assert abs(f[np.argmax(spec)] - 1 / (2 * np.pi * sig)) <= f[1]
-    lo, hi = R.pulse_band(sig)
-    above = f[spec >= 0.5 * spec.max()]
-    assert abs(above.min() - lo) <= 2 * f[1] and abs(above.max() - hi) <= 2 * f[1]
-    assert 1.0e6 < lo < 1.5e6 and 7.0e6 < hi < 8.0e6
+    f = np.fft.rfftfreq(tt.size, ds)
+    assert abs(f[np.argmax(spec)] - 1 / (np.sqrt(2) * np.pi * sig)) <= f[1]
+    for level in (0.5, 0.1):
+        lo, hi = R.pulse_band(sig, level)
+        above = f[spec >= level * spec.max()]
+        assert abs(above.min() - lo) <= 2 * f[1] and abs(above.max() - hi) <= 2 * f[1]
+    lo, hi = R.pulse_band(sig, 0.5)
+    assert 1.8e6 < lo < 2.0e6 and 6.4e6 < hi < 6.7e6
+    lo, hi = R.pulse_band(sig, 0.1)
+    assert 0.7e6 < lo < 0.9e6 and 8.7e6 < hi < 9.0e6
 
 
 def test_uniform_sos_is_straight_line_time_of_flight():
