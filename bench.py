@@ -232,7 +232,7 @@ def run_gpu(args, cfg, case, rank, world, local):
     torch.cuda.synchronize()
     rec.set_state(st0)
     try:
-        gev = _GraphEvents(4)
+        gev = _GraphEvents(5)
     except Exception:
         gev = None
     def capture(events):
@@ -249,6 +249,8 @@ def run_gpu(args, cfg, case, rank, world, local):
             if events:
                 events.record(2, h)
             pact.sos_to_delays_adj(pb, rec.sos, rec.out["dL_dw"], rec.grad, accumulate=False, ws=rec.ws_adj)
+            if events:
+                events.record(4, h)
             pact.tv(pb, rec.sos, rec.lam, value=rec.out["loss"], grad=rec.grad, accumulate=True)
             pact.adam_step(rec.sos, rec.grad, rec.adam_m, rec.adam_v, 1, rec.lr, mask=rec.mask,
                            step_counter=rec.counter)
@@ -297,7 +299,7 @@ def run_gpu(args, cfg, case, rank, world, local):
     tot_ms = sum(step_ms)
     loss_end = rec.loss()
     # breakdown: the in-graph events of single replays (each read back before the next)
-    rays_ms, mcd_ms, rest_ms = [], [], []
+    rays_ms, mcd_ms, rest_ms, adj_ms = [], [], [], []
     if gev:
         for _ in range(min(200, args.steps)):
             one(g=g_step_ev)
@@ -305,8 +307,9 @@ def run_gpu(args, cfg, case, rank, world, local):
             rays_ms.append(gev.elapsed_ms(0, 1))
             mcd_ms.append(gev.elapsed_ms(1, 2))
             rest_ms.append(gev.elapsed_ms(2, 3))
+            adj_ms.append(gev.elapsed_ms(2, 4))
     else:
-        rays_ms = mcd_ms = rest_ms = [float("nan")]
+        rays_ms = mcd_ms = rest_ms = adj_ms = [float("nan")]
     if world > 1:
         t = torch.tensor([tot_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -339,6 +342,7 @@ def run_gpu(args, cfg, case, rank, world, local):
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "measured" if peaks else "fallback",
                          "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},
+            "roofline_rays": rays_roofline(cfg, statistics.mean(adj_ms), clocks),
             "gpu_launches": launches_per_step * args.steps,
             "wall_s_timed_region": wall,
             "loss": {"start": loss_start, "end": loss_end}}
@@ -370,11 +374,54 @@ def run_gpu(args, cfg, case, rank, world, local):
                             "siren_field": siren_variant(args, cfg, case, pb, Y, flush, stream),
                             "das_stack": das_variant(dev, flush, stream),
                             "channels": channels_variant(args, cfg, dev, flush, stream),
+                            "tv_sweep": tv_sweep_variant(args, cfg, case, pb, Y),
                             "channel_data": channel_data_variant(args, dev, flush, stream)}
+        cd = line["variants"]["channel_data"]["mc_deconv_loss"]
+        line["roofline_channel_data"] = {
+            "bound": "hbm", "kernel": "mc_deconv_loss on 3721 patches x 32 channels x 64x64 (2.0 GB of spectra, 16x L2)",
+            "achieved": cd["achieved_gbs"], "peak": cd["peak_gbs"], "unit": "GB/s", "frac": cd["frac"],
+            "peak_source": cd["peak_source"], "algorithmic_bytes_per_launch": cd["algorithmic_bytes"], "traffic": None}
     if rank == 0 and not args.no_warm_start:
         line["warm_start"] = warm_start_run(args, cfg, pb, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+RAY_ADJ_OPS = 24   # FP32 lane operations of one adjoint sample (see the design notes)
+
+
+def ray_samples(cfg) -> int:
+    """Midpoint samples of all rays r'_i -> r_n inside the mask disk (from the
+    geometry: ceil(chord / h) per ray)."""
+    import numpy as np
+    c = cfg.centres()
+    x = (c[:, 1] - (cfg.img_w - 1) / 2) * cfg.dx
+    y = (c[:, 0] - (cfg.img_h - 1) / 2) * cfg.dx
+    th = 2 * np.pi * np.arange(cfg.n_t) / cfg.n_t + cfg.ring_phase
+    dx = cfg.ring_radius * np.cos(th)[None] - x[:, None]
+    dy = cfg.ring_radius * np.sin(th)[None] - y[:, None]
+    L = np.hypot(dx, dy)
+    ce = (x[:, None] * dx + y[:, None] * dy) / L
+    disc = ce ** 2 - (x[:, None] ** 2 + y[:, None] ** 2 - cfg.mask_radius ** 2)
+    sq = np.sqrt(np.maximum(disc, 0.0))
+    s0, s1 = np.clip(-ce - sq, 0, L), np.clip(-ce + sq, 0, L)
+    chord = np.where(disc > 0, np.maximum(s1 - s0, 0.0), 0.0)
+    return int(np.ceil(chord / cfg.ray_step).sum())
+
+
+def rays_roofline(cfg, adj_ms: float, clocks):
+    """The ray adjoint (the longest kernel of the iteration) against the FP32
+    issue rate: RAY_ADJ_OPS algorithmic lane operations per sample over its
+    event-timed duration (kernel + partial-grid sum), peak = 152 SMs x 128
+    lanes x the SM clock sampled during the run."""
+    samples = ray_samples(cfg)
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    ach = samples * RAY_ADJ_OPS / (adj_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "rays_adj_kernel + reduce_parts_kernel (Eq. 3 adjoint), between event nodes",
+            "achieved": ach, "peak": peak, "unit": "T lane-ops/s (FP32)", "frac": ach / peak,
+            "samples_per_launch": samples, "ops_per_sample": RAY_ADJ_OPS, "ms": adj_ms,
+            "peak_source": "152 SMs x 128 FP32 lanes x sampled SM clock"}
 
 
 def _time_graph(g, flush, stream, steps: int):
@@ -425,6 +472,32 @@ def channels_variant(args, cfg, dev, flush, stream):
             g.replay()
         ms = _time_graph(g, flush, stream, 200)
         out[str(m)] = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_iter": statistics.mean(ms)}
+    return out
+
+
+def tv_sweep_variant(args, cfg, case, pb, Y, iters: int = 1000):
+    """TV weight sweep (the paper's regulariser ablation) on the benchmark
+    problem: `iters` pixel-grid iterations from uniform 1500 m/s for each
+    lambda, with the final loss and the SOS error against the ground truth
+    (RMS over the mask), and the loss at the ground truth for reference."""
+    import numpy as np
+    import torch
+    from paper_2409_10876_gb300.recovery import PGRecovery
+    mask = case["mask"].astype(bool)
+    truth = case["sos_true"].astype(np.float64)
+    rms = lambda s: float(np.sqrt(np.mean((s.astype(np.float64)[mask] - truth[mask]) ** 2)))
+    out = {"iters": iters, "uniform_rms_mps": rms(case["sos_init"])}
+    r = PGRecovery(pb, Y, case["d"], cfg.eps, 0.0, 0.0, torch.as_tensor(case["sos_true"]), torch.as_tensor(case["mask"]))
+    r.step()
+    out["data_loss_at_truth"] = r.loss()
+    for lam in (1e-4, 1e-2, 1e-1, 1.0, 10.0):
+        rec = PGRecovery(pb, Y, case["d"], cfg.eps, lam, cfg.lr, torch.as_tensor(case["sos_init"]),
+                         torch.as_tensor(case["mask"]))
+        g = rec.capture()
+        for _ in range(iters):
+            g.replay()
+        out[f"lambda_{lam:g}"] = {"loss": rec.loss(), "rms_mps": rms(rec.sos.cpu().numpy())}
+        del rec, g
     return out
 
 
@@ -516,7 +589,44 @@ def channel_data_variant(args, dev, flush, stream):
         g.replay()
     ms = _time_graph(g, flush, stream, 20)
     out["neural_field"] = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_iter": statistics.mean(ms)}
+    del nf, g
+    out["mismatch"] = mismatch_study(pb, cfg, case, dev)
     return out
+
+
+def mismatch_study(pb, cfg, case, dev, iters: int = 200):
+    """Model mismatch in the channel data (geometric spreading, a ring-radius
+    offset): channel data -> DAS -> patch spectra, then the data loss at the
+    true SOS against uniform 1500 m/s, and how far the pixel-grid recovery
+    started at the true SOS drifts from it in `iters` iterations (RMS over
+    the mask; lambda = 0)."""
+    import numpy as np
+    import torch
+    from paper_2409_10876_gb300 import pact
+    from paper_2409_10876_gb300.recovery import PGRecovery, channel_data_stack
+    mask = case["mask"].astype(bool)
+    truth = case["sos_true"].astype(np.float64)
+    rms = lambda s: float(np.sqrt(np.mean((s.astype(np.float64)[mask] - truth[mask]) ** 2)))
+    res = {}
+    for name, spread, dr in (("model", 0.0, 0.0), ("spreading_r^-1/2", 0.5, 0.0), ("ring_+0.1mm", 0.0, 0.1e-3),
+                             ("ring_+0.3mm", 0.0, 0.3e-3)):
+        Y = pact.patch_fft(pb, channel_data_stack(pb, case, dev, spread, dr))
+        losses = {}
+        for start in ("sos_init", "sos_true"):
+            r = PGRecovery(pb, Y, case["d"], cfg.eps, 0.0, 0.0, torch.as_tensor(case[start]),
+                           torch.as_tensor(case["mask"]))
+            r.step()
+            losses[start] = r.loss()
+        rec = PGRecovery(pb, Y, case["d"], cfg.eps, 0.0, 0.3, torch.as_tensor(case["sos_true"]),
+                         torch.as_tensor(case["mask"]))
+        g = rec.capture()
+        for _ in range(iters):
+            g.replay()
+        res[name] = {"loss_true_over_uniform": losses["sos_true"] / losses["sos_init"],
+                     "drift_rms_mps": rms(rec.sos.cpu().numpy()), "iters": iters,
+                     "uniform_rms_mps": rms(case["sos_init"])}
+        del rec, g, Y
+    return res
 
 
 def das_variant(dev, flush, stream):
