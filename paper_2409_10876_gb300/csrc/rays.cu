@@ -199,6 +199,7 @@ __device__ __forceinline__ float ray_part(const RayArgs& a, const float* dv, int
     const float ulast = ry.nfull + 0.5f * (ry.rem / h);
     const float ax = PAD ? ry.ax + 2.f : ry.ax, ay = PAD ? ry.ay + 2.f : ry.ay;
     float acc = 0.f, uf = m0 + 0.5f;
+#pragma unroll 4
     for (int m = m0; m < m1; ++m, uf += 1.f) {
         const bool last = m >= ry.nfull;
         const float u = last ? ulast : uf;
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(512) rays_pix_kernel(const RayArgs a, const fl
 }
 
 constexpr int kAdjLanes = 4;   // lanes per ray in the adjoint
+constexpr int kOrder = 2048;   // largest item count per CTA put in claim order
 
 // Round-to-nearest int of |x| < 2^22 without a conversion instruction: adding
 // 1.5 * 2^23 leaves round(x) in the low mantissa bits of the sum.
@@ -388,6 +390,8 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     float* dv_s = sm;                                              // [R + 1][pitch] padded excess rows
     int* acc_s = reinterpret_cast<int*>(sm + (R + 1) * pitch);      // [R + 1][pitch] padded sums
     int* edge_s = acc_s + (R + 1) * pitch;                          // [2][G] sums of the first / last node row
+    float* cost_s = reinterpret_cast<float*>(edge_s + 2 * G);       // [kOrder] item costs, then
+    int* order_s = reinterpret_cast<int*>(cost_s + kOrder);         // [kOrder] items, longest first
     const float v0 = a.g.v0, h = a.g.h;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int L = kAdjLanes, RB = 32 / L;
@@ -446,6 +450,43 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     const float S = scale_s[0];
 
     const int sub = lane % L, grp = lane / L;
+    // claim order: the CTA's items by decreasing estimated length (the chord
+    // through the mask toward the item's middle transducer), so that the last
+    // claims are short and the warps finish together
+    const bool sorted = mine <= kOrder;
+    if (sorted) {
+        int np2 = 1;
+        while (np2 < mine) np2 <<= 1;
+        for (int j = threadIdx.x; j < np2; j += blockDim.x) {
+            float c = -1.f;
+            if (j < mine) {
+                const int t = (int)blockIdx.x + nb * j, i = t / nblk, n = min((t - i * nblk) * RB + RB / 2, n_t - 1);
+                const int2 cc = a.centres[i];
+                c = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n).chord;
+            }
+            cost_s[j] = c;
+            order_s[j] = j;
+        }
+        __syncthreads();
+        for (int k = 2; k <= np2; k <<= 1)              // bitonic sort, descending
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int x = threadIdx.x; x < np2; x += blockDim.x) {
+                    const int y = x ^ jj;
+                    if (y > x) {
+                        const bool desc = (x & k) == 0;
+                        const float cx = cost_s[x], cy = cost_s[y];
+                        if (desc ? cx < cy : cx > cy) {
+                            cost_s[x] = cy;
+                            cost_s[y] = cx;
+                            const int o = order_s[x];
+                            order_s[x] = order_s[y];
+                            order_s[y] = o;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+    }
     for (int band = 0; band < nbands; ++band) {
         const bool last_band = band == nbands - 1;
         const int r0 = band * R;
@@ -463,7 +504,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
         // (the RB rays of a warp leave the same centre in neighbouring directions:
         // staggered, their lanes are never at the same place at the same time)
         for (int j = warp; j < mine;) {
-            const int t = (int)blockIdx.x + nb * j, i = t / nblk, n = (t - i * nblk) * RB + grp;
+            const int t = (int)blockIdx.x + nb * (sorted ? order_s[j] : j), i = t / nblk, n = (t - i * nblk) * RB + grp;
             const float gr = n < n_t ? a.dLdw[(size_t)i * n_t + n] : 0.f;
             if (gr != 0.f) {
                 const int2 cc = a.centres[i];
@@ -666,7 +707,7 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt) {
     // adjoint: bands of R cell rows of the padded grid (G + 3 cell rows, row pitch
     // pad_pitch(G)); excess rows, accumulator and the two edge rows in shared memory
     const int pp = pad_pitch(G);
-    const size_t edge = 2 * sizeof(int) * (size_t)G;
+    const size_t edge = 2 * sizeof(int) * (size_t)G + 2 * sizeof(int) * (size_t)kOrder;   // + claim order
     p.R = std::max(1, std::min(G + 3, (int)((kMaxSmem - edge) / (2 * sizeof(float) * (size_t)pp)) - 1));
     p.nbands = (G + 3 + p.R - 1) / p.R;
     p.smem_adj = 2 * sizeof(float) * (size_t)(p.R + 1) * pp + edge;
