@@ -52,10 +52,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2409_10876_gb300 import ranks
+    return ranks.dist_env()
 
 
 # ---------------------------------------------------------------- CPU oracle legs
@@ -215,7 +213,7 @@ class _GraphEvents:
 
 def run_gpu(args, cfg, case, rank, world, local):
     import torch
-    from paper_2409_10876_gb300 import pact
+    from paper_2409_10876_gb300 import pact, ranks
     from paper_2409_10876_gb300.recovery import PGRecovery, measurement_spectra, recover, synthesize_stack
 
     dev = torch.device("cuda", local)
@@ -286,8 +284,7 @@ def run_gpu(args, cfg, case, rank, world, local):
         pass
     clk = ClockSampler(gpu_id) if rank == 0 else None
     time.sleep(0.3 if clk else 0)
-    if world > 1:
-        torch.distributed.barrier()
+    ranks.barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for k in range(args.steps):
@@ -310,11 +307,8 @@ def run_gpu(args, cfg, case, rank, world, local):
             adj_ms.append(gev.elapsed_ms(2, 4))
     else:
         rays_ms = mcd_ms = rest_ms = adj_ms = [float("nan")]
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    tot_ms = ranks.job_time_ms(tot_ms, world, dev)
+    value = ranks.job_value(world, args.steps, tot_ms)
 
     # roofline of the fused deconvolution + adjoint call (dominant kernel)
     N, M, F, n_t = pb.n, rec.m, pb.f, pb.n_t
@@ -360,12 +354,13 @@ def run_gpu(args, cfg, case, rank, world, local):
         recover(pb, stack, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
                 torch.as_tensor(case["mask"]), 5)               # warm-up (graph capture paths, allocator)
         torch.cuda.synchronize()
+        ranks.barrier(world)
         t0 = time.perf_counter()
         recover(pb, stack, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
                 torch.as_tensor(case["mask"]), iters)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        e2e = world * iters / el
+        el_ms = ranks.job_time_ms((time.perf_counter() - t0) * 1e3, world, dev)
+        e2e = ranks.job_value(world, iters, el_ms)
         line["e2e"] = {"value": e2e, "unit": "iters/s", "h2d_bytes_per_step": stack.numel() * 4 / iters,
                        "d2h_bytes_per_step": 4, "what": f"recover(): pinned host stack upload, patch FFT, graph "
                                                        f"capture, {iters} iterations with a loss read-back each"}
@@ -760,7 +755,8 @@ def main():
     rank, world, local = dist_env()
     from paper_2409_10876_gb300 import inputs
     cfg = inputs.config_full()
-    case = inputs.make_case(cfg, args.seed + rank)
+    from paper_2409_10876_gb300 import ranks
+    case = inputs.make_case(cfg, ranks.rank_seed(args.seed, rank))
     if world > 1:
         import torch
         import torch.distributed as dist
