@@ -58,6 +58,22 @@ def dist_env():
 
 # ---------------------------------------------------------------- CPU oracle legs
 
+def cpu_model() -> str:
+    """The host CPU's model name (Linux), else the platform's processor string."""
+    import platform
+    part = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key == "model name":
+                return line.split(":", 1)[1].strip()
+            if key == "cpu part" and part is None:
+                part = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return f"{platform.machine()} (CPU part {part})" if part else (platform.processor() or platform.machine())
+
+
 def oracle_sample_time(cfg, case, n_patch: int, min_seconds: float, max_iters: int):
     """Times the FP64 oracle iteration (Eq. 3-7 with autograd adjoint + Adam) on
     the first `n_patch` patches; returns (seconds per full-workload iteration,
@@ -345,9 +361,19 @@ def run_gpu(args, cfg, case, rank, world, local):
 
     if rank == 0 and not args.no_cpu_baseline:
         per, its, cores, _ = oracle_sample_time(cfg, case, 8, 10.0, 20)
+        nthr = torch.get_num_threads()
+        torch.set_num_threads(1)
+        try:
+            per1, its1, _, _ = oracle_sample_time(cfg, case, 2, 4.0, 5)
+        finally:
+            torch.set_num_threads(nthr)
         line["cpu_baseline"] = {"value": 1.0 / per, "unit": "iters/s", "cores": cores, "kind": "oracle",
                                 "sample": f"median of {its} FP64 oracle iterations on 8 of {cfg.n_patches} "
-                                          f"patches, scaled by {cfg.n_patches / 8:.0f}"}
+                                          f"patches, scaled by {cfg.n_patches / 8:.0f}",
+                                "one_thread": {"value": 1.0 / per1, "unit": "iters/s", "cores": 1,
+                                               "sample": f"median of {its1} iterations on 2 of {cfg.n_patches} "
+                                                         f"patches, scaled by {cfg.n_patches / 2:.0f}"},
+                                "cpu": cpu_model()}
     if not args.no_e2e:
         stack = synthesize_stack(pb, case, dev).cpu().pin_memory()
         iters = max(50, min(args.steps, 500))
