@@ -347,12 +347,13 @@ __device__ __forceinline__ T fold_col(const T* row, int c, int G) {
 // Ray adjoint.  CTA b takes the work items t = b, b + nb, b + 2 nb, ... (item =
 // a patch and a block of 32 / kAdjLanes consecutive transducers), its warps
 // items of different patches at the same time (rays of one patch all start at
-// the same centre, where their
-// scatters would collide).  Within a warp, groups of kAdjLanes lanes take the
-// rays to consecutive transducers of one patch (similar lengths, so the lanes
-// finish together); a lane walks a contiguous run of samples of its ray, from a
-// staggered start, and keeps the bilinear weights of the current cell in
-// registers, adding them to the shared grid only when the walk leaves the cell.
+// the same centre, where their scatters would collide).  Within a warp, groups
+// of kAdjLanes lanes take the rays to consecutive transducers of one patch
+// (similar lengths, so the lanes finish together); a lane walks a contiguous
+// run of samples of its ray, from a staggered start, and adds each sample's
+// four bilinear contributions to the shared grid.  (Keeping the current
+// cell's weights in registers and adding them on cell change was measured
+// slower: a cell changes every ~1.4 samples, and the branch diverges.)
 //
 // Coordinates are those of the padded grid (node (p, c) at (p + 2, c + 2), see
 // load_excess_padded), clamped to [1, G + 2]; floor() takes no conversion
@@ -366,11 +367,10 @@ __device__ __forceinline__ T fold_col(const T* row, int c, int G) {
 // combination of node values, so v >= vmin, and the weights h_s of a ray add up
 // to its chord <= 2 mask_r.  The absolute sum of all contributions of the CTA
 // is therefore at most  Mb = sum_r |g_r| 2 mask_r v0 / vmin^2 , and one
-// register flush (the samples of a ray inside one cell, a segment of length
-// <= sqrt(2) sos_dx + h) at most  F = max|g| (sqrt(2) sos_dx + h) v0 / vmin^2.
-// The scale S = 0.99 min(2^30 / Mb, 2^22 / F) keeps every node's sum inside the
-// int32 range (each flush rounds by at most 1/2) and every flushed value below
-// 2^22 (rounded without a conversion instruction).  A non-finite bound (NaN in
+// contribution at most  F = max|g| h v0 / vmin^2.  The scale
+// S = 0.99 min(2^30 / Mb, 2^22 / F) keeps every node's sum inside the int32
+// range (each addition rounds by at most 1/2) and every added value below 2^22
+// (rounded without a conversion instruction).  A non-finite bound (NaN in
 // dL/dw or the SOS, or SOS <= 0) turns the CTA's partial grid into NaN.
 //
 // The padded grid is processed in bands of R cell rows (padded node rows
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
         const float vm = vmin * (1.f - 1e-5f);
         const float k = v0 / (vm * vm);
         const float Mb = gsum * (2.f * a.g.mask_r) * k;
-        const float F = gmax * (1.41421356f * a.g.sos_dx + h) * k;
+        const float F = gmax * h * k;
         const bool poison = bad > 0.f || !isfinite(Mb) || !isfinite(F) || !isfinite(gsum);
         const float S = (Mb > 0.f && F > 0.f) ? 0.99f * fminf(fminf(1073741824.f / Mb, 4194304.f / F), 1e30f) : 0.f;
         scale_s[0] = poison ? 0.f : S;
@@ -530,8 +530,6 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                 const int off = len * grp / RB;                   // staggered start within the run
                 const float ulast = ry.nfull + 0.5f * (ry.rem * a.g.inv_h);
                 const float gv0 = gr * v0;
-                int cur = -1;
-                float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
                 int m = m0 + off;
                 float uf = m + 0.5f;
                 for (int k = 0; k < len; ++k) {
@@ -560,18 +558,9 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                     const float d = fmaf(ty, bot - top, top);
                     const float iv = __fdividef(1.f, v0 + d);
                     const float coef = gv0 * (last ? ry.rem : h) * iv * iv;
-                    if (idx != cur) {
-                        if (cur >= 0) scatter4(acc_s, pitch, cur, S, c00, c01, c10, c11);
-                        cur = idx;
-                        c00 = c01 = c10 = c11 = 0.f;
-                    }
                     const float cy0 = coef * (1.f - ty), cy1 = coef * ty;
-                    c00 = fmaf(cy0, 1.f - tx, c00);
-                    c01 = fmaf(cy0, tx, c01);
-                    c10 = fmaf(cy1, 1.f - tx, c10);
-                    c11 = fmaf(cy1, tx, c11);
+                    scatter4(acc_s, pitch, idx, S, cy0 * (1.f - tx), cy0 * tx, cy1 * (1.f - tx), cy1 * tx);
                 }
-                if (cur >= 0) scatter4(acc_s, pitch, cur, S, c00, c01, c10, c11);
             }
             // next item of this CTA: claimed dynamically, so that warps whose
             // items were short take more
