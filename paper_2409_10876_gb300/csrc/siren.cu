@@ -7,9 +7,10 @@
 // are FP32 on the CUDA cores.
 //   forward : one thread per node, parameters in shared memory; z saved for the
 //             backward pass.
-//   backward: one thread per feature over a chunk of nodes (dL/dv scaled by the
-//             output scale staged in shared memory), per-chunk partial sums in
-//             the workspace, then a fixed-order reduction (deterministic).
+//   backward: one thread per feature over a chunk of 64 nodes (dL/dv scaled by
+//             the output scale staged in shared memory; enough chunks to fill
+//             the SMs), per-chunk partial sums in the workspace, then a
+//             fixed-order reduction (deterministic).
 #include "pact_internal.cuh"
 
 namespace pact {
@@ -18,7 +19,7 @@ namespace {
 constexpr int kF = 256;                    // sine features
 constexpr int kNP = 2 * kF + kF + kF + 3;  // 1027 parameters
 constexpr int kOffB1 = 2 * kF, kOffW2 = 3 * kF, kOffB2 = 4 * kF, kOffScale = 4 * kF + 1, kOffOffset = 4 * kF + 2;
-constexpr int kChunk = 512;                // nodes per backward CTA
+constexpr int kChunk = 64;                 // nodes per backward CTA (G = 128: 256 CTAs)
 constexpr int kStride = 1088;              // partial-row stride (>= kNP + 2, multiple of 64)
 
 struct SirenArgs {
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(256) siren_fwd_kernel(const SirenArgs a) {
     a.sos[node] = inside ? fmaf(p_s[kOffScale], z, p_s[kOffOffset]) : a.v_bg;
 }
 
-// CTA c: nodes [c * 512, +512); thread f accumulates, over those nodes with
+// CTA c: nodes [c * kChunk, +kChunk); thread f accumulates, over those nodes with
 // g = dL/dv (0 outside the mask) and dz = scale g,
 //   dW1_f = sum dz w2_f omega0 cos(a_f) x,  db1_f = sum dz w2_f omega0 cos(a_f),  dw2_f = sum dz sin(a_f);
 // threads 0..2 also form sum dz (b2), sum g z (scale) and sum g (offset).
@@ -110,12 +111,25 @@ __global__ void __launch_bounds__(kF) siren_bwd_kernel(const SirenArgs a) {
     }
 }
 
-__global__ void siren_reduce_kernel(const float* part, int chunks, float* out, int accumulate) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= kNP) return;
+// Parameters e = 32 b + lane of block b: warp w adds the partial rows of its
+// chunk [chunks w / 8, chunks (w + 1) / 8) in order, warp 0 the eight chunk
+// sums in order (fixed order, eight times the loads in flight).
+__global__ void __launch_bounds__(256) siren_reduce_kernel(const float* part, int chunks, float* out,
+                                                           int accumulate) {
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    const int c0 = chunks * w / 8, c1 = chunks * (w + 1) / 8;
     float s = 0.f;
-    for (int c = 0; c < chunks; ++c) s += part[(size_t)c * kStride + e];
-    out[e] = accumulate ? out[e] + s : s;
+    if (e < kNP)
+        for (int c = c0; c < c1; ++c) s += part[(size_t)c * kStride + e];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && e < kNP) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += red[k][lane];
+        out[e] = accumulate ? out[e] + t : t;
+    }
 }
 
 struct SirenPlan {
@@ -192,6 +206,6 @@ extern "C" pact_status pact_siren_backward(const pact_geometry* g, const float* 
     cudaStream_t st = as_stream(stream);
     siren_bwd_kernel<<<pl.chunks, kF, 0, st>>>(a);
     PACT_TRY(check_launch("siren backward kernel"));
-    siren_reduce_kernel<<<(kNP + 255) / 256, 256, 0, st>>>(a.part, pl.chunks, dL_dparams, accumulate);
+    siren_reduce_kernel<<<(kNP + 31) / 32, 256, 0, st>>>(a.part, pl.chunks, dL_dparams, accumulate);
     return check_launch("siren reduction");
 }
