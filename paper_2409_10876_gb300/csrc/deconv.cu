@@ -386,6 +386,7 @@ constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer wa
 // per SM.
 template <int CPT, bool EXACT, bool FACT>
 __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kernel(const McdArgs a) {
+    pdl_trigger();                                   // the ray adjoint may stage its tables meanwhile
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int n_t = a.g.n_t, M = EXACT ? CPT : a.M, N = a.N;
     float2* stage = reinterpret_cast<float2*>(smem_raw);                          // [kStages][kCh][kTile]

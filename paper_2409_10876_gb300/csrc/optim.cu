@@ -14,6 +14,8 @@ __device__ __forceinline__ float sgn(float x) { return x > 0.f ? 1.f : (x < 0.f 
 __global__ void __launch_bounds__(256) tv_kernel(int G, const float* sos, float lambda, float* value,
                                                  float* grad, int accumulate) {
     __shared__ float red[8];
+    pdl_trigger();
+    pdl_wait();
     const int GG = G * G;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     float part = 0.f;
@@ -44,6 +46,8 @@ __global__ void __launch_bounds__(256) tv_kernel(int G, const float* sos, float 
 __global__ void adam_kernel(int n, float* param, const float* grad, float* m, float* v, float lr, float b1,
                             float b2, float eps, float bc1, float bc2, const int* counter,
                             const unsigned char* mask) {
+    pdl_trigger();
+    pdl_wait();
     if (counter) {  // t = steps so far + 1
         const float t = (float)(*counter + 1);
         bc1 = 1.f - powf(b1, t);
@@ -60,7 +64,10 @@ __global__ void adam_kernel(int n, float* param, const float* grad, float* m, fl
     }
 }
 
-__global__ void counter_increment_kernel(int* counter) { *counter += 1; }
+__global__ void counter_increment_kernel(int* counter) {
+    pdl_wait();
+    *counter += 1;
+}
 
 }  // namespace
 }  // namespace pact
@@ -76,7 +83,9 @@ extern "C" pact_status pact_tv(const pact_geometry* g, const float* sos, float l
     if (value && !accumulate && cudaMemsetAsync(value, 0, sizeof(float), st) != cudaSuccess)
         return check_launch("tv: memset");
     const int GG = g->sos_g * g->sos_g;
-    tv_kernel<<<(GG + 255) / 256, 256, 0, st>>>(g->sos_g, sos, lambda, value, dL_dsos, accumulate);
+    if (launch_pdl(tv_kernel, dim3((GG + 255) / 256), dim3(256), 0, st, g->sos_g, sos, lambda, value, dL_dsos,
+                   accumulate) != cudaSuccess)
+        return check_launch("tv kernel");
     return check_launch("tv kernel");
 }
 
@@ -93,11 +102,13 @@ extern "C" pact_status pact_adam_step(int n, float* param, const float* grad, fl
     const float bc1 = (float)(1.0 - pow((double)beta1, step));
     const float bc2 = (float)(1.0 - pow((double)beta2, step));
     const int blocks = (n + 255) / 256 < 4 * num_sms() ? (n + 255) / 256 : 4 * num_sms();
-    adam_kernel<<<blocks, 256, 0, as_stream(stream)>>>(n, param, grad, m, v, lr, beta1, beta2, eps, bc1, bc2,
-                                                       step_counter, mask);
+    if (launch_pdl(adam_kernel, dim3(blocks), dim3(256), 0, as_stream(stream), n, param, grad, m, v, lr, beta1, beta2,
+                   eps, bc1, bc2, step_counter, mask) != cudaSuccess)
+        return check_launch("adam kernel");
     PACT_TRY(check_launch("adam kernel"));
     if (step_counter) {
-        counter_increment_kernel<<<1, 1, 0, as_stream(stream)>>>(step_counter);
+        if (launch_pdl(counter_increment_kernel, dim3(1), dim3(1), 0, as_stream(stream), step_counter) != cudaSuccess)
+            return check_launch("adam step counter");
         return check_launch("adam step counter");
     }
     return PACT_OK;

@@ -38,6 +38,32 @@ pact_status check_patches(const pact_patches* pt);
 pact_status launch_pixel_rays(const pact_geometry* g, const float* sos, const float* p0, int pix0, int npix,
                               float* wT, int ld, cudaStream_t st);
 
+// Programmatic dependent launch (PDL).  A kernel launched by launch_pdl may be
+// scheduled before its predecessor in the stream has finished (once every CTA
+// of the predecessor has called pdl_trigger or exited); it must call pdl_wait
+// before it reads or writes anything a kernel launched before it may still
+// touch.  Work before pdl_wait may only use inputs no kernel writes
+// (geometry, patch centres, constant tables) and the kernel's own shared
+// memory.  Without a PDL launch both calls are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 #define PACT_TRY(expr)                       \
     do {                                     \
         pact_status _s = (expr);             \

@@ -398,6 +398,48 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     const int n_t = a.g.n_t, nblk = (n_t + RB - 1) / RB, nb = gridDim.x;
     const int items = a.N * nblk;                                  // (patch, block of RB transducers)
     const int mine = items > (int)blockIdx.x ? (items - (int)blockIdx.x + nb - 1) / nb : 0;   // items of this CTA
+    pdl_trigger();
+
+    // claim order: the CTA's items by decreasing estimated length (the chord
+    // through the mask toward the item's middle transducer), so that the last
+    // claims are short and the warps finish together
+    const bool sorted = mine <= kOrder;
+    if (sorted) {
+        int np2 = 1;
+        while (np2 < mine) np2 <<= 1;
+        for (int j = threadIdx.x; j < np2; j += blockDim.x) {
+            float c = -1.f;
+            if (j < mine) {
+                const int t = (int)blockIdx.x + nb * j, i = t / nblk, n = min((t - i * nblk) * RB + RB / 2, n_t - 1);
+                const int2 cc = a.centres[i];
+                c = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n).chord;
+            }
+            cost_s[j] = c;
+            order_s[j] = j;
+        }
+        __syncthreads();
+        for (int k = 2; k <= np2; k <<= 1)              // bitonic sort, descending
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int x = threadIdx.x; x < np2; x += blockDim.x) {
+                    const int y = x ^ jj;
+                    if (y > x) {
+                        const bool desc = (x & k) == 0;
+                        const float cx = cost_s[x], cy = cost_s[y];
+                        if (desc ? cx < cy : cx > cy) {
+                            cost_s[x] = cy;
+                            cost_s[y] = cx;
+                            const int o = order_s[x];
+                            order_s[x] = order_s[y];
+                            order_s[y] = o;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    // everything below reads or writes what earlier kernels produce (dL/dw, the
+    // SOS, the partial grids): wait for them (no-op without a dependent launch)
+    pdl_wait();
 
     // fixed-point scale of this CTA
     float gsum = 0.f, gmax = 0.f, vmin = INFINITY, bad = 0.f;
@@ -450,43 +492,6 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     const float S = scale_s[0];
 
     const int sub = lane % L, grp = lane / L;
-    // claim order: the CTA's items by decreasing estimated length (the chord
-    // through the mask toward the item's middle transducer), so that the last
-    // claims are short and the warps finish together
-    const bool sorted = mine <= kOrder;
-    if (sorted) {
-        int np2 = 1;
-        while (np2 < mine) np2 <<= 1;
-        for (int j = threadIdx.x; j < np2; j += blockDim.x) {
-            float c = -1.f;
-            if (j < mine) {
-                const int t = (int)blockIdx.x + nb * j, i = t / nblk, n = min((t - i * nblk) * RB + RB / 2, n_t - 1);
-                const int2 cc = a.centres[i];
-                c = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n).chord;
-            }
-            cost_s[j] = c;
-            order_s[j] = j;
-        }
-        __syncthreads();
-        for (int k = 2; k <= np2; k <<= 1)              // bitonic sort, descending
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int x = threadIdx.x; x < np2; x += blockDim.x) {
-                    const int y = x ^ jj;
-                    if (y > x) {
-                        const bool desc = (x & k) == 0;
-                        const float cx = cost_s[x], cy = cost_s[y];
-                        if (desc ? cx < cy : cx > cy) {
-                            cost_s[x] = cy;
-                            cost_s[y] = cx;
-                            const int o = order_s[x];
-                            order_s[x] = order_s[y];
-                            order_s[y] = o;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-    }
     for (int band = 0; band < nbands; ++band) {
         const bool last_band = band == nbands - 1;
         const int r0 = band * R;
@@ -628,6 +633,8 @@ __device__ __forceinline__ float sum_parts32(const float* part, int np, int GG, 
 __global__ void __launch_bounds__(256) reduce_parts_kernel(const float* part, int np, int GG, float* out,
                                                            int accumulate) {
     __shared__ float red[256];
+    pdl_trigger();
+    pdl_wait();
     const int q = blockIdx.x * 32 + (threadIdx.x & 31);
     const float g = sum_parts32(part, np, GG, blockIdx.x * 32, red);
     if (threadIdx.x < 32 && q < GG) out[q] = accumulate ? out[q] + g : g;
@@ -796,9 +803,13 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
     PACT_TRY(ensure_smem((const void*)rays_adj_kernel, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
-    rays_adj_kernel<<<pl.nb_adj, 1024, pl.smem_adj, st>>>(a, pl.R, pl.nbands, pl.narrow);
+    if (launch_pdl(rays_adj_kernel, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands, pl.narrow) !=
+        cudaSuccess)
+        return check_launch("sos_to_delays_adj kernel");
     PACT_TRY(check_launch("sos_to_delays_adj kernel"));
     // one partial grid per CTA: a single fixed-order sum
-    reduce_parts_kernel<<<(GG + 31) / 32, 256, 0, st>>>(a.part, pl.nparts, GG, dL_dsos, accumulate);
+    if (launch_pdl(reduce_parts_kernel, dim3((GG + 31) / 32), dim3(256), 0, st, a.part, pl.nparts, GG, dL_dsos,
+                   accumulate) != cudaSuccess)
+        return check_launch("sos_to_delays_adj reduction");
     return check_launch("sos_to_delays_adj reduction");
 }
