@@ -52,24 +52,9 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Offset in bytes of element (r, k) of an R x K tile stored MN-major: 8-row x
-// 8-k core matrices of 128 B (16 B = 8 consecutive rows per k), 8-row groups
-// 128 B apart, 8-k groups 16 R bytes apart.
-__device__ __forceinline__ uint32_t mnmaj_off(int r, int k, int R) {
-    return (uint32_t)((k >> 3) * (16 * R) + (r >> 3) * 128 + (k & 7) * 16 + (r & 7) * 2);
-}
-
-// Descriptor of the K-slice [16 kk, 16 kk + 16) of an MN-major R x K tile
-// (leading byte offset = K-direction core stride, stride byte offset =
-// MN-direction core stride).
-__device__ __forceinline__ uint64_t mn_slice(const void* tile, int R, int kk) {
-    return umma::desc(smem_addr(tile) + (uint32_t)kk * 32u * (uint32_t)R, 16u * (uint32_t)R, 128u);
-}
-
-// Instruction descriptor with both operands MN-major.
-__host__ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
-    return umma::idesc_bf16(M, N) | (1u << 15) | (1u << 16);
-}
+using umma::idesc_bf16_mn;
+using umma::mn_slice;
+using umma::mnmaj_off;
 
 __device__ __forceinline__ bool wait_or_flag(uint64_t* bar, uint32_t parity, int* status) {
     const bool ok = mbar_wait_bounded(bar, parity, kCnnWaitNs);

@@ -15,7 +15,9 @@
 // layer's output tile is also copied (in its shared-memory layout) to the
 // workspace for the backward pass.
 // pact_nf_backward: per CTA and layer, dW = dz^T h (M = out, N = in, K = 128
-// nodes) and dh = dz W (M = nodes, N = in, K = out) on the tensor cores; the
+// nodes; dz and h are the K-major node tiles read as MN-major operands, so no
+// transposed copies) and dh = dz W (M = nodes, N = in, K = out) on the tensor
+// cores; the
 // per-CTA weight gradients go to the workspace and a second kernel sums them
 // in a fixed order.
 #include <math.h>
@@ -100,21 +102,26 @@ __device__ __forceinline__ void st1(unsigned char* tile, int r, int k, int K, fl
 }
 
 // Weight W_l (bf16 [out][in]) into a K-major [out x in] tile (B operand of h W^T).
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// W [kH x K] (row-major, 16-byte aligned) into a K-major tile by asynchronous
+// 16-byte copies; the caller waits with cp_wait_all and a barrier.
 __device__ __forceinline__ void load_w(unsigned char* tile, const __nv_bfloat16* w, int K) {
     const int chunks = kH * K / 8;
     for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
         const int o = c / (K / 8), k8 = c - (c / (K / 8)) * (K / 8);
-        *reinterpret_cast<uint4*>(tile + umma::kmaj_off(o, 8 * k8, K)) = reinterpret_cast<const uint4*>(w)[c];
+        cp16(tile + umma::kmaj_off(o, 8 * k8, K), reinterpret_cast<const uint4*>(w) + c);
     }
+}
+// A whole operand tile (kTileBytes) from global memory, asynchronously.
+__device__ __forceinline__ void load_tile(unsigned char* tile, const unsigned char* src) {
+    for (int c = threadIdx.x; c < kTileBytes / 16; c += blockDim.x) cp16(tile + 16 * c, src + 16 * c);
 }
 
 // W_l^T as a K-major [in x out] tile (B operand of dz W): element (n = in, k = out).
-__device__ __forceinline__ void load_wt(unsigned char* tile, const __nv_bfloat16* w, int in) {
-    for (int e = threadIdx.x; e < kH * in; e += blockDim.x) {
-        const int o = e / in, n = e - (e / in) * in;
-        *reinterpret_cast<__nv_bfloat16*>(tile + umma::kmaj_off(n, o, kH)) = w[e];
-    }
-}
 
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status) {
     const bool ok = mbar_wait_bounded(bar, parity, kNfWaitNs);
@@ -155,6 +162,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
 #pragma unroll
         for (int k0 = 0; k0 < kF; k0 += 8) st8(A0, tid, k0, kF, f + k0);
     }
+    cp_wait_all();                                  // the weight tiles
     if (warp == 0) umma::tmem_alloc(&tmem_s, 128);
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -214,16 +222,16 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
 
 __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* hT = sm;                       // h_{l-1}^T  [in x 128 nodes]     32 KB
-    unsigned char* dzA = sm + kTileBytes;         // dz         [128 nodes x out]    32 KB
-    unsigned char* dzT = sm + 2 * kTileBytes;     // dz^T       [out x 128 nodes]    32 KB
-    unsigned char* WT = sm + 3 * kTileBytes;      // W_l^T      [in x out]           32 KB
-    unsigned char* Hr = sm + 4 * kTileBytes;      // h_{l-1}    [128 nodes x in]     32 KB
-    __shared__ float col_s[kH];
-    __shared__ float red_s[4];
+    // dz and h_{l-1} are K-major tiles [nodes x units]; read as MN-major they
+    // are the transposed operands dz^T and h^T of the weight-gradient GEMM
+    unsigned char* dzA = sm;                      // dz         [128 nodes x out]    32 KB
+    unsigned char* WT = sm + kTileBytes;          // W_l        [out x in]           32 KB
+    unsigned char* Hr = sm + 2 * kTileBytes;      // h_{l-1}    [128 nodes x in]     32 KB
+    __shared__ float g5_s[kRows];
+    __shared__ float w5_s[kH];
     __shared__ uint32_t tmem_s;
     __shared__ __align__(8) uint64_t bar;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int row = blockIdx.x * kRows + tid;
     const bool valid = row < a.rows;
     float* part = a.part + (size_t)blockIdx.x * kPartStride;   // 16-byte aligned rows for float4 stores
@@ -236,70 +244,72 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         g5 = a.dL_dsos[row] * a.v_half * (1.f - t * t);
     }
     // h4 of this CTA (operand layout) -> Hr
-    for (int c = tid; c < kTileBytes / 16; c += blockDim.x)
-        reinterpret_cast<uint4*>(Hr)[c] = reinterpret_cast<const uint4*>(tiles + (size_t)(kL - 1) * kTileBytes)[c];
-    if (tid < kH) col_s[tid] = 0.f;
+    load_tile(Hr, tiles + (size_t)(kL - 1) * kTileBytes);
+    cp_wait_all();
     if (warp == 0) umma::tmem_alloc(&tmem_s, 256);
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_init_fence();
     }
     __syncthreads();
-    // dW5 = sum_nodes g5 h4, db5 = sum g5; dz4 = g5 w5 (h4 > 0)
+    // dz4 = g5 w5 (h4 > 0) for this node; dW5 = sum_nodes g5 h4 for column `tid`
+    // and db5 = sum g5, both in a fixed order
+    g5_s[tid] = g5;
+    w5_s[tid] = __bfloat162float(a.wbf[kOffW5 + tid]);
+    __syncthreads();
     for (int c = 0; c < kH; ++c) {
         const float h = bfv(Hr, tid, c, kH);
-        float s = warp_sum(g5 * h);
-        if (lane == 0) atomicAdd(&col_s[c], s);
-        const float w5 = __bfloat162float(a.wbf[kOffW5 + c]);
-        const float dz = h > 0.f ? g5 * w5 : 0.f;
-        st1(dzA, tid, c, kH, dz);
-        st1(dzT, c, tid, kRows, dz);
+        st1(dzA, tid, c, kH, h > 0.f ? g5 * w5_s[c] : 0.f);
     }
     {
-        const float s = warp_sum(g5);
-        if (lane == 0) red_s[warp] = s;
+        float s = 0.f;
+        for (int r = 0; r < kRows; ++r) s = fmaf(g5_s[r], bfv(Hr, r, tid, kH), s);
+        part[kOffW5 + tid] = s;
+        if (tid == 0) {
+            float b = 0.f;
+            for (int r = 0; r < kRows; ++r) b += g5_s[r];
+            part[kOffB5] = b;
+        }
     }
     __syncthreads();
-    if (tid < kH) part[kOffW5 + tid] = col_s[tid];
-    if (tid == 0) part[kOffB5] = red_s[0] + red_s[1] + red_s[2] + red_s[3];
 
     const uint32_t tmem = tmem_s;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     uint32_t phase = 0;
     for (int l = kL; l >= 1; --l) {
         const int K_in = in_dim(l);
-        // db_l = column sums of dz_l (row `tid` of dz^T)
+        // db_l = column sums of dz_l (column `tid` of the dz tile)
         {
             float s = 0.f;
-            for (int r = 0; r < kRows; ++r) s += bfv(dzT, tid, r, kRows);
+            for (int r = 0; r < kRows; ++r) s += bfv(dzA, r, tid, kH);
             part[off_b(l) + tid] = s;
         }
-        // h_{l-1}^T (B operand of dW) and, for l > 1, W_l^T (B operand of dh)
+        // h_{l-1} (B operand of dW, read MN-major) and, for l > 1, W_l^T (B operand of dh)
         if (l > 1) {
-            for (int c = tid; c < kTileBytes / 16; c += blockDim.x)
-                reinterpret_cast<uint4*>(Hr)[c] = reinterpret_cast<const uint4*>(tiles + (size_t)(l - 2) * kTileBytes)[c];
-            __syncthreads();
-            for (int c = 0; c < kH; ++c) st1(hT, c, tid, kRows, bfv(Hr, tid, c, kH));
-            load_wt(WT, a.wbf + off_w(l), kH);
+            load_tile(Hr, tiles + (size_t)(l - 2) * kTileBytes);
+            load_w(WT, a.wbf + off_w(l), kH);          // W_l [out x in] K-major = W_l^T read MN-major
+            cp_wait_all();
         } else {
             float f[kF];
             features(a, valid ? row : 0, f);
-            for (int c = 0; c < kF; ++c) st1(hT, c, tid, kRows, __bfloat162float(__float2bfloat16_rn(f[c])));
+#pragma unroll
+            for (int k0 = 0; k0 < kF; k0 += 8) st8(Hr, tid, k0, kF, f + k0);
         }
         umma::fence_smem_to_async();
         umma::fence_before();
         __syncthreads();
         umma::fence_after();
         if (tid == 0) {
-            // dW_l [out x in] = dz^T [out x nodes] * (h^T [in x nodes])^T
+            // dW_l [out x in] = dz^T [out x nodes] * (h^T [in x nodes])^T, both operands
+            // the K-major node tiles read MN-major (M = out, N = in, K = nodes)
             for (int kk = 0; kk < kRows / 16; ++kk)
-                umma::mma(tmem, umma::kslice(dzT, kRows, kk), umma::kslice(hT, kRows, kk),
-                          umma::idesc_bf16(128, K_in), kk > 0);
+                umma::mma(tmem, umma::mn_slice(dzA, kH, kk), umma::mn_slice(Hr, K_in, kk),
+                          umma::idesc_bf16_mn(128, K_in), kk > 0);
             // dh_{l-1} [nodes x in] = dz [nodes x out] * (W^T [in x out])^T
             if (l > 1)
                 for (int kk = 0; kk < kH / 16; ++kk)
-                    umma::mma(tmem + 128, umma::kslice(dzA, kH, kk), umma::kslice(WT, kH, kk),
-                              umma::idesc_bf16(128, kH), kk > 0);
+                    umma::mma(tmem + 128, umma::kslice(dzA, kH, kk), umma::mn_slice(WT, kH, kk),
+                              umma::idesc_bf16(128, kH) | (1u << 16), kk > 0);
             umma::commit(&bar);
         }
         wait_bar(&bar, phase, a.status);
@@ -323,7 +333,6 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
                     const float h = bfv(Hr, tid, c0 + j, kH);
                     const float dz = h > 0.f ? v[j] : 0.f;
                     st1(dzA, tid, c0 + j, kH, dz);
-                    st1(dzT, c0 + j, tid, kRows, dz);
                 }
             }
         }
@@ -370,7 +379,7 @@ NfPlan nf_plan(const pact_geometry* g) {
     o += 256;
     p.total = o;
     p.smem_fwd = 16384 + 2 * kTileBytes + 16384 + (kL - 1) * kTileBytes;
-    p.smem_bwd = 5 * kTileBytes;
+    p.smem_bwd = 3 * kTileBytes;
     return p;
 }
 

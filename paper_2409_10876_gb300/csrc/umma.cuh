@@ -37,9 +37,30 @@ __device__ __forceinline__ uint64_t kslice(const void* tile, int K, int kk) {
     return desc(smem_addr(tile) + (uint32_t)kk * 256u, 128u, 16u * (uint32_t)K);
 }
 
+// Byte offset of element (r, k) of an R x K tile stored MN-major: 8-row x
+// 8-k core matrices of 128 B (16 B = 8 consecutive rows per k), 8-row groups
+// 128 B apart, 8-k groups 16 R bytes apart.  kmaj_off(r, k, K) ==
+// mnmaj_off(k, r, K): the K-major tile of an R x K matrix is, byte for byte,
+// the MN-major tile of its transpose, so a transposed operand needs no copy.
+__host__ __device__ __forceinline__ uint32_t mnmaj_off(int r, int k, int R) {
+    return (uint32_t)((k >> 3) * (16 * R) + (r >> 3) * 128 + (k & 7) * 16 + (r & 7) * 2);
+}
+
+// Descriptor of the K-slice [16 kk, 16 kk + 16) of an MN-major R x K tile
+// (leading byte offset = K-direction core stride, stride byte offset =
+// MN-direction core stride).
+__device__ __forceinline__ uint64_t mn_slice(const void* tile, int R, int kk) {
+    return desc(smem_addr(tile) + (uint32_t)kk * 32u * (uint32_t)R, 16u * (uint32_t)R, 128u);
+}
+
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
 __host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor with both operands MN-major.
+__host__ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
 // D[tmem] (+)= A * B^T for one K = 16 slice (single issuing thread).
