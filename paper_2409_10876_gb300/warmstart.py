@@ -3,7 +3,7 @@
 The paper's recovery (Sec. 3.3) starts every optimisation from a uniform SOS.
 Here a small CNN (pact_cnn_*, BF16 tensor cores) predicts a starting SOS map
 from the delay stack, and the plain pixel-grid optimisation refines it and
-remains the judge: the warm start only changes where Adam starts.
+has the last word: the warm start only changes where Adam starts.
 
 Training data are generated on the GPU by the library's own forward model:
 a random SOS field (1-6 Gaussian ellipses, 1400-1650 m/s) gives the
