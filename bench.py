@@ -253,30 +253,14 @@ def run_gpu(args, cfg, case, rank, world, local):
     def capture(events):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            h = torch.cuda.current_stream().cuda_stream
-            if events:
-                events.record(0, h)
-            pact.sos_to_delays(pb, rec.sos, rec.w)
-            if events:
-                events.record(1, h)
-            pact.mc_deconv_loss(pb, rec.w, rec.Y, rec.d, rec.eps, want_grad=True, out=rec.out, ws=rec.ws_mcd,
-                                tables=rec.tables)
-            if events:
-                events.record(2, h)
-            pact.sos_to_delays_adj(pb, rec.sos, rec.out["dL_dw"], rec.grad, accumulate=False, ws=rec.ws_adj)
-            if events:
-                events.record(4, h)
-            pact.tv(pb, rec.sos, rec.lam, value=rec.out["loss"], grad=rec.grad, accumulate=True)
-            pact.adam_step(rec.sos, rec.grad, rec.adam_m, rec.adam_v, 1, rec.lr, mask=rec.mask,
-                           step_counter=rec.counter)
-            if events:
-                events.record(3, h)
+            mark = (lambda k: events.record(k, torch.cuda.current_stream().cuda_stream)) if events else None
+            rec.step(mark)
         return g
 
     g_step = capture(None)                        # the timed iteration
     g_step_ev = capture(gev) if gev else None     # the same with event nodes, for the breakdown
     torch.cuda.synchronize()
-    launches_per_step = 8
+    launches_per_step = 6                         # rays, fused pass, ray adjoint, partial-grid sum, TV, Adam
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -348,7 +332,7 @@ def run_gpu(args, cfg, case, rank, world, local):
                        "seed": args.seed, "eps": cfg.eps, "tv_lambda": cfg.tv_lambda},
             "breakdown_ms": {"sos_to_delays": statistics.mean(rays_ms), "mc_deconv_loss": statistics.mean(mcd_ms),
                              "adj_tv_adam": statistics.mean(rest_ms)},
-            "roofline": {"bound": "hbm", "kernel": "mc_deconv_loss (fused Eq. 4-7 + adjoint: one kernel + the dL/dw memset, "
+            "roofline": {"bound": "hbm", "kernel": "mc_deconv_loss (fused Eq. 4-7 + adjoint, one kernel, "
                                                 "timed between event nodes inside the iteration graph)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "measured" if peaks else "fallback",
@@ -472,7 +456,7 @@ def nf_variant(args, cfg, case, pb, Y, flush, stream):
     ms = _time_graph(g, flush, stream, steps)
     return {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
             "dtype": "bf16 (field) + f32 (forward model)", "params": int(rec.params.numel()),
-            "gpu_launches_per_step": 12}
+            "gpu_launches_per_step": 9}
 
 
 def channels_variant(args, cfg, dev, flush, stream):
@@ -535,7 +519,7 @@ def siren_variant(args, cfg, case, pb, Y, flush, stream):
     steps = max(20, min(args.steps, 500))
     ms = _time_graph(g, flush, stream, steps)
     return {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
-            "dtype": "f32", "params": int(rec.params.numel()), "gpu_launches_per_step": 11}
+            "dtype": "f32", "params": int(rec.params.numel()), "gpu_launches_per_step": 8}
 
 
 def channel_data_variant(args, dev, flush, stream):

@@ -357,9 +357,11 @@ pact_status pact_tv(const pact_geometry* g, const float* sos, float lambda, floa
  * Entries whose mask byte is 0 are left unchanged (mask NULL = all train).
  *   param, m, v   DEVICE float [n] (updated in place);  grad DEVICE float [n]
  *   step          t >= 1, used when step_counter is NULL
- *   step_counter  DEVICE int [1] or NULL: steps taken so far; the update
- *                 uses t = *step_counter + 1 and then increments it (so a
- *                 call captured in a CUDA graph advances on every replay)
+ *   step_counter  DEVICE int [2] or NULL: [0] = steps taken so far, [1] =
+ *                 the kernel's completion count, 0 between calls (zero both
+ *                 before the first call).  The update uses t = [0] + 1 and
+ *                 the kernel then increments [0] itself (so a call captured
+ *                 in a CUDA graph advances on every replay).
  */
 pact_status pact_adam_step(int n, float* param, const float* grad, float* m, float* v, int step,
                            int* step_counter, float lr, float beta1, float beta2, float eps,

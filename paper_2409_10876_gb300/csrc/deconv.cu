@@ -91,8 +91,10 @@ struct McdArgs {
     int KT;                // 256-bin tiles
     const unsigned long long* tag;   // fingerprint the tables were built for
     unsigned long long want;         // fingerprint of this call's arguments
-    int* sync;                       // [KT] tile claim counters, [1] CTA-done ticket: zero at launch and left
-                                     // zero by the launch (they live in the tables)
+    int* sync;                       // [KT] tile claim counters, [1] CTA-done ticket, [1] CTAs that cleared
+                                     // their share of dL_dw: zero at launch and left zero by the launch
+                                     // (they live in the tables)
+    int clear_dw;                    // streaming kernel: zero dL_dw in the kernel (instead of a memset)
     float* loss;                     // [1] or NULL (streaming kernel: summed by the last CTA)
     float* loss_pp;                  // [N] or NULL
 };
@@ -401,6 +403,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     const int nc = EXACT ? CPT / kCh : (M + kCh - 1) / kCh;
     int* tile_next = a.sync;                      // [KT]
     int* done_ticket = a.sync + a.KT;             // [1]
+    int* cleared = a.sync + a.KT + 1;             // [1]
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -409,10 +412,19 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         }
         for (int s = 0; s < kSlots; ++s) mbar_init(&slot_free[s], kTile / 32);
         mbar_init_fence();
-        tag_ok = *a.tag == a.want;
     }
     for (int n = tid; n < 2 * n_t; n += blockDim.x) dw_s[n] = 0.f;
+    // everything below reads or writes what earlier kernels produce or read (under
+    // a dependent launch the setup above overlaps the end of the kernel before)
+    pdl_wait();
+    if (tid == 0) tag_ok = *a.tag == a.want;
+    if (a.clear_dw && tid < kTile) {                 // this CTA's share of dL_dw
+        const size_t tot = (size_t)N * n_t, nb = gridDim.x, b = blockIdx.x;
+        for (size_t q = tot * b / nb + tid; q < tot * (b + 1) / nb; q += kTile) a.dL_dw[q] = 0.f;
+        __threadfence();
+    }
     __syncthreads();
+    if (a.clear_dw && tid == 0) atomicAdd(cleared, 1);   // after every thread's fenced stores
 
     if (tid >= kTile) {                              // ---------------- producer warp
         if (lane != 0) return;
@@ -645,6 +657,8 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         // id is visible, then close unit lu with one consumer barrier
         const int qn = (lu + 1) * nc, sn = qn % kStages;
         if (ok) ok = mbar_wait_bounded(&full[sn], (uint32_t)((qn / kStages) & 1), kCopyWaitNs);
+        if (lu == 0 && a.clear_dw && tid == 0 && ok)   // before the first additions: every CTA cleared its share
+            ok = counter_wait_bounded(cleared, (int)gridDim.x, kCopyWaitNs);
         const int u_next = ring[(lu + 1) % kRing];
         const bool all_ok = bar_and(1, kTile, ok);
         if (a.dL_dw) {
@@ -677,7 +691,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     bar_and(1, kTile, true);
     if (!last_s) return;
     __threadfence();
-    for (int t = tid; t <= a.KT; t += kTile) a.sync[t] = 0;   // tile counters and the done ticket
+    for (int t = tid; t <= a.KT + 1; t += kTile) a.sync[t] = 0;   // tile counters, done ticket, clear count
     if (!a.loss && !a.loss_pp) return;
     float tot = 0.f;
     for (int i = tid; i < N; i += kTile) {
@@ -732,7 +746,7 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     p.KT = (F + kBins - 1) / kBins;
     p.KTs = (F + kTile - 1) / kTile;
     p.scratch = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
-    p.nsync = p.KTs + 1;
+    p.nsync = p.KTs + 2;
     size_t o = 256;                                // fingerprint header
     p.t_sync = o;
     o += align_up((size_t)p.nsync * sizeof(int), 256);
@@ -821,7 +835,8 @@ pact_status launch_stream(const McdArgs& a, cudaStream_t st) {
         return check_launch("mc_deconv_loss: occupancy query");
     const int units = a.KT * a.N;
     const int grid = std::min(units, per_sm * num_sms());
-    mcd_stream_kernel<CPT, EXACT, FACT><<<grid, kStreamThreads, smem, st>>>(a);
+    if (launch_pdl(mcd_stream_kernel<CPT, EXACT, FACT>, dim3(grid), dim3(kStreamThreads), smem, st, a) != cudaSuccess)
+        return check_launch("mc_deconv_loss kernel");
     return check_launch("mc_deconv_loss kernel");
 }
 
@@ -897,7 +912,8 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.loss = loss;
     a.loss_pp = loss_pp;
 
-    if (dL_dw && !accumulate &&
+    a.clear_dw = a.stream && dL_dw && !accumulate;
+    if (dL_dw && !accumulate && !a.stream &&
         cudaMemsetAsync(dL_dw, 0, (size_t)pt->n * g->n_t * sizeof(float), st) != cudaSuccess)
         return check_launch("mc_deconv_loss: clearing dL_dw");
     pact_status s;

@@ -43,13 +43,15 @@ __global__ void __launch_bounds__(256) tv_kernel(int G, const float* sos, float 
     }
 }
 
+// counter (optional): [0] steps taken so far, [1] CTAs done with this step.
+// Every thread reads [0] first; the last CTA to finish advances it, so the
+// update needs no second kernel.
 __global__ void adam_kernel(int n, float* param, const float* grad, float* m, float* v, float lr, float b1,
-                            float b2, float eps, float bc1, float bc2, const int* counter,
-                            const unsigned char* mask) {
+                            float b2, float eps, float bc1, float bc2, int* counter, const unsigned char* mask) {
     pdl_trigger();
     pdl_wait();
     if (counter) {  // t = steps so far + 1
-        const float t = (float)(*counter + 1);
+        const float t = (float)(counter[0] + 1);
         bc1 = 1.f - powf(b1, t);
         bc2 = 1.f - powf(b2, t);
     }
@@ -62,11 +64,16 @@ __global__ void adam_kernel(int n, float* param, const float* grad, float* m, fl
         v[q] = vq;
         param[q] -= lr * (mq / bc1) / (sqrtf(vq / bc2) + eps);
     }
-}
-
-__global__ void counter_increment_kernel(int* counter) {
-    pdl_wait();
-    *counter += 1;
+    if (counter) {
+        __syncthreads();                 // every thread of the CTA has read counter[0]
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {   // all CTAs have read it
+                counter[0] += 1;
+                counter[1] = 0;
+            }
+        }
+    }
 }
 
 }  // namespace
@@ -105,11 +112,5 @@ extern "C" pact_status pact_adam_step(int n, float* param, const float* grad, fl
     if (launch_pdl(adam_kernel, dim3(blocks), dim3(256), 0, as_stream(stream), n, param, grad, m, v, lr, beta1, beta2,
                    eps, bc1, bc2, step_counter, mask) != cudaSuccess)
         return check_launch("adam kernel");
-    PACT_TRY(check_launch("adam kernel"));
-    if (step_counter) {
-        if (launch_pdl(counter_increment_kernel, dim3(1), dim3(1), 0, as_stream(stream), step_counter) != cudaSuccess)
-            return check_launch("adam step counter");
-        return check_launch("adam step counter");
-    }
-    return PACT_OK;
+    return check_launch("adam kernel");
 }

@@ -285,6 +285,24 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// Waits until the global counter *p reaches `target` (acquire: what the
+// counting threads wrote before their fenced increments is then visible),
+// giving up after `limit_ns` (returns false then).
+__device__ __forceinline__ bool counter_wait_bounded(const int* p, int target, uint64_t limit_ns) {
+    auto load = [p]() {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        return v;
+    };
+    if (load() >= target) return true;
+    const uint64_t t0 = global_ns();
+    while (load() < target) {
+        if (global_ns() - t0 > limit_ns) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
 // Waits for phase `parity` of `bar` to complete, giving up after `limit_ns`
 // (returns false then; the caller reports the failure instead of hanging).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {

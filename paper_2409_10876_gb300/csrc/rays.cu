@@ -225,6 +225,7 @@ __device__ __forceinline__ float ray_part(const RayArgs& a, const float* dv, int
 template <int L, bool SMEM, bool PAD>
 __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
     extern __shared__ float dv_s[];
+    pdl_trigger();            // a dependent launch (the fused pass) may set up meanwhile
     const int G = a.g.G;
     const int pitch = PAD ? pad_pitch(G) : (SMEM ? smem_pitch(G) : G);
     if (SMEM) {
@@ -619,8 +620,17 @@ __device__ __forceinline__ float sum_parts32(const float* part, int np, int GG, 
     const int q = q0 + lane;
     const int r0 = np * w / nw, r1 = np * (w + 1) / nw;
     float s = 0.f;
-    if (q < GG)
-        for (int r = r0; r < r1; ++r) s += part[(size_t)r * GG + q];
+    if (q < GG) {
+        int r = r0;
+        for (; r + 8 <= r1; r += 8) {            // eight loads in flight, added in order
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldcg(part + (size_t)(r + k) * GG + q);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s += v[k];
+        }
+        for (; r < r1; ++r) s += __ldcg(part + (size_t)r * GG + q);
+    }
     red[w * 32 + lane] = s;
     __syncthreads();
     float tot = 0.f;

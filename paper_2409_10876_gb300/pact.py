@@ -435,15 +435,16 @@ def tv(pb: Problem, sos, lam: float, value=None, grad=None, accumulate=False):
 def adam_step(param, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, mask=None,
               step_counter=None):
     """One in-place Adam update of `param` (Sec. 3.3).  With `step_counter`
-    (int32 CUDA tensor [1]) the step count is read from and advanced on the
-    device, so the call can be replayed from a CUDA graph."""
+    (int32 CUDA tensor [2], zeros initially; [0] counts the steps) the step
+    count is read from and advanced on the device, so the call can be
+    replayed from a CUDA graph."""
     L = load()
     for t, nm in ((param, "param"), (grad, "grad"), (m, "m"), (v, "v")):
         _dev(t, nm, torch.float32, tuple(param.shape))
     if mask is not None:
         _dev(mask, "mask", torch.uint8, tuple(param.shape))
     if step_counter is not None:
-        _dev(step_counter, "step_counter", torch.int32, (1,))
+        _dev(step_counter, "step_counter", torch.int32, (2,))
     _check(L.pact_adam_step(param.numel(), _ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(step),
                             _ptr(step_counter), float(lr),
                             float(beta1), float(beta2), float(eps), _ptr(mask), _stream()), "adam_step")

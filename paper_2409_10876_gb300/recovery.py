@@ -65,27 +65,36 @@ class PGRecovery:
         self.mask = None if mask is None else mask.to(dev, torch.uint8).contiguous()
         self.adam_m = torch.zeros_like(self.sos)
         self.adam_v = torch.zeros_like(self.sos)
-        self.counter = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.counter = torch.zeros(2, dtype=torch.int32, device=dev)
         self.w = torch.empty((pb.n, pb.n_t), dtype=torch.float32, device=dev)
         self.grad = torch.empty_like(self.sos)
         self.out = {"loss": torch.zeros(1, dtype=torch.float32, device=dev),
-                    "dL_dw": torch.empty((pb.n, pb.n_t), dtype=torch.float32, device=dev)}
+                    "dL_dw": torch.zeros((pb.n, pb.n_t), dtype=torch.float32, device=dev)}
         self.tables = pact.McdTables(pb, self.d, dev)       # geometry/delay tables, built once
         self.ws_mcd = pact._ws(self.tables.scratch_bytes, dev)
         self.ws_adj = pact._ws(pact.sos_to_delays_adj_workspace_size(pb), dev)
         self.graph = None
 
-    # one iteration, enqueued on the current stream
-    def step(self):
+    # one iteration, enqueued on the current stream (one chain of kernels;
+    # running the TV term on a side stream next to the rays measured slower).
+    # `mark(k)`, if given, is called between the parts (k = 0 start, 1 after the
+    # rays, 2 after the fused pass, 4 after the ray adjoint, 3 end).
+    def step(self, mark=None):
         pb = self.pb
+        mark = mark or (lambda k: None)
+        mark(0)
         pact.sos_to_delays(pb, self.sos, self.w)
+        mark(1)
         pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
                             tables=self.tables)
+        mark(2)
         pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
+        mark(4)
         if self.lam != 0.0:
             pact.tv(pb, self.sos, self.lam, value=self.out["loss"], grad=self.grad, accumulate=True)
         pact.adam_step(self.sos, self.grad, self.adam_m, self.adam_v, 1, self.lr, self.betas[0], self.betas[1],
                        self.adam_eps, mask=self.mask, step_counter=self.counter)
+        mark(3)
 
     def state(self):
         return [t.clone() for t in (self.sos, self.adam_m, self.adam_v, self.counter)]
@@ -123,10 +132,11 @@ class PGRecovery:
         for it in range(iters):
             self.iterate()
             if record_every and (it % record_every == 0 or it == iters - 1):
-                hist.append(float(self.out["loss"].item()))
+                hist.append(self.loss())
         return hist
 
     def loss(self) -> float:
+        """Eq. 7 at the SOS the last iteration started from: data term + lambda TV."""
         return float(self.out["loss"].item())
 
 

@@ -91,7 +91,7 @@ def train(net: "pact.WarmStartCNN", x_all: torch.Tensor, v_all: torch.Tensor, ep
     xb = torch.empty((B,) + tuple(x_all.shape[1:]), dtype=x_all.dtype, device=dev)
     vb = torch.empty((B,) + tuple(v_all.shape[1:]), dtype=v_all.dtype, device=dev)
     m1, m2 = torch.zeros_like(net.params), torch.zeros_like(net.params)
-    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(2, dtype=torch.int32, device=dev)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     grad = torch.zeros_like(net.params)
     sos = torch.empty_like(vb)

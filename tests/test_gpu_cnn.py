@@ -128,7 +128,7 @@ def test_cnn_training_steps_fit_a_small_batch():
                    for _ in range(B)]).astype(np.float32)
     vt_d = torch.as_tensor(vt, device="cuda")
     m1, m2 = torch.zeros_like(net.params), torch.zeros_like(net.params)
-    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
     hist = []
     for _ in range(60):
         sos = pact.cnn_forward(net, xg)

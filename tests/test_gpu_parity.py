@@ -466,7 +466,7 @@ def test_adam_matches_oracle_and_counter():
     mask = (rng.uniform(size=n) > 0.3).astype(np.uint8)
     p, m, v = (torch.as_tensor(x, device=DEV) for x in (p0.copy(), np.zeros(n, np.float32), np.zeros(n, np.float32)))
     p2, m2, v2 = p.clone(), m.clone(), v.clone()
-    cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
+    cnt = torch.zeros(2, dtype=torch.int32, device=DEV)
     rp, rm, rv = p0.astype(np.float64), np.zeros(n), np.zeros(n)
     for t in range(1, 6):
         g = rng.standard_normal(n).astype(np.float32)
@@ -476,7 +476,32 @@ def test_adam_matches_oracle_and_counter():
         rp, rm, rv = (x.numpy() for x in O.adam_step(rp, g, rm, rv, t, 0.05, mask=mask))
     assert rel(cpu(p), rp) <= 1e-6
     assert rel(cpu(p2), rp) <= 1e-6
-    assert int(cnt.item()) == 5
+    assert cnt.tolist() == [5, 0]
+
+
+def test_adam_counter_with_many_ctas_in_a_graph():
+    """The step count advances once per call also when the update spans many
+    CTAs (the last one to finish advances it), eagerly and on graph replays."""
+    rng = np.random.default_rng(22)
+    n = 600_000
+    p0 = rng.standard_normal(n).astype(np.float32)
+    g = rng.standard_normal(n).astype(np.float32)
+    p, m, v = (torch.as_tensor(x, device=DEV) for x in (p0.copy(), np.zeros(n, np.float32), np.zeros(n, np.float32)))
+    gt = torch.as_tensor(g, device=DEV)
+    cnt = torch.zeros(2, dtype=torch.int32, device=DEV)
+    pact.adam_step(p, gt, m, v, 1, 1e-3, step_counter=cnt)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        pact.adam_step(p, gt, m, v, 1, 1e-3, step_counter=cnt)
+    for _ in range(6):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert cnt.tolist() == [7, 0]        # capture does not run the kernel: 1 eager + 6 replays
+    rp, rm, rv = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for t in range(1, 8):
+        rp, rm, rv = (x.numpy() for x in O.adam_step(rp, g, rm, rv, t, 1e-3))
+    assert rel(cpu(p), rp) <= 1e-6
 
 
 # ------------------------------------------------------------------ recovery loop, graphs, autograd
