@@ -196,24 +196,21 @@ __device__ __forceinline__ float ray_part(const RayArgs& a, const float* dv, int
     const int per = (nsamp + L - 1) / L;
     const int m0 = sub * per, m1 = min(nsamp, m0 + per);
     const float hbx = h * ry.bx, hby = h * ry.by;
-    const float ulast = ry.nfull + 0.5f * (ry.rem / h);
     const float ax = PAD ? ry.ax + 2.f : ry.ax, ay = PAD ? ry.ay + 2.f : ry.ay;
+    auto excess = [&](float u) {
+        const float x = fmaf(u, hbx, ax), y = fmaf(u, hby, ay);
+        if (PAD) return excess_padded(dv, pitch, x, y, v0);
+        const Bil b = bil(G, pitch, x, y);
+        const float d = SMEM ? interp(dv, pitch, b) : interp_global(a.sos, G, v0, b);
+        return __fdividef(d, v0 + d);
+    };
+    // full samples (length h) first, then the partial last one if this lane has it
+    const int mf = min(m1, ry.nfull);
     float acc = 0.f, uf = m0 + 0.5f;
 #pragma unroll 4
-    for (int m = m0; m < m1; ++m, uf += 1.f) {
-        const bool last = m >= ry.nfull;
-        const float u = last ? ulast : uf;
-        const float x = fmaf(u, hbx, ax), y = fmaf(u, hby, ay);
-        float e;
-        if (PAD) {
-            e = excess_padded(dv, pitch, x, y, v0);
-        } else {
-            const Bil b = bil(G, pitch, x, y);
-            const float d = SMEM ? interp(dv, pitch, b) : interp_global(a.sos, G, v0, b);
-            e = __fdividef(d, v0 + d);
-        }
-        acc = fmaf(last ? ry.rem : h, e, acc);
-    }
+    for (int m = m0; m < mf; ++m, uf += 1.f) acc += excess(uf);
+    acc *= h;
+    if (m1 > ry.nfull) acc = fmaf(ry.rem, excess(ry.nfull + 0.5f * (ry.rem / h)), acc);
     return acc;
 }
 
@@ -300,14 +297,6 @@ constexpr int kOrder = 2048;   // largest item count per CTA put in claim order
 // 1.5 * 2^23 leaves round(x) in the low mantissa bits of the sum.
 __device__ __forceinline__ int fixed_round(float x) { return __float_as_int(x + 12582912.f) - 0x4B400000; }
 
-__device__ __forceinline__ void scatter4(int* acc, int pitch, int idx, float S, float c00, float c01, float c10,
-                                         float c11) {
-    atomicAdd(acc + idx, fixed_round(c00 * S));
-    atomicAdd(acc + idx + 1, fixed_round(c01 * S));
-    atomicAdd(acc + idx + pitch, fixed_round(c10 * S));
-    atomicAdd(acc + idx + pitch + 1, fixed_round(c11 * S));
-}
-
 __device__ __forceinline__ float block_min(float x, float* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
@@ -382,7 +371,11 @@ __device__ __forceinline__ T fold_col(const T* row, int c, int G) {
 // one fixed-order kernel sums them.  (Clusters of four CTAs summing their grids
 // through distributed shared memory were measured slower: fewer SMs in use and
 // the cluster barriers per band.)
-__global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int R, int nbands, int narrow) {
+// ONE: the padded grid fits in one band (no per-sample band test).  NARROW:
+// every sample inside the mask disk has padded node coordinates in [1, G + 2]
+// (no clamps; the host checks it, as for the padded forward kernel).
+template <bool ONE, bool NARROW>
+__global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int R, int nbands) {
     extern __shared__ float sm[];
     __shared__ float red_s[32];
     __shared__ float scale_s[2];      // S and 1/S (NaN: poisoned)
@@ -515,58 +508,70 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
             if (gr != 0.f) {
                 const int2 cc = a.centres[i];
                 const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
-                const int nsamp = ry.nfull + (ry.rem > 0.f ? 1 : 0);
                 const float hbx = h * ry.bx, hby = h * ry.by;
                 const float ax = ry.ax + 2.f, ay = ry.ay + 2.f;
-                // samples whose cell row can lie in the band (the test below is exact;
-                // this range only needs to contain them; `narrow` = no sample of any
-                // ray leaves the padded grid, so that the clamp below changes nothing)
-                int mlo = 0, mhi = nsamp;
-                if (narrow && nbands > 1 && hby != 0.f) {
+                // one midpoint sample at ray parameter u (in steps), its weight
+                // (step length x dL/dw x v0 x S) given: dw/dv = weight / v^2, spread
+                // bilinearly over the four nodes as fixed-point integers
+                auto sample = [&](float u, float gsc) {
+                    float x = fmaf(u, hbx, ax), y = fmaf(u, hby, ay);
+                    if (!NARROW) {      // clamped to the padded grid: the edge-clamped interpolation
+                        x = fminf(fmaxf(x, 1.f), (float)(G + 2));
+                        y = fminf(fmaxf(y, 1.f), (float)(G + 2));
+                    }
+                    const float tY = y + 8388607.5f;
+                    const int iy = __float_as_int(tY) - 0x4B000000;
+                    if (!ONE && (iy < r0 || iy >= r1)) return;
+                    const float tX = x + 8388607.5f;
+                    const int ix = __float_as_int(tX) - 0x4B000000;
+                    const float tx = x - (tX - 8388608.f), ty = y - (tY - 8388608.f);
+                    const int idx = (ONE ? iy : iy - r0) * pitch + ix;
+                    const float* q = dv_s + idx;
+                    const float d00 = q[0], d01 = q[1], d10 = q[pitch], d11 = q[pitch + 1];
+                    const float top = fmaf(tx, d01 - d00, d00), bot = fmaf(tx, d11 - d10, d10);
+                    const float d = fmaf(ty, bot - top, top);
+                    const float iv = __fdividef(1.f, v0 + d);
+                    const float coef = gsc * iv * iv;
+                    const float cy1 = coef * ty, cy0 = coef - cy1;
+                    const float c01 = cy0 * tx, c11 = cy1 * tx;
+                    int* acc = acc_s + idx;
+                    atomicAdd(acc, fixed_round(cy0 - c01));
+                    atomicAdd(acc + 1, fixed_round(c01));
+                    atomicAdd(acc + pitch, fixed_round(cy1 - c11));
+                    atomicAdd(acc + pitch + 1, fixed_round(c11));
+                };
+                // full samples m = 0 .. nfull - 1 at u = m + 1/2, in contiguous runs
+                // per lane (only those whose cell row can lie in the band; the test
+                // in sample() is exact, this range only needs to contain them);
+                // the partial last sample (length rem) goes to the group's last lane
+                int mlo = 0, mhi = ry.nfull;
+                if (!ONE && NARROW && hby != 0.f) {
                     const float inv = 1.f / hby;
                     float ma = ((float)r0 - ay) * inv - 0.5f, mb = ((float)r1 - ay) * inv - 0.5f;
                     if (r0 == 0) ma = hby > 0.f ? -INFINITY : INFINITY;
                     if (last_band) mb = hby > 0.f ? INFINITY : -INFINITY;
                     const float lo = fmaxf(fminf(ma, mb), -1e9f), hi = fminf(fmaxf(ma, mb), 1e9f);
                     mlo = max(0, (int)floorf(lo) - 2);
-                    mhi = min(nsamp, (int)ceilf(hi) + 2);
+                    mhi = min(ry.nfull, (int)ceilf(hi) + 2);
                 }
                 const int per = (max(mhi - mlo, 0) + L - 1) / L;
                 const int m0 = mlo + sub * per, len = max(0, min(mhi, m0 + per) - m0);
                 const int off = len * grp / RB;                   // staggered start within the run
-                const float ulast = ry.nfull + 0.5f * (ry.rem * a.g.inv_h);
-                const float gv0 = gr * v0;
+                const float gfull = gr * v0 * h * S;
                 int m = m0 + off;
                 float uf = m + 0.5f;
                 for (int k = 0; k < len; ++k) {
-                    const bool last = m >= ry.nfull;
-                    const float u = last ? ulast : uf;
-                    // clamped to the padded grid: the same value as the edge-clamped
-                    // interpolation, and every access in bounds for any geometry
-                    const float x = fminf(fmaxf(fmaf(u, hbx, ax), 1.f), (float)(G + 2));
-                    const float y = fminf(fmaxf(fmaf(u, hby, ay), 1.f), (float)(G + 2));
+                    const float u = uf;
                     if (++m == m0 + len) {                        // wrap to the start of the run
                         m = m0;
                         uf = m0 + 0.5f;
                     } else {
                         uf += 1.f;
                     }
-                    const float tY = y + 8388607.5f;
-                    const int iy = __float_as_int(tY) - 0x4B000000;
-                    if (iy < r0 || iy >= r1) continue;
-                    const float tX = x + 8388607.5f;
-                    const int ix = __float_as_int(tX) - 0x4B000000;
-                    const float tx = x - (tX - 8388608.f), ty = y - (tY - 8388608.f);
-                    const int idx = (iy - r0) * pitch + ix;
-                    const float* q = dv_s + idx;
-                    const float d00 = q[0], d01 = q[1], d10 = q[pitch], d11 = q[pitch + 1];
-                    const float top = fmaf(tx, d01 - d00, d00), bot = fmaf(tx, d11 - d10, d10);
-                    const float d = fmaf(ty, bot - top, top);
-                    const float iv = __fdividef(1.f, v0 + d);
-                    const float coef = gv0 * (last ? ry.rem : h) * iv * iv;
-                    const float cy0 = coef * (1.f - ty), cy1 = coef * ty;
-                    scatter4(acc_s, pitch, idx, S, cy0 * (1.f - tx), cy0 * tx, cy1 * (1.f - tx), cy1 * tx);
+                    sample(u, gfull);
                 }
+                if (ry.rem > 0.f && sub == L - 1)
+                    sample(ry.nfull + 0.5f * (ry.rem * a.g.inv_h), gr * v0 * ry.rem * S);
             }
             // next item of this CTA: claimed dynamically, so that warps whose
             // items were short take more
@@ -697,7 +702,8 @@ int persistent_grid(const void* fn, int threads, size_t smem) {
 
 struct Plan {
     int fwd_mode, nb_fwd;
-    int R, nbands, nb_adj, nparts, narrow;
+    int R, nbands, nb_adj, nparts;
+    bool narrow;
     size_t smem_fwd, smem_adj, ws;
 };
 
@@ -812,9 +818,10 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.dLdw = dL_dw;
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
-    PACT_TRY(ensure_smem((const void*)rays_adj_kernel, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
-    if (launch_pdl(rays_adj_kernel, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands, pl.narrow) !=
-        cudaSuccess)
+    auto adj = pl.nbands == 1 ? (pl.narrow ? rays_adj_kernel<true, true> : rays_adj_kernel<true, false>)
+                              : (pl.narrow ? rays_adj_kernel<false, true> : rays_adj_kernel<false, false>);
+    PACT_TRY(ensure_smem((const void*)adj, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
+    if (launch_pdl(adj, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands) != cudaSuccess)
         return check_launch("sos_to_delays_adj kernel");
     PACT_TRY(check_launch("sos_to_delays_adj kernel"));
     // one partial grid per CTA: a single fixed-order sum
