@@ -346,6 +346,32 @@ def test_mc_deconv_loss_tabled_matches_per_call_tables(eps):
     assert np.isnan(float(bad["loss"].item())) and np.isnan(cpu(bad["dL_dw"])).any()
 
 
+def test_mc_deconv_loss_overwrites_dl_dw_back_to_back():
+    """dL/dw is overwritten whatever it held (the streaming kernel clears it
+    itself, each CTA a share, before any CTA adds to it), also for calls
+    queued back to back on one stream, where each call's kernel may start
+    while the one before is finishing; with and without prebuilt tables, on a
+    small case and on the full-size launch."""
+    for cfg in (inputs.config_small(), inputs.config_full()):
+        Y, w, d = _mcd_case(cfg, 5)
+        pb = pact.Problem(cfg, DEV)
+        wt, Yt = torch.as_tensor(w, device=DEV), to_dev_c(Y)
+        tab = pact.McdTables(pb, d)
+        ref = pact.mc_deconv_loss(pb, wt, Yt, d, cfg.eps)
+        torch.cuda.synchronize()
+        outs = []
+        for k, fill in enumerate((float("nan"), 7.0, -1e30, float("inf"), 0.0, 3.0)):
+            o = {"loss": torch.zeros(1, device=DEV), "dL_dw": torch.full((pb.n, pb.n_t), fill, device=DEV)}
+            pact.mc_deconv_loss(pb, wt, Yt, d, cfg.eps, out=o, tables=tab if k % 2 == 0 else None)
+            outs.append(o)
+        torch.cuda.synchronize()
+        g_ref = cpu(ref["dL_dw"])
+        assert np.isfinite(g_ref).all() and np.abs(g_ref).max() > 0
+        for o in outs:
+            assert float(o["loss"].item()) == float(ref["loss"].item())      # fixed-order loss sums
+            assert rel(cpu(o["dL_dw"]), g_ref) <= 1e-6
+
+
 def test_mc_deconv_loss_misaligned_w_takes_the_general_path():
     """w not 16-byte aligned (the streaming kernel copies w rows in bulk): the
     two-pass kernel serves the call with the same results."""
