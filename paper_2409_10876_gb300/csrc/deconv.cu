@@ -414,6 +414,15 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         mbar_init_fence();
     }
     for (int n = tid; n < 2 * n_t; n += blockDim.x) dw_s[n] = 0.f;
+    // The CTA's first unit is fixed (unit blockIdx.x of the claim order, grid <=
+    // units): have the L2 fetch its Y rows and ring coordinates meanwhile.
+    const int kt_first = blockIdx.x % a.KT;
+    if (tid >= kTile) {
+        const int i0 = blockIdx.x / a.KT, k0 = kt_first * kTile;
+        const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
+        for (int r = lane; r < M; r += 32) l2_prefetch(a.Y + ((size_t)i0 * M + r) * a.F + k0, bytes);
+        if (lane == 0) l2_prefetch(a.lut + (size_t)i0 * a.F + k0, bytes);
+    }
     // everything below reads or writes what earlier kernels produce or read (under
     // a dependent launch the setup above overlaps the end of the kernel before)
     pdl_wait();
@@ -437,16 +446,18 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             }
             return;
         }
-        int kt = blockIdx.x % a.KT, tried = 0, unit = -1;
+        int kt = kt_first, tried = 0, unit = -1;
+        const int KT = a.KT, grid = gridDim.x;
         for (int q = 0;; ++q) {
             const int s = q % kStages, lu = q / nc, c = q - lu * nc;
             if (q >= kStages &&                       // consumers released chunk q - kStages
                 !mbar_wait_bounded(&empty[s], (uint32_t)((q / kStages - 1) & 1), kCopyWaitNs))
                 return;                               // consumers time out on the missing chunk
             if (c == 0) {                             // claim the next unit
-                unit = -1;
-                while (tried < a.KT) {
-                    const int i = atomicAdd(tile_next + kt, 1);
+                unit = q == 0 ? kt * N + (int)blockIdx.x / KT : -1;   // the first one is fixed
+                while (unit < 0 && tried < KT) {
+                    // tile kt's first (grid - kt + KT - 1) / KT units are the CTAs' fixed first ones
+                    const int i = (grid - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
                     if (i < N) {
                         unit = kt * N + i;
                         break;

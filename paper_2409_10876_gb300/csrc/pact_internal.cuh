@@ -269,6 +269,14 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
         : "memory");
 }
 
+// Asks the L2 to fetch [p, p + bytes) (16-byte aligned, bytes a multiple of
+// 16).  A hint: no data reaches the thread, so it may be issued before the
+// kernels that write that memory have finished (the L2 is the point of
+// coherence; the reads that use the data come after pdl_wait).
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
