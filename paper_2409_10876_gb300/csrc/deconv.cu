@@ -360,6 +360,7 @@ constexpr int kCh = 8;          // channel rows per pipeline stage (16 KB)
 constexpr int kStages = 4;      // stages in flight per CTA (about one unit of look-ahead: a short tail)
 constexpr int kRing = 8;        // unit ids published ahead of their consumers
 constexpr int kSlots = 3;       // per-unit lookup rows (ring coordinates, w) staged ahead
+constexpr int kStaticWaves = 1;              // units per CTA fixed in advance and prefetched (2, 3: slower)
 constexpr int kTile = 224;                   // bins per unit of the streaming kernel, one consumer thread each
 constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two CTAs per SM)
 
@@ -414,15 +415,17 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         mbar_init_fence();
     }
     for (int n = tid; n < 2 * n_t; n += blockDim.x) dw_s[n] = 0.f;
-    // The CTA's first unit is fixed (unit blockIdx.x of the claim order, grid <=
-    // units): have the L2 fetch its Y rows and ring coordinates meanwhile.
+    // The CTA's first kStaticWaves units are fixed (units blockIdx.x + j gridDim.x
+    // of the claim order): have the L2 fetch their Y rows and ring coordinates meanwhile.
+    const int units = a.KT * N, n_static = min(units, kStaticWaves * (int)gridDim.x);
     const int kt_first = blockIdx.x % a.KT;
-    if (tid >= kTile) {
-        const int i0 = blockIdx.x / a.KT, k0 = kt_first * kTile;
-        const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
-        for (int r = lane; r < M; r += 32) l2_prefetch(a.Y + ((size_t)i0 * M + r) * a.F + k0, bytes);
-        if (lane == 0) l2_prefetch(a.lut + (size_t)i0 * a.F + k0, bytes);
-    }
+    if (tid >= kTile)
+        for (int g = blockIdx.x; g < n_static; g += gridDim.x) {
+            const int i0 = g / a.KT, k0 = (g % a.KT) * kTile;
+            const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
+            for (int r = lane; r < M; r += 32) l2_prefetch(a.Y + ((size_t)i0 * M + r) * a.F + k0, bytes);
+            if (lane == 0) l2_prefetch(a.lut + (size_t)i0 * a.F + k0, bytes);
+        }
     // everything below reads or writes what earlier kernels produce or read (under
     // a dependent launch the setup above overlaps the end of the kernel before)
     pdl_wait();
@@ -447,17 +450,18 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             return;
         }
         int kt = kt_first, tried = 0, unit = -1;
-        const int KT = a.KT, grid = gridDim.x;
+        const int KT = a.KT;
         for (int q = 0;; ++q) {
             const int s = q % kStages, lu = q / nc, c = q - lu * nc;
             if (q >= kStages &&                       // consumers released chunk q - kStages
                 !mbar_wait_bounded(&empty[s], (uint32_t)((q / kStages - 1) & 1), kCopyWaitNs))
                 return;                               // consumers time out on the missing chunk
             if (c == 0) {                             // claim the next unit
-                unit = q == 0 ? kt * N + (int)blockIdx.x / KT : -1;   // the first one is fixed
+                const int g = (int)blockIdx.x + lu * (int)gridDim.x;
+                unit = g < n_static ? (g % KT) * N + g / KT : -1;   // the first ones are fixed
                 while (unit < 0 && tried < KT) {
-                    // tile kt's first (grid - kt + KT - 1) / KT units are the CTAs' fixed first ones
-                    const int i = (grid - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
+                    // tile kt's first (n_static - kt + KT - 1) / KT units are the fixed ones
+                    const int i = (n_static - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
                     if (i < N) {
                         unit = kt * N + i;
                         break;
