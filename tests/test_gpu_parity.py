@@ -114,10 +114,14 @@ def test_sos_to_delays_adj(name):
     assert rel(g2, ref + 1.0) <= 2e-3
 
 
-def test_rays_with_mask_beyond_the_node_hull():
+@pytest.mark.parametrize("sos_g", [None, 200])
+def test_rays_with_mask_beyond_the_node_hull(sos_g):
     """A mask disk larger than the SOS grid's field of view: samples beyond the
-    node hull take the edge-clamped SOS (the kernels' clamped paths)."""
+    node hull take the edge-clamped SOS (the kernels' clamped paths; with a
+    200² grid the adjoint also runs in several row bands)."""
     cfg = inputs.config_tiny(p=16, m=4)
+    if sos_g:
+        cfg = cfg.replace(sos_g=sos_g)
     gd = cfg.geometry_dict()
     gd["mask_radius"] = 0.7 * cfg.fov
     pb = pact.Problem(cfg, DEV)
