@@ -252,7 +252,9 @@ def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: fl
             sos_init: torch.Tensor, mask: torch.Tensor, iters: int, graph: bool = True):
     """Public end-to-end API: upload a delay stack (host, ideally pinned), form
     the patch spectra, run `iters` recovery iterations reading the loss back
-    after each, and return (sos, loss history, X_hat)."""
+    after each, and return (sos, loss history, X_hat).  Each iteration's loss
+    is copied to pinned host memory behind it on the stream and read while
+    the next iteration runs, so the read-back does not stall the GPU."""
     dev = pb.device
     stack = stack_host.to(dev, non_blocking=True)
     Y = pact.patch_fft(pb, stack)
@@ -260,9 +262,20 @@ def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: fl
     if graph:
         rec.capture()
     hist = []
-    for _ in range(iters):
+    host = torch.empty(2, dtype=torch.float32, pin_memory=True)      # one slot per iteration in flight
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    stream = torch.cuda.current_stream(dev)
+    for it in range(iters):
         rec.iterate()
-        hist.append(rec.loss())
+        slot = it & 1
+        host[slot:slot + 1].copy_(rec.out["loss"], non_blocking=True)
+        done[slot].record(stream)
+        if it > 0:                               # the previous iteration's loss, copied meanwhile
+            done[slot ^ 1].synchronize()
+            hist.append(float(host[slot ^ 1]))
+    if iters > 0:
+        done[(iters - 1) & 1].synchronize()
+        hist.append(float(host[(iters - 1) & 1]))
     w = pact.sos_to_delays(pb, rec.sos)
     Xh = pact.mc_deconv_loss(pb, w, Y, d, eps, want_grad=False, want_xhat=True)["Xhat"]
     return rec.sos, hist, Xh

@@ -14,7 +14,7 @@ import torch
 
 from oracle import pact_oracle as O
 from paper_2409_10876_gb300 import inputs, pact
-from paper_2409_10876_gb300.recovery import McDeconvLoss, PGRecovery, SosToDelays
+from paper_2409_10876_gb300.recovery import McDeconvLoss, PGRecovery, SosToDelays, recover
 
 pytestmark = pytest.mark.gpu
 
@@ -570,6 +570,26 @@ def test_graph_replay_equals_eager():
     hb = b.run(6, record_every=1)
     assert np.allclose(ha, hb, rtol=1e-5)
     assert rel(cpu(a.sos), cpu(b.sos)) <= 1e-5      # atomics reorder FP32 sums
+
+
+def test_recover_reads_back_every_iteration():
+    """The public end-to-end call (host stack upload, patch spectra, graph
+    replays with each loss read back one iteration behind) gives the loss
+    history and the SOS of the same recovery stepped eagerly."""
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 2)
+    pb = pact.Problem(cfg, DEV)
+    rng = np.random.default_rng(4)
+    stack = torch.as_tensor(rng.standard_normal((cfg.m, cfg.img_h, cfg.img_w)).astype(np.float32)).pin_memory()
+    args = (case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]), torch.as_tensor(case["mask"]))
+    for iters in (1, 2, 17):
+        sos, hist, Xh = recover(pb, stack, *args, iters)
+        rec = PGRecovery(pb, pact.patch_fft(pb, stack.to(DEV)), *args)
+        ref = rec.run(iters, record_every=1)
+        assert len(hist) == iters and np.all(np.isfinite(hist))
+        assert np.allclose(hist, ref, rtol=1e-4)          # atomics reorder FP32 sums
+        assert rel(cpu(sos), cpu(rec.sos)) <= 1e-4
+        assert Xh.shape == (cfg.n_patches, cfg.p, cfg.p // 2 + 1)
 
 
 def test_autograd_functions():
