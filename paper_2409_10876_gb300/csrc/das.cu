@@ -1,8 +1,18 @@
 // Eq. 1 on the GPU: delay-and-sum stack for M extra delays (pact_das_stack).
 //
-// One thread per pixel; the CTA stages the transducer positions in shared
-// memory and every thread walks the ring, taking M linearly interpolated
-// taps of S(., n) per transducer:  q_j = |r' - r_n| fs/v0 - (d_j/v0 + t0) fs.
+// One thread per pixel; every thread walks the ring, taking M linearly
+// interpolated taps of S(., n) per transducer:
+//     q_j = |r' - r_n| fs/v0 - (d_j/v0 + t0) fs.
+// Tiled kernel (das_tile_kernel): a CTA is a 32 x 8 pixel tile.  For each
+// transducer the samples its pixels can touch form one short window (the
+// spread of |r' - r_n| over the tile plus the spread of the delays); the CTA
+// stages the windows of kChunk transducers at a time in shared memory (zero
+// outside the record), and neighbouring pixels then read neighbouring
+// addresses.  Problems whose window would not fit take das_kernel, which
+// reads S from global memory.
+#include <algorithm>
+#include <cmath>
+
 #include "pact_internal.cuh"
 
 namespace pact {
@@ -60,6 +70,83 @@ __global__ void __launch_bounds__(256) das_kernel(const DasArgs a) {
         if (j < a.M) a.stack[(size_t)j * npix + pix] = acc[j];
 }
 
+constexpr int kTX = 32, kTY = 8;       // tile: one warp per pixel row
+constexpr int kWin = 128;               // samples per staged window
+constexpr int kChunk = 32;              // transducers staged at a time
+
+struct DasTileArgs {
+    DasArgs d;
+    float qmax;                         // max_j qoff_j
+    float dmarg;                        // margin on the tile's distance range [m]
+};
+
+// Distance range from r to the pixel centres of the tile [x0, x1] x [y0, y1].
+__device__ __forceinline__ float2 rect_range(float rx, float ry, float x0, float x1, float y0, float y1) {
+    const float cx = fminf(fmaxf(rx, x0), x1), cy = fminf(fmaxf(ry, y0), y1);
+    const float fx = fmaxf(fabsf(rx - x0), fabsf(rx - x1)), fy = fmaxf(fabsf(ry - y0), fabsf(ry - y1));
+    return make_float2(sqrtf((rx - cx) * (rx - cx) + (ry - cy) * (ry - cy)), sqrtf(fx * fx + fy * fy));
+}
+
+template <int MMAX>
+__global__ void __launch_bounds__(kTX * kTY) das_tile_kernel(const DasTileArgs t) {
+    __shared__ float win[kChunk][kWin];
+    __shared__ float2 rn_s[kChunk];
+    __shared__ int ws_s[kChunk];
+    const DasArgs& a = t.d;
+    const int n_t = a.g.n_t, W = a.g.W, H = a.g.H;
+    const int c0 = blockIdx.x * kTX, r0 = blockIdx.y * kTY;
+    const int col = c0 + (threadIdx.x & (kTX - 1)), row = r0 + threadIdx.x / kTX;
+    const bool inside = col < W && row < H;
+    const float2 p = pixel_xy(a.g, min(row, H - 1), min(col, W - 1));
+    const float2 lo = pixel_xy(a.g, r0, c0), hi = pixel_xy(a.g, min(r0 + kTY, H) - 1, min(c0 + kTX, W) - 1);
+    float acc[MMAX];
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) acc[j] = 0.f;
+    for (int nc = 0; nc < n_t; nc += kChunk) {
+        const int cn = min(kChunk, n_t - nc);
+        __syncthreads();                                  // the previous chunk is consumed
+        if (threadIdx.x < cn) {
+            const int n = nc + threadIdx.x;
+            float sn, cs;
+            sincosf(kTwoPi * ((float)n / (float)n_t) + a.g.phase, &sn, &cs);
+            const float rx = a.g.R * cs, ry = a.g.R * sn;
+            rn_s[threadIdx.x] = make_float2(rx, ry);
+            const float2 dr = rect_range(rx, ry, lo.x, hi.x, lo.y, hi.y);
+            // first sample any pixel of the tile can touch, with a margin of two
+            ws_s[threadIdx.x] = (int)floorf((dr.x - t.dmarg) * a.a - t.qmax) - 2;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < cn * kWin; e += blockDim.x) {
+            const int nl = e / kWin, k = e - nl * kWin, q = ws_s[nl] + k;
+            win[nl][k] = (q >= 0 && q < a.n_s) ? __ldg(a.rf + (size_t)(nc + nl) * a.n_s + q) : 0.f;
+        }
+        __syncthreads();
+        for (int nl = 0; nl < cn; ++nl) {
+            const float2 r = rn_s[nl];
+            const float ddx = p.x - r.x, ddy = p.y - r.y;
+            // sample position relative to the window start: q_j - ws (ws exact in FP32)
+            const float base = sqrtf(ddx * ddx + ddy * ddy) * a.a - (float)ws_s[nl];
+            const float* s = win[nl];
+#pragma unroll
+            for (int j = 0; j < MMAX; ++j) {
+                if (j < a.M) {
+                    const float q = base - a.qoff[j];                  // in [2, kWin - 2] by the window
+                    const float tq = q + 8388607.5f;                   // floor without conversions
+                    const int i0 = __float_as_int(tq) - 0x4B000000;
+                    const float f = q - (tq - 8388608.f);
+                    const float s0 = s[i0], s1 = s[i0 + 1];
+                    acc[j] += fmaf(f, s1 - s0, s0);
+                }
+            }
+        }
+    }
+    if (!inside) return;
+    const int npix = H * W, pix = row * W + col;
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j)
+        if (j < a.M) a.stack[(size_t)j * npix + pix] = acc[j];
+}
+
 }  // namespace
 }  // namespace pact
 
@@ -86,6 +173,28 @@ extern "C" pact_status pact_das_stack(const pact_geometry* g, const float* rf, i
     const int npix = g->img_h * g->img_w;
     const int blocks = (npix + 255) / 256;
     cudaStream_t st = as_stream(stream);
+    // tiled path when a tile's window fits: distance spread over the tile (its
+    // diagonal) + delay spread, in samples, plus the margins
+    double qmin = 1e300, qmax = -1e300;
+    for (int j = 0; j < m; ++j) {
+        qmin = std::min(qmin, (double)a.qoff[j]);
+        qmax = std::max(qmax, (double)a.qoff[j]);
+    }
+    const double diag = (double)g->dx * std::sqrt((double)(kTX - 1) * (kTX - 1) + (double)(kTY - 1) * (kTY - 1));
+    const double marg = 1e-3 * diag + 1e-9;        // FP32 rounding of the distances, generously
+    const double need = (diag + 2.0 * marg) * (double)a.a + (qmax - qmin) + 8.0;
+    if (need <= kWin && std::fabs(qmax) < 1e6 && std::fabs(qmin) < 1e6 && g->n_t < (1 << 24)) {
+        DasTileArgs t;
+        t.d = a;
+        t.qmax = (float)qmax;
+        t.dmarg = (float)marg;
+        const dim3 grid((g->img_w + kTX - 1) / kTX, (g->img_h + kTY - 1) / kTY);
+        if (m <= 8) das_tile_kernel<8><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m <= 16) das_tile_kernel<16><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m <= 32) das_tile_kernel<32><<<grid, kTX * kTY, 0, st>>>(t);
+        else das_tile_kernel<64><<<grid, kTX * kTY, 0, st>>>(t);
+        return check_launch("das_stack kernel");
+    }
 #define PACT_DAS(MM)                                                                                 \
     do {                                                                                             \
         PACT_TRY(ensure_smem((const void*)das_kernel<MM>, shm, "das_stack: shared memory attribute")); \

@@ -472,6 +472,41 @@ def test_das_stack():
     assert rel(st, ref) <= 5e-4
 
 
+@pytest.mark.parametrize("m", [32, 5])
+def test_das_stack_tiled_windows(m):
+    """The tiled DAS path (each 32 x 8 pixel tile reads a staged window of
+    samples per transducer): 0.05 mm pixels at 40 MHz, ragged tiles (100 x 72
+    pixels) and a ragged last chunk of transducers (48), arrivals before the
+    record start and after its end (zero there), uniform and non-uniform delays."""
+    cfg = inputs.config_tiny(p=16, m=3).replace(img_h=72, img_w=100, dx=0.05e-3, n_t=48)
+    pb = pact.Problem(cfg, DEV)
+    fs, n_s, t0 = 40e6, 60, 5.5e-6
+    rng = np.random.default_rng(23)
+    rf = rng.standard_normal((cfg.n_t, n_s)).astype(np.float32)
+    d = (np.linspace(-7.5e-4, 7.5e-4, m) if m == 32 else np.array([-6e-4, -1e-4, 0.0, 2.5e-4, 7e-4])).astype(np.float32)
+    st = cpu(pact.das_stack(pb, torch.as_tensor(rf, device=DEV), fs, t0, d))
+    ref = O.das_stack(O.geom(cfg), rf, fs, t0, d).numpy()
+    assert np.abs(ref).max() > 1.0          # (sample positions run from about -70 to 110: both ends are crossed)
+    assert rel(st, ref) <= 5e-4
+
+
+def test_das_stack_channel_data_size_sampled():
+    """1024 transducers x 4096 samples at 40 MHz -> 32 x 1024 x 1024 (the
+    channel-data workload's launch), checked at sampled pixels."""
+    from oracle import rf_oracle as R
+    cfg = inputs.config_rf()
+    pb = pact.Problem(cfg, DEV)
+    rng = np.random.default_rng(24)
+    rf = rng.standard_normal((cfg.n_t, cfg.rf_ns)).astype(np.float32)
+    d = cfg.delays()
+    st = pact.das_stack(pb, torch.as_tensor(rf, device=DEV), cfg.rf_fs, cfg.rf_t0, d)
+    rows = np.array([0, 1, 7, 8, 300, 511, 512, 777, 1016, 1023])
+    cols = np.array([0, 31, 32, 500, 1023, 64, 513, 95, 1000, 1])
+    got = st[:, torch.as_tensor(rows, device=DEV), torch.as_tensor(cols, device=DEV)].cpu().numpy()
+    ref = R.das_at(O.geom(cfg), rf, cfg.rf_fs, cfg.rf_t0, d, torch.as_tensor(rows), torch.as_tensor(cols)).numpy()
+    assert rel(got, ref) <= 5e-4
+
+
 # ------------------------------------------------------------------ TV, Adam
 
 def test_tv():
