@@ -87,7 +87,7 @@ __device__ __forceinline__ float2 rect_range(float rx, float ry, float x0, float
     return make_float2(sqrtf((rx - cx) * (rx - cx) + (ry - cy) * (ry - cy)), sqrtf(fx * fx + fy * fy));
 }
 
-template <int MMAX>
+template <int MMAX, bool EXACT>   // EXACT: M == MMAX
 __global__ void __launch_bounds__(kTX * kTY) das_tile_kernel(const DasTileArgs t) {
     __shared__ float win[kChunk][kWin];
     __shared__ float2 rn_s[kChunk];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kTX * kTY) das_tile_kernel(const DasTileArgs t
             const float* s = win[nl];
 #pragma unroll
             for (int j = 0; j < MMAX; ++j) {
-                if (j < a.M) {
+                if (EXACT || j < a.M) {
                     const float q = base - a.qoff[j];                  // in [2, kWin - 2] by the window
                     const float tq = q + 8388607.5f;                   // floor without conversions
                     const int i0 = __float_as_int(tq) - 0x4B000000;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kTX * kTY) das_tile_kernel(const DasTileArgs t
     const int npix = H * W, pix = row * W + col;
 #pragma unroll
     for (int j = 0; j < MMAX; ++j)
-        if (j < a.M) a.stack[(size_t)j * npix + pix] = acc[j];
+        if (EXACT || j < a.M) a.stack[(size_t)j * npix + pix] = acc[j];
 }
 
 }  // namespace
@@ -189,10 +189,14 @@ extern "C" pact_status pact_das_stack(const pact_geometry* g, const float* rf, i
         t.qmax = (float)qmax;
         t.dmarg = (float)marg;
         const dim3 grid((g->img_w + kTX - 1) / kTX, (g->img_h + kTY - 1) / kTY);
-        if (m <= 8) das_tile_kernel<8><<<grid, kTX * kTY, 0, st>>>(t);
-        else if (m <= 16) das_tile_kernel<16><<<grid, kTX * kTY, 0, st>>>(t);
-        else if (m <= 32) das_tile_kernel<32><<<grid, kTX * kTY, 0, st>>>(t);
-        else das_tile_kernel<64><<<grid, kTX * kTY, 0, st>>>(t);
+        if (m == 8) das_tile_kernel<8, true><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m == 16) das_tile_kernel<16, true><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m == 32) das_tile_kernel<32, true><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m == 64) das_tile_kernel<64, true><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m < 8) das_tile_kernel<8, false><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m < 16) das_tile_kernel<16, false><<<grid, kTX * kTY, 0, st>>>(t);
+        else if (m < 32) das_tile_kernel<32, false><<<grid, kTX * kTY, 0, st>>>(t);
+        else das_tile_kernel<64, false><<<grid, kTX * kTY, 0, st>>>(t);
         return check_launch("das_stack kernel");
     }
 #define PACT_DAS(MM)                                                                                 \
