@@ -7,7 +7,8 @@
 // transducer the samples its pixels can touch form one short window (the
 // spread of |r' - r_n| over the tile plus the spread of the delays); the CTA
 // stages the windows of kChunk transducers at a time in shared memory (zero
-// outside the record), and neighbouring pixels then read neighbouring
+// outside the record) as linear pieces a_k + q b_k, so that a tap is one
+// 64-bit shared load and one FMA, and neighbouring pixels read neighbouring
 // addresses.  Problems whose window would not fit take das_kernel, which
 // reads S from global memory.
 #include <algorithm>
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(256) das_kernel(const DasArgs a) {
         if (j < a.M) a.stack[(size_t)j * npix + pix] = acc[j];
 }
 
-constexpr int kTX = 32, kTY = 8;       // tile: one warp per pixel row
+constexpr int kTX = 32, kTY = 8;       // tile: 4 x 2 warps of 8 x 4 pixels
 constexpr int kWin = 128;               // samples per staged window
 constexpr int kChunk = 32;              // transducers staged at a time
 
@@ -89,13 +90,19 @@ __device__ __forceinline__ float2 rect_range(float rx, float ry, float x0, float
 
 template <int MMAX, bool EXACT>   // EXACT: M == MMAX
 __global__ void __launch_bounds__(kTX * kTY) das_tile_kernel(const DasTileArgs t) {
-    __shared__ float win[kChunk][kWin];
+    // win[n][k] = (a_k, b_k): the linear piece of S(., n) on [ws + k, ws + k + 1]
+    // written as S(ws + q) = a_k + q b_k, q measured from the window start
+    __shared__ float2 win[kChunk][kWin];
     __shared__ float2 rn_s[kChunk];
     __shared__ int ws_s[kChunk];
     const DasArgs& a = t.d;
     const int n_t = a.g.n_t, W = a.g.W, H = a.g.H;
     const int c0 = blockIdx.x * kTX, r0 = blockIdx.y * kTY;
-    const int col = c0 + (threadIdx.x & (kTX - 1)), row = r0 + threadIdx.x / kTX;
+    // a warp covers an 8 x 4 pixel block: its taps of one transducer fall within
+    // about ten consecutive window entries, so its shared loads do not conflict
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int col = c0 + (wid & (kTX / 8 - 1)) * 8 + (lane & 7);
+    const int row = r0 + (wid / (kTX / 8)) * 4 + (lane >> 3);
     const bool inside = col < W && row < H;
     const float2 p = pixel_xy(a.g, min(row, H - 1), min(col, W - 1));
     const float2 lo = pixel_xy(a.g, r0, c0), hi = pixel_xy(a.g, min(r0 + kTY, H) - 1, min(c0 + kTX, W) - 1);
@@ -118,7 +125,11 @@ __global__ void __launch_bounds__(kTX * kTY) das_tile_kernel(const DasTileArgs t
         __syncthreads();
         for (int e = threadIdx.x; e < cn * kWin; e += blockDim.x) {
             const int nl = e / kWin, k = e - nl * kWin, q = ws_s[nl] + k;
-            win[nl][k] = (q >= 0 && q < a.n_s) ? __ldg(a.rf + (size_t)(nc + nl) * a.n_s + q) : 0.f;
+            const float* s = a.rf + (size_t)(nc + nl) * a.n_s;
+            const float s0 = (q >= 0 && q < a.n_s) ? __ldg(s + q) : 0.f;
+            const float s1 = (q + 1 >= 0 && q + 1 < a.n_s) ? __ldg(s + q + 1) : 0.f;
+            const float b = s1 - s0;
+            win[nl][k] = make_float2(fmaf(-(float)k, b, s0), b);
         }
         __syncthreads();
         for (int nl = 0; nl < cn; ++nl) {
@@ -126,16 +137,18 @@ __global__ void __launch_bounds__(kTX * kTY) das_tile_kernel(const DasTileArgs t
             const float ddx = p.x - r.x, ddy = p.y - r.y;
             // sample position relative to the window start: q_j - ws (ws exact in FP32)
             const float base = sqrtf(ddx * ddx + ddy * ddy) * a.a - (float)ws_s[nl];
-            const float* s = win[nl];
+            // shared address of entry floor(q) = bits(q + 2^23 - 1/2) * 8 + this offset
+            // (32-bit wrap-around)
+            const unsigned off = (unsigned)__cvta_generic_to_shared(win[nl]) - 0x4B000000u * 8u;
 #pragma unroll
             for (int j = 0; j < MMAX; ++j) {
                 if (EXACT || j < a.M) {
                     const float q = base - a.qoff[j];                  // in [2, kWin - 2] by the window
                     const float tq = q + 8388607.5f;                   // floor without conversions
-                    const int i0 = __float_as_int(tq) - 0x4B000000;
-                    const float f = q - (tq - 8388608.f);
-                    const float s0 = s[i0], s1 = s[i0 + 1];
-                    acc[j] += fmaf(f, s1 - s0, s0);
+                    const unsigned addr = (unsigned)__float_as_int(tq) * 8u + off;
+                    float pa, pb;
+                    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(pa), "=f"(pb) : "r"(addr));
+                    acc[j] += fmaf(q, pb, pa);
                 }
             }
         }
