@@ -371,7 +371,7 @@ def run_gpu(args, cfg, case, rank, world, local):
                                 "cpu": cpu_model()}
     if not args.no_e2e:
         stack = synthesize_stack(pb, case, dev).cpu().pin_memory()
-        iters = max(50, min(args.steps, 500))
+        iters = cfg.steps                                # one whole recovery of the configuration
         recover(pb, stack, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
                 torch.as_tensor(case["mask"]), 5)               # warm-up (graph capture paths, allocator)
         torch.cuda.synchronize()

@@ -4,7 +4,8 @@
 // Both run once per recovery, so they use a direct separable DFT from shared
 // memory (one CTA per patch and channel): P x P real samples, a twiddle table
 // exp(-2 pi j t / P), a row pass to the P/2+1 half-spectrum columns and a
-// column pass, in FP32 (error ~ sqrt(P) ulp).
+// column pass, in FP32 (error ~ sqrt(P) ulp).  The forward transform gives
+// each thread a register tile of outputs and pairs samples t and P - t.
 #include <algorithm>
 
 #include "pact_internal.cuh"
@@ -12,57 +13,144 @@
 namespace pact {
 namespace {
 
-__global__ void __launch_bounds__(256) patch_fft_kernel(Geo g, int P, int M, const int2* centres,
+// Shared-memory layout of patch_fft_kernel for patch size P.  xT holds the
+// windowed patch transposed (xT[b][a] = sample at row a, column b) with a row
+// stride PS: a multiple of 4 (float4 reads of four rows) whose quarter is odd,
+// so the transposing float4 stores of eight consecutive columns hit distinct
+// banks.  R holds the row spectra with an even stride HS (float4 reads of two
+// columns), tw the twiddles exp(-2 pi j t / P).
+__host__ __device__ inline int fft_ps(int P) {
+    const int p4 = (P + 3) & ~3;
+    return ((p4 / 4) & 1) ? p4 : p4 + 4;
+}
+__host__ __device__ inline int fft_hs(int P) { return ((P / 2 + 1) + 1) & ~1; }
+inline size_t fft_smem(int P) {
+    return (size_t)P * fft_ps(P) * sizeof(float) + ((size_t)P * fft_hs(P) + P) * sizeof(float2);
+}
+
+// Register tiles: the row pass gives a thread 4 patch rows x 4 half-spectrum
+// columns, the column pass 8 frequency rows x 2 columns.
+constexpr int kRA = 4, kRV = 4, kCU = 8, kCV = 2;
+
+// Windowed half-spectrum DFT of patch i = blockIdx.y, channel j = blockIdx.x.
+// Both passes pair sample t with P - t: for a real row, x_t e^{-j phi} +
+// x_{P-t} e^{j phi} = (x_t + x_{P-t}) cos phi - j (x_t - x_{P-t}) sin phi, and
+// for the complex column pass the same with R_t +- R_{P-t}, which halves the
+// multiply-adds; t = 0 and t = P/2 enter once with phase 1 and (-1)^k.
+__global__ void __launch_bounds__(256, 3) patch_fft_kernel(Geo g, int P, int M, const int2* centres,
                                                         float inv_2s2, const float* stack, float2* Y) {
-    extern __shared__ float sm[];
-    const int half = P / 2 + 1;
-    float* x = sm;                                          // [P*P]
-    float2* R = reinterpret_cast<float2*>(sm + P * P);      // [P*half]
-    float2* tw = R + P * half;                              // [P]
+    extern __shared__ float4 sm4[];
+    const int half = P / 2 + 1, h2 = P / 2, PS = fft_ps(P), HS = fft_hs(P);
+    float* xT = reinterpret_cast<float*>(sm4);
+    float2* R = reinterpret_cast<float2*>(xT + (size_t)P * PS);
+    float2* tw = R + (size_t)P * HS;
     const int i = blockIdx.y, j = blockIdx.x;
     const int2 c = centres[i];
     const int r0 = c.x - P / 2, c0 = c.y - P / 2;
     for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = cis_pi(-2.f * t / P);
     const float* img = stack + (size_t)j * g.H * g.W;
-    for (int q = threadIdx.x; q < P * P; q += blockDim.x) {
-        const int a = q / P, b = q - (q / P) * P;
-        const int row = r0 + a, col = c0 + b;
-        float val = 0.f;
-        if (row >= 0 && row < g.H && col >= 0 && col < g.W) val = img[(size_t)row * g.W + col];
-        const float oa = (a - P / 2) * g.dx, ob = (b - P / 2) * g.dx;
-        x[q] = val * expf(-(oa * oa + ob * ob) * inv_2s2);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < P * half; q += blockDim.x) {
-        const int a = q / half, v = q - (q / half) * half;
-        const float* xr = x + a * P;
-        float re = 0.f, im = 0.f;
-        int idx = 0;
-        for (int b = 0; b < P; ++b) {
-            const float2 t = tw[idx];
-            re = fmaf(xr[b], t.x, re);
-            im = fmaf(xr[b], t.y, im);
-            idx += v;
-            if (idx >= P) idx -= P;
+    // column b fastest: coalesced reads of the image, one float4 of four rows per store
+    for (int q = threadIdx.x; q < (PS / 4) * P; q += blockDim.x) {
+        const int ag = q / P, b = q - ag * P;
+        const int col = c0 + b;
+        const float ob = (b - P / 2) * g.dx;
+        float v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int a = ag * 4 + r, row = r0 + a;
+            float val = 0.f;
+            if (a < P && row >= 0 && row < g.H && col >= 0 && col < g.W) val = img[(size_t)row * g.W + col];
+            const float oa = (a - P / 2) * g.dx;
+            v[r] = val * expf(-(oa * oa + ob * ob) * inv_2s2);
         }
-        R[q] = make_float2(re, im);
+        *reinterpret_cast<float4*>(xT + (size_t)b * PS + ag * 4) = make_float4(v[0], v[1], v[2], v[3]);
     }
     __syncthreads();
+    // row pass: R[a][v] = sum_b x[a][b] exp(-2 pi j b v / P)
+    const int nv1 = (half + kRV - 1) / kRV;
+    for (int t = threadIdx.x; t < ((P + kRA - 1) / kRA) * nv1; t += blockDim.x) {
+        const int a0 = (t / nv1) * kRA, v0 = (t - (t / nv1) * nv1) * kRV;
+        int vv[kRV], id[kRV];
+        float re[kRA][kRV], im[kRA][kRV];
+        const float4 x0 = *reinterpret_cast<const float4*>(xT + a0);
+        const float4 xh = *reinterpret_cast<const float4*>(xT + (size_t)h2 * PS + a0);
+        const float xa[4] = {x0.x, x0.y, x0.z, x0.w}, xb[4] = {xh.x, xh.y, xh.z, xh.w};
+#pragma unroll
+        for (int k = 0; k < kRV; ++k) {
+            vv[k] = min(v0 + k, half - 1);
+            id[k] = vv[k];
+#pragma unroll
+            for (int r = 0; r < kRA; ++r) {
+                re[r][k] = (vv[k] & 1) ? xa[r] - xb[r] : xa[r] + xb[r];
+                im[r][k] = 0.f;
+            }
+        }
+        for (int b = 1; b < h2; ++b) {
+            const float4 p = *reinterpret_cast<const float4*>(xT + (size_t)b * PS + a0);
+            const float4 m = *reinterpret_cast<const float4*>(xT + (size_t)(P - b) * PS + a0);
+            const float s[4] = {p.x + m.x, p.y + m.y, p.z + m.z, p.w + m.w};
+            const float d[4] = {p.x - m.x, p.y - m.y, p.z - m.z, p.w - m.w};
+#pragma unroll
+            for (int k = 0; k < kRV; ++k) {
+                const float2 w = tw[id[k]];
+#pragma unroll
+                for (int r = 0; r < kRA; ++r) {
+                    re[r][k] = fmaf(s[r], w.x, re[r][k]);
+                    im[r][k] = fmaf(d[r], w.y, im[r][k]);
+                }
+                id[k] += vv[k];
+                if (id[k] >= P) id[k] -= P;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRA; ++r)
+#pragma unroll
+            for (int k = 0; k < kRV; ++k)
+                if (a0 + r < P && v0 + k < half) R[(size_t)(a0 + r) * HS + v0 + k] = make_float2(re[r][k], im[r][k]);
+    }
+    __syncthreads();
+    // column pass: Y[u][v] = sum_a R[a][v] exp(-2 pi j u a / P) / P
     const float inv_p = 1.f / P;
     float2* out = Y + ((size_t)i * M + j) * P * half;
-    for (int q = threadIdx.x; q < P * half; q += blockDim.x) {
-        const int u = q / half, v = q - (q / half) * half;
-        float re = 0.f, im = 0.f;
-        int idx = 0;
-        for (int a = 0; a < P; ++a) {
-            const float2 r = R[a * half + v];
-            const float2 t = tw[idx];
-            re = fmaf(r.x, t.x, fmaf(-r.y, t.y, re));
-            im = fmaf(r.x, t.y, fmaf(r.y, t.x, im));
-            idx += u;
-            if (idx >= P) idx -= P;
+    const int nv2 = (half + kCV - 1) / kCV;
+    for (int t = threadIdx.x; t < ((P + kCU - 1) / kCU) * nv2; t += blockDim.x) {
+        const int u0 = (t / nv2) * kCU, v0 = (t - (t / nv2) * nv2) * kCV;
+        int uu[kCU], id[kCU];
+        float re[kCU][2], im[kCU][2];
+        const float4 q0 = *reinterpret_cast<const float4*>(R + v0);
+        const float4 qh = *reinterpret_cast<const float4*>(R + (size_t)h2 * HS + v0);
+#pragma unroll
+        for (int k = 0; k < kCU; ++k) {
+            uu[k] = min(u0 + k, P - 1);
+            id[k] = uu[k];
+            const float sg = (uu[k] & 1) ? -1.f : 1.f;
+            re[k][0] = fmaf(sg, qh.x, q0.x);
+            im[k][0] = fmaf(sg, qh.y, q0.y);
+            re[k][1] = fmaf(sg, qh.z, q0.z);
+            im[k][1] = fmaf(sg, qh.w, q0.w);
         }
-        out[q] = make_float2(re * inv_p, im * inv_p);
+        for (int a = 1; a < h2; ++a) {
+            const float4 p = *reinterpret_cast<const float4*>(R + (size_t)a * HS + v0);
+            const float4 m = *reinterpret_cast<const float4*>(R + (size_t)(P - a) * HS + v0);
+            const float sr0 = p.x + m.x, si0 = p.y + m.y, dr0 = p.x - m.x, di0 = p.y - m.y;
+            const float sr1 = p.z + m.z, si1 = p.w + m.w, dr1 = p.z - m.z, di1 = p.w - m.w;
+#pragma unroll
+            for (int k = 0; k < kCU; ++k) {
+                const float2 w = tw[id[k]];
+                re[k][0] = fmaf(-di0, w.y, fmaf(sr0, w.x, re[k][0]));
+                im[k][0] = fmaf(dr0, w.y, fmaf(si0, w.x, im[k][0]));
+                re[k][1] = fmaf(-di1, w.y, fmaf(sr1, w.x, re[k][1]));
+                im[k][1] = fmaf(dr1, w.y, fmaf(si1, w.x, im[k][1]));
+                id[k] += uu[k];
+                if (id[k] >= P) id[k] -= P;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kCU; ++k)
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2)
+                if (u0 + k < P && v0 + c2 < half)
+                    out[(size_t)(u0 + k) * half + v0 + c2] = make_float2(re[k][c2] * inv_p, im[k][c2] * inv_p);
     }
 }
 
@@ -147,8 +235,8 @@ extern "C" pact_status pact_patch_fft(const pact_geometry* g, const pact_patches
     PACT_TRY(check_patches(pt));
     if (!stack || !Y) return fail(PACT_ERR_INVALID_ARG, "patch_fft: stack and Y must not be NULL");
     if (m < 1 || m > 65535) return fail(PACT_ERR_INVALID_ARG, "patch_fft: channel count %d out of range", m);
-    const int P = pt->p, half = P / 2 + 1;
-    const size_t shm = (size_t)P * P * sizeof(float) + (size_t)(P * half + P) * sizeof(float2);
+    const int P = pt->p;
+    const size_t shm = fft_smem(P);
     PACT_TRY(ensure_smem((const void*)patch_fft_kernel, shm, "patch_fft: shared memory attribute"));
     dim3 grid(m, pt->n);
     patch_fft_kernel<<<grid, 256, shm, as_stream(stream)>>>(make_geo(g), P, m,

@@ -410,9 +410,18 @@ def test_mc_deconv_loss_noise_free_truth_is_minimum():
 
 # ------------------------------------------------------------------ Sec. S1.4 spectra, stitching
 
-@pytest.mark.parametrize("name", ["tiny_p16_m4", "small_p32_m8"])
+FFT_CASES = {
+    "tiny_p8_m1": CASES["tiny_p8_m1"],
+    "tiny_p12_m3": CASES["tiny_p12_m3"],
+    "tiny_p16_m4": CASES["tiny_p16_m4"],
+    "tiny_p18_m3": lambda: inputs.config_tiny(p=18, m=3),      # P = 2 mod 4: ragged row tiles
+    "small_p32_m8": inputs.config_small,
+}
+
+
+@pytest.mark.parametrize("name", list(FFT_CASES))
 def test_patch_fft(name):
-    cfg = CASES[name]()
+    cfg = FFT_CASES[name]()
     case = inputs.make_case(cfg, 3)
     pb = pact.Problem(cfg, DEV)
     Y = cpu(pact.patch_fft(pb, torch.as_tensor(case["noise"], device=DEV)))
@@ -427,6 +436,19 @@ def test_patch_fft_full_size_sampled():
     Y = cpu(pact.patch_fft(pb, torch.as_tensor(case["noise"][:4], device=DEV)))
     idx = [0, 50, 143]
     ref = O.patch_spectra(O.geom(cfg), case["noise"][:4], case["centres"][idx]).numpy()
+    assert rel(Y[idx], ref) <= 1e-4
+
+
+def test_patch_fft_channel_data_size_sampled():
+    """64 x 64 patches of the 1024 x 1024 channel-data image (3721 patches at
+    stride 16), four channels of noise: the first, last and middle patches and
+    one on the top edge, checked against the oracle."""
+    cfg = inputs.config_rf()
+    pb = pact.Problem(cfg, DEV)
+    stack = np.random.default_rng(23).standard_normal((4, cfg.img_h, cfg.img_w)).astype(np.float32)
+    Y = cpu(pact.patch_fft(pb, torch.as_tensor(stack, device=DEV)))
+    idx = [0, 60, 1860, 3720]
+    ref = O.patch_spectra(O.geom(cfg), stack, cfg.centres()[idx]).numpy()
     assert rel(Y[idx], ref) <= 1e-4
 
 
