@@ -415,6 +415,9 @@ FFT_CASES = {
     "tiny_p12_m3": CASES["tiny_p12_m3"],
     "tiny_p16_m4": CASES["tiny_p16_m4"],
     "tiny_p18_m3": lambda: inputs.config_tiny(p=18, m=3),      # P = 2 mod 4: ragged row tiles
+    "tiny_p4_m2": lambda: inputs.config_tiny(p=4, m=2),        # smallest patch: one folded pair
+    "tiny_p128_m2": lambda: inputs.config_tiny(p=128, m=2),    # largest patch (3 row-pass tiles per thread),
+                                                               # reaching past the 64 x 64 image (zero padding)
     "small_p32_m8": inputs.config_small,
 }
 
@@ -494,18 +497,24 @@ def test_das_stack():
     assert rel(st, ref) <= 5e-4
 
 
-@pytest.mark.parametrize("m", [32, 5])
-def test_das_stack_tiled_windows(m):
-    """The tiled DAS path (each 32 x 8 pixel tile reads a staged window of
-    samples per transducer): 0.05 mm pixels at 40 MHz, ragged tiles (100 x 72
+@pytest.mark.parametrize("m,h,w", [(32, 72, 100), (5, 72, 100), (8, 70, 100), (1, 37, 45), (64, 72, 100), (17, 9, 33)])
+def test_das_stack_tiled_windows(m, h, w):
+    """The tiled DAS path (each 32 x 8 pixel tile, warps over 8 x 4 pixel
+    blocks, reads a staged window of samples per transducer): 0.05 mm pixels at
+    40 MHz, ragged tiles and warp blocks (100 x 72, 100 x 70, 45 x 37, 33 x 9
     pixels) and a ragged last chunk of transducers (48), arrivals before the
-    record start and after its end (zero there), uniform and non-uniform delays."""
-    cfg = inputs.config_tiny(p=16, m=3).replace(img_h=72, img_w=100, dx=0.05e-3, n_t=48)
+    record start and after its end (zero there), uniform and non-uniform
+    delays, channel counts with an exact kernel instance (8, 32, 64) and
+    without (1, 5, 17)."""
+    cfg = inputs.config_tiny(p=16, m=3).replace(img_h=h, img_w=w, dx=0.05e-3, n_t=48)
     pb = pact.Problem(cfg, DEV)
     fs, n_s, t0 = 40e6, 60, 5.5e-6
     rng = np.random.default_rng(23)
     rf = rng.standard_normal((cfg.n_t, n_s)).astype(np.float32)
-    d = (np.linspace(-7.5e-4, 7.5e-4, m) if m == 32 else np.array([-6e-4, -1e-4, 0.0, 2.5e-4, 7e-4])).astype(np.float32)
+    if m == 5:
+        d = np.array([-6e-4, -1e-4, 0.0, 2.5e-4, 7e-4], np.float32)
+    else:
+        d = np.linspace(-7.5e-4, 7.5e-4, m).astype(np.float32) if m > 1 else np.array([2e-4], np.float32)
     st = cpu(pact.das_stack(pb, torch.as_tensor(rf, device=DEV), fs, t0, d))
     ref = O.das_stack(O.geom(cfg), rf, fs, t0, d).numpy()
     assert np.abs(ref).max() > 1.0          # (sample positions run from about -70 to 110: both ends are crossed)
