@@ -66,10 +66,11 @@ __global__ void __launch_bounds__(256, 3) patch_fft_kernel(Geo g, int P, int M, 
         *reinterpret_cast<float4*>(xT + (size_t)b * PS + ag * 4) = make_float4(v[0], v[1], v[2], v[3]);
     }
     __syncthreads();
-    // row pass: R[a][v] = sum_b x[a][b] exp(-2 pi j b v / P)
-    const int nv1 = (half + kRV - 1) / kRV;
-    for (int t = threadIdx.x; t < ((P + kRA - 1) / kRA) * nv1; t += blockDim.x) {
-        const int a0 = (t / nv1) * kRA, v0 = (t - (t / nv1) * nv1) * kRV;
+    // row pass: R[a][v] = sum_b x[a][b] exp(-2 pi j b v / P); neighbouring lanes
+    // take neighbouring row groups, so a warp's twiddle loads are broadcasts
+    const int na1 = (P + kRA - 1) / kRA;
+    for (int t = threadIdx.x; t < na1 * ((half + kRV - 1) / kRV); t += blockDim.x) {
+        const int v0 = (t / na1) * kRV, a0 = (t - (t / na1) * na1) * kRA;
         int vv[kRV], id[kRV];
         float re[kRA][kRV], im[kRA][kRV];
         const float4 x0 = *reinterpret_cast<const float4*>(xT + a0);
