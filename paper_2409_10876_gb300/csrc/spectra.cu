@@ -240,7 +240,13 @@ extern "C" pact_status pact_patch_fft(const pact_geometry* g, const pact_patches
     const size_t shm = fft_smem(P);
     PACT_TRY(ensure_smem((const void*)patch_fft_kernel, shm, "patch_fft: shared memory attribute"));
     dim3 grid(m, pt->n);
-    patch_fft_kernel<<<grid, 256, shm, as_stream(stream)>>>(make_geo(g), P, m,
+    // one thread per register tile of the larger pass (at most 256): fewer idle
+    // warps at the barriers and more CTAs per SM for small patches
+    const int half = P / 2 + 1;
+    const int tiles = std::max(((P + kRA - 1) / kRA) * ((half + kRV - 1) / kRV),
+                               ((P + kCU - 1) / kCU) * ((half + kCV - 1) / kCV));
+    const int threads = std::min(256, (tiles + 31) / 32 * 32);
+    patch_fft_kernel<<<grid, threads, shm, as_stream(stream)>>>(make_geo(g), P, m,
                                                            reinterpret_cast<const int2*>(pt->centres),
                                                            inv_two_sigma2(pt->window_fwhm), stack,
                                                            reinterpret_cast<float2*>(Y));
