@@ -54,8 +54,8 @@ typedef enum pact_status {
     PACT_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, bad flag */
     PACT_ERR_SHAPE = 2,         /* sizes outside what the kernels support */
     PACT_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
-    PACT_ERR_TIMEOUT = 4,       /* reserved: a bounded device-side wait gave up */
-    PACT_ERR_NONFINITE = 5,     /* reserved: non-finite values detected */
+    PACT_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up (status calls) */
+    PACT_ERR_NONFINITE = 5,     /* non-finite values detected (reserved for callers' checks) */
     PACT_ERR_UNSUPPORTED = 6    /* feature not available on this device/build */
 } pact_status;
 
@@ -260,8 +260,13 @@ size_t pact_mc_deconv_loss_workspace_size(const pact_geometry* g, const pact_pat
  * rounding size relative to the residual, not to the data.
  * Errors: INVALID_ARG (null w/Y/loss/ws, eps < 0, small ws,
  * misaligned Y), SHAPE (m > PACT_MAX_CHANNELS, P odd or out of range, n_t too
- * large for shared memory).  A bulk copy that does not complete within
- * 200 ms (never expected) makes the loss and dL_dw NaN instead of hanging.
+ * large for shared memory).  Every device-side wait of the pass is bounded
+ * (pact_set_wait_limit_ns, default 200 ms); a wait that gives up (never
+ * expected) makes the loss and dL_dw NaN and sets the status word that
+ * pact_mc_deconv_status reads, instead of hanging.  dL_dw is overwritten
+ * without a separate clearing launch: the first CTA to claim work on patch
+ * i zeroes row i, and the others check (bounded wait) that it has before
+ * adding to it; no CTA waits for a CTA that may not be resident.
  */
 pact_status pact_mc_deconv_loss(const pact_geometry* g, const pact_patches* pt, const float* w,
                                 const float* Y, const float* d, int m, float eps, float* loss,
@@ -308,6 +313,37 @@ pact_status pact_mc_deconv_loss_tabled(const pact_geometry* g, const pact_patche
                                        float* dL_dw, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * Failure detection of the fused pass (no counterpart in the paper).
+ * pact_mc_deconv_status reads and clears the status word of one table block:
+ * pass the prebuilt tables (tables != NULL, ws = NULL) or the workspace of a
+ * pact_mc_deconv_loss / _adj call (ws != NULL, tables = NULL; its tables are
+ * rebuilt, and the word cleared, by every such call).  It synchronises the
+ * stream and returns PACT_ERR_TIMEOUT if a wait of a call since the last
+ * read gave up (that call's loss and dL_dw are then NaN), else PACT_OK.
+ * pact_mc_deconv_inject_stall is a test hook: it marks dL_dw row `patch` of
+ * the prebuilt tables as "being zeroed by another CTA" (a flag nothing
+ * clears during the launch), so the next overwriting call's waits on that
+ * row run into the wait limit and the call reports PACT_ERR_TIMEOUT through
+ * the status word.  The call after that runs normally (every launch leaves
+ * the row states at zero).  Nothing faults or hangs.
+ *   g, pt, m  the problem the tables were built for (layout only)
+ *   patch     0 <= patch < N
+ */
+pact_status pact_mc_deconv_status(const pact_geometry* g, const pact_patches* pt, int m, void* tables,
+                                  void* ws, void* stream);
+pact_status pact_mc_deconv_inject_stall(const pact_geometry* g, const pact_patches* pt, int m, void* tables,
+                                        void* ws, int patch, void* stream);
+
+/*
+ * Bound on every device-side wait of the kernels launched after this call
+ * (fused pass, neural-field and CNN kernels), in ns: 0 restores the default
+ * (200 ms), otherwise 1e5 <= ns <= 1e10 (INVALID_ARG outside).  Process-wide;
+ * a launch captured into a CUDA graph keeps the limit it saw at capture.
+ */
+pact_status pact_set_wait_limit_ns(unsigned long long ns);
+unsigned long long pact_get_wait_limit_ns(void);
+
+/*
  * pact_mc_deconv_loss without a workspace argument.  The paper has no
  * counterpart: this is a library-usage variant of pact_mc_deconv_loss with
  * identical arithmetic and outputs.
@@ -324,7 +360,10 @@ pact_status pact_mc_deconv_loss_tabled(const pact_geometry* g, const pact_patche
  *     and a message giving both sizes; nothing is launched.
  *   - The first call on each device looks up the device address of the
  *     array (with that device current) and caches it; make that first call
- *     before any stream capture.
+ *     before any stream capture.  A call that reports PACT_ERR_CUDA drops
+ *     the cached address, so after cudaDeviceReset (which unloads the
+ *     array with the module) the first call may fail once and the next
+ *     looks the address up again.
  *   - Every call on a device shares the one array and it keeps the last
  *     call's contents; the kernels overwrite every scratch entry they read,
  *     so no clearing is needed.  Calls that overlap on the GPU (different

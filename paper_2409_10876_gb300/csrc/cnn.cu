@@ -31,7 +31,6 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr uint64_t kCnnWaitNs = 200ull * 1000ull * 1000ull;   // bound on every tensor-core wait
 constexpr int kConvStages = 3;
 constexpr int kWgPix = 64;          // pixels (K) per wgrad stage
 constexpr int kWgStages = 3;
@@ -56,8 +55,8 @@ using umma::idesc_bf16_mn;
 using umma::mn_slice;
 using umma::mnmaj_off;
 
-__device__ __forceinline__ bool wait_or_flag(uint64_t* bar, uint32_t parity, int* status) {
-    const bool ok = mbar_wait_bounded(bar, parity, kCnnWaitNs);
+__device__ __forceinline__ bool wait_or_flag(uint64_t* bar, uint32_t parity, int* status, unsigned long long limit) {
+    const bool ok = mbar_wait_bounded(bar, parity, limit);
     if (!ok) atomicExch(status, 1);
     return ok;
 }
@@ -76,6 +75,7 @@ struct ConvArgs {
     int sign;              // +1: tap offset (dy - 1, dx - 1); -1: its negative (dgrad)
     int relu;
     int* status;
+    unsigned long long limit_ns;   // bound on every tensor-core wait (pact_set_wait_limit_ns)
 };
 
 // CTA: 128 consecutive pixels p = (b H + y) W + x, all N output channels.
@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(128) conv_kernel(const ConvArgs a) {
         if (tn < 9) {
             const int sn = tn % kConvStages;
             if (tn >= kConvStages)    // the MMAs of tap tn - 3 read stage sn
-                ok = wait_or_flag(&done[sn], (uint32_t)(((tn - kConvStages) / kConvStages) & 1), a.status) && ok;
+                ok = wait_or_flag(&done[sn], (uint32_t)(((tn - kConvStages) / kConvStages) & 1), a.status, a.limit_ns) && ok;
             gather(tn, sn);
         }
     }
-    ok = wait_or_flag(&done[8 % kConvStages], (uint32_t)((8 / kConvStages) & 1), a.status) && ok;
+    ok = wait_or_flag(&done[8 % kConvStages], (uint32_t)((8 / kConvStages) & 1), a.status, a.limit_ns) && ok;
     umma::fence_after();
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     for (int c0 = 0; c0 < N; c0 += 32) {
@@ -180,6 +180,7 @@ struct WgradArgs {
     int B, H, W, Cin, Cout;
     int taps_per_group;    // 128 / Cin
     int* status;
+    unsigned long long limit_ns;   // bound on every tensor-core wait (pact_set_wait_limit_ns)
 };
 
 // CTA (chunk, group): pixels [chunk*4096, +4096), rows r = tl * Cin + ci for the
@@ -271,12 +272,12 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const WgradArgs a) {
         if (jn < nst) {
             const int sn = jn % kWgStages;
             if (jn >= kWgStages)
-                ok = wait_or_flag(&done[sn], (uint32_t)(((jn - kWgStages) / kWgStages) & 1), a.status) && ok;
+                ok = wait_or_flag(&done[sn], (uint32_t)(((jn - kWgStages) / kWgStages) & 1), a.status, a.limit_ns) && ok;
             gather(jn, sn);
         }
     }
     const int last = nst - 1;
-    ok = wait_or_flag(&done[last % kWgStages], (uint32_t)((last / kWgStages) & 1), a.status) && ok;
+    ok = wait_or_flag(&done[last % kWgStages], (uint32_t)((last / kWgStages) & 1), a.status, a.limit_ns) && ok;
     umma::fence_after();
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const int groups = gridDim.y;
@@ -651,6 +652,7 @@ pact_status launch_conv(const Ctx& c, const bf16* in, const bf16* wpk, const flo
     a.sign = sign;
     a.relu = relu;
     a.status = c.status;
+    a.limit_ns = wait_limit_ns();
     const size_t smem = (size_t)kConvStages * (128 * K * 2 + (size_t)N * K * 2);
     PACT_TRY(ensure_smem((const void*)conv_kernel, smem, "cnn: conv shared memory attribute"));
     const int P = B * res * res;
@@ -673,6 +675,7 @@ pact_status launch_wgrad(const Ctx& c, const Layer& y, const bf16* x, const bf16
     a.Cout = y.cout;
     a.taps_per_group = 128 / y.cin_pad;
     a.status = c.status;
+    a.limit_ns = wait_limit_ns();
     const int groups = (9 + a.taps_per_group - 1) / a.taps_per_group;
     const int nchunks = (P + kWgChunk - 1) / kWgChunk;
     const size_t smem = (size_t)kWgStages * (128 * kWgPix * 2 + (size_t)y.cout * kWgPix * 2);

@@ -2,6 +2,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -28,18 +29,35 @@ pact_status check_launch(const char* what) {
     return PACT_OK;
 }
 
-int num_sms() {
-    static int cache[64] = {0};
+namespace {
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_sms[kMaxDevices];                 // SM count per device, 0 = not queried yet
+constexpr unsigned long long kDefaultWaitNs = 200ull * 1000ull * 1000ull;
+std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+}  // namespace
+
+pact_status require_sms() {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
-    if (cache[dev] == 0) {
-        int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 148;
-        cache[dev] = n;
-    }
-    return cache[dev];
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(PACT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PACT_ERR_UNSUPPORTED, "device index %d is not supported", dev);
+    if (g_sms[dev].load(std::memory_order_acquire) > 0) return PACT_OK;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || n <= 0)
+        return fail(PACT_ERR_CUDA, "SM count query failed: %s", cudaGetErrorString(e));
+    g_sms[dev].store(n, std::memory_order_release);
+    return PACT_OK;
 }
+
+int num_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    const int n = g_sms[dev].load(std::memory_order_acquire);
+    return n > 0 ? n : 1;    // entry points call require_sms() first, so 1 is never used
+}
+
+unsigned long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 pact_status ensure_smem(const void* fn, size_t bytes, const char* what) {
     if (bytes <= 48 * 1024) return PACT_OK;
@@ -87,3 +105,15 @@ pact_status check_patches(const pact_patches* pt) {
 extern "C" const char* pact_version(void) { return "pact-gb300 0.1 (sm_103a)"; }
 
 extern "C" const char* pact_last_error_message(void) { return g_msg; }
+
+using namespace pact;
+
+extern "C" pact_status pact_set_wait_limit_ns(unsigned long long ns) {
+    if (ns == 0) ns = kDefaultWaitNs;
+    if (ns < 100000ull || ns > 10000000000ull)
+        return fail(PACT_ERR_INVALID_ARG, "wait limit must be 0 (default) or in [1e5, 1e10] ns (got %llu)", ns);
+    g_wait_ns.store(ns, std::memory_order_relaxed);
+    return PACT_OK;
+}
+
+extern "C" unsigned long long pact_get_wait_limit_ns(void) { return wait_limit_ns(); }

@@ -91,10 +91,14 @@ struct McdArgs {
     int KT;                // 256-bin tiles
     const unsigned long long* tag;   // fingerprint the tables were built for
     unsigned long long want;         // fingerprint of this call's arguments
-    int* sync;                       // [KT] tile claim counters, [1] CTA-done ticket, [1] CTAs that cleared
-                                     // their share of dL_dw: zero at launch and left zero by the launch
-                                     // (they live in the tables)
-    int clear_dw;                    // streaming kernel: zero dL_dw in the kernel (instead of a memset)
+    int* sync;                       // [KT] tile claim counters and [1] CTA-done ticket of the streaming
+                                     // kernel: zero at launch and left zero by the launch (in the tables)
+    int* pstate;                     // [N] per-patch state of dL_dw row i in this launch: 0 untouched,
+                                     // 1 being zeroed, 2 zeroed; zero at launch and left zero
+    int* status;                     // [1] sticky: bit 0 set when a bounded wait gave up
+    unsigned long long limit_ns;     // bound on every wait of the launch
+    int clear_dw;                    // streaming kernel: zero dL_dw rows in the kernel (instead of a memset)
+    int dw_vec;                      // dL_dw is 16-byte aligned (rows zeroed with 16-byte stores)
     float* loss;                     // [1] or NULL (streaming kernel: summed by the last CTA)
     float* loss_pp;                  // [N] or NULL
 };
@@ -172,7 +176,9 @@ __global__ void mcd_c2d_kernel(int P, int F, double dx, Delays dl, double2* out)
 
 
 constexpr int kBins = 256;                                 // bins per CTA, one thread each
-constexpr uint64_t kCopyWaitNs = 200ull * 1000ull * 1000ull;   // bound on the bulk-copy wait
+
+// Records that a bounded wait gave up (read back by pact_mc_deconv_status).
+__device__ __forceinline__ void note_timeout(int* status) { atomicOr(status, 1); }
 
 // CTA (kt, i): bins kt*256 .. kt*256+255 of patch i, one thread per bin.  The
 // M channel rows Y_ij(k0 .. k0+255) arrive by 1-D bulk copies (TMA) into
@@ -247,7 +253,9 @@ __global__ void __launch_bounds__(kBins, 2) mcd_kernel(const McdArgs a) {
     const float2 be = cis_pi(2.f * fm * W2);       // exp(+j|k| W(ang k + pi))
 
     __syncthreads();                                // dw_s cleared
-    const bool ok = mbar_wait_bounded(&bar, 0, kCopyWaitNs) && tag_ok;
+    const bool copied = mbar_wait_bounded(&bar, 0, a.limit_ns);
+    if (!copied && tid == 0) note_timeout(a.status);
+    const bool ok = copied && tag_ok;
     const float2* ys = ytile + tid;
 
     // pass 1: S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j
@@ -387,6 +395,15 @@ constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer wa
 // chunk sums P = sum_r cos(|k| r delta) Y, Q = sum_r sin(|k| r delta) Y and
 // rotate them by the chunk's base phase, which frees registers for a third CTA
 // per SM.
+// Patch of claim c (0 <= c < N) of tile kt in the streaming kernel: the claims
+// of tile kt start at patch kt N / KT, so that CTAs working on different tiles
+// at the same time mostly work on different patches (the first claim of a
+// patch zeroes its dL_dw row; the others check that it has).
+__device__ __forceinline__ int claim_patch(int kt, int c, int N, int KT) {
+    const int i = c + (int)(((long long)kt * N) / KT);
+    return i >= N ? i - N : i;
+}
+
 template <int CPT, bool EXACT, bool FACT>
 __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kernel(const McdArgs a) {
     pdl_trigger();                                   // the ray adjoint may stage its tables meanwhile
@@ -404,7 +421,6 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     const int nc = EXACT ? CPT / kCh : (M + kCh - 1) / kCh;
     int* tile_next = a.sync;                      // [KT]
     int* done_ticket = a.sync + a.KT;             // [1]
-    int* cleared = a.sync + a.KT + 1;             // [1]
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -421,7 +437,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     const int kt_first = blockIdx.x % a.KT;
     if (tid >= kTile)
         for (int g = blockIdx.x; g < n_static; g += gridDim.x) {
-            const int i0 = g / a.KT, k0 = (g % a.KT) * kTile;
+            const int i0 = claim_patch(g % a.KT, g / a.KT, N, a.KT), k0 = (g % a.KT) * kTile;
             const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
             for (int r = lane; r < M; r += 32) l2_prefetch(a.Y + ((size_t)i0 * M + r) * a.F + k0, bytes);
             if (lane == 0) l2_prefetch(a.lut + (size_t)i0 * a.F + k0, bytes);
@@ -430,40 +446,39 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     // a dependent launch the setup above overlaps the end of the kernel before)
     pdl_wait();
     if (tid == 0) tag_ok = *a.tag == a.want;
-    if (a.clear_dw && tid < kTile) {                 // this CTA's share of dL_dw
-        const size_t tot = (size_t)N * n_t, nb = gridDim.x, b = blockIdx.x;
-        for (size_t q = tot * b / nb + tid; q < tot * (b + 1) / nb; q += kTile) a.dL_dw[q] = 0.f;
-        __threadfence();
-    }
     __syncthreads();
-    if (a.clear_dw && tid == 0) atomicAdd(cleared, 1);   // after every thread's fenced stores
 
     if (tid >= kTile) {                              // ---------------- producer warp
-        if (lane != 0) return;
-        if (!tag_ok) {                                // tables built for other arguments: no work
+        if (!tag_ok) {                                // tables built for other arguments: no work,
+            if (a.dL_dw) {                            // every output NaN
+                const size_t tot = (size_t)N * n_t, nb = gridDim.x, b = blockIdx.x;
+                for (size_t q = tot * b / nb + lane; q < tot * (b + 1) / nb; q += 32)
+                    a.dL_dw[q] = __int_as_float(0x7fc00000);
+            }
+            if (lane != 0) return;
             ring[0] = -1;
             mbar_arrive(&full[0]);
-            if (blockIdx.x == 0) {
-                a.part_loss[0] = __int_as_float(0x7fc00000);
-                if (a.dL_dw) atomicAdd(a.dL_dw, __int_as_float(0x7fc00000));
-            }
+            if (blockIdx.x == 0) a.part_loss[0] = __int_as_float(0x7fc00000);
             return;
         }
+        if (lane != 0) return;
         int kt = kt_first, tried = 0, unit = -1;
         const int KT = a.KT;
         for (int q = 0;; ++q) {
             const int s = q % kStages, lu = q / nc, c = q - lu * nc;
             if (q >= kStages &&                       // consumers released chunk q - kStages
-                !mbar_wait_bounded(&empty[s], (uint32_t)((q / kStages - 1) & 1), kCopyWaitNs))
+                !mbar_wait_bounded(&empty[s], (uint32_t)((q / kStages - 1) & 1), a.limit_ns)) {
+                note_timeout(a.status);
                 return;                               // consumers time out on the missing chunk
+            }
             if (c == 0) {                             // claim the next unit
                 const int g = (int)blockIdx.x + lu * (int)gridDim.x;
-                unit = g < n_static ? (g % KT) * N + g / KT : -1;   // the first ones are fixed
+                unit = g < n_static ? (g % KT) * N + claim_patch(g % KT, g / KT, N, KT) : -1;   // the first ones are fixed
                 while (unit < 0 && tried < KT) {
-                    // tile kt's first (n_static - kt + KT - 1) / KT units are the fixed ones
-                    const int i = (n_static - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
-                    if (i < N) {
-                        unit = kt * N + i;
+                    // tile kt's first (n_static - kt + KT - 1) / KT claims are the fixed ones
+                    const int cl = (n_static - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
+                    if (cl < N) {
+                        unit = kt * N + claim_patch(kt, cl, N, KT);
                         break;
                     }
                     kt = kt + 1 == a.KT ? 0 : kt + 1;
@@ -474,6 +489,25 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                     mbar_arrive(&full[s]);
                     return;
                 }
+                // The first claim of patch i in this launch zeroes dL_dw row i (no
+                // memset and no grid-wide wait): the row's state goes 0 -> 1 -> 2, and
+                // the consumers of every unit of patch i check for 2 before adding.
+                // The zeroing runs about one unit ahead of this CTA's own additions
+                // and far ahead of the other tiles' units of the patch.
+                if (a.clear_dw) {
+                    const int ip = unit - (unit / N) * N;
+                    if (atomicCAS(a.pstate + ip, 0, 1) == 0) {
+                        float* row = a.dL_dw + (size_t)ip * n_t;
+                        if (a.dw_vec) {
+                            float4* r4 = reinterpret_cast<float4*>(row);
+                            for (int n = 0; n < n_t / 4; ++n) r4[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        } else {
+                            for (int n = 0; n < n_t; ++n) row[n] = 0.f;
+                        }
+                        __threadfence();
+                        atomicExch(a.pstate + ip, 2);
+                    }
+                }
             }
             const int ukt = unit / N, i = unit - ukt * N;
             const int k0 = ukt * kTile;
@@ -481,8 +515,10 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             const int j0 = c * kCh, rows = min(kCh, M - j0);
             const int slot = lu % kSlots;
             if (c == 0 && lu >= kSlots &&             // consumers read the slot's previous unit
-                !mbar_wait_bounded(&slot_free[slot], (uint32_t)((lu / kSlots - 1) & 1), kCopyWaitNs))
+                !mbar_wait_bounded(&slot_free[slot], (uint32_t)((lu / kSlots - 1) & 1), a.limit_ns)) {
+                note_timeout(a.status);
                 return;
+            }
             const uint32_t wbytes = (uint32_t)n_t * 4u;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)rows + (c == 0 ? bytes + wbytes : 0u));
@@ -507,7 +543,10 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     const float sc = a.scale ? *a.scale : 1.f;
 
     // the first chunk of a unit also publishes its id
-    if (ok) ok = mbar_wait_bounded(&full[0], 0u, kCopyWaitNs);
+    if (ok) {
+        ok = mbar_wait_bounded(&full[0], 0u, a.limit_ns);
+        if (!ok) note_timeout(a.status);
+    }
     int u = ring[0];
     if (!bar_and(1, kTile, ok)) u = -1;
     for (int lu = 0; u >= 0; ++lu) {
@@ -555,7 +594,10 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         for (int c = 0; c < CPT / kCh; ++c) {
             if (EXACT || c < nc) {
                 const int q = qb + c, s = q % kStages;
-                if (c > 0 && ok) ok = mbar_wait_bounded(&full[s], (uint32_t)((q / kStages) & 1), kCopyWaitNs);
+                if (c > 0 && ok) {
+                    ok = mbar_wait_bounded(&full[s], (uint32_t)((q / kStages) & 1), a.limit_ns);
+                    if (!ok) note_timeout(a.status);
+                }
                 const float2* ys = stage + (size_t)s * kCh * kTile + tid;
                 if (FACT) {
                     float2 P = make_float2(0.f, 0.f), Q = P, Po = P, Qo = P;
@@ -671,9 +713,16 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         // wait for the next unit's first chunk (normally long landed) so that its
         // id is visible, then close unit lu with one consumer barrier
         const int qn = (lu + 1) * nc, sn = qn % kStages;
-        if (ok) ok = mbar_wait_bounded(&full[sn], (uint32_t)((qn / kStages) & 1), kCopyWaitNs);
-        if (lu == 0 && a.clear_dw && tid == 0 && ok)   // before the first additions: every CTA cleared its share
-            ok = counter_wait_bounded(cleared, (int)gridDim.x, kCopyWaitNs);
+        if (ok) {
+            ok = mbar_wait_bounded(&full[sn], (uint32_t)((qn / kStages) & 1), a.limit_ns);
+            if (!ok) note_timeout(a.status);
+        }
+        // before the additions to row i: the producer that claimed patch i first has
+        // zeroed it (normally long ago; that producer is running, so the wait ends)
+        if (a.clear_dw && a.dL_dw && tid == 0 && ok) {
+            ok = counter_wait_bounded(a.pstate + i, 2, a.limit_ns);
+            if (!ok) note_timeout(a.status);
+        }
         const int u_next = ring[(lu + 1) % kRing];
         const bool all_ok = bar_and(1, kTile, ok);
         if (a.dL_dw) {
@@ -706,7 +755,8 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     bar_and(1, kTile, true);
     if (!last_s) return;
     __threadfence();
-    for (int t = tid; t <= a.KT + 1; t += kTile) a.sync[t] = 0;   // tile counters, done ticket, clear count
+    for (int t = tid; t <= a.KT; t += kTile) a.sync[t] = 0;      // tile counters, done ticket
+    for (int t = tid; t < N; t += kTile) a.pstate[t] = 0;          // row states
     if (!a.loss && !a.loss_pp) return;
     float tot = 0.f;
     for (int i = tid; i < N; i += kTile) {
@@ -761,7 +811,8 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     p.KT = (F + kBins - 1) / kBins;
     p.KTs = (F + kTile - 1) / kTile;
     p.scratch = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
-    p.nsync = p.KTs + 2;
+    // sync block: [KTs] tile claim counters, [1] done ticket, [1] status word, [N] row states
+    p.nsync = p.KTs + 2 + pt->n;
     size_t o = 256;                                // fingerprint header
     p.t_sync = o;
     o += align_up((size_t)p.nsync * sizeof(int), 256);
@@ -890,6 +941,7 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
         if (tables_bytes < pl.tables)
             return fail(PACT_ERR_INVALID_ARG, "tables too small: %zu < %zu bytes", tables_bytes, pl.tables);
     }
+    PACT_TRY(require_sms());                       // after every host-side check
     cudaStream_t st = as_stream(stream);
     char* base = static_cast<char*>(ws);
     char* tb = tables ? const_cast<char*>(static_cast<const char*>(tables)) : base + pl.scratch;
@@ -923,11 +975,15 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.tag = reinterpret_cast<const unsigned long long*>(tb);
     a.want = fingerprint(g, pt, d, m);
     a.sync = reinterpret_cast<int*>(tb + pl.t_sync);
+    a.status = a.sync + pl.KTs + 1;
+    a.pstate = a.sync + pl.KTs + 2;
+    a.limit_ns = wait_limit_ns();
     if (!tables) PACT_TRY(build_tables(g, pt, d, m, a.fp64, pl, tb, st));
     a.loss = loss;
     a.loss_pp = loss_pp;
 
     a.clear_dw = a.stream && dL_dw && !accumulate;
+    a.dw_vec = reinterpret_cast<uintptr_t>(dL_dw) % 16 == 0 && g->n_t % 4 == 0;
     if (dL_dw && !accumulate && !a.stream &&
         cudaMemsetAsync(dL_dw, 0, (size_t)pt->n * g->n_t * sizeof(float), st) != cudaSuccess)
         return check_launch("mc_deconv_loss: clearing dL_dw");
@@ -1130,6 +1186,53 @@ extern "C" pact_status pact_psf_synth_adj(const pact_geometry* g, const pact_pat
     return run_psf(g, pt, w, d, m, 2, dL_dH, nullptr, dL_dw, accumulate, stream);
 }
 
+namespace pact {
+namespace {
+// Status word and row states inside a table block (prebuilt tables, or the
+// table part of a pact_mc_deconv_loss workspace).
+pact_status table_words(const pact_geometry* g, const pact_patches* pt, int m, void* tables, void* ws,
+                        int** status, int** pstate) {
+    PACT_TRY(check_geometry(g));
+    PACT_TRY(check_patches(pt));
+    if (m < 1 || m > PACT_MAX_CHANNELS) return fail(PACT_ERR_INVALID_ARG, "channel count out of range (got %d)", m);
+    if ((tables == nullptr) == (ws == nullptr))
+        return fail(PACT_ERR_INVALID_ARG, "pass exactly one of tables and ws");
+    const Plan pl = make_plan(g, pt, m);
+    char* t = tables ? static_cast<char*>(tables) : static_cast<char*>(ws) + pl.scratch;
+    int* sync = reinterpret_cast<int*>(t + pl.t_sync);
+    *status = sync + pl.KTs + 1;
+    *pstate = sync + pl.KTs + 2;
+    return PACT_OK;
+}
+
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+}  // namespace
+}  // namespace pact
+
+extern "C" pact_status pact_mc_deconv_status(const pact_geometry* g, const pact_patches* pt, int m, void* tables,
+                                             void* ws, void* stream) {
+    int *status = nullptr, *pstate = nullptr;
+    PACT_TRY(table_words(g, pt, m, tables, ws, &status, &pstate));
+    cudaStream_t st = as_stream(stream);
+    int host = 0;
+    if (cudaMemcpyAsync(&host, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return check_launch("mc_deconv_status");
+    if (host & 1)
+        return fail(PACT_ERR_TIMEOUT, "mc_deconv_loss: a bounded wait gave up (outputs of that call are NaN)");
+    return PACT_OK;
+}
+
+extern "C" pact_status pact_mc_deconv_inject_stall(const pact_geometry* g, const pact_patches* pt, int m,
+                                                   void* tables, void* ws, int patch, void* stream) {
+    int *status = nullptr, *pstate = nullptr;
+    PACT_TRY(table_words(g, pt, m, tables, ws, &status, &pstate));
+    if (!tables) return fail(PACT_ERR_INVALID_ARG, "inject_stall: prebuilt tables are required");
+    if (patch < 0 || patch >= pt->n) return fail(PACT_ERR_INVALID_ARG, "inject_stall: patch %d out of range", patch);
+    set_int_kernel<<<1, 1, 0, as_stream(stream)>>>(pstate + patch, 1);
+    return check_launch("mc_deconv_inject_stall");
+}
+
 // ---------------------------------------------------------------------------
 // pact_mc_deconv_loss_noalloc: the fused pass with its scratch taken from a
 // fixed device array instead of a caller-provided workspace, for callers that
@@ -1162,6 +1265,14 @@ pact_status noalloc_scratch(void** out) {
     *out = g_noalloc_ptr[dev];
     return PACT_OK;
 }
+
+// Drops the cached address of the current device.
+void forget_noalloc_scratch() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    g_noalloc_ptr[dev] = nullptr;
+}
 }  // namespace
 
 extern "C" pact_status pact_mc_deconv_loss_noalloc(const pact_geometry* g, const pact_patches* pt, const float* w,
@@ -1179,6 +1290,8 @@ extern "C" pact_status pact_mc_deconv_loss_noalloc(const pact_geometry* g, const
                     need, (size_t)PACT_NOALLOC_SCRATCH_BYTES);
     void* scratch = nullptr;
     PACT_TRY(noalloc_scratch(&scratch));
-    return run_mcd(g, pt, w, Y, d, m, eps, loss, loss_pp, Xhat, dL_dw, nullptr, 0, scratch,
-                   (size_t)PACT_NOALLOC_SCRATCH_BYTES, stream);
+    const pact_status s = run_mcd(g, pt, w, Y, d, m, eps, loss, loss_pp, Xhat, dL_dw, nullptr, 0, scratch,
+                                  (size_t)PACT_NOALLOC_SCRATCH_BYTES, stream);
+    if (s == PACT_ERR_CUDA) forget_noalloc_scratch();   // e.g. a reset context: look the address up again
+    return s;
 }

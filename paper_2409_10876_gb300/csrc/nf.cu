@@ -34,7 +34,6 @@ constexpr int kF = 64;      // Fourier features
 constexpr int kH = 128;     // hidden width
 constexpr int kL = 4;       // hidden layers
 constexpr int kRows = 128;  // nodes per CTA (one TMEM lane each)
-constexpr uint64_t kNfWaitNs = 200ull * 1000ull * 1000ull;
 
 __host__ __device__ constexpr int in_dim(int l) { return l == 1 ? kF : kH; }
 __host__ __device__ constexpr int off_w(int l) { return l == 1 ? 0 : kH * kF + kH + (l - 2) * (kH * kH + kH); }
@@ -60,6 +59,7 @@ struct NfArgs {
     const float* dL_dsos;  // backward input
     float* part;           // [cta][kPartStride] per-CTA parameter gradients (workspace)
     int* status;           // workspace word: set to 1 if a wait gave up
+    unsigned long long limit_ns;   // bound on every wait (pact_set_wait_limit_ns)
 };
 
 // Features of node `row` written as row `r` of a K-major [128 x 64] tile.
@@ -123,8 +123,8 @@ __device__ __forceinline__ void load_tile(unsigned char* tile, const unsigned ch
 
 // W_l^T as a K-major [in x out] tile (B operand of dz W): element (n = in, k = out).
 
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status) {
-    const bool ok = mbar_wait_bounded(bar, parity, kNfWaitNs);
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status, unsigned long long limit) {
+    const bool ok = mbar_wait_bounded(bar, parity, limit);
     if (!ok) atomicExch(status, 1);
     return ok;
 }
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
                           kk > 0);
             umma::commit(&bar);
         }
-        ok = wait_bar(&bar, (uint32_t)((l - 1) & 1), a.status) && ok;
+        ok = wait_bar(&bar, (uint32_t)((l - 1) & 1), a.status, a.limit_ns) && ok;
         umma::fence_after();
         for (int c0 = 0; c0 < kH; c0 += 32) {
             float v[32];
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
                               umma::idesc_bf16(128, kH) | (1u << 16), kk > 0);
             umma::commit(&bar);
         }
-        wait_bar(&bar, phase, a.status);
+        wait_bar(&bar, phase, a.status, a.limit_ns);
         phase ^= 1u;
         umma::fence_after();
         // weight-gradient row `tid` (TMEM lane = output unit)
@@ -407,6 +407,7 @@ pact_status nf_args(const pact_geometry* g, const float* params, const unsigned 
     a.t5 = reinterpret_cast<float*>(base + pl.off_t5);
     a.part = reinterpret_cast<float*>(base + pl.off_part);
     a.status = reinterpret_cast<int*>(base + pl.off_status);
+    a.limit_ns = wait_limit_ns();
     a.sos = nullptr;
     a.dL_dsos = nullptr;
     return PACT_OK;

@@ -106,6 +106,7 @@ extern "C" pact_status pact_adam_step(int n, float* param, const float* grad, fl
     if (step < 1) step = 1;
     if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f))
         return fail(PACT_ERR_INVALID_ARG, "adam: betas must be in [0, 1)");
+    PACT_TRY(require_sms());
     const float bc1 = (float)(1.0 - pow((double)beta1, step));
     const float bc2 = (float)(1.0 - pow((double)beta2, step));
     const int blocks = (n + 255) / 256 < 4 * num_sms() ? (n + 255) / 256 : 4 * num_sms();

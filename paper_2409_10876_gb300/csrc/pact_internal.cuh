@@ -17,8 +17,14 @@ namespace pact {
 pact_status fail(pact_status s, const char* fmt, ...);
 // Maps a pending launch error (cudaGetLastError) to PACT_ERR_CUDA.
 pact_status check_launch(const char* what);
-// Number of SMs of the current device (cached per device).
+// Queries (once per device) and caches the SM count of the current device;
+// PACT_ERR_CUDA if the query fails.  Every entry point that sizes a grid
+// from num_sms() calls this first.
+pact_status require_sms();
+// SM count of the current device from the cache filled by require_sms().
 int num_sms();
+// Bound on every device-side wait of a launch, in ns (pact_set_wait_limit_ns).
+unsigned long long wait_limit_ns();
 // Raises the dynamic shared-memory limit of kernel `fn` on the current device
 // to at least `bytes` (cached: the attribute call happens once per kernel and
 // device, so later launches, e.g. under CUDA-graph capture, make no calls).

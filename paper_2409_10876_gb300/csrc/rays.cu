@@ -751,6 +751,7 @@ RayArgs make_args(const pact_geometry* g, const pact_patches* pt, const Plan& pl
 pact_status launch_pixel_rays(const pact_geometry* g, const float* sos, const float* p0, int pix0, int npix,
                               float* wT, int ld, cudaStream_t st) {
     if (npix <= 0) return PACT_OK;
+    PACT_TRY(require_sms());
     size_t smem = 0;
     const int mode = fwd_mode(g, &smem);
     const void* fn = mode == kFwdPadded   ? (const void*)rays_pix_kernel<kRayLanes, true, true>
@@ -780,6 +781,7 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
                                           float* w, void* stream) {
     PACT_TRY(check_geometry(g));
     PACT_TRY(check_patches(pt));
+    PACT_TRY(require_sms());
     if (!sos || !w) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays: sos and w must not be NULL");
     const Plan pl = make_plan(g, pt);
     RayArgs a = make_args(g, pt, pl, sos);
@@ -798,6 +800,11 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
 
 extern "C" size_t pact_sos_to_delays_adj_workspace_size(const pact_geometry* g, const pact_patches* pt) {
     if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK) return 0;
+    if (require_sms() != PACT_OK) {              // no device to ask: enough for any GPU of up to 256 SMs
+        const int nrays = pt->n * g->n_t;
+        const size_t parts = (size_t)std::max(1, std::min(256, (nrays + 31) / 32));
+        return align_up(parts * g->sos_g * g->sos_g * sizeof(float), 256);
+    }
     return make_plan(g, pt).ws;
 }
 
@@ -810,6 +817,7 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
         return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_adj: sos, dL_dw and dL_dsos must not be NULL");
     if (!ws) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_adj: workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    PACT_TRY(require_sms());                       // the plan's grid (and workspace) follow the SM count
     const Plan pl = make_plan(g, pt);
     if (ws_bytes < pl.ws) return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, pl.ws);
     cudaStream_t st = as_stream(stream);

@@ -20,8 +20,17 @@ from . import build as _build
 _LIB = None
 
 
+# status codes of include/pact.h
+PACT_OK, PACT_ERR_INVALID_ARG, PACT_ERR_SHAPE, PACT_ERR_CUDA, PACT_ERR_TIMEOUT, PACT_ERR_NONFINITE, \
+    PACT_ERR_UNSUPPORTED = range(7)
+
+
 class PactError(RuntimeError):
-    pass
+    """A libpact call failed; `status` is its pact_status code (or None)."""
+
+    def __init__(self, msg, status=None):
+        super().__init__(msg)
+        self.status = status
 
 
 class Geometry(ctypes.Structure):
@@ -67,6 +76,10 @@ _SIGS = {
     "pact_mc_deconv_loss_tabled": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _SZ, _VP, _VP, _VP, _VP, _VP, _SZ, _VP],
                                    _I),
     "pact_mc_deconv_loss_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
+    "pact_mc_deconv_status": ([_GP, _PP, _I, _VP, _VP, _VP], _I),
+    "pact_mc_deconv_inject_stall": ([_GP, _PP, _I, _VP, _VP, _I, _VP], _I),
+    "pact_set_wait_limit_ns": ([ctypes.c_ulonglong], _I),
+    "pact_get_wait_limit_ns": ([], ctypes.c_ulonglong),
     "pact_tv": ([_GP, _VP, _F, _VP, _VP, _I, _VP], _I),
     "pact_adam_step": ([_I, _VP, _VP, _VP, _VP, _I, _VP, _F, _F, _F, _F, _VP, _VP], _I),
     "pact_stitch_workspace_size": ([_GP, _PP], _SZ),
@@ -120,7 +133,7 @@ def load(build_if_missing: bool = True):
 def _check(status: int, what: str):
     if status != 0:
         msg = load().pact_last_error_message().decode()
-        raise PactError(f"{what} failed (status {status}): {msg}")
+        raise PactError(f"{what} failed (status {status}): {msg}", status)
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -371,6 +384,32 @@ class McdTables:
         self.scratch_bytes = int(L.pact_mc_deconv_loss_tabled_workspace_size(pb.gp(), pb.pp(), self.m))
         _check(L.pact_mc_deconv_tables(pb.gp(), pb.pp(), dp, self.m, _ptr(self.buf), self.buf.numel(), _stream()),
                "mc_deconv_tables")
+
+
+def mc_deconv_status(pb: Problem, m: int, tables: Optional["McdTables"] = None, ws=None) -> None:
+    """Raises PactError (status PACT_ERR_TIMEOUT) if a bounded wait of a fused
+    pass using these tables (or this workspace) gave up since the last check;
+    clears the flag.  Synchronises the stream."""
+    L = load()
+    _check(L.pact_mc_deconv_status(pb.gp(), pb.pp(), int(m), _ptr(tables.buf if tables is not None else None),
+                                   _ptr(ws), _stream()), "mc_deconv_status")
+
+
+def mc_deconv_inject_stall(pb: Problem, tables: "McdTables", patch: int = 0) -> None:
+    """Test hook: the next overwriting fused pass with these tables waits on
+    dL_dw row `patch` until the wait limit and reports a timeout."""
+    L = load()
+    _check(L.pact_mc_deconv_inject_stall(pb.gp(), pb.pp(), tables.m, _ptr(tables.buf), None, int(patch),
+                                         _stream()), "mc_deconv_inject_stall")
+
+
+def set_wait_limit_ns(ns: int) -> None:
+    """Bound on every device-side wait of later launches (0 = default 200 ms)."""
+    _check(load().pact_set_wait_limit_ns(int(ns)), "set_wait_limit_ns")
+
+
+def wait_limit_ns() -> int:
+    return int(load().pact_get_wait_limit_ns())
 
 
 def mc_deconv_loss_noalloc(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=False, want_loss_pp=False,

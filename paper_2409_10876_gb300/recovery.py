@@ -12,10 +12,12 @@ model with their own parametrisations.
 """
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 import torch
 
-from . import pact
+from . import checkpoint, pact
 
 
 class SosToDelays(torch.autograd.Function):
@@ -103,6 +105,31 @@ class PGRecovery:
         for dst, src in zip((self.sos, self.adam_m, self.adam_v, self.counter), st):
             dst.copy_(src)
 
+    STATE_NAMES = ("sos", "adam_m", "adam_v", "counter")
+
+    def checkpoint(self, path: str, iteration: int, seed: int, cfg_hash: str) -> None:
+        """Saves the state a run needs to continue (parameters, Adam moments and
+        step counter), with the iteration, the seed and the configuration hash."""
+        arrays = {n: t.detach().cpu().numpy() for n, t in zip(self.STATE_NAMES, self.state())}
+        checkpoint.save(path, arrays, {"iteration": int(iteration), "seed": int(seed), "config_hash": cfg_hash,
+                                       "lr": self.lr, "lam": self.lam, "eps": self.eps, "kind": type(self).__name__})
+
+    def resume(self, path: str, cfg_hash: str) -> dict:
+        """Restores a checkpoint made by checkpoint() for the same configuration
+        hash and recovery kind; returns its metadata (iteration, seed, ...)."""
+        arrays, meta = checkpoint.load(path, cfg_hash)
+        if meta.get("kind") != type(self).__name__:
+            raise checkpoint.CheckpointError(f"{path}: a {meta.get('kind')} checkpoint, not {type(self).__name__}")
+        cur = self.state()
+        st = []
+        for n, t in zip(self.STATE_NAMES, cur):
+            a = arrays.get(n)
+            if a is None or tuple(a.shape) != tuple(t.shape) or str(a.dtype) != str(t.dtype).replace("torch.", ""):
+                raise checkpoint.CheckpointError(f"{path}: array {n} missing or of another shape/type")
+            st.append(torch.as_tensor(a))
+        self.set_state([x.to(t.device) for x, t in zip(st, cur)])
+        return meta
+
     def capture(self):
         """Captures one iteration into a CUDA graph (after one eager warm-up
         iteration whose effect on the state is undone)."""
@@ -145,6 +172,8 @@ class NFRecovery(PGRecovery):
     every iteration is nf_forward -> sos_to_delays -> fused deconvolution/loss/
     adjoint -> sos_to_delays_adj -> nf_backward -> Adam, one CUDA graph."""
 
+    STATE_NAMES = ("params", "adam_m", "adam_v", "counter")
+
     def __init__(self, pb: "pact.Problem", Y: torch.Tensor, d, eps: float, lr: float, params,
                  mask=None, betas=(0.9, 0.999), adam_eps=1e-8, v_mid: float = 1525.0, v_half: float = 125.0):
         dev = Y.device
@@ -179,6 +208,8 @@ class SirenRecovery(PGRecovery):
     parameters; every iteration is siren_forward -> sos_to_delays -> fused
     deconvolution/loss/adjoint -> sos_to_delays_adj -> siren_backward -> Adam,
     one CUDA graph."""
+
+    STATE_NAMES = ("params", "adam_m", "adam_v", "counter")
 
     def __init__(self, pb: "pact.Problem", Y: torch.Tensor, d, eps: float, lr: float, params, mask=None,
                  betas=(0.9, 0.999), adam_eps=1e-8, omega0: float = 30.0):
@@ -248,34 +279,102 @@ def channel_data_stack(pb: "pact.Problem", case: dict, device, spread: float = 0
     return pact.das_stack(pb, rf, cfg.rf_fs, cfg.rf_t0, case["d"])
 
 
+@dataclasses.dataclass
+class Recovered:
+    """Result of recover(): the SOS [G, G] and the stitched initial-pressure
+    image [H, W] (host tensors when asked for), the loss of every iteration,
+    the deconvolved patches X_hat (device) and the restarts that the loss
+    checks triggered, as (iteration, reason, new learning rate)."""
+    sos: torch.Tensor
+    hist: list
+    xhat: torch.Tensor
+    image: torch.Tensor
+    restarts: list
+
+
 def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: float, lr: float,
-            sos_init: torch.Tensor, mask: torch.Tensor, iters: int, graph: bool = True):
+            sos_init: torch.Tensor, mask: torch.Tensor, iters: int, graph: bool = True, to_host: bool = True,
+            snapshot_every: int = 50, explode: float = 1e3, lr_decay: float = 0.1, max_restarts: int = 8):
     """Public end-to-end API: upload a delay stack (host, ideally pinned), form
     the patch spectra, run `iters` recovery iterations reading the loss back
-    after each, and return (sos, loss history, X_hat).  Each iteration's loss
-    is copied to pinned host memory behind it on the stream and read while
-    the next iteration runs, so the read-back does not stall the GPU."""
+    after each, and return the recovered SOS, the stitched image (Sec. S1.4)
+    and the loss history (a Recovered).  With `to_host` the SOS and the image
+    are copied to pinned host memory before the call returns.
+
+    Each iteration's loss is copied to pinned host memory behind it on the
+    stream and read while the next iteration runs, so the read-back does not
+    stall the GPU.  Every loss is checked: a non-finite loss, or one above
+    `explode` times the first, restores the last state whose loss was good
+    (a device snapshot taken every `snapshot_every` iterations), divides the
+    learning rate by 1/lr_decay and continues from there; after
+    `max_restarts` restarts the call raises PactError."""
     dev = pb.device
     stack = stack_host.to(dev, non_blocking=True)
     Y = pact.patch_fft(pb, stack)
     rec = PGRecovery(pb, Y, d, eps, lam, lr, sos_init, mask)
     if graph:
         rec.capture()
-    hist = []
+    hist, restarts = [], []
     host = torch.empty(2, dtype=torch.float32, pin_memory=True)      # one slot per iteration in flight
     done = [torch.cuda.Event(), torch.cuda.Event()]
     stream = torch.cuda.current_stream(dev)
-    for it in range(iters):
+    good = (0, rec.state())                       # (iteration, state) whose loss was checked
+    pending = None                                # snapshot whose loss is not read yet
+    L0 = None
+    it = 0
+
+    def bad(L):
+        return not np.isfinite(L) or (L0 is not None and L > explode * abs(L0))
+
+    def restart(at, reason):
+        nonlocal it, pending
+        if len(restarts) >= max_restarts:
+            raise pact.PactError(f"recover: {reason} at iteration {at}; {max_restarts} restarts did not help",
+                                 pact.PACT_ERR_NONFINITE)
+        torch.cuda.synchronize(dev)
+        rec.lr *= lr_decay
+        rec.set_state(good[1])
+        if graph:
+            rec.capture()
+        restarts.append((at, reason, rec.lr))
+        del hist[good[0]:]
+        it, pending = good[0], None
+
+    while it < iters:
+        if it % snapshot_every == 0:
+            pending = (it, rec.state())
         rec.iterate()
         slot = it & 1
         host[slot:slot + 1].copy_(rec.out["loss"], non_blocking=True)
         done[slot].record(stream)
-        if it > 0:                               # the previous iteration's loss, copied meanwhile
+        if it > len(hist):                        # the previous iteration's loss, copied meanwhile
             done[slot ^ 1].synchronize()
-            hist.append(float(host[slot ^ 1]))
-    if iters > 0:
-        done[(iters - 1) & 1].synchronize()
-        hist.append(float(host[(iters - 1) & 1]))
+            L = float(host[slot ^ 1])
+            L0 = L if L0 is None and np.isfinite(L) else L0
+            if bad(L):
+                restart(it - 1, "non-finite loss" if not np.isfinite(L) else "exploding loss")
+                continue
+            hist.append(L)
+            if pending is not None and pending[0] == it - 1:
+                good, pending = pending, None
+        it += 1
+        if it == iters:                           # the last iteration's loss
+            done[(iters - 1) & 1].synchronize()
+            L = float(host[(iters - 1) & 1])
+            L0 = L if L0 is None and np.isfinite(L) else L0
+            if bad(L):
+                restart(iters - 1, "non-finite loss" if not np.isfinite(L) else "exploding loss")
+                continue
+            hist.append(L)
     w = pact.sos_to_delays(pb, rec.sos)
     Xh = pact.mc_deconv_loss(pb, w, Y, d, eps, want_grad=False, want_xhat=True)["Xhat"]
-    return rec.sos, hist, Xh
+    image = pact.stitch(pb, Xh)
+    sos = rec.sos
+    if to_host:
+        sos_h = torch.empty(sos.shape, dtype=sos.dtype, pin_memory=True)
+        img_h = torch.empty(image.shape, dtype=image.dtype, pin_memory=True)
+        sos_h.copy_(sos, non_blocking=True)
+        img_h.copy_(image, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        sos, image = sos_h, img_h
+    return Recovered(sos, hist, Xh, image, restarts)

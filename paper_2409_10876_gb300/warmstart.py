@@ -49,14 +49,12 @@ class StackGenerator:
                                       * np.float32(cfg.noise_sigma), device=dev) for _ in range(n_noise)]
         self.sos_cfg = inputs.config_cnn().replace(img_h=cfg.img_h, img_w=cfg.img_w, dx=cfg.dx, sos_g=cfg.sos_g,
                                                    n_t=cfg.n_t, ring_radius=cfg.ring_radius)
+        assert self.sos_cfg.sos_kind == "ellipses"
         self.ws_stitch = pact._ws(pact.load().pact_stitch_channels_workspace_size(pb.gp(), pb.pp(), cfg.m), dev)
         self.ws_pool = pact._ws(pact.load().pact_cnn_pool_workspace_size(pb.gp(), cfg.m), dev)
         self.Yc = torch.empty(pb.spectra_shape(cfg.m), dtype=torch.complex64, device=dev)
         self.stack = torch.empty((cfg.m, cfg.img_h, cfg.img_w), dtype=torch.float32, device=dev)
         self.w = torch.empty((pb.n, pb.n_t), dtype=torch.float32, device=dev)
-
-    def sos(self) -> np.ndarray:
-        return inputs.sos_phantom(self.sos_cfg, self.rng).astype(np.float32)
 
     def stack_of(self, sos: torch.Tensor, X: torch.Tensor, noise: torch.Tensor) -> torch.Tensor:
         """Delay stack [M, H, W] of Eq. 5: stitch(H(v) X) + noise."""
@@ -67,16 +65,24 @@ class StackGenerator:
         self.stack += noise
         return self.stack
 
-    def fill(self, x_out: torch.Tensor, v_out: torch.Tensor, first: int = 0) -> None:
+    def fill(self, x_out: torch.Tensor, v_out: torch.Tensor, first: int = 0, chunk: int = 512) -> None:
         """Writes samples first .. len(x_out)-1 of a dataset: x_out [S, G, G, Cp]
-        BF16, v_out [S, G, G] float32."""
-        for s in range(first, x_out.shape[0]):
-            v = torch.as_tensor(self.sos(), device=self.pb.device)
-            X = self.X[int(self.rng.integers(len(self.X)))]
-            nz = self.noise[int(self.rng.integers(len(self.noise)))]
-            st = self.stack_of(v, X, nz)
-            pact.cnn_pool_stack(self.pb, st, x_out[s], ws=self.ws_pool)
-            v_out[s].copy_(v)
+        BF16, v_out [S, G, G] float32.  The phantoms' parameters are drawn on
+        the host (seeded) and the phantoms evaluated on the device in chunks."""
+        S = x_out.shape[0]
+        dev = self.pb.device
+        for c0 in range(first, S, chunk):
+            c1 = min(S, c0 + chunk)
+            params, picks = [], []
+            for _ in range(c0, c1):
+                params.append(inputs.ellipse_params(self.sos_cfg, self.rng))
+                picks.append((int(self.rng.integers(len(self.X))), int(self.rng.integers(len(self.noise)))))
+            V = inputs.ellipse_phantoms_batch(self.sos_cfg, params, dev)
+            for k, s in enumerate(range(c0, c1)):
+                xi, ni = picks[k]
+                st = self.stack_of(V[k], self.X[xi], self.noise[ni])
+                pact.cnn_pool_stack(self.pb, st, x_out[s], ws=self.ws_pool)
+            v_out[c0:c1].copy_(V)
 
 
 def train(net: "pact.WarmStartCNN", x_all: torch.Tensor, v_all: torch.Tensor, epochs: int, lr: float = 1e-3,
@@ -169,3 +175,84 @@ def time_to_target(pb, Y, d, eps, lam, lr, sos0, mask, target: float, max_iters:
     ev1.record()
     torch.cuda.synchronize()
     return reached, ev0.elapsed_time(ev1) * 1e-3, hist, rec
+
+
+def recover_warm(pb, Y, d, eps, lam, lr, v_warm, mask, iters: int, target: float = None, ratio: int = 4,
+                 check_every: int = 5, window: int = 50, tol: float = 2e-3):
+    """Warm-started plain recovery with the plain method as judge and fallback.
+
+    Two recoveries run side by side on the GPU (each one CUDA graph per
+    iteration): W from the network's SOS `v_warm`, C from the uniform SOS of
+    the paper's method (Sec. 3.3).  The self-supervised loss (Eq. 7) judges
+    them; no ground truth is used:
+      * if the loss at the warm start is not below the loss at the uniform
+        start, W is dropped at once (fallback to C);
+      * while W improves it takes `ratio` iterations for each one of C;
+      * once W's loss improves by less than `tol` (relative) over `window`
+        of its iterations, W pauses and C takes every iteration;
+      * C stops when it too has settled above W's best loss; W is dropped if
+        C goes below its best loss.
+    `iters` bounds the iterations of both branches together.  With `target`,
+    the run stops as soon as either branch's loss is at most `target`.
+    Returns a dict: 'sos' (the better branch's SOS), 'branch', 'fallback'
+    (why W was dropped, or None), 'iters' {W, C}, 'hist' [(seconds, W its,
+    C its, W loss, C loss)], 'reached_s' (seconds to target, or None)."""
+    dev = Y.device
+    W = PGRecovery(pb, Y, d, eps, lam, lr, v_warm, mask)
+    C = PGRecovery(pb, Y, d, eps, lam, lr, torch.full_like(v_warm, pb.cfg.v_bg), mask)
+    W.capture()
+    C.capture()
+    torch.cuda.synchronize(dev)
+    its = {"W": 0, "C": 0}
+    best = {"W": float("inf"), "C": float("inf")}
+    track = {"W": [], "C": []}                    # (iterations, loss) per branch
+    state = {"W": "run", "C": "run"}              # run | paused | dropped | settled
+    fallback, hist, reached = None, [], None
+
+    def settled(b):
+        tr = track[b]
+        if not tr or tr[-1][0] < window:
+            return False
+        old = next(L for k, L in reversed(tr) if k <= tr[-1][0] - window)
+        return old - tr[-1][1] < tol * abs(old)
+
+    t0 = time.perf_counter()
+    while its["W"] + its["C"] < iters:
+        share = {"W": check_every if state["W"] == "run" else 0,
+                 "C": (max(1, check_every // ratio) if state["W"] == "run" else check_every)
+                 if state["C"] == "run" else 0}
+        if share["W"] + share["C"] == 0:
+            break
+        for b, rec in (("W", W), ("C", C)):
+            for _ in range(share[b]):
+                rec.iterate()
+            its[b] += share[b]
+        lw, lc = W.loss(), C.loss()
+        el = time.perf_counter() - t0
+        hist.append((el, its["W"], its["C"], lw, lc))
+        for b, L in (("W", lw), ("C", lc)):
+            if share[b]:
+                track[b].append((its[b], L))
+                if np.isfinite(L):
+                    best[b] = min(best[b], L)
+        if target is not None and reached is None and min(best.values()) <= target:
+            reached = el
+            break
+        if fallback is None and len(hist) == 1 and not (lw < lc):      # losses of the first iterations:
+            fallback = "the loss at the warm start is not below the loss at the uniform start"
+        if fallback is None and not np.isfinite(lw):
+            fallback = "non-finite loss on the warm branch"
+        if fallback is not None:
+            state["W"] = "dropped"
+        if state["W"] == "run" and settled("W"):
+            state["W"] = "paused"
+        if state["W"] != "dropped" and best["C"] < best["W"]:
+            state["W"] = "dropped"
+            fallback = fallback or "the cold branch went below the warm branch's best loss"
+        if state["W"] != "run" and state["C"] == "run" and settled("C") and best["C"] >= best["W"]:
+            state["C"] = "settled"
+    branch = "W" if best["W"] <= best["C"] else "C"
+    rec = W if branch == "W" else C
+    return {"sos": rec.sos.clone(), "branch": "warm" if branch == "W" else "cold", "fallback": fallback,
+            "iters": dict(its), "best": dict(best), "hist": hist, "reached_s": reached,
+            "seconds": time.perf_counter() - t0}

@@ -314,6 +314,92 @@ def test_mc_deconv_loss_channel_data_size_sampled():
     _check_mcd(cfg, Y, w, cfg.delays(), cfg.eps, idx=[0, 60, 1234, 1860, 3720])
 
 
+_REALISTIC = {}
+
+
+def _realistic_full(seed):
+    """The benchmark problem's measurement spectra, Y = H(v_true) X + N (Eq. 5
+    plus the seeded noise stack), made by the FP64 oracle."""
+    if seed not in _REALISTIC:
+        cfg = inputs.config_full()
+        case = inputs.make_case(cfg, seed)
+        Y, _, _ = O.make_measurement(O.geom(cfg), case)
+        _REALISTIC[seed] = (cfg, case, Y.numpy().astype(np.complex64))
+    return _REALISTIC[seed]
+
+
+def _near_truth(cfg, case, seed, amp):
+    """The true SOS plus a seeded perturbation of a few m/s (Gaussian ellipses
+    from the input generator, shifted to zero background)."""
+    rng = np.random.default_rng(seed)
+    bump = inputs.sos_phantom(cfg.replace(sos_lo=cfg.v_bg - amp, sos_hi=cfg.v_bg + amp), rng) - cfg.v_bg
+    return (case["sos_true"] + bump * case["mask"]).astype(np.float32)
+
+
+@pytest.mark.parametrize("point", ["truth", "near_truth", "uniform"])
+def test_mc_deconv_loss_realistic_full_size(point):
+    """All 144 patches of the benchmark launch on realistic spectra, where the
+    loss is small against the data energy (at the truth it is the noise floor):
+    the regime in which the closed-form residual energy of the streaming kernel
+    is least accurate.  Loss, per-patch loss, X_hat (1e-4) and dL/dw (2e-3)."""
+    cfg, case, Y = _realistic_full(0)
+    g = O.geom(cfg)
+    sos = {"truth": case["sos_true"], "near_truth": None, "uniform": case["sos_init"]}[point]
+    if sos is None:
+        sos = _near_truth(cfg, case, 17, 3.0)
+    w = O.wavefront_errors(g, sos.astype(np.float64), case["centres"]).numpy().astype(np.float32)
+    _check_mcd(cfg, Y, w, cfg.delays(), cfg.eps)
+    if point == "truth":
+        _check_mcd(cfg, Y, w, cfg.delays(), 1e-8)        # FP64 denominators, explicit residual
+
+
+def test_mc_deconv_loss_on_das_spectra_sampled():
+    """Spectra made the way the channel-data workload makes them -- ring channel
+    data (oracle) -> DAS (Eq. 1, oracle, at the pixels of the sampled patches)
+    -> windowed patch DFT (oracle) -- on the 1024 x 1024 / 1024-element
+    geometry with a sparse source image, for three patches; then the fused pass
+    against the oracle at the true and at the uniform SOS."""
+    from oracle import rf_oracle as R
+    cfg = inputs.config_rf()
+    case = inputs.make_case(cfg, 4)
+    g = O.geom(cfg)
+    rng = np.random.default_rng(8)
+    ip = case["ip"].copy()
+    on = np.argwhere(ip != 0)
+    keep = on[rng.choice(len(on), size=min(400, len(on)), replace=False)]
+    src = np.zeros_like(ip)
+    src[keep[:, 0], keep[:, 1]] = ip[keep[:, 0], keep[:, 1]]
+    rf = R.rf_synth(g, src, case["sos_true"], cfg.rf_fs, cfg.rf_t0, cfg.rf_ns, cfg.rf_sigma)
+    idx = [1830, 1860, 1890]                               # patches near the centre row
+    cen = case["centres"][idx]
+    P = cfg.p
+    rr, cc = np.meshgrid(np.arange(P), np.arange(P), indexing="ij")
+    stack = np.zeros((cfg.m, cfg.img_h, cfg.img_w))
+    for ca, cb in cen:
+        rows = (ca - P // 2 + rr).ravel()
+        cols = (cb - P // 2 + cc).ravel()
+        vals = R.das_at(g, rf, cfg.rf_fs, cfg.rf_t0, cfg.delays(), torch.as_tensor(rows), torch.as_tensor(cols))
+        stack[:, rows, cols] = vals.numpy()
+    Y = O.patch_spectra(g, torch.as_tensor(stack), cen).numpy().astype(np.complex64)
+    sub = cfg.replace(centres_rows=(0,), centres_cols=(0,))
+    for sos in (case["sos_true"], case["sos_init"]):
+        w = O.wavefront_errors(g, sos.astype(np.float64), cen).numpy().astype(np.float32)
+        _check_mcd_centres(sub, cen, Y, w, cfg.delays(), cfg.eps)
+
+
+def _check_mcd_centres(cfg, cen, Y, w, d, eps):
+    """_check_mcd for an explicit list of patch centres."""
+    pb = pact.Problem(cfg, DEV, centres=np.asarray(cen, np.int32))
+    out = pact.mc_deconv_loss(pb, torch.as_tensor(w, device=DEV), to_dev_c(Y), d, eps, want_grad=True,
+                              want_xhat=True, want_loss_pp=True)
+    torch.cuda.synchronize()
+    L, lp, Xh, gw = O.mc_deconv_loss(O.geom(cfg), w.astype(np.float64), torch.as_tensor(Y), cen, d, eps)
+    assert abs(float(out["loss"].item()) - float(L)) <= 1e-4 * abs(float(L))
+    assert np.linalg.norm(cpu(out["loss_pp"]) - lp.numpy()) <= 1e-4 * np.linalg.norm(lp.numpy())
+    assert rel(cpu(out["Xhat"]), Xh.numpy()) <= 1e-4
+    assert rel(cpu(out["dL_dw"]), gw.numpy()) <= 2e-3
+
+
 def test_mc_deconv_loss_adj_scale_and_accumulate():
     cfg = inputs.config_tiny(p=16, m=4)
     Y, w, d = _mcd_case(cfg, 16)
@@ -648,14 +734,47 @@ def test_recover_reads_back_every_iteration():
     rng = np.random.default_rng(4)
     stack = torch.as_tensor(rng.standard_normal((cfg.m, cfg.img_h, cfg.img_w)).astype(np.float32)).pin_memory()
     args = (case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]), torch.as_tensor(case["mask"]))
-    for iters in (1, 2, 17):
-        sos, hist, Xh = recover(pb, stack, *args, iters)
+    for iters in (1, 2, 17, 60):
+        r = recover(pb, stack, *args, iters)
         rec = PGRecovery(pb, pact.patch_fft(pb, stack.to(DEV)), *args)
         ref = rec.run(iters, record_every=1)
-        assert len(hist) == iters and np.all(np.isfinite(hist))
-        assert np.allclose(hist, ref, rtol=1e-4)          # atomics reorder FP32 sums
-        assert rel(cpu(sos), cpu(rec.sos)) <= 1e-4
-        assert Xh.shape == (cfg.n_patches, cfg.p, cfg.p // 2 + 1)
+        assert len(r.hist) == iters and np.all(np.isfinite(r.hist)) and not r.restarts
+        assert np.allclose(r.hist, ref, rtol=1e-4)          # atomics reorder FP32 sums
+        assert r.sos.device.type == "cpu" and r.image.device.type == "cpu"
+        assert rel(r.sos.numpy(), cpu(rec.sos)) <= 1e-4
+        assert r.xhat.shape == (cfg.n_patches, cfg.p, cfg.p // 2 + 1)
+        assert r.image.shape == (cfg.img_h, cfg.img_w)
+        img = pact.stitch(pb, r.xhat)
+        assert rel(r.image.numpy(), cpu(img)) <= 1e-6
+
+
+def test_recover_restores_after_a_non_finite_loss():
+    """A learning rate far too large drives the SOS to non-physical values
+    (negative speeds: the rays return NaN); the loss check restores the last
+    good state with a smaller learning rate until the losses stay finite."""
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 2)
+    pb = pact.Problem(cfg, DEV)
+    rng = np.random.default_rng(4)
+    stack = torch.as_tensor(rng.standard_normal((cfg.m, cfg.img_h, cfg.img_w)).astype(np.float32)).pin_memory()
+    r = recover(pb, stack, case["d"], cfg.eps, cfg.tv_lambda, 1e5, torch.as_tensor(case["sos_init"]),
+                torch.as_tensor(case["mask"]), 80, snapshot_every=10)
+    assert r.restarts and len(r.hist) == 80 and np.all(np.isfinite(r.hist))
+    assert r.restarts[-1][2] < 1e5
+
+
+def test_recover_raises_on_non_finite_input():
+    """NaN in the host stack: every loss is non-finite, the restarts cannot
+    help and the call raises with PACT_ERR_NONFINITE."""
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 2)
+    pb = pact.Problem(cfg, DEV)
+    stack = torch.zeros((cfg.m, cfg.img_h, cfg.img_w), dtype=torch.float32)
+    stack[0, 64, 64] = float("nan")
+    with pytest.raises(pact.PactError) as e:
+        recover(pb, stack.pin_memory(), case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
+                torch.as_tensor(case["mask"]), 20, max_restarts=2)
+    assert e.value.status == pact.PACT_ERR_NONFINITE
 
 
 def test_autograd_functions():
@@ -671,3 +790,41 @@ def test_autograd_functions():
     _, _, _, gref = O.objective(O.geom(cfg), case["sos_true"], torch.as_tensor(Y.astype(np.complex128)),
                                 case["centres"], d, 1e-3, 0.0)
     assert rel(cpu(sos.grad), 3.0 * gref.numpy()) <= 2e-3
+
+
+@pytest.mark.parametrize("kind", ["pixel_grid", "siren"])
+def test_checkpoint_resume_reproduces_the_loss_curve(tmp_path, kind):
+    """Run 20 iterations; save after 10; a fresh recovery resumed from the file
+    runs the last 10 with the same losses (the fused pass's float atomics may
+    reorder sums: 1e-5) and ends at the same parameters."""
+    from paper_2409_10876_gb300 import checkpoint
+    from paper_2409_10876_gb300.recovery import SirenRecovery
+    cfg = inputs.config_small()
+    case = inputs.make_case(cfg, 5)
+    pb = pact.Problem(cfg, DEV)
+    Y = to_dev_c(O.make_measurement(O.geom(cfg), case)[0].numpy())
+
+    def make():
+        if kind == "siren":
+            return SirenRecovery(pb, Y, case["d"], cfg.eps, inputs.SIREN_LR, inputs.siren_init(0), case["mask"])
+        return PGRecovery(pb, Y, case["d"], cfg.eps, cfg.tv_lambda, cfg.lr, torch.as_tensor(case["sos_init"]),
+                          torch.as_tensor(case["mask"]))
+
+    h = checkpoint.config_hash(cfg, kind=kind)
+    a = make()
+    a.capture()
+    first = a.run(10, record_every=1)
+    path = str(tmp_path / "ck.npz")
+    a.checkpoint(path, 10, 5, h)
+    rest = a.run(10, record_every=1)
+    b = make()
+    meta = b.resume(path, h)
+    assert meta["iteration"] == 10 and meta["seed"] == 5
+    b.capture()
+    again = b.run(10, record_every=1)
+    assert np.all(np.isfinite(first + rest))
+    assert np.allclose(again, rest, rtol=1e-5)
+    pa, pb_ = (cpu(r.params if kind == "siren" else r.sos) for r in (a, b))
+    assert rel(pb_, pa) <= 1e-5
+    with pytest.raises(checkpoint.CheckpointError):
+        make().resume(path, checkpoint.config_hash(cfg, kind="other"))

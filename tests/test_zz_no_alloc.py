@@ -57,6 +57,9 @@ def test_noalloc_rejects_problems_larger_than_its_scratch():
     assert pact.mc_deconv_loss_workspace_size(pb, cfg.m) > (16 << 20)
     lib = pact.load()
     d = (ctypes.c_float * cfg.m)(*cfg.delays())
-    st = lib.pact_mc_deconv_loss_noalloc(pb.gp(), pb.pp(), 256, 256, d, cfg.m, 1e-3, 256, None, None, None, None)
+    # real device buffers, not made-up addresses (the size check returns before any launch)
+    w, Y, loss = (torch.zeros(16, device="cuda") for _ in range(3))
+    st = lib.pact_mc_deconv_loss_noalloc(pb.gp(), pb.pp(), w.data_ptr(), Y.data_ptr(), d, cfg.m, 1e-3,
+                                         loss.data_ptr(), None, None, None, None)
     assert st == 2
     assert b"scratch" in lib.pact_last_error_message()
