@@ -369,6 +369,7 @@ constexpr int kStages = 4;      // stages in flight per CTA (about one unit of l
 constexpr int kRing = 8;        // unit ids published ahead of their consumers
 constexpr int kSlots = 3;       // per-unit lookup rows (ring coordinates, w) staged ahead
 constexpr int kStaticWaves = 1;              // units per CTA fixed in advance and prefetched (2, 3: slower)
+constexpr int kRowFailed = 1 << 30;          // flag on a published unit id: its dL_dw row was not zeroed
 constexpr int kTile = 224;                   // bins per unit of the streaming kernel, one consumer thread each
 constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two CTAs per SM)
 
@@ -490,12 +491,15 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                     return;
                 }
                 // The first claim of patch i in this launch zeroes dL_dw row i (no
-                // memset and no grid-wide wait): the row's state goes 0 -> 1 -> 2, and
-                // the consumers of every unit of patch i check for 2 before adding.
-                // The zeroing runs about one unit ahead of this CTA's own additions
-                // and far ahead of the other tiles' units of the patch.
+                // memset and no grid-wide wait): the row's state goes 0 -> 1 -> 2.
+                // Every other claim of patch i waits (bounded) until it reads 2 --
+                // normally at once, and otherwise only for a producer that is running
+                // -- and passes the result to its consumers with the unit id, so the
+                // consumers' additions are ordered after the zeroing (acquire here,
+                // then the mbarrier hand-off) without a wait of their own.
                 if (a.clear_dw) {
                     const int ip = unit - (unit / N) * N;
+                    bool row_ok = true;
                     if (atomicCAS(a.pstate + ip, 0, 1) == 0) {
                         float* row = a.dL_dw + (size_t)ip * n_t;
                         if (a.dw_vec) {
@@ -506,7 +510,11 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                         }
                         __threadfence();
                         atomicExch(a.pstate + ip, 2);
+                    } else if (!counter_wait_bounded(a.pstate + ip, 2, a.limit_ns)) {
+                        note_timeout(a.status);
+                        row_ok = false;
                     }
+                    if (!row_ok) ring[lu % kRing] = unit | kRowFailed;
                 }
             }
             const int ukt = unit / N, i = unit - ukt * N;
@@ -550,6 +558,8 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     int u = ring[0];
     if (!bar_and(1, kTile, ok)) u = -1;
     for (int lu = 0; u >= 0; ++lu) {
+        const bool row_failed = (u & kRowFailed) != 0;
+        u &= ~kRowFailed;
         const int kt = u / N, i = u - kt * N;
         const int k = kt * kTile + tid;
         const bool valid = k < a.F;
@@ -717,12 +727,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             ok = mbar_wait_bounded(&full[sn], (uint32_t)((qn / kStages) & 1), a.limit_ns);
             if (!ok) note_timeout(a.status);
         }
-        // before the additions to row i: the producer that claimed patch i first has
-        // zeroed it (normally long ago; that producer is running, so the wait ends)
-        if (a.clear_dw && a.dL_dw && tid == 0 && ok) {
-            ok = counter_wait_bounded(a.pstate + i, 2, a.limit_ns);
-            if (!ok) note_timeout(a.status);
-        }
+        if (row_failed) ok = false;                 // row i was never zeroed (the producer gave up waiting)
         const int u_next = ring[(lu + 1) % kRing];
         const bool all_ok = bar_and(1, kTile, ok);
         if (a.dL_dw) {

@@ -211,10 +211,10 @@ def recover_warm(pb, Y, d, eps, lam, lr, v_warm, mask, iters: int, target: float
 
     def settled(b):
         tr = track[b]
-        if not tr or tr[-1][0] < window:
+        if not tr:
             return False
-        old = next(L for k, L in reversed(tr) if k <= tr[-1][0] - window)
-        return old - tr[-1][1] < tol * abs(old)
+        old = next((L for k, L in reversed(tr) if k <= tr[-1][0] - window), None)
+        return old is not None and old - tr[-1][1] < tol * abs(old)
 
     t0 = time.perf_counter()
     while its["W"] + its["C"] < iters:
@@ -242,6 +242,7 @@ def recover_warm(pb, Y, d, eps, lam, lr, v_warm, mask, iters: int, target: float
             fallback = "the loss at the warm start is not below the loss at the uniform start"
         if fallback is None and not np.isfinite(lw):
             fallback = "non-finite loss on the warm branch"
+            best["W"] = float("inf")             # its state is no longer usable
         if fallback is not None:
             state["W"] = "dropped"
         if state["W"] == "run" and settled("W"):
