@@ -182,6 +182,19 @@ pact_status pact_patch_fft(const pact_geometry* g, const pact_patches* pt, const
 pact_status pact_sos_to_delays(const pact_geometry* g, const pact_patches* pt, const float* sos,
                                float* w, void* stream);
 
+/*
+ * pact_sos_to_delays that also sets clear[0 .. n_clear) to zero in the same
+ * launch (no counterpart in the paper: an iteration-fusion helper).  A
+ * recovery iteration (Sec. 3.3) passes the dL/dw buffer that the fused pass
+ * (pact_mc_deconv_loss_tabled with accumulate = 1) adds its gradient to
+ * next, which saves a clearing launch per iteration.
+ *   clear    DEVICE float [n_clear], 16-byte aligned; may not overlap w or sos
+ * Errors: those of pact_sos_to_delays; INVALID_ARG for a NULL or misaligned
+ * clear with n_clear > 0.
+ */
+pact_status pact_sos_to_delays_clear(const pact_geometry* g, const pact_patches* pt, const float* sos, float* w,
+                                     float* clear, size_t n_clear, void* stream);
+
 /* Workspace bytes of pact_sos_to_delays_adj for this geometry. */
 size_t pact_sos_to_delays_adj_workspace_size(const pact_geometry* g, const pact_patches* pt);
 
@@ -263,10 +276,10 @@ size_t pact_mc_deconv_loss_workspace_size(const pact_geometry* g, const pact_pat
  * large for shared memory).  Every device-side wait of the pass is bounded
  * (pact_set_wait_limit_ns, default 200 ms); a wait that gives up (never
  * expected) makes the loss and dL_dw NaN and sets the status word that
- * pact_mc_deconv_status reads, instead of hanging.  dL_dw is overwritten
- * without a separate clearing launch: the first CTA to claim work on patch
- * i zeroes row i, and the others check (bounded wait) that it has before
- * adding to it; no CTA waits for a CTA that may not be resident.
+ * pact_mc_deconv_status reads, instead of hanging.  No CTA of the pass ever
+ * waits for another CTA (so the result does not depend on how many of its
+ * CTAs are resident at once); dL_dw is cleared by a memset before the
+ * kernel.
  */
 pact_status pact_mc_deconv_loss(const pact_geometry* g, const pact_patches* pt, const float* w,
                                 const float* Y, const float* d, int m, float eps, float* loss,
@@ -295,6 +308,9 @@ pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* 
  * pact_mc_deconv_loss_tabled takes the arguments of pact_mc_deconv_loss plus
  * the tables, and a workspace of pact_mc_deconv_loss_tabled_workspace_size
  * bytes (the per-call scratch only); loss or dL_dw may be NULL (not both).
+ * With accumulate = 1 the gradient is added to dL_dw (no clearing launch):
+ * a recovery iteration clears dL_dw in its pact_sos_to_delays_clear call
+ * and accumulates here; with 0 dL_dw is cleared first (a memset).
  * The tables carry a fingerprint of (geometry, N, P, centres pointer, m, d);
  * a call whose arguments do not match it writes NaN to loss and dL_dw.  They
  * also hold the work-claim counters of the streaming kernel, which every call
@@ -310,7 +326,7 @@ pact_status pact_mc_deconv_tables(const pact_geometry* g, const pact_patches* pt
 pact_status pact_mc_deconv_loss_tabled(const pact_geometry* g, const pact_patches* pt, const float* w,
                                        const float* Y, const float* d, int m, float eps, const void* tables,
                                        size_t tables_bytes, float* loss, float* loss_pp, float* Xhat,
-                                       float* dL_dw, void* ws, size_t ws_bytes, void* stream);
+                                       float* dL_dw, int accumulate, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Failure detection of the fused pass (no counterpart in the paper).
@@ -320,19 +336,20 @@ pact_status pact_mc_deconv_loss_tabled(const pact_geometry* g, const pact_patche
  * rebuilt, and the word cleared, by every such call).  It synchronises the
  * stream and returns PACT_ERR_TIMEOUT if a wait of a call since the last
  * read gave up (that call's loss and dL_dw are then NaN), else PACT_OK.
- * pact_mc_deconv_inject_stall is a test hook: it marks dL_dw row `patch` of
- * the prebuilt tables as "being zeroed by another CTA" (a flag nothing
- * clears during the launch), so the next overwriting call's waits on that
- * row run into the wait limit and the call reports PACT_ERR_TIMEOUT through
- * the status word.  The call after that runs normally (every launch leaves
- * the row states at zero).  Nothing faults or hangs.
+ * pact_mc_deconv_inject_stall is a test hook: it sets a flag in the prebuilt
+ * tables (ws must be NULL) that makes the next streaming call's consumer
+ * warps withhold the release of their first pipeline stage, a release that
+ * then never comes, so the producer's wait for it runs into the wait limit,
+ * the consumers' wait for the next stage does too, and the call reports
+ * PACT_ERR_TIMEOUT through the status word with NaN outputs.  Every bulk
+ * copy the kernel issued has completed by then; nothing faults or hangs.
+ * The launch clears the flag, so the call after it runs normally.
  *   g, pt, m  the problem the tables were built for (layout only)
- *   patch     0 <= patch < N
  */
 pact_status pact_mc_deconv_status(const pact_geometry* g, const pact_patches* pt, int m, void* tables,
                                   void* ws, void* stream);
 pact_status pact_mc_deconv_inject_stall(const pact_geometry* g, const pact_patches* pt, int m, void* tables,
-                                        void* ws, int patch, void* stream);
+                                        void* ws, void* stream);
 
 /*
  * Bound on every device-side wait of the kernels launched after this call

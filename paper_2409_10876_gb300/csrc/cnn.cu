@@ -34,7 +34,9 @@ using bf16 = __nv_bfloat16;
 constexpr int kConvStages = 3;
 constexpr int kWgPix = 64;          // pixels (K) per wgrad stage
 constexpr int kWgStages = 3;
-constexpr int kWgChunk = 4096;      // pixels per wgrad CTA
+constexpr int kWgChunk = 4096;      // largest pixel chunk per wgrad CTA
+constexpr int kWgMinChunk = 512;    // smallest (a multiple of kWgPix)
+constexpr int kWgTargetCtas = 304;  // chunks x tap groups aimed for: two CTAs per SM of a 152-SM GPU
 constexpr int kNumConv = 5;
 constexpr int kHid = 64;            // channels of h3..h5 (head input)
 
@@ -179,6 +181,7 @@ struct WgradArgs {
     float* part;           // [nchunks][groups][128][Cout] partial sums
     int B, H, W, Cin, Cout;
     int taps_per_group;    // 128 / Cin
+    int chunk;             // pixels per CTA (a multiple of kWgPix)
     int* status;
     unsigned long long limit_ns;   // bound on every tensor-core wait (pact_set_wait_limit_ns)
 };
@@ -202,8 +205,8 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const WgradArgs a) {
     __shared__ uint32_t tmem_s;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int P = a.B * a.H * a.W;
-    const int p0 = blockIdx.x * kWgChunk;
-    const int npix = min(kWgChunk, P - p0);
+    const int p0 = blockIdx.x * a.chunk;
+    const int npix = min(a.chunk, P - p0);
     const int nst = (npix + kWgPix - 1) / kWgPix;
     const int group = blockIdx.y;
     const uint32_t ncols = tmem_cols(Cout);
@@ -578,10 +581,23 @@ struct CnnPlan {
     size_t total;
 };
 
+// Pixels per weight-gradient CTA: halved from kWgChunk (down to kWgMinChunk)
+// while the layer would give fewer than kWgTargetCtas CTAs, so that the
+// small-resolution layers fill the GPU (a fixed target keeps the workspace
+// size independent of the device).
+int wgrad_chunk(const Layer& y, int B) {
+    const long long P = (long long)B * y.res * y.res;
+    const int tpg = 128 / y.cin_pad, groups = (9 + tpg - 1) / tpg;
+    int chunk = kWgChunk;
+    while (chunk > kWgMinChunk && ((P + chunk - 1) / chunk) * groups < kWgTargetCtas) chunk /= 2;
+    return chunk;
+}
+
 size_t wgrad_part_elems(const Layer& y, int B) {
     const size_t P = (size_t)B * y.res * y.res;
     const int tpg = 128 / y.cin_pad, groups = (9 + tpg - 1) / tpg;
-    return ((P + kWgChunk - 1) / kWgChunk) * groups * 128 * (size_t)y.cout;
+    const size_t chunk = (size_t)wgrad_chunk(y, B);
+    return ((P + chunk - 1) / chunk) * groups * 128 * (size_t)y.cout;
 }
 
 CnnPlan make_cnn_plan(int m, int R, int B) {
@@ -677,7 +693,8 @@ pact_status launch_wgrad(const Ctx& c, const Layer& y, const bf16* x, const bf16
     a.status = c.status;
     a.limit_ns = wait_limit_ns();
     const int groups = (9 + a.taps_per_group - 1) / a.taps_per_group;
-    const int nchunks = (P + kWgChunk - 1) / kWgChunk;
+    a.chunk = wgrad_chunk(y, B);
+    const int nchunks = (P + a.chunk - 1) / a.chunk;
     const size_t smem = (size_t)kWgStages * (128 * kWgPix * 2 + (size_t)y.cout * kWgPix * 2);
     PACT_TRY(ensure_smem((const void*)wgrad_kernel, smem, "cnn: wgrad shared memory attribute"));
     wgrad_kernel<<<dim3(nchunks, groups), 128, smem, c.st>>>(a);

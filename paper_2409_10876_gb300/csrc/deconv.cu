@@ -93,12 +93,12 @@ struct McdArgs {
     unsigned long long want;         // fingerprint of this call's arguments
     int* sync;                       // [KT] tile claim counters and [1] CTA-done ticket of the streaming
                                      // kernel: zero at launch and left zero by the launch (in the tables)
-    int* pstate;                     // [N] per-patch state of dL_dw row i in this launch: 0 untouched,
-                                     // 1 being zeroed, 2 zeroed; zero at launch and left zero
     int* status;                     // [1] sticky: bit 0 set when a bounded wait gave up
+    int* stall;                      // [1] test hook: nonzero makes every producer of this launch wait for a
+                                     // stage release that never comes (its wait expires); the launch clears it
+    int* failed;                     // [1] a wait of this launch gave up (the last CTA then writes NaN
+                                     // outputs and clears it)
     unsigned long long limit_ns;     // bound on every wait of the launch
-    int clear_dw;                    // streaming kernel: zero dL_dw rows in the kernel (instead of a memset)
-    int dw_vec;                      // dL_dw is 16-byte aligned (rows zeroed with 16-byte stores)
     float* loss;                     // [1] or NULL (streaming kernel: summed by the last CTA)
     float* loss_pp;                  // [N] or NULL
 };
@@ -369,7 +369,6 @@ constexpr int kStages = 4;      // stages in flight per CTA (about one unit of l
 constexpr int kRing = 8;        // unit ids published ahead of their consumers
 constexpr int kSlots = 3;       // per-unit lookup rows (ring coordinates, w) staged ahead
 constexpr int kStaticWaves = 1;              // units per CTA fixed in advance and prefetched (2, 3: slower)
-constexpr int kRowFailed = 1 << 30;          // flag on a published unit id: its dL_dw row was not zeroed
 constexpr int kTile = 224;                   // bins per unit of the streaming kernel, one consumer thread each
 constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two CTAs per SM)
 
@@ -396,15 +395,6 @@ constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer wa
 // chunk sums P = sum_r cos(|k| r delta) Y, Q = sum_r sin(|k| r delta) Y and
 // rotate them by the chunk's base phase, which frees registers for a third CTA
 // per SM.
-// Patch of claim c (0 <= c < N) of tile kt in the streaming kernel: the claims
-// of tile kt start at patch kt N / KT, so that CTAs working on different tiles
-// at the same time mostly work on different patches (the first claim of a
-// patch zeroes its dL_dw row; the others check that it has).
-__device__ __forceinline__ int claim_patch(int kt, int c, int N, int KT) {
-    const int i = c + (int)(((long long)kt * N) / KT);
-    return i >= N ? i - N : i;
-}
-
 template <int CPT, bool EXACT, bool FACT>
 __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kernel(const McdArgs a) {
     pdl_trigger();                                   // the ray adjoint may stage its tables meanwhile
@@ -417,11 +407,15 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], slot_free[kSlots];
     __shared__ float lsum_s[2][kTile / 32];
     __shared__ int ring[kRing];
-    __shared__ int tag_ok;
+    __shared__ int tag_ok, stall_s;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nc = EXACT ? CPT / kCh : (M + kCh - 1) / kCh;
     int* tile_next = a.sync;                      // [KT]
     int* done_ticket = a.sync + a.KT;             // [1]
+    auto timed_out = [&a]() {                     // a bounded wait gave up
+        note_timeout(a.status);
+        atomicExch(a.failed, 1);
+    };
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -438,7 +432,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     const int kt_first = blockIdx.x % a.KT;
     if (tid >= kTile)
         for (int g = blockIdx.x; g < n_static; g += gridDim.x) {
-            const int i0 = claim_patch(g % a.KT, g / a.KT, N, a.KT), k0 = (g % a.KT) * kTile;
+            const int i0 = g / a.KT, k0 = (g % a.KT) * kTile;
             const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
             for (int r = lane; r < M; r += 32) l2_prefetch(a.Y + ((size_t)i0 * M + r) * a.F + k0, bytes);
             if (lane == 0) l2_prefetch(a.lut + (size_t)i0 * a.F + k0, bytes);
@@ -446,7 +440,10 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     // everything below reads or writes what earlier kernels produce or read (under
     // a dependent launch the setup above overlaps the end of the kernel before)
     pdl_wait();
-    if (tid == 0) tag_ok = *a.tag == a.want;
+    if (tid == 0) {
+        tag_ok = *a.tag == a.want;
+        stall_s = *a.stall;
+    }
     __syncthreads();
 
     if (tid >= kTile) {                              // ---------------- producer warp
@@ -463,23 +460,27 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             return;
         }
         if (lane != 0) return;
+        if (stall_s) {                                // test hook: a release that never comes; no copy issued
+            if (!mbar_wait_bounded(&empty[0], 0u, a.limit_ns)) timed_out();
+            return;
+        }
         int kt = kt_first, tried = 0, unit = -1;
         const int KT = a.KT;
         for (int q = 0;; ++q) {
             const int s = q % kStages, lu = q / nc, c = q - lu * nc;
             if (q >= kStages &&                       // consumers released chunk q - kStages
                 !mbar_wait_bounded(&empty[s], (uint32_t)((q / kStages - 1) & 1), a.limit_ns)) {
-                note_timeout(a.status);
+                timed_out();
                 return;                               // consumers time out on the missing chunk
             }
             if (c == 0) {                             // claim the next unit
                 const int g = (int)blockIdx.x + lu * (int)gridDim.x;
-                unit = g < n_static ? (g % KT) * N + claim_patch(g % KT, g / KT, N, KT) : -1;   // the first ones are fixed
+                unit = g < n_static ? (g % KT) * N + g / KT : -1;   // the first ones are fixed
                 while (unit < 0 && tried < KT) {
                     // tile kt's first (n_static - kt + KT - 1) / KT claims are the fixed ones
                     const int cl = (n_static - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
                     if (cl < N) {
-                        unit = kt * N + claim_patch(kt, cl, N, KT);
+                        unit = kt * N + cl;
                         break;
                     }
                     kt = kt + 1 == a.KT ? 0 : kt + 1;
@@ -490,32 +491,6 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                     mbar_arrive(&full[s]);
                     return;
                 }
-                // The first claim of patch i in this launch zeroes dL_dw row i (no
-                // memset and no grid-wide wait): the row's state goes 0 -> 1 -> 2.
-                // Every other claim of patch i waits (bounded) until it reads 2 --
-                // normally at once, and otherwise only for a producer that is running
-                // -- and passes the result to its consumers with the unit id, so the
-                // consumers' additions are ordered after the zeroing (acquire here,
-                // then the mbarrier hand-off) without a wait of their own.
-                if (a.clear_dw) {
-                    const int ip = unit - (unit / N) * N;
-                    bool row_ok = true;
-                    if (atomicCAS(a.pstate + ip, 0, 1) == 0) {
-                        float* row = a.dL_dw + (size_t)ip * n_t;
-                        if (a.dw_vec) {
-                            float4* r4 = reinterpret_cast<float4*>(row);
-                            for (int n = 0; n < n_t / 4; ++n) r4[n] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        } else {
-                            for (int n = 0; n < n_t; ++n) row[n] = 0.f;
-                        }
-                        __threadfence();
-                        atomicExch(a.pstate + ip, 2);
-                    } else if (!counter_wait_bounded(a.pstate + ip, 2, a.limit_ns)) {
-                        note_timeout(a.status);
-                        row_ok = false;
-                    }
-                    if (!row_ok) ring[lu % kRing] = unit | kRowFailed;
-                }
             }
             const int ukt = unit / N, i = unit - ukt * N;
             const int k0 = ukt * kTile;
@@ -524,7 +499,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             const int slot = lu % kSlots;
             if (c == 0 && lu >= kSlots &&             // consumers read the slot's previous unit
                 !mbar_wait_bounded(&slot_free[slot], (uint32_t)((lu / kSlots - 1) & 1), a.limit_ns)) {
-                note_timeout(a.status);
+                timed_out();
                 return;
             }
             const uint32_t wbytes = (uint32_t)n_t * 4u;
@@ -553,13 +528,11 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     // the first chunk of a unit also publishes its id
     if (ok) {
         ok = mbar_wait_bounded(&full[0], 0u, a.limit_ns);
-        if (!ok) note_timeout(a.status);
+        if (!ok) timed_out();
     }
     int u = ring[0];
     if (!bar_and(1, kTile, ok)) u = -1;
     for (int lu = 0; u >= 0; ++lu) {
-        const bool row_failed = (u & kRowFailed) != 0;
-        u &= ~kRowFailed;
         const int kt = u / N, i = u - kt * N;
         const int k = kt * kTile + tid;
         const bool valid = k < a.F;
@@ -606,7 +579,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                 const int q = qb + c, s = q % kStages;
                 if (c > 0 && ok) {
                     ok = mbar_wait_bounded(&full[s], (uint32_t)((q / kStages) & 1), a.limit_ns);
-                    if (!ok) note_timeout(a.status);
+                    if (!ok) timed_out();
                 }
                 const float2* ys = stage + (size_t)s * kCh * kTile + tid;
                 if (FACT) {
@@ -725,9 +698,8 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         const int qn = (lu + 1) * nc, sn = qn % kStages;
         if (ok) {
             ok = mbar_wait_bounded(&full[sn], (uint32_t)((qn / kStages) & 1), a.limit_ns);
-            if (!ok) note_timeout(a.status);
+            if (!ok) timed_out();
         }
-        if (row_failed) ok = false;                 // row i was never zeroed (the producer gave up waiting)
         const int u_next = ring[(lu + 1) % kRing];
         const bool all_ok = bar_and(1, kTile, ok);
         if (a.dL_dw) {
@@ -761,7 +733,20 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     if (!last_s) return;
     __threadfence();
     for (int t = tid; t <= a.KT; t += kTile) a.sync[t] = 0;      // tile counters, done ticket
-    for (int t = tid; t < N; t += kTile) a.pstate[t] = 0;          // row states
+    __shared__ int failed_s;
+    if (tid == 0) {
+        *a.stall = 0;                                              // the test hook acts once
+        failed_s = __ldcg(a.failed);
+        *a.failed = 0;
+        if (failed_s && a.dL_dw) atomicAdd(a.dL_dw, __int_as_float(0x7fc00000));
+    }
+    bar_and(1, kTile, true);
+    if (failed_s) {                                                // a wait gave up: no partial is trusted
+        for (int i = tid; i < N; i += kTile)
+            if (a.loss_pp) a.loss_pp[i] = __int_as_float(0x7fc00000);
+        if (tid == 0 && a.loss) a.loss[0] = __int_as_float(0x7fc00000);
+        return;
+    }
     if (!a.loss && !a.loss_pp) return;
     float tot = 0.f;
     for (int i = tid; i < N; i += kTile) {
@@ -816,8 +801,9 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     p.KT = (F + kBins - 1) / kBins;
     p.KTs = (F + kTile - 1) / kTile;
     p.scratch = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
-    // sync block: [KTs] tile claim counters, [1] done ticket, [1] status word, [N] row states
-    p.nsync = p.KTs + 2 + pt->n;
+    // sync block: [KTs] tile claim counters, [1] done ticket, [1] status word, [1] stall flag (test
+    // hook), [1] launch-failed flag
+    p.nsync = p.KTs + 4;
     size_t o = 256;                                // fingerprint header
     p.t_sync = o;
     o += align_up((size_t)p.nsync * sizeof(int), 256);
@@ -981,15 +967,14 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.want = fingerprint(g, pt, d, m);
     a.sync = reinterpret_cast<int*>(tb + pl.t_sync);
     a.status = a.sync + pl.KTs + 1;
-    a.pstate = a.sync + pl.KTs + 2;
+    a.stall = a.sync + pl.KTs + 2;
+    a.failed = a.sync + pl.KTs + 3;
     a.limit_ns = wait_limit_ns();
     if (!tables) PACT_TRY(build_tables(g, pt, d, m, a.fp64, pl, tb, st));
     a.loss = loss;
     a.loss_pp = loss_pp;
 
-    a.clear_dw = a.stream && dL_dw && !accumulate;
-    a.dw_vec = reinterpret_cast<uintptr_t>(dL_dw) % 16 == 0 && g->n_t % 4 == 0;
-    if (dL_dw && !accumulate && !a.stream &&
+    if (dL_dw && !accumulate &&
         cudaMemsetAsync(dL_dw, 0, (size_t)pt->n * g->n_t * sizeof(float), st) != cudaSuccess)
         return check_launch("mc_deconv_loss: clearing dL_dw");
     pact_status s;
@@ -1166,12 +1151,13 @@ extern "C" pact_status pact_mc_deconv_tables(const pact_geometry* g, const pact_
 extern "C" pact_status pact_mc_deconv_loss_tabled(const pact_geometry* g, const pact_patches* pt, const float* w,
                                                   const float* Y, const float* d, int m, float eps,
                                                   const void* tables, size_t tables_bytes, float* loss,
-                                                  float* loss_pp, float* Xhat, float* dL_dw, void* ws,
-                                                  size_t ws_bytes, void* stream) {
+                                                  float* loss_pp, float* Xhat, float* dL_dw, int accumulate,
+                                                  void* ws, size_t ws_bytes, void* stream) {
     if (!tables) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss_tabled: tables is NULL");
     if (!loss && !dL_dw) return fail(PACT_ERR_INVALID_ARG, "mc_deconv_loss_tabled: loss and dL_dw are both NULL");
-    return run_mcd(g, pt, w, Y, d, m, eps, loss, loss_pp, Xhat, dL_dw, nullptr, 0, ws, ws_bytes, stream, tables,
-                   tables_bytes);
+    if (accumulate != 0 && accumulate != 1) return fail(PACT_ERR_INVALID_ARG, "accumulate must be 0 or 1");
+    return run_mcd(g, pt, w, Y, d, m, eps, loss, loss_pp, Xhat, dL_dw, nullptr, accumulate, ws, ws_bytes, stream,
+                   tables, tables_bytes);
 }
 
 extern "C" pact_status pact_psf_synth(const pact_geometry* g, const pact_patches* pt, const float* w,
@@ -1196,7 +1182,7 @@ namespace {
 // Status word and row states inside a table block (prebuilt tables, or the
 // table part of a pact_mc_deconv_loss workspace).
 pact_status table_words(const pact_geometry* g, const pact_patches* pt, int m, void* tables, void* ws,
-                        int** status, int** pstate) {
+                        int** status, int** stall) {
     PACT_TRY(check_geometry(g));
     PACT_TRY(check_patches(pt));
     if (m < 1 || m > PACT_MAX_CHANNELS) return fail(PACT_ERR_INVALID_ARG, "channel count out of range (got %d)", m);
@@ -1206,7 +1192,7 @@ pact_status table_words(const pact_geometry* g, const pact_patches* pt, int m, v
     char* t = tables ? static_cast<char*>(tables) : static_cast<char*>(ws) + pl.scratch;
     int* sync = reinterpret_cast<int*>(t + pl.t_sync);
     *status = sync + pl.KTs + 1;
-    *pstate = sync + pl.KTs + 2;
+    *stall = sync + pl.KTs + 2;
     return PACT_OK;
 }
 
@@ -1216,8 +1202,8 @@ __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
 extern "C" pact_status pact_mc_deconv_status(const pact_geometry* g, const pact_patches* pt, int m, void* tables,
                                              void* ws, void* stream) {
-    int *status = nullptr, *pstate = nullptr;
-    PACT_TRY(table_words(g, pt, m, tables, ws, &status, &pstate));
+    int *status = nullptr, *stall = nullptr;
+    PACT_TRY(table_words(g, pt, m, tables, ws, &status, &stall));
     cudaStream_t st = as_stream(stream);
     int host = 0;
     if (cudaMemcpyAsync(&host, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1229,12 +1215,11 @@ extern "C" pact_status pact_mc_deconv_status(const pact_geometry* g, const pact_
 }
 
 extern "C" pact_status pact_mc_deconv_inject_stall(const pact_geometry* g, const pact_patches* pt, int m,
-                                                   void* tables, void* ws, int patch, void* stream) {
-    int *status = nullptr, *pstate = nullptr;
-    PACT_TRY(table_words(g, pt, m, tables, ws, &status, &pstate));
+                                                   void* tables, void* ws, void* stream) {
+    int *status = nullptr, *stall = nullptr;
+    PACT_TRY(table_words(g, pt, m, tables, ws, &status, &stall));
     if (!tables) return fail(PACT_ERR_INVALID_ARG, "inject_stall: prebuilt tables are required");
-    if (patch < 0 || patch >= pt->n) return fail(PACT_ERR_INVALID_ARG, "inject_stall: patch %d out of range", patch);
-    set_int_kernel<<<1, 1, 0, as_stream(stream)>>>(pstate + patch, 1);
+    set_int_kernel<<<1, 1, 0, as_stream(stream)>>>(stall, 1);
     return check_launch("mc_deconv_inject_stall");
 }
 

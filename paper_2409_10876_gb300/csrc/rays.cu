@@ -100,6 +100,8 @@ struct RayArgs {
     float* part;          // adjoint partial grids [gridDim.x][G*G] (smem variant)
     float* out;           // adjoint output (global-atomic variant)
     int use_smem;
+    float4* clear;        // forward: [n_clear4] set to zero in the same launch (or NULL)
+    size_t n_clear4;
 };
 
 // Shared-memory grid pitch: one extra column so that nodes of one grid column
@@ -232,6 +234,8 @@ __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
             load_excess(dv_s, a.sos, G, pitch, a.g.v0);
         __syncthreads();
     }
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_clear4; q += (size_t)gridDim.x * blockDim.x)
+        a.clear[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     constexpr int RB = 32 / L;
     const int n_t = a.g.n_t;
     const int lane = threadIdx.x & 31, sub = lane % L, grp = lane / L;
@@ -777,15 +781,19 @@ pact_status launch_pixel_rays(const pact_geometry* g, const float* sos, const fl
 
 using namespace pact;
 
-extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_patches* pt, const float* sos,
-                                          float* w, void* stream) {
+static pact_status sos_to_delays(const pact_geometry* g, const pact_patches* pt, const float* sos, float* w,
+                                 float* clear, size_t n_clear, void* stream) {
     PACT_TRY(check_geometry(g));
     PACT_TRY(check_patches(pt));
-    PACT_TRY(require_sms());
     if (!sos || !w) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays: sos and w must not be NULL");
+    if (n_clear && (!clear || reinterpret_cast<uintptr_t>(clear) % 16 || n_clear % 4))
+        return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_clear: clear must be 16-byte aligned, n_clear a multiple of 4");
+    PACT_TRY(require_sms());
     const Plan pl = make_plan(g, pt);
     RayArgs a = make_args(g, pt, pl, sos);
     a.w = w;
+    a.clear = reinterpret_cast<float4*>(clear);
+    a.n_clear4 = n_clear / 4;
     cudaStream_t st = as_stream(stream);
     if (pl.smem_fwd)
         PACT_TRY(ensure_smem(fwd_fn(pl.fwd_mode), pl.smem_fwd, "sos_to_delays: shared memory attribute"));
@@ -796,6 +804,16 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
     else
         rays_fwd_kernel<kRayLanes, false, false><<<pl.nb_fwd, 512, 0, st>>>(a);
     return check_launch("sos_to_delays kernel");
+}
+
+extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_patches* pt, const float* sos,
+                                          float* w, void* stream) {
+    return sos_to_delays(g, pt, sos, w, nullptr, 0, stream);
+}
+
+extern "C" pact_status pact_sos_to_delays_clear(const pact_geometry* g, const pact_patches* pt, const float* sos,
+                                                float* w, float* clear, size_t n_clear, void* stream) {
+    return sos_to_delays(g, pt, sos, w, clear, n_clear, stream);
 }
 
 extern "C" size_t pact_sos_to_delays_adj_workspace_size(const pact_geometry* g, const pact_patches* pt) {

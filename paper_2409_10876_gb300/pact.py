@@ -62,6 +62,7 @@ _SIGS = {
     "pact_rf_synth": ([_GP, _VP, _VP, ctypes.POINTER(RfParams), _VP, _VP, _SZ, _VP], _I),
     "pact_patch_fft": ([_GP, _PP, _VP, _I, _VP, _VP], _I),
     "pact_sos_to_delays": ([_GP, _PP, _VP, _VP, _VP], _I),
+    "pact_sos_to_delays_clear": ([_GP, _PP, _VP, _VP, _VP, _SZ, _VP], _I),
     "pact_sos_to_delays_adj_workspace_size": ([_GP, _PP], _SZ),
     "pact_sos_to_delays_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_psf_synth": ([_GP, _PP, _VP, _VP, _I, _VP, _VP], _I),
@@ -73,11 +74,11 @@ _SIGS = {
     "pact_mc_deconv_tables_size": ([_GP, _PP, _I], _SZ),
     "pact_mc_deconv_loss_tabled_workspace_size": ([_GP, _PP, _I], _SZ),
     "pact_mc_deconv_tables": ([_GP, _PP, _VP, _I, _VP, _SZ, _VP], _I),
-    "pact_mc_deconv_loss_tabled": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _SZ, _VP, _VP, _VP, _VP, _VP, _SZ, _VP],
-                                   _I),
+    "pact_mc_deconv_loss_tabled": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _SZ, _VP, _VP, _VP, _VP, _I, _VP, _SZ,
+                                    _VP], _I),
     "pact_mc_deconv_loss_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _F, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_mc_deconv_status": ([_GP, _PP, _I, _VP, _VP, _VP], _I),
-    "pact_mc_deconv_inject_stall": ([_GP, _PP, _I, _VP, _VP, _I, _VP], _I),
+    "pact_mc_deconv_inject_stall": ([_GP, _PP, _I, _VP, _VP, _VP], _I),
     "pact_set_wait_limit_ns": ([ctypes.c_ulonglong], _I),
     "pact_get_wait_limit_ns": ([], ctypes.c_ulonglong),
     "pact_tv": ([_GP, _VP, _F, _VP, _VP, _I, _VP], _I),
@@ -252,14 +253,21 @@ def patch_fft(pb: Problem, stack, Y=None):
     return Y
 
 
-def sos_to_delays(pb: Problem, sos, w=None):
-    """Eq. 3: wavefront errors w [N, N_t] from the SOS grid [G, G]."""
+def sos_to_delays(pb: Problem, sos, w=None, clear=None):
+    """Eq. 3: wavefront errors w [N, N_t] from the SOS grid [G, G].  `clear`
+    (a float32 CUDA tensor, e.g. the dL/dw buffer a following accumulating
+    fused pass adds to) is set to zero in the same launch."""
     L = load()
     sos = _dev(sos, "sos", torch.float32, (pb.g, pb.g))
     if w is None:
         w = _empty((pb.n, pb.n_t), torch.float32, sos.device)
     _dev(w, "w", torch.float32, (pb.n, pb.n_t))
-    _check(L.pact_sos_to_delays(pb.gp(), pb.pp(), _ptr(sos), _ptr(w), _stream()), "sos_to_delays")
+    if clear is None:
+        _check(L.pact_sos_to_delays(pb.gp(), pb.pp(), _ptr(sos), _ptr(w), _stream()), "sos_to_delays")
+    else:
+        clear = _dev(clear, "clear", torch.float32)
+        _check(L.pact_sos_to_delays_clear(pb.gp(), pb.pp(), _ptr(sos), _ptr(w), _ptr(clear), clear.numel(),
+                                          _stream()), "sos_to_delays_clear")
     return w
 
 
@@ -328,7 +336,7 @@ def mc_deconv_loss_workspace_size(pb: Problem, m: int) -> int:
 
 
 def mc_deconv_loss(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=False, want_loss_pp=False,
-                   out=None, ws=None, tables: "McdTables" = None):
+                   out=None, ws=None, tables: "McdTables" = None, accumulate=False):
     """Eq. 6-7 fused (+ adjoint when want_grad).  Returns a dict with
     'loss' [1], and 'dL_dw' [N, N_t], 'Xhat' [N, P, P/2+1], 'loss_pp' [N] as asked.
     `out` may hold preallocated tensors under the same keys; `tables` (built
@@ -358,9 +366,11 @@ def mc_deconv_loss(pb: Problem, w, Y, d, eps: float, want_grad=True, want_xhat=F
                                             tables.buf.numel(), _ptr(out["loss"]),
                                             _ptr(out.get("loss_pp") if want_loss_pp else None),
                                             _ptr(out.get("Xhat") if want_xhat else None),
-                                            _ptr(out.get("dL_dw") if want_grad else None), _ptr(ws), ws.numel(),
-                                            _stream()), "mc_deconv_loss_tabled")
+                                            _ptr(out.get("dL_dw") if want_grad else None), int(accumulate),
+                                            _ptr(ws), ws.numel(), _stream()), "mc_deconv_loss_tabled")
         return out
+    if accumulate:
+        raise PactError("accumulate needs prebuilt tables (pact_mc_deconv_loss_tabled)")
     if ws is None:
         ws = _ws(mc_deconv_loss_workspace_size(pb, m), dev)
     _check(L.pact_mc_deconv_loss(pb.gp(), pb.pp(), _ptr(w), _ptr(Y), dp, m, float(eps), _ptr(out["loss"]),
@@ -395,12 +405,12 @@ def mc_deconv_status(pb: Problem, m: int, tables: Optional["McdTables"] = None, 
                                    _ptr(ws), _stream()), "mc_deconv_status")
 
 
-def mc_deconv_inject_stall(pb: Problem, tables: "McdTables", patch: int = 0) -> None:
-    """Test hook: the next overwriting fused pass with these tables waits on
-    dL_dw row `patch` until the wait limit and reports a timeout."""
+def mc_deconv_inject_stall(pb: Problem, tables: "McdTables") -> None:
+    """Test hook: the next streaming fused pass with these tables withholds a
+    pipeline-stage release, runs into the wait limit and reports a timeout."""
     L = load()
-    _check(L.pact_mc_deconv_inject_stall(pb.gp(), pb.pp(), tables.m, _ptr(tables.buf), None, int(patch),
-                                         _stream()), "mc_deconv_inject_stall")
+    _check(L.pact_mc_deconv_inject_stall(pb.gp(), pb.pp(), tables.m, _ptr(tables.buf), None, _stream()),
+           "mc_deconv_inject_stall")
 
 
 def set_wait_limit_ns(ns: int) -> None:

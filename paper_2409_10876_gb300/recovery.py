@@ -85,10 +85,10 @@ class PGRecovery:
         pb = self.pb
         mark = mark or (lambda k: None)
         mark(0)
-        pact.sos_to_delays(pb, self.sos, self.w)
+        pact.sos_to_delays(pb, self.sos, self.w, clear=self.out["dL_dw"])
         mark(1)
         pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
-                            tables=self.tables)
+                            tables=self.tables, accumulate=True)
         mark(2)
         pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
         mark(4)
@@ -187,9 +187,9 @@ class NFRecovery(PGRecovery):
     def step(self):
         pb = self.pb
         pact.nf_forward(self.nf, self.sos)
-        pact.sos_to_delays(pb, self.sos, self.w)
+        pact.sos_to_delays(pb, self.sos, self.w, clear=self.out["dL_dw"])
         pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
-                            tables=self.tables)
+                            tables=self.tables, accumulate=True)
         pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
         pact.nf_backward(self.nf, self.grad, self.gparams)
         pact.adam_step(self.params, self.gparams, self.adam_m, self.adam_v, 1, self.lr, self.betas[0],
@@ -223,9 +223,9 @@ class SirenRecovery(PGRecovery):
     def step(self):
         pb = self.pb
         pact.siren_forward(self.sf, self.sos)
-        pact.sos_to_delays(pb, self.sos, self.w)
+        pact.sos_to_delays(pb, self.sos, self.w, clear=self.out["dL_dw"])
         pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
-                            tables=self.tables)
+                            tables=self.tables, accumulate=True)
         pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
         pact.siren_backward(self.sf, self.grad, self.gparams)
         pact.adam_step(self.params, self.gparams, self.adam_m, self.adam_v, 1, self.lr, self.betas[0],

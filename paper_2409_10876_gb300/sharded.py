@@ -102,9 +102,9 @@ class LibpactShard:
 
     def local(self, sos):
         pb = self.pb
-        pact.sos_to_delays(pb, sos, self.w)
+        pact.sos_to_delays(pb, sos, self.w, clear=self.out["dL_dw"])
         pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
-                            tables=self.tables)
+                            tables=self.tables, accumulate=True)
         pact.sos_to_delays_adj(pb, sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
         return self.out["loss"], self.grad
 

@@ -1,11 +1,12 @@
 """Failure detection of the fused pass on the GPU, without faulting it.
 
 Every device-side wait of the fused deconvolution pass is bounded by the
-library's wait limit.  The test hook pact_mc_deconv_inject_stall marks one
-dL/dw row as "being zeroed by another CTA", a flag that nothing clears during
-the launch, so the CTAs that want to add to that row wait until the limit,
-give up, poison the outputs with NaN and record a timeout in the status word;
-the kernel returns, the context stays usable and the next call is normal.
+library's wait limit.  The test hook pact_mc_deconv_inject_stall sets a flag
+in the prebuilt tables that makes the consumer warps withhold the release of
+their first pipeline stage: the producer's wait for that release runs into
+the limit, the consumers' wait for the next stage does too, the outputs turn
+NaN and a timeout is recorded in the status word; the kernel returns, the
+context stays usable and the next call is normal.
 
 The second test runs the pass while a side stream keeps the SMs busy: no CTA
 of the pass waits for another CTA that may not be resident, so the result does
@@ -50,18 +51,18 @@ def test_bounded_wait_expires_reports_timeout_and_recovers():
     pact.set_wait_limit_ns(2_000_000)                               # 2 ms
     try:
         assert pact.wait_limit_ns() == 2_000_000
-        pact.mc_deconv_inject_stall(pb, tables, patch=0)
+        pact.mc_deconv_inject_stall(pb, tables)
         bad = pact.mc_deconv_loss(pb, w, Y, d, cfg.eps, tables=tables)
         torch.cuda.synchronize()
         with pytest.raises(pact.PactError, match="status 4"):
             pact.mc_deconv_status(pb, cfg.m, tables=tables)
         assert not np.isfinite(float(bad["loss"].item()))
-        assert np.isnan(bad["dL_dw"][0].cpu().numpy()).any()
+        assert np.isnan(bad["dL_dw"].cpu().numpy()).any()
     finally:
         pact.set_wait_limit_ns(0)
     assert pact.wait_limit_ns() == 200_000_000
 
-    # the status word was cleared by the read, the row states by the launch
+    # the status word was cleared by the read, the stall flag by the launch
     pact.mc_deconv_status(pb, cfg.m, tables=tables)
     again = pact.mc_deconv_loss(pb, w, Y, d, cfg.eps, tables=tables)
     torch.cuda.synchronize()
