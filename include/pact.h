@@ -36,7 +36,7 @@
  *  Patch i covers rows c_a - P/2 .. c_a + P/2 - 1 (and the same for
  *  columns) around its centre pixel (c_a, c_b) = r'_i, zero outside the
  *  image, and is weighted by a Gaussian window of the given FWHM
- *  (Sec. S1.4).  Spectra are the orthonormal 2-D DFT (kernel
+ *  (Sec. S1.5).  Spectra are the orthonormal 2-D DFT (kernel
  *  exp(-j k.rho), scale 1/P) on the rfft half-spectrum: [P][P/2+1] with
  *  rows in fftfreq order, F = P (P/2 + 1) bins per patch, k in rad/m.
  */
@@ -75,7 +75,7 @@ typedef struct pact_geometry {
     float ray_step;     /* midpoint-rule step of the ray integral [m] */
 } pact_geometry;
 
-/* Patch set (Sec. S1.4). */
+/* Patch set (Sec. S1.5). */
 typedef struct pact_patches {
     int        n;            /* number of patches N >= 1 */
     int        p;            /* patch size P, even, 4 <= P <= 128 */
@@ -159,7 +159,7 @@ pact_status pact_rf_synth(const pact_geometry* g, const float* p0, const float* 
                           float* rf, void* ws, size_t ws_bytes, void* stream);
 
 /*
- * Patch spectra (Sec. S1.4, the Y_i(k; d_j) of Eq. 5): crop each of the m
+ * Patch spectra (Sec. S1.5, the Y_i(k; d_j) of Eq. 5): crop each of the m
  * channels around every patch centre, multiply by the Gaussian window
  * exp(-|rho|^2 / (2 sigma^2)), FWHM = 2 sqrt(2 ln 2) sigma, rho measured from
  * local index P/2, and take the orthonormal 2-D DFT on the half-spectrum.
@@ -483,7 +483,7 @@ pact_status pact_siren_backward(const pact_geometry* g, const float* params, con
 size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt);
 
 /*
- * Stitching (Sec. S1.4): every deconvolved patch irfft2(Xhat_i) (orthonormal
+ * Stitching (Sec. S1.5): every deconvolved patch irfft2(Xhat_i) (orthonormal
  * inverse of the half-spectrum, window already applied at cropping) is
  * translated to its centre and summed; the sum is divided by the summed
  * Gaussian windows (0 where no window reaches).
@@ -495,7 +495,7 @@ pact_status pact_stitch(const pact_geometry* g, const pact_patches* pt, const fl
 /*
  * pact_stitch for every channel of a patch-spectrum set at once: the delay
  * stack of the forward model (Eq. 5) in the image domain,
- *   stack[j] = stitch of the patches Y[:, j]   (Sec. S1.4, window once at crop).
+ *   stack[j] = stitch of the patches Y[:, j]   (Sec. S1.5, window once at crop).
  *   Y      DEVICE c64 [N][m][P][P/2+1];  stack DEVICE float [m][H][W] output
  *   ws     DEVICE workspace of pact_stitch_channels_workspace_size bytes
  */

@@ -9,14 +9,14 @@ shares no code with it; the only common module is the seeded input generator
 Everything here is a literal FP64 evaluation of the paper's definitions:
 
 * Eq. 1   delay-and-sum (DAS) image for an extra delay d      -> das_stack
-* Sec. S1.4 Gaussian-windowed patches, orthonormal 2-D DFT     -> patch_spectra
+* Sec. S1.5 Gaussian-windowed patches, orthonormal 2-D DFT     -> patch_spectra
 * Eq. 2-3 straight-ray wavefront error w = int (1 - v0/v) dl   -> wavefront_errors
 * Eq. 4   wavefront transfer function H_i(k; d, v)             -> transfer_functions
 * Eq. 5   multi-channel forward model Y_i = H_i X_i            -> forward_spectra
 * Eq. 6   pseudo-inverse multi-channel deconvolution           -> deconvolve
 * Eq. 7   |k|-weighted aberrated-image-matching loss + TV      -> data_loss, tv, objective
 * Sec. 3.3 Adam on the SOS parameters                          -> adam_step
-* Sec. S1.4 stitching: place patches, divide by summed windows  -> stitch
+* Sec. S1.5 stitching: place patches, divide by summed windows  -> stitch
 * Sec. 3.3 neural fields: the Fourier-feature MLP               -> nf_sos
   and the paper's SIREN (256 sine features, no hidden layer)    -> siren_sos
 
@@ -127,7 +127,7 @@ def das_stack(g, rf, fs: float, t0: float, d) -> torch.Tensor:
 
 
 # --------------------------------------------------------------------------
-# Sec. S1.4: Gaussian-windowed patches and their spectra
+# Sec. S1.5: Gaussian-windowed patches and their spectra
 # --------------------------------------------------------------------------
 
 def window(g) -> torch.Tensor:
@@ -419,7 +419,7 @@ def adam_step(param, grad, m, v, step: int, lr: float, b1: float = 0.9, b2: floa
 
 
 # --------------------------------------------------------------------------
-# Sec. S1.4: stitching
+# Sec. S1.5: stitching
 # --------------------------------------------------------------------------
 
 def stitch(g, Xh, centres) -> torch.Tensor:

@@ -1,4 +1,4 @@
-// Sec. S1.4 on the GPU: Gaussian-windowed patch spectra (pact_patch_fft) and
+// Sec. S1.5 on the GPU: Gaussian-windowed patch spectra (pact_patch_fft) and
 // stitching of deconvolved patches (pact_stitch).
 //
 // Both run once per recovery, so they use a direct separable DFT from shared

@@ -242,7 +242,7 @@ def rf_synth(pb: Problem, p0, sos, fs: float, t0: float, n_s: int, sigma: float,
 
 
 def patch_fft(pb: Problem, stack, Y=None):
-    """Sec. S1.4: windowed patch spectra Y [N, M, P, P/2+1] (complex64)."""
+    """Sec. S1.5: windowed patch spectra Y [N, M, P, P/2+1] (complex64)."""
     L = load()
     stack = _dev(stack, "stack", torch.float32)
     m = stack.shape[0]
@@ -505,7 +505,7 @@ def stitch_workspace_size(pb: Problem) -> int:
 
 
 def stitch(pb: Problem, Xhat, image=None, ws=None):
-    """Sec. S1.4: stitched image [H, W] from deconvolved patches."""
+    """Sec. S1.5: stitched image [H, W] from deconvolved patches."""
     L = load()
     Xhat = _dev(Xhat, "Xhat", torch.complex64, (pb.n, pb.p, pb.p // 2 + 1))
     if image is None:
@@ -517,7 +517,7 @@ def stitch(pb: Problem, Xhat, image=None, ws=None):
 
 
 def stitch_channels(pb: Problem, Y, stack=None, ws=None):
-    """Sec. S1.4 for every channel: delay stack [M, H, W] from patch spectra
+    """Sec. S1.5 for every channel: delay stack [M, H, W] from patch spectra
     [N, M, P, P/2+1]."""
     L = load()
     Y = _dev(Y, "Y", torch.complex64)

@@ -44,7 +44,7 @@ def ssim(img: np.ndarray, ref: np.ndarray, data_range: float = 1.0, mask: np.nda
 
 
 def recovered_image(pb: "pact.Problem", Y: torch.Tensor, d, eps: float, sos: torch.Tensor) -> np.ndarray:
-    """Stitched initial-pressure image (Sec. S1.4) from the deconvolved patches
+    """Stitched initial-pressure image (Sec. S1.5) from the deconvolved patches
     X_hat (Eq. 6) at the SOS `sos`."""
     w = pact.sos_to_delays(pb, sos.contiguous())
     Xh = pact.mc_deconv_loss(pb, w, Y, d, eps, want_grad=False, want_xhat=True)["Xhat"]

@@ -297,7 +297,7 @@ def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: fl
             snapshot_every: int = 50, explode: float = 1e3, lr_decay: float = 0.1, max_restarts: int = 8):
     """Public end-to-end API: upload a delay stack (host, ideally pinned), form
     the patch spectra, run `iters` recovery iterations reading the loss back
-    after each, and return the recovered SOS, the stitched image (Sec. S1.4)
+    after each, and return the recovered SOS, the stitched image (Sec. S1.5)
     and the loss history (a Recovered).  With `to_host` the SOS and the image
     are copied to pinned host memory before the call returns.
 

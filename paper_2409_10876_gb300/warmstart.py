@@ -9,7 +9,7 @@ Training data are generated on the GPU by the library's own forward model:
 a random SOS field (1-6 Gaussian ellipses, 1400-1650 m/s) gives the
 wavefront errors (Eq. 2-3); a vessel-tree initial pressure gives patch
 spectra X; Y = H(v) X (Eq. 5) is stitched channel by channel into the delay
-stack (Sec. S1.4), a seeded noise stack is added, and the stack is pooled
+stack (Sec. S1.5), a seeded noise stack is added, and the stack is pooled
 into the network input.  The target is the SOS field itself.
 """
 from __future__ import annotations

@@ -494,7 +494,7 @@ def test_mc_deconv_loss_noise_free_truth_is_minimum():
     assert l0 <= 1e-6 * l1
 
 
-# ------------------------------------------------------------------ Sec. S1.4 spectra, stitching
+# ------------------------------------------------------------------ Sec. S1.5 spectra, stitching
 
 FFT_CASES = {
     "tiny_p8_m1": CASES["tiny_p8_m1"],

@@ -18,7 +18,7 @@ def _g(cfg):
     return O.geom(cfg)
 
 
-# ---------------------------------------------------------------- DFT (Sec. S1.4)
+# ---------------------------------------------------------------- DFT (Sec. S1.5)
 
 @pytest.mark.parametrize("P", [8, 16, 32, 80])
 def test_rfft2_matches_numpy(P):
@@ -487,7 +487,7 @@ def test_adam_mask_freezes_nodes():
     assert abs(float(p[0]) - (0.0 - 0.5)) < 1e-7
 
 
-# ---------------------------------------------------------------- stitching (Sec. S1.4)
+# ---------------------------------------------------------------- stitching (Sec. S1.5)
 
 def test_stitch_of_windowed_patches_is_identity():
     """Patches that are the windowed crops of an image stitch back to that image
