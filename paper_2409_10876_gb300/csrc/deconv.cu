@@ -748,12 +748,33 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         return;
     }
     if (!a.loss && !a.loss_pp) return;
+    // per patch, the tiles' partials in order; 16 loads in flight per round (one
+    // round for P <= 84), two patches per pass, so the tail pays little L2 latency
     float tot = 0.f;
-    for (int i = tid; i < N; i += kTile) {
-        float acc = 0.f;
-        for (int t = 0; t < a.KT; ++t) acc += __ldcg(a.part_loss + (size_t)i * a.KT + t);
-        if (a.loss_pp) a.loss_pp[i] = acc;
-        tot += acc;
+    for (int i0 = tid; i0 < N; i0 += 2 * kTile) {
+        float acc[2] = {0.f, 0.f};
+        for (int t = 0; t < a.KT; t += 16) {
+            float v[2][16];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = i0 + h * kTile;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    v[h][k] = (i < N && t + k < a.KT) ? __ldcg(a.part_loss + (size_t)i * a.KT + t + k) : 0.f;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) acc[h] += v[h][k];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + h * kTile;
+            if (i < N) {
+                if (a.loss_pp) a.loss_pp[i] = acc[h];
+                tot += acc[h];
+            }
+        }
     }
     tot = warp_sum(tot);
     if (lane == 0) red_s[tid >> 5] = tot;

@@ -620,6 +620,161 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     }
 }
 
+// Ray adjoint, one lane per ray (grids whose padded rows fit in one band, every
+// sample inside the mask disk within the padded node hull).  A work item is
+// (patch i, block of 32 consecutive transducers, segment s of nseg): lane l
+// takes the ray to transducer 32 b + l and the full samples of segment s of
+// that ray (the partial last sample goes with the last segment), starting at
+// a staggered offset l / 32 of its segment and wrapping around, so that the
+// 32 rays leaving one centre are at different radii.  While a lane's samples
+// stay in one cell it adds their four bilinear contributions to registers; on
+// leaving the cell it adds the four sums to the shared fixed-point grid (four
+// integer atomics) and loads the four node excesses of the next cell, so a
+// sample costs no shared-memory access unless the walk changes cell.
+// The items of CTA b are b, b + nb, ... (claimed dynamically by its warps);
+// the CTA's fixed-point scale follows from a bound as in rays_adj_kernel, with
+// a segment's chord at most 2 mask_r / nseg + 2 h and a single flush at most
+// the contributions of the samples inside one cell's support (fewer than 8).
+__global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a, int nseg) {
+    extern __shared__ float sm[];
+    __shared__ float red_s[32];
+    __shared__ float scale_s[2];      // S and 1/S (NaN: poisoned)
+    __shared__ int next_s;
+    const int G = a.g.G, pitch = pad_pitch(G), PG = G + 4;
+    float* dv_s = sm;                                              // [PG][pitch] padded excess
+    int* acc_s = reinterpret_cast<int*>(sm + PG * pitch);           // [PG][pitch] padded sums
+    const float v0 = a.g.v0, h = a.g.h;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int n_t = a.g.n_t, nblk = (n_t + 31) / 32, nb = gridDim.x;
+    const int items = a.N * nblk * nseg;
+    const int mine = items > (int)blockIdx.x ? (items - (int)blockIdx.x + nb - 1) / nb : 0;
+    pdl_trigger();
+    pdl_wait();                       // dL/dw and the SOS come from earlier kernels
+
+    // fixed-point scale of this CTA
+    float gsum = 0.f, gmax = 0.f, vmin = INFINITY, bad = 0.f;
+    for (int q = threadIdx.x; q < mine * 32; q += blockDim.x) {
+        const int t = (int)blockIdx.x + nb * (q >> 5), pb = t / nseg, i = pb / nblk;
+        const int n = (pb - i * nblk) * 32 + (q & 31);
+        const float gv = n < n_t ? fabsf(a.dLdw[(size_t)i * n_t + n]) : 0.f;
+        gsum += gv;
+        gmax = fmaxf(gmax, gv);
+    }
+    stage_padded_async(dv_s, a.sos, G, 0, PG);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int pl = warp; pl < PG; pl += nw)
+        for (int cc = lane; cc < PG; cc += 32) {
+            const float v = dv_s[pl * pitch + cc];
+            if (!(v > 0.f) || !isfinite(v)) bad = 1.f;
+            vmin = fminf(vmin, v);
+            dv_s[pl * pitch + cc] = v - v0;
+            acc_s[pl * pitch + cc] = 0;
+        }
+    gsum = block_sum(gsum, red_s);
+    gmax = block_max(gmax, red_s);
+    bad = block_sum(bad, red_s);
+    vmin = block_min(vmin, red_s);
+    if (threadIdx.x == 0) {
+        const float vm = vmin * (1.f - 1e-5f);
+        const float k = v0 / (vm * vm);
+        const float Mb = gsum * (2.f * a.g.mask_r / nseg + 2.f * h) * k;
+        const float F = 8.f * gmax * h * k;
+        const bool poison = bad > 0.f || !isfinite(Mb) || !isfinite(F) || !isfinite(gsum);
+        const float S = (Mb > 0.f && F > 0.f) ? 0.99f * fminf(fminf(1073741824.f / Mb, 4194304.f / F), 1e30f) : 0.f;
+        scale_s[0] = poison ? 0.f : S;
+        scale_s[1] = poison ? __int_as_float(0x7fc00000) : (S > 0.f ? 1.f / S : 0.f);
+        next_s = nw;
+    }
+    __syncthreads();
+    const float S = scale_s[0];
+
+    for (int j = warp; j < mine;) {
+        const int t = (int)blockIdx.x + nb * j, pb = t / nseg, seg = t - pb * nseg;
+        const int i = pb / nblk, n = (pb - i * nblk) * 32 + lane;
+        const float gr = n < n_t ? a.dLdw[(size_t)i * n_t + n] : 0.f;
+        int len = 0, m_lo = 0, nfull = 0;
+        float ax = 0.f, ay = 0.f, hbx = 0.f, hby = 0.f, upart = 0.f, wfull = 0.f, wpart = 0.f;
+        if (gr != 0.f) {
+            const int2 cc = a.centres[i];
+            const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
+            nfull = ry.nfull;
+            m_lo = nfull * seg / nseg;
+            const int m_hi = nfull * (seg + 1) / nseg;
+            len = m_hi - m_lo + ((seg == nseg - 1 && ry.rem > 0.f) ? 1 : 0);
+            ax = ry.ax + 2.f;
+            ay = ry.ay + 2.f;
+            hbx = h * ry.bx;
+            hby = h * ry.by;
+            upart = nfull + 0.5f * (ry.rem * a.g.inv_h);
+            wfull = gr * v0 * h * S;
+            wpart = gr * v0 * ry.rem * S;
+        }
+        int k = (len * lane) >> 5;                   // staggered start within the segment
+        int cur = -1;
+        float d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
+        float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+        for (int step = 0; step < len; ++step) {
+            const int m = m_lo + k;
+            k = k + 1 == len ? 0 : k + 1;
+            const bool part = m >= nfull;
+            const float u = part ? upart : (float)m + 0.5f;
+            const float wgt = part ? wpart : wfull;
+            const float x = fmaf(u, hbx, ax), y = fmaf(u, hby, ay);
+            const float tX = x + 8388607.5f, tY = y + 8388607.5f;
+            const int cell = (__float_as_int(tY) - 0x4B000000) * pitch + (__float_as_int(tX) - 0x4B000000);
+            if (cell != cur) {                       // leave the cell: flush its sums, load the next one
+                if (cur >= 0) {
+                    int* acc = acc_s + cur;
+                    atomicAdd(acc, fixed_round(a00));
+                    atomicAdd(acc + 1, fixed_round(a01));
+                    atomicAdd(acc + pitch, fixed_round(a10));
+                    atomicAdd(acc + pitch + 1, fixed_round(a11));
+                }
+                const float* q = dv_s + cell;
+                d00 = q[0];
+                d01 = q[1];
+                d10 = q[pitch];
+                d11 = q[pitch + 1];
+                a00 = a01 = a10 = a11 = 0.f;
+                cur = cell;
+            }
+            const float tx = x - (tX - 8388608.f), ty = y - (tY - 8388608.f);
+            const float top = fmaf(tx, d01 - d00, d00), bot = fmaf(tx, d11 - d10, d10);
+            const float d = fmaf(ty, bot - top, top);
+            const float iv = __fdividef(1.f, v0 + d);
+            const float coef = wgt * iv * iv;
+            const float cy1 = coef * ty, cy0 = coef - cy1;
+            const float c01 = cy0 * tx, c11 = cy1 * tx;
+            a00 += cy0 - c01;
+            a01 += c01;
+            a10 += cy1 - c11;
+            a11 += c11;
+        }
+        if (cur >= 0) {
+            int* acc = acc_s + cur;
+            atomicAdd(acc, fixed_round(a00));
+            atomicAdd(acc + 1, fixed_round(a01));
+            atomicAdd(acc + pitch, fixed_round(a10));
+            atomicAdd(acc + pitch + 1, fixed_round(a11));
+        }
+        int nj = 0;
+        if (lane == 0) nj = atomicAdd(&next_s, 1);
+        j = __shfl_sync(0xffffffffu, nj, 0);
+    }
+    __syncthreads();
+    // the CTA's partial grid: padded rows and columns folded onto the edge nodes
+    const float invS = scale_s[1];
+    float* dst = a.part + (size_t)blockIdx.x * G * G;
+    for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
+        const int p = q / G, c = q - (q / G) * G;
+        const int pr0 = p == 0 ? 0 : p + 2, pr1 = p == G - 1 ? G + 3 : p + 2;
+        int sum = 0;
+        for (int pr = pr0; pr <= pr1; ++pr) sum += fold_col(acc_s + pr * pitch, c, G);
+        dst[q] = (float)sum * invS;
+    }
+}
+
 // Sum of the partial grids part[0 .. np) at the 32 consecutive nodes q0 + lane
 // of this block: warp w adds the partials of its chunk [np w / nw, np (w+1) / nw)
 // in order, warp 0 then adds the chunk sums in order (a fixed order, with
@@ -844,11 +999,23 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.dLdw = dL_dw;
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
-    auto adj = pl.nbands == 1 ? (pl.narrow ? rays_adj_kernel<true, true> : rays_adj_kernel<true, false>)
-                              : (pl.narrow ? rays_adj_kernel<false, true> : rays_adj_kernel<false, false>);
-    PACT_TRY(ensure_smem((const void*)adj, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
-    if (launch_pdl(adj, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands) != cudaSuccess)
-        return check_launch("sos_to_delays_adj kernel");
+    if (pl.nbands == 1 && pl.narrow) {
+        // one lane per ray, cell sums in registers (every sample in one shared-memory band)
+        const int G = g->sos_g, nblk32 = (g->n_t + 31) / 32;
+        const size_t smem = 2 * sizeof(float) * (size_t)(G + 4) * pad_pitch(G);
+        const long long want = 2LL * pl.nb_adj * 32;                   // about two items per warp
+        const int nseg = (int)std::max(1LL, std::min(8LL, (want + (long long)pt->n * nblk32 - 1) /
+                                                                ((long long)pt->n * nblk32)));
+        PACT_TRY(ensure_smem((const void*)rays_adj_walk_kernel, smem, "sos_to_delays_adj: shared memory attribute"));
+        if (launch_pdl(rays_adj_walk_kernel, dim3(pl.nb_adj), dim3(1024), smem, st, a, nseg) != cudaSuccess)
+            return check_launch("sos_to_delays_adj kernel");
+    } else {
+        auto adj = pl.nbands == 1 ? rays_adj_kernel<true, false>
+                                  : (pl.narrow ? rays_adj_kernel<false, true> : rays_adj_kernel<false, false>);
+        PACT_TRY(ensure_smem((const void*)adj, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
+        if (launch_pdl(adj, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands) != cudaSuccess)
+            return check_launch("sos_to_delays_adj kernel");
+    }
     PACT_TRY(check_launch("sos_to_delays_adj kernel"));
     // one partial grid per CTA: a single fixed-order sum
     if (launch_pdl(reduce_parts_kernel, dim3((GG + 31) / 32), dim3(256), 0, st, a.part, pl.nparts, GG, dL_dsos,

@@ -164,20 +164,22 @@ __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* c
     const int half = P / 2 + 1;
     float2* Z = reinterpret_cast<float2*>(sm);     // [P*half]
     float2* tw = Z + P * half;                     // [P]: exp(+2 pi j t / P)
+    float2* Xs = tw + P;                           // [P*half]: the patch's half spectrum
     const int i = blockIdx.x;
     const int2 c = centres[i];
     const int r0 = c.x - P / 2, c0 = c.y - P / 2;
-    for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = cis_pi(2.f * t / P);
-    __syncthreads();
     const int j = blockIdx.y, m = gridDim.y;
     const float2* Xi = X + ((size_t)i * m + j) * P * half;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = cis_pi(2.f * t / P);
+    for (int q = threadIdx.x; q < P * half; q += blockDim.x) Xs[q] = Xi[q];
+    __syncthreads();
     num += (size_t)j * g.H * g.W;
     for (int q = threadIdx.x; q < P * half; q += blockDim.x) {
         const int a = q / half, v = q - (q / half) * half;
         float re = 0.f, im = 0.f;
         int idx = 0;
         for (int u = 0; u < P; ++u) {
-            const float2 xv = Xi[u * half + v];
+            const float2 xv = Xs[u * half + v];
             const float2 t = tw[idx];
             re = fmaf(xv.x, t.x, fmaf(-xv.y, t.y, re));
             im = fmaf(xv.x, t.y, fmaf(xv.y, t.x, im));
@@ -271,7 +273,7 @@ pact_status run_stitch(const pact_geometry* g, const pact_patches* pt, int m, co
     float* den = num + (size_t)m * g->img_h * g->img_w;
     if (cudaMemsetAsync(ws, 0, (size_t)(m + 1) * plane, st) != cudaSuccess) return check_launch("stitch: memset");
     const int P = pt->p, half = P / 2 + 1;
-    const size_t shm = (size_t)(P * half + P) * sizeof(float2);
+    const size_t shm = (size_t)(2 * P * half + P) * sizeof(float2);
     PACT_TRY(ensure_smem((const void*)stitch_kernel, shm, "stitch: shared memory attribute"));
     stitch_kernel<<<dim3(pt->n, m), 256, shm, st>>>(make_geo(g), P, reinterpret_cast<const int2*>(pt->centres),
                                                     inv_two_sigma2(pt->window_fwhm),
