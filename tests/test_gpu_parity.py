@@ -353,6 +353,21 @@ def test_mc_deconv_loss_realistic_full_size(point):
         _check_mcd(cfg, Y, w, cfg.delays(), 1e-8)        # FP64 denominators, explicit residual
 
 
+def test_mc_deconv_loss_at_the_fp64_cold_end_point():
+    """The held-out warm-start problem at the end point of the FP64 oracle's own
+    1000-iteration cold recovery (tests/golden/make_cold_optimum.py): all 144
+    patches, near a local optimum of Eq. 7, against the oracle."""
+    import os
+    cfg = inputs.config_held_out()
+    path = os.path.join(os.path.dirname(__file__), "golden", f"cold_optimum_{cfg.name}_seed1000.npy")
+    sos = np.load(path).astype(np.float64)
+    case = inputs.make_case(cfg, 1000)
+    g = O.geom(cfg)
+    Y = O.make_measurement(g, case)[0].numpy().astype(np.complex64)
+    w = O.wavefront_errors(g, sos, case["centres"]).numpy().astype(np.float32)
+    _check_mcd(cfg, Y, w, cfg.delays(), cfg.eps)
+
+
 def test_mc_deconv_loss_on_das_spectra_sampled():
     """Spectra made the way the channel-data workload makes them -- ring channel
     data (oracle) -> DAS (Eq. 1, oracle, at the pixels of the sampled patches)
