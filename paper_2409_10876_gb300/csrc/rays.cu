@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(512) rays_pix_kernel(const RayArgs a, const fl
 }
 
 constexpr int kAdjLanes = 4;   // lanes per ray in the adjoint
+constexpr bool kWalkAdjoint = true;    // rays_adj_walk_kernel for single-band grids
 constexpr int kOrder = 2048;   // largest item count per CTA put in claim order
 
 // Round-to-nearest int of |x| < 2^22 without a conversion instruction: adding
@@ -620,22 +621,27 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     }
 }
 
-// Ray adjoint, one lane per ray (grids whose padded rows fit in one band, every
-// sample inside the mask disk within the padded node hull).  A work item is
-// (patch i, block of 32 consecutive transducers, segment s of nseg): lane l
-// takes the ray to transducer 32 b + l and the full samples of segment s of
-// that ray (the partial last sample goes with the last segment), starting at
-// a staggered offset l / 32 of its segment and wrapping around, so that the
-// 32 rays leaving one centre are at different radii.  While a lane's samples
-// stay in one cell it adds their four bilinear contributions to registers; on
-// leaving the cell it adds the four sums to the shared fixed-point grid (four
-// integer atomics) and loads the four node excesses of the next cell, so a
-// sample costs no shared-memory access unless the walk changes cell.
-// The items of CTA b are b, b + nb, ... (claimed dynamically by its warps);
-// the CTA's fixed-point scale follows from a bound as in rays_adj_kernel, with
-// a segment's chord at most 2 mask_r / nseg + 2 h and a single flush at most
-// the contributions of the samples inside one cell's support (fewer than 8).
-__global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a, int nseg) {
+// Ray adjoint with register sums per cell (grids whose padded rows fit in one
+// shared-memory band, every sample inside the mask disk within the padded
+// node hull).  A work item is (patch i, block of 32 consecutive transducers,
+// part p of nparts).  The samples of the item's 32 rays, laid end to end
+// (ray by ray, each in walking order, the partial last sample at its end),
+// form one list; part p of that list is split into 32 equal contiguous
+// chunks, one per lane, so every lane has the same number of samples whatever
+// the rays' lengths (a chunk may run from one ray into the next).  The rays'
+// parameters sit in a per-warp shared table.  While a lane's consecutive
+// samples stay in one cell it adds their four bilinear contributions to
+// registers; on leaving the cell it adds the four sums to the shared
+// fixed-point grid (four integer atomics) and loads the four node excesses of
+// the next cell.  The items of CTA b are b, b + nb, ... (claimed dynamically
+// by its warps); its fixed-point scale follows from a bound as in
+// rays_adj_kernel: a part of an item holds at most 1/nparts of the samples of
+// 32 rays of chord <= 2 mask_r, plus one, each weighted by at most the item's
+// largest |dL/dw|, and one flush adds the contributions of fewer than 8
+// samples (the samples of one cell visit).
+constexpr int kRayPar = 8;   // per-ray parameters in the warp table
+
+__global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a, int nparts) {
     extern __shared__ float sm[];
     __shared__ float red_s[32];
     __shared__ float scale_s[2];      // S and 1/S (NaN: poisoned)
@@ -645,19 +651,25 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a,
     int* acc_s = reinterpret_cast<int*>(sm + PG * pitch);           // [PG][pitch] padded sums
     const float v0 = a.g.v0, h = a.g.h;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float* tab = reinterpret_cast<float*>(acc_s + PG * pitch) + warp * (32 * kRayPar + 33);   // this warp's rays
+    int* incl = reinterpret_cast<int*>(tab + 32 * kRayPar);        // [33] exclusive prefix of sample counts
     const int n_t = a.g.n_t, nblk = (n_t + 31) / 32, nb = gridDim.x;
-    const int items = a.N * nblk * nseg;
+    const int items = a.N * nblk * nparts;
     const int mine = items > (int)blockIdx.x ? (items - (int)blockIdx.x + nb - 1) / nb : 0;
     pdl_trigger();
     pdl_wait();                       // dL/dw and the SOS come from earlier kernels
 
-    // fixed-point scale of this CTA
+    // fixed-point scale of this CTA: a part of an item holds at most
+    // 32 (2 mask_r / h + 1) / nparts + 1 samples, each of weight at most h |g|max(item)
     float gsum = 0.f, gmax = 0.f, vmin = INFINITY, bad = 0.f;
-    for (int q = threadIdx.x; q < mine * 32; q += blockDim.x) {
-        const int t = (int)blockIdx.x + nb * (q >> 5), pb = t / nseg, i = pb / nblk;
-        const int n = (pb - i * nblk) * 32 + (q & 31);
+    for (int jj = warp; jj < mine; jj += nw) {
+        const int t = (int)blockIdx.x + nb * jj, pb = t / nparts, i = pb / nblk;
+        const int n = (pb - i * nblk) * 32 + lane;
         const float gv = n < n_t ? fabsf(a.dLdw[(size_t)i * n_t + n]) : 0.f;
-        gsum += gv;
+        float mx = gv;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) gsum += mx;                 // sum over items of the item's largest |g|
         gmax = fmaxf(gmax, gv);
     }
     stage_padded_async(dv_s, a.sos, G, 0, PG);
@@ -678,7 +690,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a,
     if (threadIdx.x == 0) {
         const float vm = vmin * (1.f - 1e-5f);
         const float k = v0 / (vm * vm);
-        const float Mb = gsum * (2.f * a.g.mask_r / nseg + 2.f * h) * k;
+        const float Mb = gsum * (32.f * (2.f * a.g.mask_r + h) / nparts + h) * k;
         const float F = 8.f * gmax * h * k;
         const bool poison = bad > 0.f || !isfinite(Mb) || !isfinite(F) || !isfinite(gsum);
         const float S = (Mb > 0.f && F > 0.f) ? 0.99f * fminf(fminf(1073741824.f / Mb, 4194304.f / F), 1e30f) : 0.f;
@@ -690,40 +702,74 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a,
     const float S = scale_s[0];
 
     for (int j = warp; j < mine;) {
-        const int t = (int)blockIdx.x + nb * j, pb = t / nseg, seg = t - pb * nseg;
+        const int t = (int)blockIdx.x + nb * j, pb = t / nparts, part = t - pb * nparts;
         const int i = pb / nblk, n = (pb - i * nblk) * 32 + lane;
+        // this lane's ray into the warp table; its sample count
         const float gr = n < n_t ? a.dLdw[(size_t)i * n_t + n] : 0.f;
-        int len = 0, m_lo = 0, nfull = 0;
-        float ax = 0.f, ay = 0.f, hbx = 0.f, hby = 0.f, upart = 0.f, wfull = 0.f, wpart = 0.f;
-        if (gr != 0.f) {
-            const int2 cc = a.centres[i];
-            const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
-            nfull = ry.nfull;
-            m_lo = nfull * seg / nseg;
-            const int m_hi = nfull * (seg + 1) / nseg;
-            len = m_hi - m_lo + ((seg == nseg - 1 && ry.rem > 0.f) ? 1 : 0);
-            ax = ry.ax + 2.f;
-            ay = ry.ay + 2.f;
-            hbx = h * ry.bx;
-            hby = h * ry.by;
-            upart = nfull + 0.5f * (ry.rem * a.g.inv_h);
-            wfull = gr * v0 * h * S;
-            wpart = gr * v0 * ry.rem * S;
+        int ns = 0;
+        {
+            float* r = tab + lane * kRayPar;
+            if (gr != 0.f) {
+                const int2 cc = a.centres[i];
+                const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
+                ns = ry.nfull + (ry.rem > 0.f ? 1 : 0);
+                r[0] = ry.ax + 2.f;
+                r[1] = ry.ay + 2.f;
+                r[2] = h * ry.bx;
+                r[3] = h * ry.by;
+                r[4] = __int_as_float(ry.nfull);
+                r[5] = ry.nfull + 0.5f * (ry.rem * a.g.inv_h);
+                r[6] = gr * v0 * h * S;
+                r[7] = gr * v0 * ry.rem * S;
+            }
         }
-        int k = (len * lane) >> 5;                   // staggered start within the segment
+        int sc = ns;                                   // inclusive prefix sum over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += y;
+        }
+        incl[lane + 1] = sc;
+        if (lane == 0) incl[0] = 0;
+        const int T = __shfl_sync(0xffffffffu, sc, 31);
+        __syncwarp();
+        // this lane's chunk [c0, c1) of part `part` of the list
+        const long long lo = (long long)T * part / nparts, hi = (long long)T * (part + 1) / nparts;
+        const int c0 = (int)(lo + (hi - lo) * lane / 32), c1 = (int)(lo + (hi - lo) * (lane + 1) / 32);
+        int ray = 0;                                   // the ray holding sample c0: incl[ray] <= c0 < incl[ray + 1]
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            if (ray + o <= 31 && incl[ray + o] <= c0) ray += o;
+        int m = c0 - incl[ray];
+        const float* r = tab + ray * kRayPar;
+        float ax = r[0], ay = r[1], hbx = r[2], hby = r[3], upart = r[5], wfull = r[6], wpart = r[7];
+        int nfull = __float_as_int(r[4]), end = incl[ray + 1] - incl[ray];
         int cur = -1;
         float d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
         float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
-        for (int step = 0; step < len; ++step) {
-            const int m = m_lo + k;
-            k = k + 1 == len ? 0 : k + 1;
-            const bool part = m >= nfull;
-            const float u = part ? upart : (float)m + 0.5f;
-            const float wgt = part ? wpart : wfull;
+        for (int c = c0; c < c1; ++c) {
+            while (m >= end) {                         // next ray of the list (rays without samples skipped)
+                ++ray;
+                m = 0;
+                r = tab + ray * kRayPar;
+                ax = r[0];
+                ay = r[1];
+                hbx = r[2];
+                hby = r[3];
+                nfull = __float_as_int(r[4]);
+                upart = r[5];
+                wfull = r[6];
+                wpart = r[7];
+                end = incl[ray + 1] - incl[ray];
+            }
+            const bool partial = m >= nfull;
+            const float u = partial ? upart : (float)m + 0.5f;
+            const float wgt = partial ? wpart : wfull;
+            ++m;
             const float x = fmaf(u, hbx, ax), y = fmaf(u, hby, ay);
             const float tX = x + 8388607.5f, tY = y + 8388607.5f;
             const int cell = (__float_as_int(tY) - 0x4B000000) * pitch + (__float_as_int(tX) - 0x4B000000);
-            if (cell != cur) {                       // leave the cell: flush its sums, load the next one
+            if (cell != cur) {                         // leave the cell: flush its sums, load the next one
                 if (cur >= 0) {
                     int* acc = acc_s + cur;
                     atomicAdd(acc, fixed_round(a00));
@@ -758,6 +804,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a,
             atomicAdd(acc + pitch, fixed_round(a10));
             atomicAdd(acc + pitch + 1, fixed_round(a11));
         }
+        __syncwarp();                                  // the table is rewritten by the next item
         int nj = 0;
         if (lane == 0) nj = atomicAdd(&next_s, 1);
         j = __shfl_sync(0xffffffffu, nj, 0);
@@ -999,18 +1046,19 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.dLdw = dL_dw;
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
-    if (pl.nbands == 1 && pl.narrow) {
+    if (pl.nbands == 1 && pl.narrow && kWalkAdjoint) {
         // one lane per ray, cell sums in registers (every sample in one shared-memory band)
         const int G = g->sos_g, nblk32 = (g->n_t + 31) / 32;
-        const size_t smem = 2 * sizeof(float) * (size_t)(G + 4) * pad_pitch(G);
+        const size_t smem = 2 * sizeof(float) * (size_t)(G + 4) * pad_pitch(G) +
+                            sizeof(float) * 32 * (32 * kRayPar + 33);
         const long long want = 2LL * pl.nb_adj * 32;                   // about two items per warp
-        const int nseg = (int)std::max(1LL, std::min(8LL, (want + (long long)pt->n * nblk32 - 1) /
-                                                                ((long long)pt->n * nblk32)));
+        const int nparts = (int)std::max(1LL, std::min(8LL, (want + (long long)pt->n * nblk32 - 1) /
+                                                                  ((long long)pt->n * nblk32)));
         PACT_TRY(ensure_smem((const void*)rays_adj_walk_kernel, smem, "sos_to_delays_adj: shared memory attribute"));
-        if (launch_pdl(rays_adj_walk_kernel, dim3(pl.nb_adj), dim3(1024), smem, st, a, nseg) != cudaSuccess)
+        if (launch_pdl(rays_adj_walk_kernel, dim3(pl.nb_adj), dim3(1024), smem, st, a, nparts) != cudaSuccess)
             return check_launch("sos_to_delays_adj kernel");
     } else {
-        auto adj = pl.nbands == 1 ? rays_adj_kernel<true, false>
+        auto adj = pl.nbands == 1 ? (pl.narrow ? rays_adj_kernel<true, true> : rays_adj_kernel<true, false>)
                                   : (pl.narrow ? rays_adj_kernel<false, true> : rays_adj_kernel<false, false>);
         PACT_TRY(ensure_smem((const void*)adj, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
         if (launch_pdl(adj, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands) != cudaSuccess)
