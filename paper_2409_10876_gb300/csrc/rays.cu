@@ -295,7 +295,6 @@ __global__ void __launch_bounds__(512) rays_pix_kernel(const RayArgs a, const fl
 }
 
 constexpr int kAdjLanes = 4;   // lanes per ray in the adjoint
-constexpr bool kWalkAdjoint = true;    // rays_adj_walk_kernel for single-band grids
 constexpr int kOrder = 2048;   // largest item count per CTA put in claim order
 
 // Round-to-nearest int of |x| < 2^22 without a conversion instruction: adding
@@ -621,207 +620,6 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
     }
 }
 
-// Ray adjoint with register sums per cell (grids whose padded rows fit in one
-// shared-memory band, every sample inside the mask disk within the padded
-// node hull).  A work item is (patch i, block of 32 consecutive transducers,
-// part p of nparts).  The samples of the item's 32 rays, laid end to end
-// (ray by ray, each in walking order, the partial last sample at its end),
-// form one list; part p of that list is split into 32 equal contiguous
-// chunks, one per lane, so every lane has the same number of samples whatever
-// the rays' lengths (a chunk may run from one ray into the next).  The rays'
-// parameters sit in a per-warp shared table.  While a lane's consecutive
-// samples stay in one cell it adds their four bilinear contributions to
-// registers; on leaving the cell it adds the four sums to the shared
-// fixed-point grid (four integer atomics) and loads the four node excesses of
-// the next cell.  The items of CTA b are b, b + nb, ... (claimed dynamically
-// by its warps); its fixed-point scale follows from a bound as in
-// rays_adj_kernel: a part of an item holds at most 1/nparts of the samples of
-// 32 rays of chord <= 2 mask_r, plus one, each weighted by at most the item's
-// largest |dL/dw|, and one flush adds the contributions of fewer than 8
-// samples (the samples of one cell visit).
-constexpr int kRayPar = 8;   // per-ray parameters in the warp table
-
-__global__ void __launch_bounds__(1024, 1) rays_adj_walk_kernel(const RayArgs a, int nparts) {
-    extern __shared__ float sm[];
-    __shared__ float red_s[32];
-    __shared__ float scale_s[2];      // S and 1/S (NaN: poisoned)
-    __shared__ int next_s;
-    const int G = a.g.G, pitch = pad_pitch(G), PG = G + 4;
-    float* dv_s = sm;                                              // [PG][pitch] padded excess
-    int* acc_s = reinterpret_cast<int*>(sm + PG * pitch);           // [PG][pitch] padded sums
-    const float v0 = a.g.v0, h = a.g.h;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float* tab = reinterpret_cast<float*>(acc_s + PG * pitch) + warp * (32 * kRayPar + 33);   // this warp's rays
-    int* incl = reinterpret_cast<int*>(tab + 32 * kRayPar);        // [33] exclusive prefix of sample counts
-    const int n_t = a.g.n_t, nblk = (n_t + 31) / 32, nb = gridDim.x;
-    const int items = a.N * nblk * nparts;
-    const int mine = items > (int)blockIdx.x ? (items - (int)blockIdx.x + nb - 1) / nb : 0;
-    pdl_trigger();
-    pdl_wait();                       // dL/dw and the SOS come from earlier kernels
-
-    // fixed-point scale of this CTA: a part of an item holds at most
-    // 32 (2 mask_r / h + 1) / nparts + 1 samples, each of weight at most h |g|max(item)
-    float gsum = 0.f, gmax = 0.f, vmin = INFINITY, bad = 0.f;
-    for (int jj = warp; jj < mine; jj += nw) {
-        const int t = (int)blockIdx.x + nb * jj, pb = t / nparts, i = pb / nblk;
-        const int n = (pb - i * nblk) * 32 + lane;
-        const float gv = n < n_t ? fabsf(a.dLdw[(size_t)i * n_t + n]) : 0.f;
-        float mx = gv;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) gsum += mx;                 // sum over items of the item's largest |g|
-        gmax = fmaxf(gmax, gv);
-    }
-    stage_padded_async(dv_s, a.sos, G, 0, PG);
-    cp_async_wait_all();
-    __syncthreads();
-    for (int pl = warp; pl < PG; pl += nw)
-        for (int cc = lane; cc < PG; cc += 32) {
-            const float v = dv_s[pl * pitch + cc];
-            if (!(v > 0.f) || !isfinite(v)) bad = 1.f;
-            vmin = fminf(vmin, v);
-            dv_s[pl * pitch + cc] = v - v0;
-            acc_s[pl * pitch + cc] = 0;
-        }
-    gsum = block_sum(gsum, red_s);
-    gmax = block_max(gmax, red_s);
-    bad = block_sum(bad, red_s);
-    vmin = block_min(vmin, red_s);
-    if (threadIdx.x == 0) {
-        const float vm = vmin * (1.f - 1e-5f);
-        const float k = v0 / (vm * vm);
-        const float Mb = gsum * (32.f * (2.f * a.g.mask_r + h) / nparts + h) * k;
-        const float F = 8.f * gmax * h * k;
-        const bool poison = bad > 0.f || !isfinite(Mb) || !isfinite(F) || !isfinite(gsum);
-        const float S = (Mb > 0.f && F > 0.f) ? 0.99f * fminf(fminf(1073741824.f / Mb, 4194304.f / F), 1e30f) : 0.f;
-        scale_s[0] = poison ? 0.f : S;
-        scale_s[1] = poison ? __int_as_float(0x7fc00000) : (S > 0.f ? 1.f / S : 0.f);
-        next_s = nw;
-    }
-    __syncthreads();
-    const float S = scale_s[0];
-
-    for (int j = warp; j < mine;) {
-        const int t = (int)blockIdx.x + nb * j, pb = t / nparts, part = t - pb * nparts;
-        const int i = pb / nblk, n = (pb - i * nblk) * 32 + lane;
-        // this lane's ray into the warp table; its sample count
-        const float gr = n < n_t ? a.dLdw[(size_t)i * n_t + n] : 0.f;
-        int ns = 0;
-        {
-            float* r = tab + lane * kRayPar;
-            if (gr != 0.f) {
-                const int2 cc = a.centres[i];
-                const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
-                ns = ry.nfull + (ry.rem > 0.f ? 1 : 0);
-                r[0] = ry.ax + 2.f;
-                r[1] = ry.ay + 2.f;
-                r[2] = h * ry.bx;
-                r[3] = h * ry.by;
-                r[4] = __int_as_float(ry.nfull);
-                r[5] = ry.nfull + 0.5f * (ry.rem * a.g.inv_h);
-                r[6] = gr * v0 * h * S;
-                r[7] = gr * v0 * ry.rem * S;
-            }
-        }
-        int sc = ns;                                   // inclusive prefix sum over the lanes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, sc, o);
-            if (lane >= o) sc += y;
-        }
-        incl[lane + 1] = sc;
-        if (lane == 0) incl[0] = 0;
-        const int T = __shfl_sync(0xffffffffu, sc, 31);
-        __syncwarp();
-        // this lane's chunk [c0, c1) of part `part` of the list
-        const long long lo = (long long)T * part / nparts, hi = (long long)T * (part + 1) / nparts;
-        const int c0 = (int)(lo + (hi - lo) * lane / 32), c1 = (int)(lo + (hi - lo) * (lane + 1) / 32);
-        int ray = 0;                                   // the ray holding sample c0: incl[ray] <= c0 < incl[ray + 1]
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            if (ray + o <= 31 && incl[ray + o] <= c0) ray += o;
-        int m = c0 - incl[ray];
-        const float* r = tab + ray * kRayPar;
-        float ax = r[0], ay = r[1], hbx = r[2], hby = r[3], upart = r[5], wfull = r[6], wpart = r[7];
-        int nfull = __float_as_int(r[4]), end = incl[ray + 1] - incl[ray];
-        int cur = -1;
-        float d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
-        float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
-        for (int c = c0; c < c1; ++c) {
-            while (m >= end) {                         // next ray of the list (rays without samples skipped)
-                ++ray;
-                m = 0;
-                r = tab + ray * kRayPar;
-                ax = r[0];
-                ay = r[1];
-                hbx = r[2];
-                hby = r[3];
-                nfull = __float_as_int(r[4]);
-                upart = r[5];
-                wfull = r[6];
-                wpart = r[7];
-                end = incl[ray + 1] - incl[ray];
-            }
-            const bool partial = m >= nfull;
-            const float u = partial ? upart : (float)m + 0.5f;
-            const float wgt = partial ? wpart : wfull;
-            ++m;
-            const float x = fmaf(u, hbx, ax), y = fmaf(u, hby, ay);
-            const float tX = x + 8388607.5f, tY = y + 8388607.5f;
-            const int cell = (__float_as_int(tY) - 0x4B000000) * pitch + (__float_as_int(tX) - 0x4B000000);
-            if (cell != cur) {                         // leave the cell: flush its sums, load the next one
-                if (cur >= 0) {
-                    int* acc = acc_s + cur;
-                    atomicAdd(acc, fixed_round(a00));
-                    atomicAdd(acc + 1, fixed_round(a01));
-                    atomicAdd(acc + pitch, fixed_round(a10));
-                    atomicAdd(acc + pitch + 1, fixed_round(a11));
-                }
-                const float* q = dv_s + cell;
-                d00 = q[0];
-                d01 = q[1];
-                d10 = q[pitch];
-                d11 = q[pitch + 1];
-                a00 = a01 = a10 = a11 = 0.f;
-                cur = cell;
-            }
-            const float tx = x - (tX - 8388608.f), ty = y - (tY - 8388608.f);
-            const float top = fmaf(tx, d01 - d00, d00), bot = fmaf(tx, d11 - d10, d10);
-            const float d = fmaf(ty, bot - top, top);
-            const float iv = __fdividef(1.f, v0 + d);
-            const float coef = wgt * iv * iv;
-            const float cy1 = coef * ty, cy0 = coef - cy1;
-            const float c01 = cy0 * tx, c11 = cy1 * tx;
-            a00 += cy0 - c01;
-            a01 += c01;
-            a10 += cy1 - c11;
-            a11 += c11;
-        }
-        if (cur >= 0) {
-            int* acc = acc_s + cur;
-            atomicAdd(acc, fixed_round(a00));
-            atomicAdd(acc + 1, fixed_round(a01));
-            atomicAdd(acc + pitch, fixed_round(a10));
-            atomicAdd(acc + pitch + 1, fixed_round(a11));
-        }
-        __syncwarp();                                  // the table is rewritten by the next item
-        int nj = 0;
-        if (lane == 0) nj = atomicAdd(&next_s, 1);
-        j = __shfl_sync(0xffffffffu, nj, 0);
-    }
-    __syncthreads();
-    // the CTA's partial grid: padded rows and columns folded onto the edge nodes
-    const float invS = scale_s[1];
-    float* dst = a.part + (size_t)blockIdx.x * G * G;
-    for (int q = threadIdx.x; q < G * G; q += blockDim.x) {
-        const int p = q / G, c = q - (q / G) * G;
-        const int pr0 = p == 0 ? 0 : p + 2, pr1 = p == G - 1 ? G + 3 : p + 2;
-        int sum = 0;
-        for (int pr = pr0; pr <= pr1; ++pr) sum += fold_col(acc_s + pr * pitch, c, G);
-        dst[q] = (float)sum * invS;
-    }
-}
-
 // Sum of the partial grids part[0 .. np) at the 32 consecutive nodes q0 + lane
 // of this block: warp w adds the partials of its chunk [np w / nw, np (w+1) / nw)
 // in order, warp 0 then adds the chunk sums in order (a fixed order, with
@@ -1046,24 +844,11 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
     a.dLdw = dL_dw;
     a.part = static_cast<float*>(ws);
     a.out = dL_dsos;
-    if (pl.nbands == 1 && pl.narrow && kWalkAdjoint) {
-        // one lane per ray, cell sums in registers (every sample in one shared-memory band)
-        const int G = g->sos_g, nblk32 = (g->n_t + 31) / 32;
-        const size_t smem = 2 * sizeof(float) * (size_t)(G + 4) * pad_pitch(G) +
-                            sizeof(float) * 32 * (32 * kRayPar + 33);
-        const long long want = 2LL * pl.nb_adj * 32;                   // about two items per warp
-        const int nparts = (int)std::max(1LL, std::min(8LL, (want + (long long)pt->n * nblk32 - 1) /
-                                                                  ((long long)pt->n * nblk32)));
-        PACT_TRY(ensure_smem((const void*)rays_adj_walk_kernel, smem, "sos_to_delays_adj: shared memory attribute"));
-        if (launch_pdl(rays_adj_walk_kernel, dim3(pl.nb_adj), dim3(1024), smem, st, a, nparts) != cudaSuccess)
-            return check_launch("sos_to_delays_adj kernel");
-    } else {
-        auto adj = pl.nbands == 1 ? (pl.narrow ? rays_adj_kernel<true, true> : rays_adj_kernel<true, false>)
-                                  : (pl.narrow ? rays_adj_kernel<false, true> : rays_adj_kernel<false, false>);
-        PACT_TRY(ensure_smem((const void*)adj, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
-        if (launch_pdl(adj, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands) != cudaSuccess)
-            return check_launch("sos_to_delays_adj kernel");
-    }
+    auto adj = pl.nbands == 1 ? (pl.narrow ? rays_adj_kernel<true, true> : rays_adj_kernel<true, false>)
+                              : (pl.narrow ? rays_adj_kernel<false, true> : rays_adj_kernel<false, false>);
+    PACT_TRY(ensure_smem((const void*)adj, pl.smem_adj, "sos_to_delays_adj: shared memory attribute"));
+    if (launch_pdl(adj, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands) != cudaSuccess)
+        return check_launch("sos_to_delays_adj kernel");
     PACT_TRY(check_launch("sos_to_delays_adj kernel"));
     // one partial grid per CTA: a single fixed-order sum
     if (launch_pdl(reduce_parts_kernel, dim3((GG + 31) / 32), dim3(256), 0, st, a.part, pl.nparts, GG, dL_dsos,
