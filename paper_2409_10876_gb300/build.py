@@ -30,17 +30,14 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpact")
 
 
-def _flags(debug: bool):
-    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                "--use_fast_math" if False else "-ftz=false", "-prec-div=true", "-prec-sqrt=true"]
-    if debug:
-        f += ["-DPACT_DEBUG=1"]
-    return f
+def _flags():
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+                   "-ftz=false", "-prec-div=true", "-prec-sqrt=true"]
 
 
-def _compile(src: str, debug: bool, verbose: bool) -> str:
+def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".o"))
-    cmd = [nvcc(), "-c", src, "-o", obj] + _flags(debug)
+    cmd = [nvcc(), "-c", src, "-o", obj] + _flags()
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,14 +60,14 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(force: bool = False, debug: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     """Compiles and links libpact.so if any source is newer; returns its path."""
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, debug, verbose), srcs))
+        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -305,9 +305,11 @@ def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: fl
     stream and read while the next iteration runs, so the read-back does not
     stall the GPU.  Every loss is checked: a non-finite loss, or one above
     `explode` times the first, restores the last state whose loss was good
-    (a device snapshot taken every `snapshot_every` iterations), divides the
-    learning rate by 1/lr_decay and continues from there; after
-    `max_restarts` restarts the call raises PactError."""
+    (a device snapshot taken every `snapshot_every` iterations; the initial
+    state and the last four are kept, and a restart that fails again within
+    one interval goes one snapshot further back), multiplies the learning
+    rate by `lr_decay` and continues from there; after `max_restarts`
+    restarts the call raises PactError (PACT_ERR_NONFINITE)."""
     dev = pb.device
     stack = stack_host.to(dev, non_blocking=True)
     Y = pact.patch_fft(pb, stack)
@@ -318,7 +320,7 @@ def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: fl
     host = torch.empty(2, dtype=torch.float32, pin_memory=True)      # one slot per iteration in flight
     done = [torch.cuda.Event(), torch.cuda.Event()]
     stream = torch.cuda.current_stream(dev)
-    good = (0, rec.state())                       # (iteration, state) whose loss was checked
+    goods = [(0, rec.state())]                    # (iteration, state) whose loss was checked, oldest first
     pending = None                                # snapshot whose loss is not read yet
     L0 = None
     it = 0
@@ -332,13 +334,18 @@ def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: fl
             raise pact.PactError(f"recover: {reason} at iteration {at}; {max_restarts} restarts did not help",
                                  pact.PACT_ERR_NONFINITE)
         torch.cuda.synchronize(dev)
+        # a state whose loss was finite can still be non-physical (a negative
+        # speed gives a NaN gradient): if the last restart from it failed
+        # within one snapshot interval, go one snapshot further back
+        if restarts and len(goods) > 1 and at - goods[-1][0] <= snapshot_every:
+            goods.pop()
         rec.lr *= lr_decay
-        rec.set_state(good[1])
+        rec.set_state(goods[-1][1])
         if graph:
             rec.capture()
         restarts.append((at, reason, rec.lr))
-        del hist[good[0]:]
-        it, pending = good[0], None
+        del hist[goods[-1][0]:]
+        it, pending = goods[-1][0], None
 
     while it < iters:
         if it % snapshot_every == 0:
@@ -356,7 +363,9 @@ def recover(pb: "pact.Problem", stack_host: torch.Tensor, d, eps: float, lam: fl
                 continue
             hist.append(L)
             if pending is not None and pending[0] == it - 1:
-                good, pending = pending, None
+                goods.append(pending)
+                del goods[1:-4]                   # the initial state and the last four
+                pending = None
         it += 1
         if it == iters:                           # the last iteration's loss
             done[(iters - 1) & 1].synchronize()
