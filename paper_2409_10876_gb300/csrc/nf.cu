@@ -34,7 +34,6 @@ constexpr int kF = 64;      // Fourier features
 constexpr int kH = 128;     // hidden width
 constexpr int kL = 4;       // hidden layers
 constexpr int kRows = 128;  // nodes per CTA (one TMEM lane each)
-constexpr int kThreads = 256;   // two threads per node: warps w and w + 4 split the units
 
 __host__ __device__ constexpr int in_dim(int l) { return l == 1 ? kF : kH; }
 __host__ __device__ constexpr int off_w(int l) { return l == 1 ? 0 : kH * kF + kH + (l - 2) * (kH * kH + kH); }
@@ -79,23 +78,6 @@ __device__ __forceinline__ void features(const NfArgs& a, int row, float (&f)[kF
     }
 }
 
-// Features 32 hf .. 32 hf + 31 of node `row` (frequencies 8 hf .. 8 hf + 7).
-__device__ __forceinline__ void features_half(const NfArgs& a, int row, int hf, float (&f)[kF / 2]) {
-    const int p = row / a.G, q = row - (row / a.G) * a.G;
-    const float x = (q - 0.5f * (a.G - 1)) / a.G, y = (p - 0.5f * (a.G - 1)) / a.G;
-#pragma unroll
-    for (int l = 0; l < 8; ++l) {
-        float sx, cx, sy, cy;
-        const float fr = a.freqs[8 * hf + l];
-        sincospif(2.f * fr * x, &sx, &cx);
-        sincospif(2.f * fr * y, &sy, &cy);
-        f[4 * l + 0] = sx;
-        f[4 * l + 1] = cx;
-        f[4 * l + 2] = sy;
-        f[4 * l + 3] = cy;
-    }
-}
-
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
@@ -124,10 +106,6 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Waits until at most N of this thread's committed copy groups are pending.
-template <int N>
-__device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // W [kH x K] (row-major, 16-byte aligned) into a K-major tile by asynchronous
 // 16-byte copies; the caller waits with cp_wait_all and a barrier.
@@ -160,7 +138,7 @@ __global__ void nf_cast_kernel(const float* params, __nv_bfloat16* wbf) {
     wbf[i] = __float2bfloat16_rn(is_w ? params[i] : 0.f);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) nf_fwd_kernel(const NfArgs a) {
+__global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* A0 = sm;                                 // features  [128 x 64]   16 KB
     unsigned char* Hb[2] = {sm + 16384, sm + 16384 + kTileBytes};   // layer outputs  2 x 32 KB
@@ -169,24 +147,20 @@ __global__ void __launch_bounds__(kThreads, 1) nf_fwd_kernel(const NfArgs a) {
     for (int l = 1; l < kL; ++l) Wt[l] = Wt[0] + 16384 + (l - 1) * kTileBytes;
     __shared__ float bias_s[kL][kH];
     __shared__ float w5_s[kH];
-    __shared__ float z5_s[kThreads];
     __shared__ uint32_t tmem_s;
     __shared__ __align__(8) uint64_t bar;
-    // warps w and w + 4 serve the same 32 nodes (TMEM lanes 32 (w % 4) ..) and
-    // split every per-node loop over units between them
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nd = tid & (kRows - 1), hf = tid >> 7;
-    const int row = blockIdx.x * kRows + nd;
+    const int row = blockIdx.x * kRows + tid;
     const bool valid = row < a.rows;
 
     for (int l = 1; l <= kL; ++l) load_w(Wt[l - 1], a.wbf + off_w(l), in_dim(l));
     for (int c = tid; c < kL * kH; c += blockDim.x) bias_s[c / kH][c % kH] = a.params[off_b(c / kH + 1) + c % kH];
     for (int c = tid; c < kH; c += blockDim.x) w5_s[c] = __bfloat162float(a.wbf[kOffW5 + c]);
     {
-        float f[kF / 2];
-        features_half(a, valid ? row : 0, hf, f);
+        float f[kF];
+        features(a, valid ? row : 0, f);
 #pragma unroll
-        for (int k0 = 0; k0 < kF / 2; k0 += 8) st8(A0, nd, hf * (kF / 2) + k0, kF, f + k0);
+        for (int k0 = 0; k0 < kF; k0 += 8) st8(A0, tid, k0, kF, f + k0);
     }
     cp_wait_all();                                  // the weight tiles
     if (warp == 0) umma::tmem_alloc(&tmem_s, 128);
@@ -199,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) nf_fwd_kernel(const NfArgs a) {
     __syncthreads();
     umma::fence_after();
     const uint32_t tmem = tmem_s;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     bool ok = true;
     float z5 = 0.f;
     for (int l = 1; l <= kL; ++l) {
@@ -214,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) nf_fwd_kernel(const NfArgs a) {
         }
         ok = wait_bar(&bar, (uint32_t)((l - 1) & 1), a.status, a.limit_ns) && ok;
         umma::fence_after();
-        for (int c0 = hf * (kH / 2); c0 < (hf + 1) * (kH / 2); c0 += 32) {
+        for (int c0 = 0; c0 < kH; c0 += 32) {
             float v[32];
             umma::ld32(tmem + lane_base + c0, v);
 #pragma unroll
@@ -224,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) nf_fwd_kernel(const NfArgs a) {
                 if (l == kL) z5 = fmaf(v[j], w5_s[c0 + j], z5);
             }
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) st8(out, nd, c0 + j, kH, v + j);
+            for (int j = 0; j < 32; j += 8) st8(out, tid, c0 + j, kH, v + j);
         }
         umma::fence_smem_to_async();
         umma::fence_before();
@@ -235,162 +209,137 @@ __global__ void __launch_bounds__(kThreads, 1) nf_fwd_kernel(const NfArgs a) {
         uint4* dst = reinterpret_cast<uint4*>(a.htiles + ((size_t)blockIdx.x * kL + (l - 1)) * kTileBytes);
         for (int c = tid; c < kTileBytes / 16; c += blockDim.x) dst[c] = src[c];
     }
-    z5_s[tid] = z5;
-    __syncthreads();
-    if (hf == 0) {
-        const float t = tanhf((z5_s[nd] + z5_s[nd + kRows]) + a.params[kOffB5]);   // the two halves in order
-        if (valid) {
-            a.t5[row] = ok ? t : __int_as_float(0x7fc00000);
-            const bool inside = a.mask ? a.mask[row] != 0 : true;
-            a.sos[row] = inside ? (ok ? fmaf(a.v_half, t, a.v_mid) : __int_as_float(0x7fc00000)) : a.v_bg;
-        }
+    const float t = tanhf(z5 + a.params[kOffB5]);
+    if (valid) {
+        a.t5[row] = ok ? t : __int_as_float(0x7fc00000);
+        const bool inside = a.mask ? a.mask[row] != 0 : true;
+        a.sos[row] = inside ? (ok ? fmaf(a.v_half, t, a.v_mid) : __int_as_float(0x7fc00000)) : a.v_bg;
     }
     umma::fence_before();
     __syncthreads();
     if (warp == 0) umma::tmem_dealloc(tmem, 128);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) nf_bwd_kernel(const NfArgs a) {
+__global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     // dz and h_{l-1} are K-major tiles [nodes x units]; read as MN-major they
-    // are the transposed operands dz^T and h^T of the weight-gradient GEMM.
-    // h_{l-1} and W_l come in two buffers: layer l - 1's tiles load while
-    // layer l is computed.
-    unsigned char* dzA = sm;                                        // dz [128 nodes x out]  32 KB
-    unsigned char* Hr[2] = {sm + kTileBytes, sm + 2 * kTileBytes};  // h_{l-1} [128 nodes x in]
-    unsigned char* WT[2] = {sm + 3 * kTileBytes, sm + 4 * kTileBytes};   // W_l [out x in]
+    // are the transposed operands dz^T and h^T of the weight-gradient GEMM
+    unsigned char* dzA = sm;                      // dz         [128 nodes x out]    32 KB
+    unsigned char* WT = sm + kTileBytes;          // W_l        [out x in]           32 KB
+    unsigned char* Hr = sm + 2 * kTileBytes;      // h_{l-1}    [128 nodes x in]     32 KB
     __shared__ float g5_s[kRows];
     __shared__ float w5_s[kH];
-    __shared__ float red_s[kThreads];
     __shared__ uint32_t tmem_s;
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nd = tid & (kRows - 1), hf = tid >> 7;   // node (TMEM lane) and half of the units / nodes
-    const int row = blockIdx.x * kRows + nd;
+    const int row = blockIdx.x * kRows + tid;
     const bool valid = row < a.rows;
     float* part = a.part + (size_t)blockIdx.x * kPartStride;   // 16-byte aligned rows for float4 stores
     const unsigned char* tiles = a.htiles + (size_t)blockIdx.x * kL * kTileBytes;
 
-    // h4 into Hr[0] (group 1); h3 and W4, the operands of layer 4, into Hr[1], WT[1] (group 2)
-    load_tile(Hr[0], tiles + (size_t)(kL - 1) * kTileBytes);
-    cp_commit();
-    load_tile(Hr[1], tiles + (size_t)(kL - 2) * kTileBytes);
-    load_w(WT[1], a.wbf + off_w(kL), kH);
-    cp_commit();
     // output layer: g5 = dL/dv dv/dz = dL/dv v_half (1 - t^2), inside the mask
-    if (hf == 0) {
-        float g5 = 0.f;
-        if (valid && (a.mask ? a.mask[row] != 0 : true)) {
-            const float t = a.t5[row];
-            g5 = a.dL_dsos[row] * a.v_half * (1.f - t * t);
-        }
-        g5_s[nd] = g5;
-        w5_s[nd] = __bfloat162float(a.wbf[kOffW5 + nd]);
+    float g5 = 0.f;
+    if (valid && (a.mask ? a.mask[row] != 0 : true)) {
+        const float t = a.t5[row];
+        g5 = a.dL_dsos[row] * a.v_half * (1.f - t * t);
     }
+    // h4 of this CTA (operand layout) -> Hr
+    load_tile(Hr, tiles + (size_t)(kL - 1) * kTileBytes);
+    cp_wait_all();
     if (warp == 0) umma::tmem_alloc(&tmem_s, 256);
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_init_fence();
     }
-    cp_wait_group<1>();
     __syncthreads();
-    // dz4 = g5 w5 (h4 > 0) for node nd, units of this half; dW5 = sum_nodes g5 h4
-    // for unit nd over this half's nodes, db5 = sum g5 (fixed orders)
-    {
-        const float g5 = g5_s[nd];
-        for (int c = hf * (kH / 2); c < (hf + 1) * (kH / 2); ++c) {
-            const float h = bfv(Hr[0], nd, c, kH);
-            st1(dzA, nd, c, kH, h > 0.f ? g5 * w5_s[c] : 0.f);
-        }
-        float s5 = 0.f;
-        for (int r = hf * (kRows / 2); r < (hf + 1) * (kRows / 2); ++r) s5 = fmaf(g5_s[r], bfv(Hr[0], r, nd, kH), s5);
-        red_s[tid] = s5;
+    // dz4 = g5 w5 (h4 > 0) for this node; dW5 = sum_nodes g5 h4 for column `tid`
+    // and db5 = sum g5, both in a fixed order
+    g5_s[tid] = g5;
+    w5_s[tid] = __bfloat162float(a.wbf[kOffW5 + tid]);
+    __syncthreads();
+    for (int c = 0; c < kH; ++c) {
+        const float h = bfv(Hr, tid, c, kH);
+        st1(dzA, tid, c, kH, h > 0.f ? g5 * w5_s[c] : 0.f);
     }
-    __syncthreads();
-    if (hf == 0) {
-        part[kOffW5 + nd] = red_s[nd] + red_s[nd + kRows];
+    {
+        float s = 0.f;
+        for (int r = 0; r < kRows; ++r) s = fmaf(g5_s[r], bfv(Hr, r, tid, kH), s);
+        part[kOffW5 + tid] = s;
         if (tid == 0) {
             float b = 0.f;
             for (int r = 0; r < kRows; ++r) b += g5_s[r];
             part[kOffB5] = b;
         }
     }
-    __syncthreads();                                   // red_s is rewritten below
+    __syncthreads();
 
     const uint32_t tmem = tmem_s;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     uint32_t phase = 0;
-    int buf = 1;
     for (int l = kL; l >= 1; --l) {
         const int K_in = in_dim(l);
-        // db_l = column sums of dz_l: column nd over this half's nodes (combined below)
+        // db_l = column sums of dz_l (column `tid` of the dz tile)
         {
-            float sb = 0.f;
-            for (int r = hf * (kRows / 2); r < (hf + 1) * (kRows / 2); ++r) sb += bfv(dzA, r, nd, kH);
-            red_s[tid] = sb;
+            float s = 0.f;
+            for (int r = 0; r < kRows; ++r) s += bfv(dzA, r, tid, kH);
+            part[off_b(l) + tid] = s;
         }
-        // prefetch the operands of layer l - 1 into the other buffers (their
-        // previous contents, layer l + 1's, are no longer read)
-        if (l > 2) {
-            load_tile(Hr[buf ^ 1], tiles + (size_t)(l - 3) * kTileBytes);
-            load_w(WT[buf ^ 1], a.wbf + off_w(l - 1), kH);
-        }
-        cp_commit();
-        if (l == 1) {
-            float f[kF / 2];
-            features_half(a, valid ? row : 0, hf, f);
+        // h_{l-1} (B operand of dW, read MN-major) and, for l > 1, W_l^T (B operand of dh)
+        if (l > 1) {
+            load_tile(Hr, tiles + (size_t)(l - 2) * kTileBytes);
+            load_w(WT, a.wbf + off_w(l), kH);          // W_l [out x in] K-major = W_l^T read MN-major
+            cp_wait_all();
+        } else {
+            float f[kF];
+            features(a, valid ? row : 0, f);
 #pragma unroll
-            for (int k0 = 0; k0 < kF / 2; k0 += 8) st8(Hr[buf], nd, hf * (kF / 2) + k0, kF, f + k0);
+            for (int k0 = 0; k0 < kF; k0 += 8) st8(Hr, tid, k0, kF, f + k0);
         }
-        cp_wait_group<1>();                            // this layer's tiles (the prefetch may still run)
         umma::fence_smem_to_async();
         umma::fence_before();
         __syncthreads();
         umma::fence_after();
-        if (hf == 0) part[off_b(l) + nd] = red_s[nd] + red_s[nd + kRows];
         if (tid == 0) {
             // dW_l [out x in] = dz^T [out x nodes] * (h^T [in x nodes])^T, both operands
             // the K-major node tiles read MN-major (M = out, N = in, K = nodes)
             for (int kk = 0; kk < kRows / 16; ++kk)
-                umma::mma(tmem, umma::mn_slice(dzA, kH, kk), umma::mn_slice(Hr[buf], K_in, kk),
+                umma::mma(tmem, umma::mn_slice(dzA, kH, kk), umma::mn_slice(Hr, K_in, kk),
                           umma::idesc_bf16_mn(128, K_in), kk > 0);
             // dh_{l-1} [nodes x in] = dz [nodes x out] * (W^T [in x out])^T
             if (l > 1)
                 for (int kk = 0; kk < kH / 16; ++kk)
-                    umma::mma(tmem + 128, umma::kslice(dzA, kH, kk), umma::mn_slice(WT[buf], kH, kk),
+                    umma::mma(tmem + 128, umma::kslice(dzA, kH, kk), umma::mn_slice(WT, kH, kk),
                               umma::idesc_bf16(128, kH) | (1u << 16), kk > 0);
             umma::commit(&bar);
         }
         wait_bar(&bar, phase, a.status, a.limit_ns);
         phase ^= 1u;
         umma::fence_after();
-        // weight-gradient row nd (TMEM lane = output unit), this half's columns
-        for (int c0 = hf * (K_in / 2); c0 < (hf + 1) * (K_in / 2); c0 += 32) {
+        // weight-gradient row `tid` (TMEM lane = output unit)
+        for (int c0 = 0; c0 < K_in; c0 += 32) {
             float v[32];
             umma::ld32(tmem + lane_base + c0, v);
-            float4* dst = reinterpret_cast<float4*>(part + off_w(l) + nd * K_in + c0);
+            float4* dst = reinterpret_cast<float4*>(part + off_w(l) + tid * K_in + c0);
 #pragma unroll
             for (int j = 0; j < 32; j += 4) dst[j / 4] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
         if (l > 1) {
-            // dz_{l-1} = dh (h_{l-1} > 0), node nd, this half's units
-            for (int c0 = hf * (kH / 2); c0 < (hf + 1) * (kH / 2); c0 += 32) {
+            // dz_{l-1} = dh (h_{l-1} > 0), node `tid`
+            for (int c0 = 0; c0 < kH; c0 += 32) {
                 float v[32];
                 umma::ld32(tmem + 128 + lane_base + c0, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float h = bfv(Hr[buf], nd, c0 + j, kH);
+                    const float h = bfv(Hr, tid, c0 + j, kH);
                     const float dz = h > 0.f ? v[j] : 0.f;
-                    st1(dzA, nd, c0 + j, kH, dz);
+                    st1(dzA, tid, c0 + j, kH, dz);
                 }
             }
         }
         umma::fence_before();
         __syncthreads();
         umma::fence_after();
-        buf ^= 1;
     }
-    cp_wait_group<0>();
     umma::fence_before();
     __syncthreads();
     if (warp == 0) umma::tmem_dealloc(tmem, 256);
@@ -430,7 +379,7 @@ NfPlan nf_plan(const pact_geometry* g) {
     o += 256;
     p.total = o;
     p.smem_fwd = 16384 + 2 * kTileBytes + 16384 + (kL - 1) * kTileBytes;
-    p.smem_bwd = 5 * kTileBytes;
+    p.smem_bwd = 3 * kTileBytes;
     return p;
 }
 
@@ -489,7 +438,7 @@ extern "C" pact_status pact_nf_forward(const pact_geometry* g, const float* para
     nf_cast_kernel<<<(kWbf + 255) / 256, 256, 0, st>>>(params, a.wbf);
     PACT_TRY(check_launch("nf_forward: weight cast"));
     PACT_TRY(ensure_smem((const void*)nf_fwd_kernel, pl.smem_fwd, "nf_forward: shared memory attribute"));
-    nf_fwd_kernel<<<pl.nct, kThreads, pl.smem_fwd, st>>>(a);
+    nf_fwd_kernel<<<pl.nct, kRows, pl.smem_fwd, st>>>(a);
     return check_launch("nf_forward kernel");
 }
 
@@ -503,7 +452,7 @@ extern "C" pact_status pact_nf_backward(const pact_geometry* g, const float* par
     a.dL_dsos = dL_dsos;
     cudaStream_t st = as_stream(stream);
     PACT_TRY(ensure_smem((const void*)nf_bwd_kernel, pl.smem_bwd, "nf_backward: shared memory attribute"));
-    nf_bwd_kernel<<<pl.nct, kThreads, pl.smem_bwd, st>>>(a);
+    nf_bwd_kernel<<<pl.nct, kRows, pl.smem_bwd, st>>>(a);
     PACT_TRY(check_launch("nf_backward kernel"));
     nf_reduce_kernel<<<(kNParam + 255) / 256, 256, 0, st>>>(a.part, pl.nct, dL_dparams, accumulate);
     return check_launch("nf_backward reduction");
