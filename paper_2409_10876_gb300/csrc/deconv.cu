@@ -466,18 +466,6 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         }
         int kt = kt_first, tried = 0, unit = -1;
         const int KT = a.KT;
-        // claim cl of tile t: the tile's last quarter of patches is claimed as
-        // two half units (112 bins each), so that the last wave is short.
-        // Returns the unit code ((t N + i) << 2 | kind: 0 full, 2/3 half 0/1) or -1.
-        const int Nh = N >= 8 ? N / 4 : 0;
-        auto claim_unit = [&](int t, int cl) -> int {
-            const int s_t = (n_static - t + KT - 1) / KT;          // the tile's fixed (full) claims
-            const int split = min(kTile, a.F - t * kTile) > kTile / 2 ? max(s_t, N - Nh) : N;
-            if (cl < split) return (t * N + cl) << 2;
-            const int r = cl - split;
-            if (r >= 2 * (N - split)) return -1;
-            return ((t * N + split + (r >> 1)) << 2) | 2 | (r & 1);
-        };
         for (int q = 0;; ++q) {
             const int s = q % kStages, lu = q / nc, c = q - lu * nc;
             if (q >= kStages &&                       // consumers released chunk q - kStages
@@ -487,11 +475,14 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             }
             if (c == 0) {                             // claim the next unit
                 const int g = (int)blockIdx.x + lu * (int)gridDim.x;
-                unit = g < n_static ? ((g % KT) * N + g / KT) << 2 : -1;   // the first ones are fixed
+                unit = g < n_static ? (g % KT) * N + g / KT : -1;   // the first ones are fixed
                 while (unit < 0 && tried < KT) {
                     // tile kt's first (n_static - kt + KT - 1) / KT claims are the fixed ones
-                    unit = claim_unit(kt, (n_static - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1));
-                    if (unit >= 0) break;
+                    const int cl = (n_static - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
+                    if (cl < N) {
+                        unit = kt * N + cl;
+                        break;
+                    }
                     kt = kt + 1 == a.KT ? 0 : kt + 1;
                     ++tried;
                 }
@@ -501,11 +492,9 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                     return;
                 }
             }
-            const int ub = unit >> 2, ukt = ub / N, i = ub - ukt * N;
-            const int hoff = (unit & 2) ? (unit & 1) * (kTile / 2) : 0;   // bins of a half unit start here
-            const int k0 = ukt * kTile + hoff;
-            const int nbins = min((unit & 2) ? kTile / 2 : kTile, a.F - k0);
-            const uint32_t bytes = (uint32_t)(nbins * sizeof(float2));
+            const int ukt = unit / N, i = unit - ukt * N;
+            const int k0 = ukt * kTile;
+            const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
             const int j0 = c * kCh, rows = min(kCh, M - j0);
             const int slot = lu % kSlots;
             if (c == 0 && lu >= kSlots &&             // consumers read the slot's previous unit
@@ -517,11 +506,11 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)rows + (c == 0 ? bytes + wbytes : 0u));
             const float2* src = a.Y + ((size_t)i * M + j0) * a.F + k0;
-            float2* dst = stage + (size_t)s * kCh * kTile + hoff;
+            float2* dst = stage + (size_t)s * kCh * kTile;
             for (int r = 0; r < rows; ++r)
                 tma_bulk_g2s(dst + (size_t)r * kTile, src + (size_t)r * a.F, bytes, &full[s]);
             if (c == 0) {
-                tma_bulk_g2s(slot_lut + (size_t)slot * kTile + hoff, a.lut + (size_t)i * a.F + k0, bytes, &full[s]);
+                tma_bulk_g2s(slot_lut + (size_t)slot * kTile, a.lut + (size_t)i * a.F + k0, bytes, &full[s]);
                 tma_bulk_g2s(slot_w + (size_t)slot * n_t, a.w + (size_t)i * n_t, wbytes, &full[s]);
             }
         }
@@ -544,11 +533,9 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     int u = ring[0];
     if (!bar_and(1, kTile, ok)) u = -1;
     for (int lu = 0; u >= 0; ++lu) {
-        const int ub = u >> 2, kt = ub / N, i = ub - kt * N, kind = u & 3;
+        const int kt = u / N, i = u - kt * N;
         const int k = kt * kTile + tid;
         const bool valid = k < a.F;
-        // a half unit (kind 2, 3) covers the tile's bins [112 h, 112 h + 112), h = kind & 1
-        const bool act = valid && (kind < 2 || tid / (kTile / 2) == (kind & 1));
         const int buf = lu & 1;
         if (kt != kt_loaded) {                       // per-bin tables of this tile
             kt_loaded = kt;
@@ -568,7 +555,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         }
         // the two lookups of w of Eq. 4, from the unit's shared slot (landed with its first chunk)
         const int slot = lu % kSlots;
-        const float2 tr = act ? slot_lut[slot * kTile + tid] : make_float2(0.f, 0.f);
+        const float2 tr = valid ? slot_lut[slot * kTile + tid] : make_float2(0.f, 0.f);
         const float* wr = slot_w + (size_t)slot * n_t;
         const float fla = floorf(tr.x), flb = floorf(tr.y);
         const float fa = tr.x - fla, fb = tr.y - flb;
@@ -650,7 +637,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         Ey += Eyo;
 
         float contrib = 0.f, gW1 = 0.f, gW2 = 0.f;
-        if (act) {
+        if (valid) {
             const float fm = bt.x, om = bt.y;
             const float2 C2 = make_float2(bt.z, bt.w);
             const float Mf = (float)M, eps = a.eps;
@@ -727,12 +714,10 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             }
             if (!all_ok && tid == 0) atomicAdd(dst, nan);   // a copy never arrived: poison the gradient
         }
-        if (tid == 0) {                              // slots [i][kt][2]: a full unit fills both
+        if (tid == 0) {
             float acc = 0.f;
             for (int q = 0; q < kTile / 32; ++q) acc += lsum_s[buf][q];   // fixed order: deterministic
-            float* pl = a.part_loss + ((size_t)i * a.KT + kt) * 2;
-            pl[kind < 2 ? 0 : (kind & 1)] = all_ok ? acc : nan;
-            if (kind < 2) pl[1] = 0.f;
+            a.part_loss[(size_t)i * a.KT + kt] = all_ok ? acc : nan;
         }
         u = all_ok ? u_next : -1;
     }
@@ -763,20 +748,19 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         return;
     }
     if (!a.loss && !a.loss_pp) return;
-    // per patch, the tiles' partials in order; 16 loads in flight per round (two
-    // rounds for P <= 84), two patches per pass, so the tail pays little L2 latency
+    // per patch, the tiles' partials in order; 16 loads in flight per round (one
+    // round for P <= 84), two patches per pass, so the tail pays little L2 latency
     float tot = 0.f;
     for (int i0 = tid; i0 < N; i0 += 2 * kTile) {
         float acc[2] = {0.f, 0.f};
-        const int ns = 2 * a.KT;                                  // two slots per tile
-        for (int t = 0; t < ns; t += 16) {
+        for (int t = 0; t < a.KT; t += 16) {
             float v[2][16];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int i = i0 + h * kTile;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    v[h][k] = (i < N && t + k < ns) ? __ldcg(a.part_loss + (size_t)i * ns + t + k) : 0.f;
+                    v[h][k] = (i < N && t + k < a.KT) ? __ldcg(a.part_loss + (size_t)i * a.KT + t + k) : 0.f;
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h)
@@ -837,7 +821,7 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     const int F = pt->p * (pt->p / 2 + 1);
     p.KT = (F + kBins - 1) / kBins;
     p.KTs = (F + kTile - 1) / kTile;
-    p.scratch = align_up((size_t)pt->n * std::max(p.KT, 2 * p.KTs) * sizeof(float), 256);
+    p.scratch = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
     // sync block: [KTs] tile claim counters, [1] done ticket, [1] status word, [1] stall flag (test
     // hook), [1] launch-failed flag
     p.nsync = p.KTs + 4;
