@@ -155,59 +155,150 @@ __global__ void __launch_bounds__(256, 3) patch_fft_kernel(Geo g, int P, int M, 
     }
 }
 
+// Shared memory of stitch_kernel: the patch's half spectrum X and the column
+// pass output Z, both [P][HS] float2 (HS = fft_hs(P): float4 reads of two
+// columns), and the twiddles exp(+2 pi j t / P).
+inline size_t stitch_smem(int P) { return ((size_t)2 * P * fft_hs(P) + P) * sizeof(float2); }
+
+// Register tiles of the inverse: the column pass gives a thread 8 rows x 2
+// half-spectrum columns (as the forward column pass), the row pass 4 rows x 4
+// column pairs (b, P - b).
+constexpr int kSA = 4, kSB = 4;
+
 // Inverse half-spectrum DFT of patch i = blockIdx.x, channel j = blockIdx.y
 // (X [N][m][P][P/2+1]), then scatter-add into the channel's numerator image
 // and, for channel 0, into the window-sum image.
+// Column pass: Z[a][v] = sum_u X[u][v] exp(+2 pi j a u / P), pairing u with
+// P - u as the forward column pass does.  Row pass: every row of Z is the
+// half of a Hermitian row spectrum, so with C = sum_v c_v Re Z[a][v] cos(2 pi v b / P)
+// and S = sum_v c_v Im Z[a][v] sin(2 pi v b / P) (c_v = 1 at v = 0, P/2, else 2)
+// the pixel pair is x[a][b] = (C - S) / P, x[a][P - b] = (C + S) / P: one set
+// of sums gives both.
 __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* centres, float inv_2s2,
                                                      const float2* X, float* num, float* den) {
-    extern __shared__ float sm[];
-    const int half = P / 2 + 1;
-    float2* Z = reinterpret_cast<float2*>(sm);     // [P*half]
-    float2* tw = Z + P * half;                     // [P]: exp(+2 pi j t / P)
-    float2* Xs = tw + P;                           // [P*half]: the patch's half spectrum
-    const int i = blockIdx.x;
+    extern __shared__ float4 sm4[];
+    const int half = P / 2 + 1, h2 = P / 2, HS = fft_hs(P);
+    float2* Xs = reinterpret_cast<float2*>(sm4);   // [P][HS]
+    float2* Z = Xs + (size_t)P * HS;               // [P][HS]
+    float2* tw = Z + (size_t)P * HS;               // [P]: exp(+2 pi j t / P)
+    const int i = blockIdx.x, j = blockIdx.y, m = gridDim.y;
     const int2 c = centres[i];
     const int r0 = c.x - P / 2, c0 = c.y - P / 2;
-    const int j = blockIdx.y, m = gridDim.y;
     const float2* Xi = X + ((size_t)i * m + j) * P * half;
     for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = cis_pi(2.f * t / P);
-    for (int q = threadIdx.x; q < P * half; q += blockDim.x) Xs[q] = Xi[q];
-    __syncthreads();
-    num += (size_t)j * g.H * g.W;
     for (int q = threadIdx.x; q < P * half; q += blockDim.x) {
-        const int a = q / half, v = q - (q / half) * half;
-        float re = 0.f, im = 0.f;
-        int idx = 0;
-        for (int u = 0; u < P; ++u) {
-            const float2 xv = Xs[u * half + v];
-            const float2 t = tw[idx];
-            re = fmaf(xv.x, t.x, fmaf(-xv.y, t.y, re));
-            im = fmaf(xv.x, t.y, fmaf(xv.y, t.x, im));
-            idx += a;
-            if (idx >= P) idx -= P;
+        const int u = q / half, v = q - (q / half) * half;
+        Xs[(size_t)u * HS + v] = Xi[q];
+    }
+    if (HS > half)
+        for (int u = threadIdx.x; u < P; u += blockDim.x) Xs[(size_t)u * HS + half] = make_float2(0.f, 0.f);
+    __syncthreads();
+    // column pass
+    const int nv2 = (half + kCV - 1) / kCV;
+    for (int t = threadIdx.x; t < ((P + kCU - 1) / kCU) * nv2; t += blockDim.x) {
+        const int a0 = (t / nv2) * kCU, v0 = (t - (t / nv2) * nv2) * kCV;
+        int aa[kCU], id[kCU];
+        float re[kCU][2], im[kCU][2];
+        const float4 q0 = *reinterpret_cast<const float4*>(Xs + v0);
+        const float4 qh = *reinterpret_cast<const float4*>(Xs + (size_t)h2 * HS + v0);
+#pragma unroll
+        for (int k = 0; k < kCU; ++k) {
+            aa[k] = min(a0 + k, P - 1);
+            id[k] = aa[k];
+            const float sg = (aa[k] & 1) ? -1.f : 1.f;
+            re[k][0] = fmaf(sg, qh.x, q0.x);
+            im[k][0] = fmaf(sg, qh.y, q0.y);
+            re[k][1] = fmaf(sg, qh.z, q0.z);
+            im[k][1] = fmaf(sg, qh.w, q0.w);
         }
-        Z[q] = make_float2(re, im);
+        for (int u = 1; u < h2; ++u) {
+            const float4 p = *reinterpret_cast<const float4*>(Xs + (size_t)u * HS + v0);
+            const float4 mm = *reinterpret_cast<const float4*>(Xs + (size_t)(P - u) * HS + v0);
+            const float sr0 = p.x + mm.x, si0 = p.y + mm.y, dr0 = p.x - mm.x, di0 = p.y - mm.y;
+            const float sr1 = p.z + mm.z, si1 = p.w + mm.w, dr1 = p.z - mm.z, di1 = p.w - mm.w;
+#pragma unroll
+            for (int k = 0; k < kCU; ++k) {
+                const float2 w = tw[id[k]];
+                re[k][0] = fmaf(-di0, w.y, fmaf(sr0, w.x, re[k][0]));
+                im[k][0] = fmaf(dr0, w.y, fmaf(si0, w.x, im[k][0]));
+                re[k][1] = fmaf(-di1, w.y, fmaf(sr1, w.x, re[k][1]));
+                im[k][1] = fmaf(dr1, w.y, fmaf(si1, w.x, im[k][1]));
+                id[k] += aa[k];
+                if (id[k] >= P) id[k] -= P;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kCU; ++k)
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2)
+                if (a0 + k < P && v0 + c2 < half) Z[(size_t)(a0 + k) * HS + v0 + c2] = make_float2(re[k][c2], im[k][c2]);
     }
     __syncthreads();
+    // row pass and scatter: rows a0 .. a0 + 3, columns b0 .. b0 + 3 (<= P/2) and their mirrors
     const float inv_p = 1.f / P;
-    for (int q = threadIdx.x; q < P * P; q += blockDim.x) {
-        const int a = q / P, b = q - (q / P) * P;
-        const int row = r0 + a, col = c0 + b;
-        if (row < 0 || row >= g.H || col < 0 || col >= g.W) continue;
-        const float2* za = Z + a * half;
-        float s = za[0].x + ((b & 1) ? -za[P / 2].x : za[P / 2].x);
-        int idx = b;
-        float acc = 0.f;
-        for (int v = 1; v < P / 2; ++v) {
-            const float2 t = tw[idx];
-            acc = fmaf(za[v].x, t.x, fmaf(-za[v].y, t.y, acc));
-            idx += b;
-            if (idx >= P) idx -= P;
+    num += (size_t)j * g.H * g.W;
+    const int nb4 = (h2 + 1 + kSB - 1) / kSB, na4 = (P + kSA - 1) / kSA;
+    for (int t = threadIdx.x; t < na4 * nb4; t += blockDim.x) {
+        const int a0 = (t / nb4) * kSA, b0 = (t - (t / nb4) * nb4) * kSB;
+        int bb[kSB], id[kSB];
+        float C[kSA][kSB], S[kSA][kSB];
+#pragma unroll
+        for (int k = 0; k < kSB; ++k) {
+            bb[k] = min(b0 + k, h2);
+            id[k] = bb[k];
         }
-        s = fmaf(2.f, acc, s);
-        const float oa = (a - P / 2) * g.dx, ob = (b - P / 2) * g.dx;
-        atomicAdd(num + (size_t)row * g.W + col, s * inv_p);
-        if (j == 0) atomicAdd(den + (size_t)row * g.W + col, expf(-(oa * oa + ob * ob) * inv_2s2));
+#pragma unroll
+        for (int r = 0; r < kSA; ++r) {
+            const int a = min(a0 + r, P - 1);
+            const float z0 = Z[(size_t)a * HS].x, zh = Z[(size_t)a * HS + h2].x;
+#pragma unroll
+            for (int k = 0; k < kSB; ++k) {
+                C[r][k] = (bb[k] & 1) ? z0 - zh : z0 + zh;
+                S[r][k] = 0.f;
+            }
+        }
+        for (int v = 1; v < h2; ++v) {
+            float2 w[kSB];
+#pragma unroll
+            for (int k = 0; k < kSB; ++k) {
+                w[k] = tw[id[k]];
+                id[k] += bb[k];
+                if (id[k] >= P) id[k] -= P;
+            }
+#pragma unroll
+            for (int r = 0; r < kSA; ++r) {
+                const float2 zv = Z[(size_t)min(a0 + r, P - 1) * HS + v];
+#pragma unroll
+                for (int k = 0; k < kSB; ++k) {
+                    C[r][k] = fmaf(2.f * zv.x, w[k].x, C[r][k]);
+                    S[r][k] = fmaf(2.f * zv.y, w[k].y, S[r][k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kSA; ++r) {
+            const int a = a0 + r, row = r0 + a;
+            if (a >= P || row < 0 || row >= g.H) continue;
+            const float oa = (a - P / 2) * g.dx;
+#pragma unroll
+            for (int k = 0; k < kSB; ++k) {
+                const int b = b0 + k;
+                if (b > h2) continue;
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int bc = side ? P - b : b;
+                    if (side && (b == 0 || b == h2)) continue;
+                    const int col = c0 + bc;
+                    if (col < 0 || col >= g.W) continue;
+                    const float val = (side ? C[r][k] + S[r][k] : C[r][k] - S[r][k]) * inv_p;
+                    atomicAdd(num + (size_t)row * g.W + col, val);
+                    if (j == 0) {
+                        const float ob = (bc - P / 2) * g.dx;
+                        atomicAdd(den + (size_t)row * g.W + col, expf(-(oa * oa + ob * ob) * inv_2s2));
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -272,8 +363,8 @@ pact_status run_stitch(const pact_geometry* g, const pact_patches* pt, int m, co
     float* num = static_cast<float*>(ws);
     float* den = num + (size_t)m * g->img_h * g->img_w;
     if (cudaMemsetAsync(ws, 0, (size_t)(m + 1) * plane, st) != cudaSuccess) return check_launch("stitch: memset");
-    const int P = pt->p, half = P / 2 + 1;
-    const size_t shm = (size_t)(2 * P * half + P) * sizeof(float2);
+    const int P = pt->p;
+    const size_t shm = stitch_smem(P);
     PACT_TRY(ensure_smem((const void*)stitch_kernel, shm, "stitch: shared memory attribute"));
     stitch_kernel<<<dim3(pt->n, m), 256, shm, st>>>(make_geo(g), P, reinterpret_cast<const int2*>(pt->centres),
                                                     inv_two_sigma2(pt->window_fwhm),
