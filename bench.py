@@ -36,6 +36,9 @@ WORKLOAD = "pg512_ring512_p80_m32: 512x512 @0.1mm, 512-el ring R=40mm, 144 patch
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
+VARIANTS = ("neural_field", "siren_field", "das_stack", "channels", "tv_sweep", "channel_data")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -49,7 +52,16 @@ def parse():
     ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--ws-samples", type=int, default=20000, help="training stacks for the warm-start CNN")
     ap.add_argument("--ws-epochs", type=int, default=8)
-    return ap.parse_args()
+    ap.add_argument("--variants", default="all",
+                    help="comma-separated subset of " + ",".join(VARIANTS) + " (default: all)")
+    ap.add_argument("--ws-stages", default="all", choices=["all", "train"],
+                    help="'train': the warm start stops after generating the stacks and training the CNN")
+    args = ap.parse_args()
+    args.variants = list(VARIANTS) if args.variants == "all" else args.variants.split(",")
+    bad = [v for v in args.variants if v not in VARIANTS]
+    if bad:
+        ap.error(f"unknown variants {bad}")
+    return args
 
 
 def dist_env():
@@ -366,6 +378,8 @@ def run_gpu(args, cfg, case, rank, world, local):
             "roofline_rays": rays_roofline(cfg, adj_call_s * 1e3, clocks,
                                            torch.cuda.get_device_properties(dev).multi_processor_count),
             "gpu_launches": launches_per_step * args.steps,
+            "context": "paper: full NF recovery 40.3 s vs 23 min for APACT ('35x faster'), PG 113.3 s, SOS-oracle "
+                       "deconvolution 2.6 s, on an RTX A6000 in PyTorch (Table 1); no per-iteration figures",
             "wall_s_timed_region": wall,
             "loss": {"start": loss_start, "end": loss_end}}
     if clocks:
@@ -385,6 +399,8 @@ def run_gpu(args, cfg, case, rank, world, local):
                                 "one_thread": {"value": 1.0 / per1, "unit": "iters/s", "cores": 1,
                                                "sample": "one whole iteration after one untimed"},
                                 "nproc": os.cpu_count(), "cpu": cpu_model()}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["error_vs_fp64_oracle"] = oracle_errors(cfg, case, pb, dev)
     if not args.no_e2e:
         stack = synthesize_stack(pb, case, dev).cpu().pin_memory()
         iters = cfg.steps                                # one whole recovery of the configuration
@@ -406,12 +422,14 @@ def run_gpu(args, cfg, case, rank, world, local):
                                f"the stitched image copied to pinned host memory",
                        "restarts": len(r.restarts)}
     if not args.no_variants:
-        line["variants"] = {"neural_field": nf_variant(args, cfg, case, pb, Y, flush, stream),
-                            "siren_field": siren_variant(args, cfg, case, pb, Y, flush, stream),
-                            "das_stack": das_variant(dev, flush, stream),
-                            "channels": channels_variant(args, cfg, dev, flush, stream),
-                            "tv_sweep": tv_sweep_variant(args, cfg, case, pb, Y),
-                            "channel_data": channel_data_variant(args, dev, flush, stream)}
+        run = {"neural_field": lambda: nf_variant(args, cfg, case, pb, Y, flush, stream),
+               "siren_field": lambda: siren_variant(args, cfg, case, pb, Y, flush, stream),
+               "das_stack": lambda: das_variant(dev, flush, stream),
+               "channels": lambda: channels_variant(args, cfg, dev, flush, stream),
+               "tv_sweep": lambda: tv_sweep_variant(args, cfg, case, pb, Y),
+               "channel_data": lambda: channel_data_variant(args, dev, flush, stream)}
+        line["variants"] = {name: run[name]() for name in VARIANTS if name in args.variants}
+    if "channel_data" in line.get("variants", {}):
         cd = line["variants"]["channel_data"]["mc_deconv_loss"]
         line["roofline_channel_data"] = {
             "bound": "hbm", "kernel": "mc_deconv_loss on 3721 patches x 32 channels x 64x64 (2.0 GB of spectra, 16x L2)",
@@ -421,6 +439,35 @@ def run_gpu(args, cfg, case, rank, world, local):
         line["warm_start"] = warm_start_run(args, cfg, pb, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def oracle_errors(cfg, case, pb, dev):
+    """Relative L2 errors of the GPU forward model and adjoint against the FP64
+    oracle on the benchmark workload (all 144 patches, the oracle's own
+    measurement spectra), at the uniform start and at the true SOS: w (Eq. 3),
+    the data loss (Eq. 7), dL/dw (fused adjoint) and dL/dv (ray adjoint)."""
+    import torch
+    from oracle import pact_oracle as O
+    from paper_2409_10876_gb300 import pact
+    g = O.geom(cfg)
+    Y64, _, _ = O.make_measurement(g, case)
+    Y = torch.as_tensor(Y64.numpy().astype(np.complex64), device=dev)
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - np.asarray(b, np.float64)) /
+                             max(np.linalg.norm(np.asarray(b, np.float64)), 1e-300))
+    out = {"tolerances": {"w_loss": 1e-4, "gradients": 2e-3}}
+    for name in ("sos_init", "sos_true"):
+        sos = torch.as_tensor(case[name], device=dev)
+        w = pact.sos_to_delays(pb, sos)
+        r = pact.mc_deconv_loss(pb, w, Y, case["d"], cfg.eps, want_grad=True)
+        gs = pact.sos_to_delays_adj(pb, sos, r["dL_dw"])
+        torch.cuda.synchronize()
+        L64, _, w64, gs64 = O.objective(g, case[name].astype(np.float64), Y64, case["centres"], case["d"], cfg.eps, 0.0)
+        _, _, _, gw64 = O.mc_deconv_loss(g, w64, Y64, case["centres"], case["d"], cfg.eps)
+        out["at_" + name.split("_")[1]] = {"w": rel(w.cpu().numpy(), w64.numpy()),
+                                          "loss": abs(float(r["loss"].item()) - float(L64)) / abs(float(L64)),
+                                          "dL_dw": rel(r["dL_dw"].cpu().numpy(), gw64.numpy()),
+                                          "dL_dsos": rel(gs.cpu().numpy(), gs64.numpy())}
+    return out
 
 
 RAY_ADJ_OPS = 24   # FP32 lane operations of one adjoint sample (see the design notes)
@@ -780,6 +827,11 @@ def warm_start_run(args, cfg, pb, dev):
         res = res // 2 if pool else res
     train_tflops = fl * B * steps / t_train / 1e12
     del X, V
+    train = {"train_samples": S, "epochs": args.ws_epochs, "batch": B, "generate_s": t_gen, "train_s": t_train,
+             "train_step_ms": 1e3 * t_train / steps, "train_tflops_bf16": train_tflops,
+             "train_loss": {"first_epoch": hist[0], "last_epoch": hist[-1]}}
+    if args.ws_stages == "train":
+        return train
     net1 = pact.WarmStartCNN(pb, cfg.m, 1, net.params.cpu().numpy(), mask)
     mask_d = torch.as_tensor(mask.astype(np.uint8), device=dev)
     held = inputs.config_held_out()
@@ -822,9 +874,7 @@ def warm_start_run(args, cfg, pb, dev):
                     "sos_rms_mps": rms(v)}
     warm_s = (r["reached_s"] + s_pred) if r["reached_s"] is not None else None
     cold_s = s_c if it_c else None
-    out = {"image_quality": iq, "train_samples": S, "epochs": args.ws_epochs, "batch": B, "generate_s": t_gen,
-           "train_s": t_train, "train_step_ms": 1e3 * t_train / steps, "train_tflops_bf16": train_tflops,
-           "train_loss": {"first_epoch": hist[0], "last_epoch": hist[-1]},
+    out = {"image_quality": iq, **train,
            "sos_mae_mps": {"cnn": float((v_warm - v_true)[m].abs().mean()),
                            "uniform_1500": float((v_cold - v_true)[m].abs().mean())},
            "held_out": {"workload": held.name, "seed": seed},

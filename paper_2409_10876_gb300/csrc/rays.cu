@@ -209,7 +209,7 @@ __device__ __forceinline__ float ray_part(const RayArgs& a, const float* dv, int
     // full samples (length h) first, then the partial last one if this lane has it
     const int mf = min(m1, ry.nfull);
     float acc = 0.f, uf = m0 + 0.5f;
-#pragma unroll 4
+#pragma unroll 8
     for (int m = m0; m < mf; ++m, uf += 1.f) acc += excess(uf);
     acc *= h;
     if (m1 > ry.nfull) acc = fmaf(ry.rem, excess(ry.nfull + 0.5f * (ry.rem / h)), acc);
@@ -564,6 +564,7 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                 const float gfull = gr * v0 * h * S;
                 int m = m0 + off;
                 float uf = m + 0.5f;
+#pragma unroll 2
                 for (int k = 0; k < len; ++k) {
                     const float u = uf;
                     if (++m == m0 + len) {                        // wrap to the start of the run
