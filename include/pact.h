@@ -313,7 +313,7 @@ pact_status pact_mc_deconv_loss_adj(const pact_geometry* g, const pact_patches* 
  * and accumulates here; with 0 dL_dw is cleared first (a memset).
  * The tables carry a fingerprint of (geometry, N, P, centres pointer, m, d);
  * a call whose arguments do not match it writes NaN to loss and dL_dw.  They
- * also hold the work-claim counters of the streaming kernel, which every call
+ * also hold the CTA-done ticket of the streaming kernel, which every call
  * leaves at zero: calls that share one table set must be ordered (one stream),
  * and after a call that reported a timeout the tables must be rebuilt.
  * Errors as pact_mc_deconv_loss, plus INVALID_ARG for NULL, misaligned or

@@ -91,8 +91,8 @@ struct McdArgs {
     int KT;                // 256-bin tiles
     const unsigned long long* tag;   // fingerprint the tables were built for
     unsigned long long want;         // fingerprint of this call's arguments
-    int* sync;                       // [KT] tile claim counters and [1] CTA-done ticket of the streaming
-                                     // kernel: zero at launch and left zero by the launch (in the tables)
+    int* sync;                       // [1] CTA-done ticket of the streaming kernel: zero at launch and
+                                     // left zero by the launch (in the tables)
     int* status;                     // [1] sticky: bit 0 set when a bounded wait gave up
     int* stall;                      // [1] test hook: nonzero makes every producer of this launch wait for a
                                      // stage release that never comes (its wait expires); the launch clears it
@@ -368,20 +368,37 @@ constexpr int kCh = 8;          // channel rows per pipeline stage (14 KB; 4 row
 constexpr int kStages = 4;      // stages in flight per CTA (about one unit of look-ahead: a short tail)
 constexpr int kRing = 8;        // unit ids published ahead of their consumers
 constexpr int kSlots = 3;       // per-unit lookup rows (ring coordinates, w) staged ahead
-constexpr int kStaticWaves = 1;              // units per CTA fixed in advance and prefetched (2, 3: slower)
 constexpr int kTile = 224;                   // bins per unit of the streaming kernel, one consumer thread each
-constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two CTAs per SM)
+constexpr int kStreamThreads = kTile + 32;   // 7 consumer warps + 1 producer warp (two or three CTAs per SM)
+
+// Unit lu (0, 1, ...) of this CTA, as kt * N + i, or -1 when the CTA is done.  The
+// assignment is static (measured: per-unit claims on shared counters cost about
+// 4 us of a 37 us pass, the claim's round trip stalling the producer).  With G =
+// gridDim.x >= KT, CTA b stays on tile kt = b mod KT, where it is one of
+// c = ceil((G - kt) / KT) CTAs, and takes patches r, r + c, r + 2c, ... (r = b div
+// KT): the per-bin factors of its tile stay in registers, and at any moment the
+// grid streams one band of consecutive patches.  With fewer CTAs than tiles, CTA
+// b takes tiles b, b + G, ... whole.
+__device__ __forceinline__ int stream_unit(int KT, int N, int lu) {
+    const int G = gridDim.x, b = blockIdx.x;
+    if (G >= KT) {
+        const int kt = b % KT, c = G / KT + (kt < G % KT ? 1 : 0);
+        const int i = b / KT + lu * c;
+        return i < N ? kt * N + i : -1;
+    }
+    const int t = lu / N, kt = b + t * G;
+    return kt < KT ? kt * N + (lu - t * N) : -1;
+}
 
 // Streaming form of the fused pass (eps >= 1e-6).  The residual energy follows
 // from the same sums as the deconvolution,
 //   sum_j |Y_j - H_j X|^2 = sum_j |Y_j|^2 - |A|^2 (B + 2 eps) / (B + eps)^2,
 // so every Y element is used once and the tile need not stay resident.  Work
 // units are (224-bin tile kt, patch i).  A persistent CTA has seven consumer
-// warps (one thread per bin) and one producer warp.  The producer claims units
-// one at a time from per-tile counters (starting at tile blockIdx.x mod KT and
-// moving on when a tile is exhausted, so the CTAs of a tile share
-// exp(j|k|d_j), which the consumers keep in registers, and a slow SM simply
-// takes fewer units), publishes each unit id in a small ring, and streams the
+// warps (one thread per bin) and one producer warp.  The producer takes the
+// CTA's units in the static order of stream_unit (one tile per CTA, so the
+// consumers keep that tile's exp(j|k|d_j) in registers, loaded while the first
+// copies are in flight), publishes each unit id in a small ring, and streams the
 // unit's Y rows through kStages stages of kCh rows by 1-D bulk copies (TMA) on
 // a "full" mbarrier per stage; the consumer warps release a stage on its
 // "empty" mbarrier.  With the first chunk of a unit the producer also copies
@@ -410,8 +427,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     __shared__ int tag_ok, stall_s;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nc = EXACT ? CPT / kCh : (M + kCh - 1) / kCh;
-    int* tile_next = a.sync;                      // [KT]
-    int* done_ticket = a.sync + a.KT;             // [1]
+    int* done_ticket = a.sync;                    // [1]
     auto timed_out = [&a]() {                     // a bounded wait gave up
         note_timeout(a.status);
         atomicExch(a.failed, 1);
@@ -426,17 +442,16 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         mbar_init_fence();
     }
     for (int n = tid; n < 2 * n_t; n += blockDim.x) dw_s[n] = 0.f;
-    // The CTA's first kStaticWaves units are fixed (units blockIdx.x + j gridDim.x
-    // of the claim order): have the L2 fetch their Y rows and ring coordinates meanwhile.
-    const int units = a.KT * N, n_static = min(units, kStaticWaves * (int)gridDim.x);
-    const int kt_first = blockIdx.x % a.KT;
-    if (tid >= kTile)
-        for (int g = blockIdx.x; g < n_static; g += gridDim.x) {
-            const int i0 = g / a.KT, k0 = (g % a.KT) * kTile;
+    // Have the L2 fetch the Y rows and ring coordinates of the CTA's first unit meanwhile.
+    if (tid >= kTile) {
+        const int u0 = stream_unit(a.KT, N, 0);
+        if (u0 >= 0) {
+            const int i0 = u0 % N, k0 = (u0 / N) * kTile;
             const uint32_t bytes = (uint32_t)(min(kTile, a.F - k0) * sizeof(float2));
             for (int r = lane; r < M; r += 32) l2_prefetch(a.Y + ((size_t)i0 * M + r) * a.F + k0, bytes);
             if (lane == 0) l2_prefetch(a.lut + (size_t)i0 * a.F + k0, bytes);
         }
+    }
     // everything below reads or writes what earlier kernels produce or read (under
     // a dependent launch the setup above overlaps the end of the kernel before)
     pdl_wait();
@@ -464,8 +479,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
             if (!mbar_wait_bounded(&empty[0], 0u, a.limit_ns)) timed_out();
             return;
         }
-        int kt = kt_first, tried = 0, unit = -1;
-        const int KT = a.KT;
+        int unit = -1;
         for (int q = 0;; ++q) {
             const int s = q % kStages, lu = q / nc, c = q - lu * nc;
             if (q >= kStages &&                       // consumers released chunk q - kStages
@@ -473,19 +487,8 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                 timed_out();
                 return;                               // consumers time out on the missing chunk
             }
-            if (c == 0) {                             // claim the next unit
-                const int g = (int)blockIdx.x + lu * (int)gridDim.x;
-                unit = g < n_static ? (g % KT) * N + g / KT : -1;   // the first ones are fixed
-                while (unit < 0 && tried < KT) {
-                    // tile kt's first (n_static - kt + KT - 1) / KT claims are the fixed ones
-                    const int cl = (n_static - kt + KT - 1) / KT + atomicAdd(tile_next + kt, 1);
-                    if (cl < N) {
-                        unit = kt * N + cl;
-                        break;
-                    }
-                    kt = kt + 1 == a.KT ? 0 : kt + 1;
-                    ++tried;
-                }
+            if (c == 0) {                             // the CTA's next unit
+                unit = stream_unit(a.KT, N, lu);
                 ring[lu % kRing] = unit;
                 if (unit < 0) {                       // no work left: release the consumers
                     mbar_arrive(&full[s]);
@@ -524,6 +527,28 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     bool ok = tag_ok;
     const float nan = __int_as_float(0x7fc00000);
     const float sc = a.scale ? *a.scale : 1.f;
+    auto load_tile = [&](int kt) {                   // per-bin tables of tile kt
+        kt_loaded = kt;
+        const int k = kt * kTile + tid;
+        const bool valid = k < a.F;
+        if (FACT) {                                  // E[c]: exp(j|k|d_{8c}); E[CPT/8 + r]: exp(j|k| r delta)
+#pragma unroll
+            for (int c = 0; c < CPT / kCh; ++c)
+                E[c] = valid ? __ldg(a.etab + (size_t)(c * kCh) * a.F + k) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < kCh; ++r)
+                E[CPT / kCh + r] = valid ? __ldg(a.estep + (size_t)r * a.F + k) : make_float2(0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int m = 0; m < NE; ++m)
+                E[m] = (valid && (EXACT || m < M)) ? __ldg(a.etab + (size_t)m * a.F + k) : make_float2(0.f, 0.f);
+        }
+        bt = valid ? __ldg(a.btab + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    {   // the CTA's first tile is known: fetch its tables while the first copies are in flight
+        const int u0 = stream_unit(a.KT, N, 0);
+        if (ok && u0 >= 0) load_tile(u0 / N);
+    }
 
     // the first chunk of a unit also publishes its id
     if (ok) {
@@ -537,22 +562,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         const int k = kt * kTile + tid;
         const bool valid = k < a.F;
         const int buf = lu & 1;
-        if (kt != kt_loaded) {                       // per-bin tables of this tile
-            kt_loaded = kt;
-            if (FACT) {                              // E[c]: exp(j|k|d_{8c}); E[CPT/8 + r]: exp(j|k| r delta)
-#pragma unroll
-                for (int c = 0; c < CPT / kCh; ++c)
-                    E[c] = valid ? __ldg(a.etab + (size_t)(c * kCh) * a.F + k) : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int r = 0; r < kCh; ++r)
-                    E[CPT / kCh + r] = valid ? __ldg(a.estep + (size_t)r * a.F + k) : make_float2(0.f, 0.f);
-            } else {
-#pragma unroll
-                for (int m = 0; m < NE; ++m)
-                    E[m] = (valid && (EXACT || m < M)) ? __ldg(a.etab + (size_t)m * a.F + k) : make_float2(0.f, 0.f);
-            }
-            bt = valid ? __ldg(a.btab + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        if (kt != kt_loaded) load_tile(kt);
         // the two lookups of w of Eq. 4, from the unit's shared slot (landed with its first chunk)
         const int slot = lu % kSlots;
         const float2 tr = valid ? slot_lut[slot * kTile + tid] : make_float2(0.f, 0.f);
@@ -571,6 +581,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         // S1 = sum cos(|k|d_j) Y_j, S2 = sum sin(|k|d_j) Y_j, Ey = sum |Y_j|^2, each as
         // two partial sums over even and odd channels (shorter dependency chains)
         float2 S1 = make_float2(0.f, 0.f), S2 = S1, S1o = S1, S2o = S1;
+        float2 Ey2 = S1, Eo2 = S1;                   // FACT: sum |Y|^2 as (re^2, im^2) pairs
         float Ey = 0.f, Eyo = 0.f;
         const int qb = lu * nc;
 #pragma unroll
@@ -583,32 +594,31 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
                 }
                 const float2* ys = stage + (size_t)s * kCh * kTile + tid;
                 if (FACT) {
+                    // packed FP32 pairs (re, im): one f32x2 FMA per real-by-complex product
                     float2 P = make_float2(0.f, 0.f), Q = P, Po = P, Qo = P;
 #pragma unroll
                     for (int r = 0; r < kCh; ++r) {
                         const float2 y = ys[(size_t)r * kTile];
                         const float2 es = E[CPT / kCh + r];
-                        float2& pp = (r & 1) ? Po : P;
-                        float2& qq = (r & 1) ? Qo : Q;
-                        pp.x = fmaf(es.x, y.x, pp.x);
-                        pp.y = fmaf(es.x, y.y, pp.y);
-                        qq.x = fmaf(es.y, y.x, qq.x);
-                        qq.y = fmaf(es.y, y.y, qq.y);
-                        Ey = fmaf(y.x, y.x, Ey);
-                        Eyo = fmaf(y.y, y.y, Eyo);
+                        // PQx = (P.x, Q.x), PQy = (P.y, Q.y)
+                        float2& px = (r & 1) ? Po : P;
+                        float2& py = (r & 1) ? Qo : Q;
+                        float2& ee = (r & 1) ? Eo2 : Ey2;
+                        px = __ffma2_rn(es, make_float2(y.x, y.x), px);
+                        py = __ffma2_rn(es, make_float2(y.y, y.y), py);
+                        ee = __ffma2_rn(y, y, ee);
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&empty[s]);
-                    P.x += Po.x;
-                    P.y += Po.y;
-                    Q.x += Qo.x;
-                    Q.y += Qo.y;
+                    {
+                        const float2 px = __fadd2_rn(P, Po), py = __fadd2_rn(Q, Qo);
+                        P = make_float2(px.x, py.x);
+                        Q = make_float2(px.y, py.y);
+                    }
                     // cos(a + b) = cos a cos b - sin a sin b, sin(a + b) = sin a cos b + cos a sin b
                     const float2 eb = E[c];
-                    S1.x = fmaf(eb.x, P.x, fmaf(-eb.y, Q.x, S1.x));
-                    S1.y = fmaf(eb.x, P.y, fmaf(-eb.y, Q.y, S1.y));
-                    S2.x = fmaf(eb.y, P.x, fmaf(eb.x, Q.x, S2.x));
-                    S2.y = fmaf(eb.y, P.y, fmaf(eb.x, Q.y, S2.y));
+                    S1 = __ffma2_rn(make_float2(eb.x, eb.x), P, __ffma2_rn(make_float2(-eb.y, -eb.y), Q, S1));
+                    S2 = __ffma2_rn(make_float2(eb.y, eb.y), P, __ffma2_rn(make_float2(eb.x, eb.x), Q, S2));
                 } else {
 #pragma unroll
                     for (int r = 0; r < kCh; ++r) {
@@ -635,6 +645,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
         S2.x += S2o.x;
         S2.y += S2o.y;
         Ey += Eyo;
+        if (FACT) Ey = (Ey2.x + Ey2.y) + (Eo2.x + Eo2.y);
 
         float contrib = 0.f, gW1 = 0.f, gW2 = 0.f;
         if (valid) {
@@ -723,7 +734,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     }
 
     // The last CTA to finish sums the per-unit partials (fixed order) into the
-    // per-patch and total loss and leaves the claim counters at zero.
+    // per-patch and total loss and leaves the done ticket at zero.
     __shared__ int last_s;
     __shared__ float red_s[kTile / 32];
     __threadfence();
@@ -732,7 +743,7 @@ __global__ void __launch_bounds__(kStreamThreads, FACT ? 3 : 2) mcd_stream_kerne
     bar_and(1, kTile, true);
     if (!last_s) return;
     __threadfence();
-    for (int t = tid; t <= a.KT; t += kTile) a.sync[t] = 0;      // tile counters, done ticket
+    if (tid == 0) *done_ticket = 0;
     __shared__ int failed_s;
     if (tid == 0) {
         *a.stall = 0;                                              // the test hook acts once
@@ -822,9 +833,8 @@ Plan make_plan(const pact_geometry* g, const pact_patches* pt, int m) {
     p.KT = (F + kBins - 1) / kBins;
     p.KTs = (F + kTile - 1) / kTile;
     p.scratch = align_up((size_t)pt->n * std::max(p.KT, p.KTs) * sizeof(float), 256);
-    // sync block: [KTs] tile claim counters, [1] done ticket, [1] status word, [1] stall flag (test
-    // hook), [1] launch-failed flag
-    p.nsync = p.KTs + 4;
+    // sync block: [1] done ticket, [1] status word, [1] stall flag (test hook), [1] launch-failed flag
+    p.nsync = 4;
     size_t o = 256;                                // fingerprint header
     p.t_sync = o;
     o += align_up((size_t)p.nsync * sizeof(int), 256);
@@ -987,9 +997,9 @@ pact_status run_mcd(const pact_geometry* g, const pact_patches* pt, const float*
     a.tag = reinterpret_cast<const unsigned long long*>(tb);
     a.want = fingerprint(g, pt, d, m);
     a.sync = reinterpret_cast<int*>(tb + pl.t_sync);
-    a.status = a.sync + pl.KTs + 1;
-    a.stall = a.sync + pl.KTs + 2;
-    a.failed = a.sync + pl.KTs + 3;
+    a.status = a.sync + 1;
+    a.stall = a.sync + 2;
+    a.failed = a.sync + 3;
     a.limit_ns = wait_limit_ns();
     if (!tables) PACT_TRY(build_tables(g, pt, d, m, a.fp64, pl, tb, st));
     a.loss = loss;
@@ -1212,8 +1222,8 @@ pact_status table_words(const pact_geometry* g, const pact_patches* pt, int m, v
     const Plan pl = make_plan(g, pt, m);
     char* t = tables ? static_cast<char*>(tables) : static_cast<char*>(ws) + pl.scratch;
     int* sync = reinterpret_cast<int*>(t + pl.t_sync);
-    *status = sync + pl.KTs + 1;
-    *stall = sync + pl.KTs + 2;
+    *status = sync + 1;
+    *stall = sync + 2;
     return PACT_OK;
 }
 
