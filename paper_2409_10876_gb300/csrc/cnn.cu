@@ -100,9 +100,25 @@ __global__ void __launch_bounds__(128) conv_kernel(const ConvArgs a) {
     const int P = a.B * a.H * a.W;
     const int p = blockIdx.x * 128 + tid;
     const bool pvalid = p < P;
-    const int pb = pvalid ? p : 0;
-    const int x = pb % a.W, y = (pb / a.W) % a.H;
     const uint32_t ncols = tmem_cols(N);
+    // Gather mapping: element e = tid + 128 it of the 128 pixels x K/8 16-byte
+    // chunks, pixel-fastest in groups of eight (pixel 8 ph + pl, chunk c8): each
+    // 8-thread phase writes 128 contiguous bytes of the K-major tile, and each
+    // warp reads whole pixel rows.  A thread's pixels and their image
+    // coordinates are the same for all nine taps.
+    const int K8 = K / 8, nit = K8;                 // 128 * K8 elements, 128 threads
+    const int pl = tid & 7, c8 = (tid >> 3) % K8, ph0 = (tid >> 3) / K8, ph_step = 16 / K8;
+    int gx[8], gy[8], gp[8];                        // K8 <= 8 (K <= 64)
+    const float invW = 1.f / (float)a.W, invH = 1.f / (float)a.H;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        if (it >= nit) break;
+        const int q = blockIdx.x * 128 + 8 * (ph0 + it * ph_step) + pl;
+        const int r = (int)(((float)q + 0.5f) * invW);      // q / W (exact: q + W < 2^22)
+        gx[it] = q - r * a.W;
+        gy[it] = r - (int)(((float)r + 0.5f) * invH) * a.H;
+        gp[it] = q < P ? q : -1;
+    }
 
     if (warp == 0) umma::tmem_alloc(&tmem_s, ncols);
     if (tid == 0) {
@@ -116,10 +132,15 @@ __global__ void __launch_bounds__(128) conv_kernel(const ConvArgs a) {
 
     auto gather = [&](int tap, int s) {
         const int oy = a.sign * (tap / 3 - 1), ox = a.sign * (tap % 3 - 1);
-        const int ys = y + oy, xs = x + ox;
-        const bool ok = pvalid && ys >= 0 && ys < a.H && xs >= 0 && xs < a.W;
-        const bf16* src = a.in + (size_t)(ok ? pb + oy * a.W + ox : 0) * K;
-        for (int c = 0; c < K / 8; ++c) cp_async16(As[s] + umma::kmaj_off(tid, 8 * c, K), src + 8 * c, ok);
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            if (it >= nit) break;
+            const int ys = gy[it] + oy, xs = gx[it] + ox;
+            const bool ok = gp[it] >= 0 && ys >= 0 && ys < a.H && xs >= 0 && xs < a.W;
+            const bf16* src = a.in + (size_t)(ok ? gp[it] + oy * a.W + ox : 0) * K + 8 * c8;
+            const int pix = 8 * (ph0 + it * ph_step) + pl;
+            cp_async16(As[s] + umma::kmaj_off(pix, 8 * c8, K), src, ok);
+        }
         const bf16* wt = a.wpk + (size_t)tap * N * K;
         for (int c = tid; c < N * K / 8; c += 128) cp_async16(Bs[s] + 16 * c, wt + 8 * c, true);
         cp_async_commit();
@@ -221,37 +242,48 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const WgradArgs a) {
     umma::fence_after();
     const uint32_t tmem = tmem_s;
 
+    // Gather mapping (the same for every stage): element e = tid + 128 it, with
+    // k & 7 = e & 7 fastest, so that each 8-thread phase writes 128 contiguous
+    // bytes of the MN-major tile and each warp reads whole pixel rows.
+    // A (128 rows x 64 pixels): rows 8 (tid >> 3) .. +7, pixels k = 8 it + (tid & 7).
+    const int kk = tid & 7, r8 = tid >> 3;
+    const int tl = (8 * r8) / Cin, ci = 8 * r8 - tl * Cin;
+    const int tap = group * a.taps_per_group + tl;
+    const bool bias_row = tap == 9, tap_ok = tap < 9;
+    const int oy = tap_ok ? tap / 3 - 1 : 0, ox = tap_ok ? tap % 3 - 1 : 0;
+    const uint32_t a_off = (uint32_t)(r8 * 128 + kk * 16);     // mnmaj_off(8 r8, 8 it + kk, 128) - 2048 it
+    // B (Cout rows x 64 pixels): rows 8 c8 .. +7, pixels k = 8 (kb0 + it kb_step) + kk
+    const int co8 = Cout / 8, c8 = (tid >> 3) % co8, kb0 = (tid >> 3) / co8, kb_step = 16 / co8;
+    const float invW = 1.f / (float)a.W, invH = 1.f / (float)a.H;
     // stage j: pixels p0 + 64 j .. +63
     auto gather = [&](int j, int s) {
-        const int rows8 = 16;                       // 128 rows / 8
-        for (int e = tid; e < kWgPix * rows8; e += 128) {
-            const int k = e / rows8, r8 = e - (e / rows8) * rows8;
-            const int r = 8 * r8, tl = r / Cin, ci = r - tl * Cin;
-            const int tap = group * a.taps_per_group + tl;
-            const int p = p0 + j * kWgPix + k;
-            const bool inpix = k < npix - j * kWgPix;
-            if (tap == 9) {                         // bias row: 1 at ci = 0, pixel in range
+        const int pbase = p0 + j * kWgPix, lim = npix - j * kWgPix;
+#pragma unroll
+        for (int it = 0; it < kWgPix / 8; ++it) {
+            const int k = 8 * it + kk;
+            const uint32_t off = a_off + (uint32_t)it * 2048u;
+            const bool inpix = k < lim;
+            if (bias_row) {                         // bias row: 1 at ci = 0, pixel in range
                 uint4 v = make_uint4(0u, 0u, 0u, 0u);
                 if (ci == 0 && inpix) v.x = 0x3F80u;  // bf16 1.0 in the low half
-                *reinterpret_cast<uint4*>(As[s] + mnmaj_off(r, k, 128)) = v;
+                *reinterpret_cast<uint4*>(As[s] + off) = v;
                 continue;
             }
-            bool ok = tap < 9 && inpix;
+            bool ok = tap_ok && inpix;
             int src = 0;
             if (ok) {
-                const int x = p % a.W, y = (p / a.W) % a.H;
-                const int oy = tap / 3 - 1, ox = tap % 3 - 1;
+                const int p = pbase + k;
+                const int q = (int)(((float)p + 0.5f) * invW);      // p / W (exact: p + W < 2^22)
+                const int x = p - q * a.W, y = q - (int)(((float)q + 0.5f) * invH) * a.H;
                 ok = y + oy >= 0 && y + oy < a.H && x + ox >= 0 && x + ox < a.W;
                 src = ok ? p + oy * a.W + ox : 0;
             }
-            cp_async16(As[s] + mnmaj_off(r, k, 128), a.x + (size_t)src * Cin + ci, ok);
+            cp_async16(As[s] + off, a.x + (size_t)src * Cin + ci, ok);
         }
-        const int co8 = Cout / 8;
-        for (int e = tid; e < kWgPix * co8; e += 128) {
-            const int k = e / co8, c8 = e - (e / co8) * co8;
-            const int p = p0 + j * kWgPix + k;
-            const bool ok = k < npix - j * kWgPix;
-            cp_async16(Bs[s] + mnmaj_off(8 * c8, k, Cout), a.dz + (size_t)(ok ? p : 0) * Cout + 8 * c8, ok);
+        for (int it = 0; it < co8 / 2; ++it) {
+            const int k = 8 * (kb0 + it * kb_step) + kk;
+            const bool ok = k < lim;
+            cp_async16(Bs[s] + mnmaj_off(8 * c8, k, Cout), a.dz + (size_t)(ok ? pbase + k : 0) * Cout + 8 * c8, ok);
         }
         cp_async_commit();
     };
@@ -299,28 +331,30 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const WgradArgs a) {
 }
 
 // dW[co][ci][tap] (+)= sum over chunks of part[chunk][group][r][co] and
-// db[co] (+)= the same sum at the ones row (fixed order).  cin: channels of
-// the parameter layout, cin_pad: rows per tap in the partials.
+// db[co] (+)= the same sum at the ones row.  One thread per partial element
+// (group, r, co), co fastest so that a warp reads contiguous partials; the
+// chunks are summed in a fixed order (four interleaved sums, then their pairs).
+// cin: channels of the parameter layout, cin_pad: rows per tap in the partials.
 __global__ void wgrad_reduce_kernel(const float* part, int nchunks, int groups, int cin, int cin_pad, int Cout,
                                     int tpg, float* dW, float* db, int accumulate) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nw = Cout * cin * 9;
-    if (e >= nw + Cout) return;
-    int co, group, r;
-    if (e < nw) {
-        co = e / (cin * 9);
-        const int rem = e - co * cin * 9, ci = rem / 9, tap = rem - (rem / 9) * 9;
-        group = tap / tpg;
-        r = (tap - group * tpg) * cin_pad + ci;
-    } else {
-        co = e - nw;
-        group = 9 / tpg;
-        r = (9 - group * tpg) * cin_pad;
-    }
-    float s = 0.f;
-    for (int c = 0; c < nchunks; ++c) s += part[(((size_t)c * groups + group) * 128 + r) * Cout + co];
-    float* dst = e < nw ? dW + e : db + co;
-    *dst = accumulate ? *dst + s : s;
+    if (e >= groups * 128 * Cout) return;
+    const int co = e % Cout, gr = e / Cout, r = gr % 128, group = gr / 128;
+    const int tl = r / cin_pad, ci = r - tl * cin_pad, tap = group * tpg + tl;
+    float* dst;
+    if (tap < 9 && ci < cin) dst = dW + ((size_t)co * cin + ci) * 9 + tap;
+    else if (tap == 9 && ci == 0) dst = db + co;
+    else return;
+    const size_t stride = (size_t)groups * 128 * Cout;
+    const float* src = part + e;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    int c = 0;
+    for (; c + 4 <= nchunks; c += 4)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += src[(size_t)(c + u) * stride];
+    for (; c < nchunks; ++c) s[0] += src[(size_t)c * stride];
+    const float t = (s[0] + s[1]) + (s[2] + s[3]);
+    *dst = accumulate ? *dst + t : t;
 }
 
 // -------------------------------------------------------------- elementwise kernels
@@ -640,6 +674,10 @@ pact_status check_cnn(const pact_geometry* g, int m, int B) {
     if (B < 1) return fail(PACT_ERR_INVALID_ARG, "cnn: batch must be >= 1");
     if (g->img_h != g->img_w || g->img_h != 4 * g->sos_g || g->sos_g % 8 != 0)
         return fail(PACT_ERR_SHAPE, "cnn: needs a square image of 4 G pixels per side with G a multiple of 8");
+    // the convolution kernels divide pixel indices by a float reciprocal, exact below 2^22
+    if ((long long)B * g->sos_g * g->sos_g + g->sos_g >= (1ll << 22))
+        return fail(PACT_ERR_SHAPE, "cnn: batch x G^2 = %lld pixels, must be below 2^22 - G",
+                    (long long)B * g->sos_g * g->sos_g);
     return PACT_OK;
 }
 
@@ -669,6 +707,7 @@ pact_status launch_conv(const Ctx& c, const bf16* in, const bf16* wpk, const flo
     a.relu = relu;
     a.status = c.status;
     a.limit_ns = wait_limit_ns();
+    if (K % 8 || K > 64 || 16 % (K / 8)) return fail(PACT_ERR_SHAPE, "cnn: conv K = %d unsupported", K);
     const size_t smem = (size_t)kConvStages * (128 * K * 2 + (size_t)N * K * 2);
     PACT_TRY(ensure_smem((const void*)conv_kernel, smem, "cnn: conv shared memory attribute"));
     const int P = B * res * res;
@@ -699,7 +738,7 @@ pact_status launch_wgrad(const Ctx& c, const Layer& y, const bf16* x, const bf16
     PACT_TRY(ensure_smem((const void*)wgrad_kernel, smem, "cnn: wgrad shared memory attribute"));
     wgrad_kernel<<<dim3(nchunks, groups), 128, smem, c.st>>>(a);
     PACT_TRY(check_launch("cnn wgrad kernel"));
-    const int ne = y.cout * y.cin * 9 + y.cout;
+    const int ne = groups * 128 * y.cout;
     wgrad_reduce_kernel<<<(ne + 255) / 256, 256, 0, c.st>>>(a.part, nchunks, groups, y.cin, y.cin_pad, y.cout,
                                                            a.taps_per_group, dW, db, accumulate);
     return check_launch("cnn wgrad reduction");
