@@ -44,6 +44,7 @@ constexpr int kNParam = kOffB5 + 1;
 constexpr int kPartStride = (kNParam + 63) / 64 * 64;   // per-CTA gradient row, 256-byte aligned
 constexpr int kWbf = kOffW5 + kH;             // bf16 weight copy: W1..W4 with their biases' slots unused, w5
 constexpr int kTileBytes = kRows * kH * 2;    // one 128 x 128 bf16 operand tile
+constexpr int kOnesBytes = 16 * kRows * 2;    // the backward's [16 x 128] tile of ones
 
 struct NfArgs {
     int G;                 // nodes per side
@@ -97,8 +98,11 @@ __device__ __forceinline__ float bfv(const unsigned char* tile, int r, int k, in
     return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + umma::kmaj_off(r, k, K)));
 }
 
-__device__ __forceinline__ void st1(unsigned char* tile, int r, int k, int K, float v) {
-    *reinterpret_cast<__nv_bfloat16*>(tile + umma::kmaj_off(r, k, K)) = __float2bfloat16_rn(v);
+// Element u (0..7) of eight BF16 values packed in a uint4, as FP32 (a BF16 is
+// the upper half of the FP32 with the same bits).
+__device__ __forceinline__ float bf16_at(const uint4& v, int u) {
+    const uint32_t w = u < 2 ? v.x : u < 4 ? v.y : u < 6 ? v.z : v.w;
+    return __uint_as_float((u & 1) ? (w & 0xFFFF0000u) : (w << 16));
 }
 
 // Weight W_l (bf16 [out][in]) into a K-major [out x in] tile (B operand of h W^T).
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
     unsigned char* Wt[kL];                                  // W1 (16 KB), W2..W4 (32 KB each)
     Wt[0] = sm + 16384 + 2 * kTileBytes;
     for (int l = 1; l < kL; ++l) Wt[l] = Wt[0] + 16384 + (l - 1) * kTileBytes;
-    __shared__ float bias_s[kL][kH];
+    __shared__ __align__(16) float bias_s[kL][kH];
     __shared__ float w5_s[kH];
     __shared__ uint32_t tmem_s;
     __shared__ __align__(8) uint64_t bar;
@@ -192,10 +196,16 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
             float v[32];
             umma::ld32(tmem + lane_base + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float h = fmaxf(v[j] + bias_s[l - 1][c0 + j], 0.f);
-                v[j] = __bfloat162float(__float2bfloat16_rn(h));
-                if (l == kL) z5 = fmaf(v[j], w5_s[c0 + j], z5);
+            for (int j = 0; j < 32; j += 4) {
+                const float4 b4 = *reinterpret_cast<const float4*>(&bias_s[l - 1][c0 + j]);
+                v[j] = fmaxf(v[j] + b4.x, 0.f);
+                v[j + 1] = fmaxf(v[j + 1] + b4.y, 0.f);
+                v[j + 2] = fmaxf(v[j + 2] + b4.z, 0.f);
+                v[j + 3] = fmaxf(v[j + 3] + b4.w, 0.f);
+            }
+            if (l == kL) {                          // the head sees the BF16 values the tile holds
+#pragma unroll
+                for (int j = 0; j < 32; ++j) z5 = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), w5_s[c0 + j], z5);
             }
 #pragma unroll
             for (int j = 0; j < 32; j += 8) st8(out, tid, c0 + j, kH, v + j);
@@ -227,6 +237,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     unsigned char* dzA = sm;                      // dz         [128 nodes x out]    32 KB
     unsigned char* WT = sm + kTileBytes;          // W_l        [out x in]           32 KB
     unsigned char* Hr = sm + 2 * kTileBytes;      // h_{l-1}    [128 nodes x in]     32 KB
+    unsigned char* ones = sm + 3 * kTileBytes;    // [16 x 128 nodes] of 1.0: db = dz^T 1 on the tensor core   4 KB
     __shared__ float g5_s[kRows];
     __shared__ float w5_s[kH];
     __shared__ uint32_t tmem_s;
@@ -246,7 +257,9 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     // h4 of this CTA (operand layout) -> Hr
     load_tile(Hr, tiles + (size_t)(kL - 1) * kTileBytes);
     cp_wait_all();
-    if (warp == 0) umma::tmem_alloc(&tmem_s, 256);
+    for (int c = tid; c < kOnesBytes / 16; c += blockDim.x)
+        reinterpret_cast<uint4*>(ones)[c] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    if (warp == 0) umma::tmem_alloc(&tmem_s, 512);
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_init_fence();
@@ -257,9 +270,13 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     g5_s[tid] = g5;
     w5_s[tid] = __bfloat162float(a.wbf[kOffW5 + tid]);
     __syncthreads();
-    for (int c = 0; c < kH; ++c) {
-        const float h = bfv(Hr, tid, c, kH);
-        st1(dzA, tid, c, kH, h > 0.f ? g5 * w5_s[c] : 0.f);
+#pragma unroll 1
+    for (int c = 0; c < kH; c += 8) {
+        const uint4 hv = *reinterpret_cast<const uint4*>(Hr + umma::kmaj_off(tid, c, kH));
+        float dz[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) dz[u] = bf16_at(hv, u) > 0.f ? g5 * w5_s[c + u] : 0.f;
+        st8(dzA, tid, c, kH, dz);
     }
     {
         float s = 0.f;
@@ -278,12 +295,6 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     uint32_t phase = 0;
     for (int l = kL; l >= 1; --l) {
         const int K_in = in_dim(l);
-        // db_l = column sums of dz_l (column `tid` of the dz tile)
-        {
-            float s = 0.f;
-            for (int r = 0; r < kRows; ++r) s += bfv(dzA, r, tid, kH);
-            part[off_b(l) + tid] = s;
-        }
         // h_{l-1} (B operand of dW, read MN-major) and, for l > 1, W_l^T (B operand of dh)
         if (l > 1) {
             load_tile(Hr, tiles + (size_t)(l - 2) * kTileBytes);
@@ -310,11 +321,16 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
                 for (int kk = 0; kk < kH / 16; ++kk)
                     umma::mma(tmem + 128, umma::kslice(dzA, kH, kk), umma::mn_slice(WT, kH, kk),
                               umma::idesc_bf16(128, kH) | (1u << 16), kk > 0);
+            // db_l [out x 16] = dz^T [out x nodes] * (ones [16 x nodes])^T: every column is the sum over nodes
+            for (int kk = 0; kk < kRows / 16; ++kk)
+                umma::mma(tmem + 256, umma::mn_slice(dzA, kH, kk), umma::kslice(ones, kRows, kk),
+                          umma::idesc_bf16(128, 16) | (1u << 15), kk > 0);
             umma::commit(&bar);
         }
         wait_bar(&bar, phase, a.status, a.limit_ns);
         phase ^= 1u;
         umma::fence_after();
+        part[off_b(l) + tid] = umma::ld1(tmem + 256 + lane_base);   // db_l[tid]
         // weight-gradient row `tid` (TMEM lane = output unit)
         for (int c0 = 0; c0 < K_in; c0 += 32) {
             float v[32];
@@ -329,10 +345,12 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
                 float v[32];
                 umma::ld32(tmem + 128 + lane_base + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float h = bfv(Hr, tid, c0 + j, kH);
-                    const float dz = h > 0.f ? v[j] : 0.f;
-                    st1(dzA, tid, c0 + j, kH, dz);
+                for (int j = 0; j < 32; j += 8) {
+                    const uint4 hv = *reinterpret_cast<const uint4*>(Hr + umma::kmaj_off(tid, c0 + j, kH));
+                    float dz[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) dz[u] = bf16_at(hv, u) > 0.f ? v[j + u] : 0.f;
+                    st8(dzA, tid, c0 + j, kH, dz);
                 }
             }
         }
@@ -342,7 +360,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     }
     umma::fence_before();
     __syncthreads();
-    if (warp == 0) umma::tmem_dealloc(tmem, 256);
+    if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
 __global__ void nf_reduce_kernel(const float* part, int nct, float* out, int accumulate) {
@@ -379,7 +397,7 @@ NfPlan nf_plan(const pact_geometry* g) {
     o += 256;
     p.total = o;
     p.smem_fwd = 16384 + 2 * kTileBytes + 16384 + (kL - 1) * kTileBytes;
-    p.smem_bwd = 3 * kTileBytes;
+    p.smem_bwd = 3 * kTileBytes + kOnesBytes;
     return p;
 }
 
