@@ -110,6 +110,11 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // W [kH x K] (row-major, 16-byte aligned) into a K-major tile by asynchronous
 // 16-byte copies; the caller waits with cp_wait_all and a barrier.
@@ -145,10 +150,10 @@ __global__ void nf_cast_kernel(const float* params, __nv_bfloat16* wbf) {
 __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* A0 = sm;                                 // features  [128 x 64]   16 KB
-    unsigned char* Hb[2] = {sm + 16384, sm + 16384 + kTileBytes};   // layer outputs  2 x 32 KB
-    unsigned char* Wt[kL];                                  // W1 (16 KB), W2..W4 (32 KB each)
-    Wt[0] = sm + 16384 + 2 * kTileBytes;
-    for (int l = 1; l < kL; ++l) Wt[l] = Wt[0] + 16384 + (l - 1) * kTileBytes;
+    auto Hb = [](int i) { return sm + 16384 + i * kTileBytes; };            // layer outputs  2 x 32 KB
+    auto Wt = [](int i) {                                   // W1 (16 KB), W2..W4 (32 KB each)
+        return sm + 16384 + 2 * kTileBytes + (i == 0 ? 0 : 16384 + (i - 1) * kTileBytes);
+    };
     __shared__ __align__(16) float bias_s[kL][kH];
     __shared__ float w5_s[kH];
     __shared__ uint32_t tmem_s;
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
     const int row = blockIdx.x * kRows + tid;
     const bool valid = row < a.rows;
 
-    for (int l = 1; l <= kL; ++l) load_w(Wt[l - 1], a.wbf + off_w(l), in_dim(l));
+    for (int l = 1; l <= kL; ++l) load_w(Wt(l - 1), a.wbf + off_w(l), in_dim(l));
     for (int c = tid; c < kL * kH; c += blockDim.x) bias_s[c / kH][c % kH] = a.params[off_b(c / kH + 1) + c % kH];
     for (int c = tid; c < kH; c += blockDim.x) w5_s[c] = __bfloat162float(a.wbf[kOffW5 + c]);
     {
@@ -181,12 +186,12 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
     bool ok = true;
     float z5 = 0.f;
     for (int l = 1; l <= kL; ++l) {
-        const unsigned char* in = l == 1 ? A0 : Hb[l % 2];
-        unsigned char* out = Hb[(l + 1) % 2];
+        const unsigned char* in = l == 1 ? A0 : Hb(l % 2);
+        unsigned char* out = Hb((l + 1) % 2);
         const int K = in_dim(l);
         if (tid == 0) {
             for (int kk = 0; kk < K / 16; ++kk)
-                umma::mma(tmem, umma::kslice(in, K, kk), umma::kslice(Wt[l - 1], K, kk), umma::idesc_bf16(128, 128),
+                umma::mma(tmem, umma::kslice(in, K, kk), umma::kslice(Wt(l - 1), K, kk), umma::idesc_bf16(128, 128),
                           kk > 0);
             umma::commit(&bar);
         }
@@ -234,10 +239,12 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     // dz and h_{l-1} are K-major tiles [nodes x units]; read as MN-major they
     // are the transposed operands dz^T and h^T of the weight-gradient GEMM
+    // Layer l reads h_{l-1} and W_l from buffers l & 1; the copies for layer l - 1
+    // go into the other pair while layer l runs (the pair layer l + 1 has finished with).
     unsigned char* dzA = sm;                      // dz         [128 nodes x out]    32 KB
-    unsigned char* WT = sm + kTileBytes;          // W_l        [out x in]           32 KB
-    unsigned char* Hr = sm + 2 * kTileBytes;      // h_{l-1}    [128 nodes x in]     32 KB
-    unsigned char* ones = sm + 3 * kTileBytes;    // [16 x 128 nodes] of 1.0: db = dz^T 1 on the tensor core   4 KB
+    auto Hb = [](int i) { return sm + (1 + i) * kTileBytes; };   // h_{l-1} [128 nodes x in]  2 x 32 KB
+    auto Wb = [](int i) { return sm + (3 + i) * kTileBytes; };   // W_l     [out x in]        2 x 32 KB
+    unsigned char* ones = sm + 5 * kTileBytes;    // [16 x 128 nodes] of 1.0: db = dz^T 1 on the tensor core   4 KB
     __shared__ float g5_s[kRows];
     __shared__ float w5_s[kH];
     __shared__ uint32_t tmem_s;
@@ -254,9 +261,14 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         const float t = a.t5[row];
         g5 = a.dL_dsos[row] * a.v_half * (1.f - t * t);
     }
-    // h4 of this CTA (operand layout) -> Hr
-    load_tile(Hr, tiles + (size_t)(kL - 1) * kTileBytes);
-    cp_wait_all();
+    // h4 of this CTA (operand layout) -> Hb(1); then layer kL's h3 and W4 -> Hb(0), Wb(0)
+    unsigned char* H4 = Hb(1);
+    load_tile(H4, tiles + (size_t)(kL - 1) * kTileBytes);
+    cp_async_commit_group();
+    load_tile(Hb(kL & 1), tiles + (size_t)(kL - 2) * kTileBytes);
+    load_w(Wb(kL & 1), a.wbf + off_w(kL), kH);
+    cp_async_commit_group();
+    cp_async_wait_group<1>();                       // h4 has landed
     for (int c = tid; c < kOnesBytes / 16; c += blockDim.x)
         reinterpret_cast<uint4*>(ones)[c] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
     if (warp == 0) umma::tmem_alloc(&tmem_s, 512);
@@ -272,7 +284,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < kH; c += 8) {
-        const uint4 hv = *reinterpret_cast<const uint4*>(Hr + umma::kmaj_off(tid, c, kH));
+        const uint4 hv = *reinterpret_cast<const uint4*>(H4 + umma::kmaj_off(tid, c, kH));
         float dz[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) dz[u] = bf16_at(hv, u) > 0.f ? g5 * w5_s[c + u] : 0.f;
@@ -280,7 +292,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     }
     {
         float s = 0.f;
-        for (int r = 0; r < kRows; ++r) s = fmaf(g5_s[r], bfv(Hr, r, tid, kH), s);
+        for (int r = 0; r < kRows; ++r) s = fmaf(g5_s[r], bfv(H4, r, tid, kH), s);
         part[kOffW5 + tid] = s;
         if (tid == 0) {
             float b = 0.f;
@@ -295,11 +307,16 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     uint32_t phase = 0;
     for (int l = kL; l >= 1; --l) {
         const int K_in = in_dim(l);
-        // h_{l-1} (B operand of dW, read MN-major) and, for l > 1, W_l^T (B operand of dh)
+        unsigned char* Hr = Hb(l & 1);
+        unsigned char* WT = Wb(l & 1);
+        // copies for layer l - 1 (h_{l-2}, W_{l-1}) into the other pair, then wait for layer l's
+        if (l - 1 >= 2) {
+            load_tile(Hb((l - 1) & 1), tiles + (size_t)(l - 3) * kTileBytes);
+            load_w(Wb((l - 1) & 1), a.wbf + off_w(l - 1), kH);   // W [out x in] K-major = W^T read MN-major
+        }
+        cp_async_commit_group();
         if (l > 1) {
-            load_tile(Hr, tiles + (size_t)(l - 2) * kTileBytes);
-            load_w(WT, a.wbf + off_w(l), kH);          // W_l [out x in] K-major = W_l^T read MN-major
-            cp_wait_all();
+            cp_async_wait_group<1>();              // h_{l-1} and W_l have landed
         } else {
             float f[kF];
             features(a, valid ? row : 0, f);
@@ -397,7 +414,7 @@ NfPlan nf_plan(const pact_geometry* g) {
     o += 256;
     p.total = o;
     p.smem_fwd = 16384 + 2 * kTileBytes + 16384 + (kL - 1) * kTileBytes;
-    p.smem_bwd = 3 * kTileBytes + kOnesBytes;
+    p.smem_bwd = 5 * kTileBytes + kOnesBytes;
     return p;
 }
 
