@@ -197,11 +197,11 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
         }
         ok = wait_bar(&bar, (uint32_t)((l - 1) & 1), a.status, a.limit_ns) && ok;
         umma::fence_after();
-        for (int c0 = 0; c0 < kH; c0 += 32) {
-            float v[32];
-            umma::ld32(tmem + lane_base + c0, v);
+        for (int c0 = 0; c0 < kH; c0 += 64) {
+            float v[64];
+            umma::ld64(tmem + lane_base + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
+            for (int j = 0; j < 64; j += 4) {
                 const float4 b4 = *reinterpret_cast<const float4*>(&bias_s[l - 1][c0 + j]);
                 v[j] = fmaxf(v[j] + b4.x, 0.f);
                 v[j + 1] = fmaxf(v[j + 1] + b4.y, 0.f);
@@ -210,10 +210,10 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
             }
             if (l == kL) {                          // the head sees the BF16 values the tile holds
 #pragma unroll
-                for (int j = 0; j < 32; ++j) z5 = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), w5_s[c0 + j], z5);
+                for (int j = 0; j < 64; ++j) z5 = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), w5_s[c0 + j], z5);
             }
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) st8(out, tid, c0 + j, kH, v + j);
+            for (int j = 0; j < 64; j += 8) st8(out, tid, c0 + j, kH, v + j);
         }
         umma::fence_smem_to_async();
         umma::fence_before();
@@ -349,20 +349,20 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         umma::fence_after();
         part[off_b(l) + tid] = umma::ld1(tmem + 256 + lane_base);   // db_l[tid]
         // weight-gradient row `tid` (TMEM lane = output unit)
-        for (int c0 = 0; c0 < K_in; c0 += 32) {
-            float v[32];
-            umma::ld32(tmem + lane_base + c0, v);
+        for (int c0 = 0; c0 < K_in; c0 += 64) {
+            float v[64];
+            umma::ld64(tmem + lane_base + c0, v);
             float4* dst = reinterpret_cast<float4*>(part + off_w(l) + tid * K_in + c0);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) dst[j / 4] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            for (int j = 0; j < 64; j += 4) dst[j / 4] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
         if (l > 1) {
             // dz_{l-1} = dh (h_{l-1} > 0), node `tid`
-            for (int c0 = 0; c0 < kH; c0 += 32) {
-                float v[32];
-                umma::ld32(tmem + 128 + lane_base + c0, v);
+            for (int c0 = 0; c0 < kH; c0 += 64) {
+                float v[64];
+                umma::ld64(tmem + 128 + lane_base + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; j += 8) {
+                for (int j = 0; j < 64; j += 8) {
                     const uint4 hv = *reinterpret_cast<const uint4*>(Hr + umma::kmaj_off(tid, c0 + j, kH));
                     float dz[8];
 #pragma unroll
