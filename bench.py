@@ -286,7 +286,7 @@ def run_gpu(args, cfg, case, rank, world, local):
     g_step = capture(None)                        # the timed iteration
     g_step_ev = capture(gev) if gev else None     # the same with event nodes, for the breakdown
     torch.cuda.synchronize()
-    launches_per_step = 6                         # rays, fused pass, ray adjoint, partial-grid sum, TV, Adam
+    launches_per_step = 4                         # rays (+ TV terms), fused pass, ray adjoint, partial sums + Adam
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 

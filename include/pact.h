@@ -212,6 +212,50 @@ pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact_patches* p
                                    size_t ws_bytes, void* stream);
 
 /*
+ * The two ends of a pixel-grid recovery iteration (Sec. 3.3: Adam on the
+ * Eq. 7 loss, data term plus lambda TV) with fewer launches; no counterpart in
+ * the paper (iteration fusion).  An iteration is
+ *   pact_sos_to_delays_tv -> pact_mc_deconv_loss_tabled (accumulate = 1)
+ *   -> pact_sos_to_delays_adj_adam
+ * and equals pact_sos_to_delays_clear -> the fused pass -> pact_sos_to_delays_adj
+ * -> pact_tv (value and gradient, accumulate = 1) -> pact_adam_step, up to the
+ * rounding of the additions.
+ *
+ * pact_sos_to_delays_tv: pact_sos_to_delays_clear, and in the same launch the
+ * TV terms of Eq. 7 at the SOS it reads: lambda times the subgradient
+ * (sign(0) = 0) and lambda times TV(v) in per-CTA parts, into tv_ws.
+ *   tv_ws   DEVICE, 256-byte aligned, pact_sos_to_delays_tv_workspace_size
+ *           bytes; its contents are for the pact_sos_to_delays_adj_adam call
+ *           of the same iteration (same geometry and patches).
+ * Errors: those of pact_sos_to_delays_clear; INVALID_ARG for a NULL,
+ * misaligned or small tv_ws or a non-finite lambda.
+ *
+ * pact_sos_to_delays_adj_adam: the adjoint of Eq. 3 as pact_sos_to_delays_adj,
+ * then one kernel that per node adds the partial grids (fixed order) and the
+ * TV subgradient from tv_ws, writes the gradient to dL_dsos (if not NULL),
+ * and takes one Adam step on sos in place exactly as pact_adam_step (m, v,
+ * step, step_counter, lr, betas, eps, mask with the same meaning); it also
+ * adds lambda TV(v) to *loss (if loss and tv_ws are not NULL; the per-CTA parts
+ * in a fixed order).  The TV terms were taken before this update, so no node
+ * is read after another thread has moved it.
+ *   sos      DEVICE float [G][G], updated in place
+ *   tv_ws    as above, or NULL for lambda = 0 (no TV term)
+ *   loss     DEVICE float [1] or NULL
+ *   dL_dsos  DEVICE float [G][G] or NULL: the gradient of the step
+ *   ws       as pact_sos_to_delays_adj
+ * Errors: those of pact_sos_to_delays_adj and pact_adam_step.
+ */
+size_t pact_sos_to_delays_tv_workspace_size(const pact_geometry* g, const pact_patches* pt);
+pact_status pact_sos_to_delays_tv(const pact_geometry* g, const pact_patches* pt, const float* sos, float* w,
+                                  float* clear, size_t n_clear, float lambda, void* tv_ws, size_t tv_ws_bytes,
+                                  void* stream);
+pact_status pact_sos_to_delays_adj_adam(const pact_geometry* g, const pact_patches* pt, float* sos,
+                                        const float* dL_dw, const void* tv_ws, float* loss, float* dL_dsos,
+                                        float* m, float* v, int step, int* step_counter, float lr, float beta1,
+                                        float beta2, float eps, const unsigned char* mask, void* ws,
+                                        size_t ws_bytes, void* stream);
+
+/*
  * Wavefront transfer functions, Eq. 4, in the sign that Eq. 1 implies for
  * the forward DFT kernel exp(-j k.rho) (the complex conjugate of the
  * printed form):

@@ -17,6 +17,7 @@
 // fixed order (deterministic).  Grids too large for shared memory read the SOS
 // from global memory and scatter with global atomics instead.
 #include <algorithm>
+#include <cmath>
 
 #include "pact_internal.cuh"
 
@@ -102,7 +103,44 @@ struct RayArgs {
     int use_smem;
     float4* clear;        // forward: [n_clear4] set to zero in the same launch (or NULL)
     size_t n_clear4;
+    float tv_lambda;      // forward: with tv_grad, lambda times the TV terms of Eq. 7
+    float* tv_grad;       //   [G*G] lambda * TV subgradient (or NULL)
+    float* tv_part;       //   [gridDim.x] lambda * TV(v) over each CTA's nodes
 };
+
+__device__ __forceinline__ float tv_sgn(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+// TV regulariser of Eq. 7, TV(v) = sum |v[p+1][q] - v[p][q]| + |v[p][q+1] - v[p][q]|,
+// on this CTA's share of the nodes: lambda times its subgradient (sign(0) = 0)
+// into tv_grad, lambda times its part of the value into tv_part[blockIdx.x]
+// (summed later in a fixed order).  All threads of the CTA take part.
+__device__ void tv_terms(const RayArgs& a) {
+    __shared__ float red[32];
+    const int G = a.g.G, GG = G * G;
+    const int q0 = (int)((long long)GG * blockIdx.x / gridDim.x);
+    const int q1 = (int)((long long)GG * (blockIdx.x + 1) / gridDim.x);
+    float part = 0.f;
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
+        const int p = q / G, c = q - p * G;
+        const float v = __ldg(a.sos + q);
+        float gq = 0.f;
+        if (p + 1 < G) {
+            const float dn = __ldg(a.sos + q + G) - v;
+            part += fabsf(dn);
+            gq -= tv_sgn(dn);
+        }
+        if (c + 1 < G) {
+            const float rt = __ldg(a.sos + q + 1) - v;
+            part += fabsf(rt);
+            gq -= tv_sgn(rt);
+        }
+        if (p > 0) gq += tv_sgn(v - __ldg(a.sos + q - G));
+        if (c > 0) gq += tv_sgn(v - __ldg(a.sos + q - 1));
+        a.tv_grad[q] = a.tv_lambda * gq;
+    }
+    const float tot = block_sum(part, red);
+    if (threadIdx.x == 0) a.tv_part[blockIdx.x] = a.tv_lambda * tot;
+}
 
 // Shared-memory grid pitch: one extra column so that nodes of one grid column
 // fall into different banks.
@@ -236,6 +274,7 @@ __global__ void __launch_bounds__(512) rays_fwd_kernel(const RayArgs a) {
     }
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_clear4; q += (size_t)gridDim.x * blockDim.x)
         a.clear[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.tv_grad) tv_terms(a);
     constexpr int RB = 32 / L;
     const int n_t = a.g.n_t;
     const int lane = threadIdx.x & 31, sub = lane % L, grp = lane / L;
@@ -660,7 +699,70 @@ __global__ void __launch_bounds__(256) reduce_parts_kernel(const float* part, in
     if (threadIdx.x < 32 && q < GG) out[q] = accumulate ? out[q] + g : g;
 }
 
+// The tail of a recovery iteration (Sec. 3.3) in one launch: per node
+//   g = (sum of the adjoint's partial grids, fixed order) + tv_grad (optional),
+// written to grad_out (optional), then one Adam step on param in place.  The
+// TV terms come from the ray forward kernel of the same iteration, taken
+// before this update, so no CTA reads a node another CTA updates.  CTA 0 also
+// adds the forward kernel's lambda * TV partials (fixed order) to loss.
+struct TailArgs {
+    const float* part;
+    int np, GG;
+    const float* tv_grad;
+    const float* tv_part;
+    int ntv;
+    float* loss;
+    float* grad_out;
+    float* param;
+    float* m;
+    float* v;
+    float lr, b1, b2, eps, bc1, bc2;
+    int* counter;                 // [2] as pact_adam_step's step counter, or NULL (bc1, bc2 fixed)
+    const unsigned char* mask;
+};
+
+__global__ void __launch_bounds__(256) adj_adam_kernel(const TailArgs a) {
+    __shared__ float red[256];
+    pdl_trigger();
+    pdl_wait();
+    float bc1 = a.bc1, bc2 = a.bc2;
+    if (a.counter) {              // t = steps so far + 1
+        const float t = (float)(a.counter[0] + 1);
+        bc1 = 1.f - powf(a.b1, t);
+        bc2 = 1.f - powf(a.b2, t);
+    }
+    const int q = blockIdx.x * 32 + (threadIdx.x & 31);
+    float g = sum_parts32(a.part, a.np, a.GG, blockIdx.x * 32, red);
+    if (threadIdx.x < 32 && q < a.GG) {
+        if (a.tv_grad) g += a.tv_grad[q];
+        if (a.grad_out) a.grad_out[q] = g;
+        if (!a.mask || a.mask[q]) {
+            const float mq = fmaf(a.b1, a.m[q], (1.f - a.b1) * g);
+            const float vq = fmaf(a.b2, a.v[q], (1.f - a.b2) * g * g);
+            a.m[q] = mq;
+            a.v[q] = vq;
+            a.param[q] -= a.lr * (mq / bc1) / (sqrtf(vq / bc2) + a.eps);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.loss && a.tv_part) {
+        float s = 0.f;
+        for (int k = 0; k < a.ntv; ++k) s += a.tv_part[k];
+        a.loss[0] += s;
+    }
+    if (a.counter) {
+        __syncthreads();          // every thread of the CTA has read counter[0]
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(a.counter + 1, 1) == (int)gridDim.x - 1) {   // all CTAs have read it
+                a.counter[0] += 1;
+                a.counter[1] = 0;
+            }
+        }
+    }
+}
+
 constexpr size_t kMaxSmem = 200 * 1024;
+constexpr int kTvParts = 4096;    // per-CTA TV partials the TV workspace holds
 
 
 constexpr int kRayLanes = 1;   // lanes per ray in the forward integrals
@@ -783,18 +885,33 @@ pact_status launch_pixel_rays(const pact_geometry* g, const float* sos, const fl
 using namespace pact;
 
 static pact_status sos_to_delays(const pact_geometry* g, const pact_patches* pt, const float* sos, float* w,
-                                 float* clear, size_t n_clear, void* stream) {
+                                 float* clear, size_t n_clear, void* stream, float tv_lambda = 0.f,
+                                 void* tv_ws = nullptr, size_t tv_ws_bytes = 0) {
     PACT_TRY(check_geometry(g));
     PACT_TRY(check_patches(pt));
     if (!sos || !w) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays: sos and w must not be NULL");
     if (n_clear && (!clear || reinterpret_cast<uintptr_t>(clear) % 16 || n_clear % 4))
         return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_clear: clear must be 16-byte aligned, n_clear a multiple of 4");
+    const size_t GG = (size_t)g->sos_g * g->sos_g;
+    if (tv_ws) {
+        if (reinterpret_cast<uintptr_t>(tv_ws) % 256) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_tv: tv_ws must be 256-byte aligned");
+        if (tv_ws_bytes < (GG + kTvParts) * sizeof(float))
+            return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_tv: tv_ws too small: %zu < %zu bytes", tv_ws_bytes,
+                        (GG + kTvParts) * sizeof(float));
+        if (!std::isfinite(tv_lambda)) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_tv: lambda must be finite");
+    }
     PACT_TRY(require_sms());
     const Plan pl = make_plan(g, pt);
+    if (tv_ws && pl.nb_fwd > kTvParts) return fail(PACT_ERR_UNSUPPORTED, "sos_to_delays_tv: %d CTAs", pl.nb_fwd);
     RayArgs a = make_args(g, pt, pl, sos);
     a.w = w;
     a.clear = reinterpret_cast<float4*>(clear);
     a.n_clear4 = n_clear / 4;
+    if (tv_ws) {
+        a.tv_lambda = tv_lambda;
+        a.tv_grad = static_cast<float*>(tv_ws);
+        a.tv_part = static_cast<float*>(tv_ws) + GG;
+    }
     cudaStream_t st = as_stream(stream);
     if (pl.smem_fwd)
         PACT_TRY(ensure_smem(fwd_fn(pl.fwd_mode), pl.smem_fwd, "sos_to_delays: shared memory attribute"));
@@ -815,6 +932,18 @@ extern "C" pact_status pact_sos_to_delays(const pact_geometry* g, const pact_pat
 extern "C" pact_status pact_sos_to_delays_clear(const pact_geometry* g, const pact_patches* pt, const float* sos,
                                                 float* w, float* clear, size_t n_clear, void* stream) {
     return sos_to_delays(g, pt, sos, w, clear, n_clear, stream);
+}
+
+extern "C" size_t pact_sos_to_delays_tv_workspace_size(const pact_geometry* g, const pact_patches* pt) {
+    if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK) return 0;
+    return align_up(((size_t)g->sos_g * g->sos_g + kTvParts) * sizeof(float), 256);
+}
+
+extern "C" pact_status pact_sos_to_delays_tv(const pact_geometry* g, const pact_patches* pt, const float* sos,
+                                             float* w, float* clear, size_t n_clear, float lambda, void* tv_ws,
+                                             size_t tv_ws_bytes, void* stream) {
+    if (!tv_ws) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_tv: tv_ws is NULL");
+    return sos_to_delays(g, pt, sos, w, clear, n_clear, stream, lambda, tv_ws, tv_ws_bytes);
 }
 
 extern "C" size_t pact_sos_to_delays_adj_workspace_size(const pact_geometry* g, const pact_patches* pt) {
@@ -856,4 +985,61 @@ extern "C" pact_status pact_sos_to_delays_adj(const pact_geometry* g, const pact
                    accumulate) != cudaSuccess)
         return check_launch("sos_to_delays_adj reduction");
     return check_launch("sos_to_delays_adj reduction");
+}
+
+extern "C" pact_status pact_sos_to_delays_adj_adam(const pact_geometry* g, const pact_patches* pt, float* sos,
+                                                   const float* dL_dw, const void* tv_ws, float* loss, float* dL_dsos,
+                                                   float* m, float* v, int step, int* step_counter, float lr,
+                                                   float beta1, float beta2, float eps, const unsigned char* mask,
+                                                   void* ws, size_t ws_bytes, void* stream) {
+    PACT_TRY(check_geometry(g));
+    PACT_TRY(check_patches(pt));
+    if (!sos || !dL_dw || !m || !v)
+        return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_adj_adam: sos, dL_dw, m and v must not be NULL");
+    if (!step_counter && step < 1) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_adj_adam: step must be >= 1");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f))
+        return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_adj_adam: betas must be in [0, 1)");
+    if (!ws) return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_adj_adam: workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (tv_ws && reinterpret_cast<uintptr_t>(tv_ws) % 256)
+        return fail(PACT_ERR_INVALID_ARG, "sos_to_delays_adj_adam: tv_ws must be 256-byte aligned");
+    PACT_TRY(require_sms());
+    const Plan pl = make_plan(g, pt);
+    if (ws_bytes < pl.ws) return fail(PACT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, pl.ws);
+    if (tv_ws && pl.nb_fwd > kTvParts) return fail(PACT_ERR_UNSUPPORTED, "sos_to_delays_adj_adam: %d CTAs", pl.nb_fwd);
+    cudaStream_t st = as_stream(stream);
+    const int GG = g->sos_g * g->sos_g;
+    RayArgs a = make_args(g, pt, pl, sos);
+    a.dLdw = dL_dw;
+    a.part = static_cast<float*>(ws);
+    auto adj = pl.nbands == 1 ? (pl.narrow ? rays_adj_kernel<true, true> : rays_adj_kernel<true, false>)
+                              : (pl.narrow ? rays_adj_kernel<false, true> : rays_adj_kernel<false, false>);
+    PACT_TRY(ensure_smem((const void*)adj, pl.smem_adj, "sos_to_delays_adj_adam: shared memory attribute"));
+    if (launch_pdl(adj, dim3(pl.nb_adj), dim3(1024), pl.smem_adj, st, a, pl.R, pl.nbands) != cudaSuccess)
+        return check_launch("sos_to_delays_adj_adam: adjoint kernel");
+    PACT_TRY(check_launch("sos_to_delays_adj_adam: adjoint kernel"));
+    TailArgs t;
+    t.part = a.part;
+    t.np = pl.nparts;
+    t.GG = GG;
+    t.tv_grad = tv_ws ? static_cast<const float*>(tv_ws) : nullptr;
+    t.tv_part = tv_ws ? static_cast<const float*>(tv_ws) + GG : nullptr;
+    t.ntv = pl.nb_fwd;
+    t.loss = loss;
+    t.grad_out = dL_dsos;
+    t.param = sos;
+    t.m = m;
+    t.v = v;
+    t.lr = lr;
+    t.b1 = beta1;
+    t.b2 = beta2;
+    t.eps = eps;
+    const int s1 = step < 1 ? 1 : step;
+    t.bc1 = (float)(1.0 - pow((double)beta1, s1));
+    t.bc2 = (float)(1.0 - pow((double)beta2, s1));
+    t.counter = step_counter;
+    t.mask = mask;
+    if (launch_pdl(adj_adam_kernel, dim3((GG + 31) / 32), dim3(256), 0, st, t) != cudaSuccess)
+        return check_launch("sos_to_delays_adj_adam: tail kernel");
+    return check_launch("sos_to_delays_adj_adam: tail kernel");
 }

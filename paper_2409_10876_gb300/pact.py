@@ -63,6 +63,10 @@ _SIGS = {
     "pact_patch_fft": ([_GP, _PP, _VP, _I, _VP, _VP], _I),
     "pact_sos_to_delays": ([_GP, _PP, _VP, _VP, _VP], _I),
     "pact_sos_to_delays_clear": ([_GP, _PP, _VP, _VP, _VP, _SZ, _VP], _I),
+    "pact_sos_to_delays_tv_workspace_size": ([_GP, _PP], _SZ),
+    "pact_sos_to_delays_tv": ([_GP, _PP, _VP, _VP, _VP, _SZ, _F, _VP, _SZ, _VP], _I),
+    "pact_sos_to_delays_adj_adam": ([_GP, _PP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _F, _F, _F, _F, _VP,
+                                     _VP, _SZ, _VP], _I),
     "pact_sos_to_delays_adj_workspace_size": ([_GP, _PP], _SZ),
     "pact_sos_to_delays_adj": ([_GP, _PP, _VP, _VP, _VP, _I, _VP, _SZ, _VP], _I),
     "pact_psf_synth": ([_GP, _PP, _VP, _VP, _I, _VP, _VP], _I),
@@ -269,6 +273,48 @@ def sos_to_delays(pb: Problem, sos, w=None, clear=None):
         _check(L.pact_sos_to_delays_clear(pb.gp(), pb.pp(), _ptr(sos), _ptr(w), _ptr(clear), clear.numel(),
                                           _stream()), "sos_to_delays_clear")
     return w
+
+
+def sos_to_delays_tv_workspace_size(pb: Problem) -> int:
+    return int(load().pact_sos_to_delays_tv_workspace_size(pb.gp(), pb.pp()))
+
+
+def sos_to_delays_tv(pb: Problem, sos, w, clear, lam: float, tv_ws):
+    """Eq. 3 with `clear` zeroed, plus lam times the TV terms of Eq. 7 at `sos`
+    into `tv_ws` (uint8 CUDA tensor of sos_to_delays_tv_workspace_size bytes)
+    for the sos_to_delays_adj_adam call of the same iteration."""
+    L = load()
+    sos = _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    _dev(w, "w", torch.float32, (pb.n, pb.n_t))
+    clear = _dev(clear, "clear", torch.float32)
+    _check(L.pact_sos_to_delays_tv(pb.gp(), pb.pp(), _ptr(sos), _ptr(w), _ptr(clear), clear.numel(), float(lam),
+                                   _ptr(tv_ws), tv_ws.numel(), _stream()), "sos_to_delays_tv")
+    return w
+
+
+def sos_to_delays_adj_adam(pb: Problem, sos, dL_dw, m, v, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, mask=None,
+                           step_counter=None, step: int = 1, tv_ws=None, loss=None, grad=None, ws=None):
+    """Adjoint of Eq. 3, the TV subgradient from `tv_ws` (if given) and one
+    in-place Adam step on `sos` in two launches; `grad` (if given) receives
+    the gradient, `loss` (if given, with tv_ws) gets lam TV added."""
+    L = load()
+    sos = _dev(sos, "sos", torch.float32, (pb.g, pb.g))
+    dL_dw = _dev(dL_dw, "dL_dw", torch.float32, (pb.n, pb.n_t))
+    for t, nm in ((m, "m"), (v, "v")):
+        _dev(t, nm, torch.float32, (pb.g, pb.g))
+    if grad is not None:
+        _dev(grad, "grad", torch.float32, (pb.g, pb.g))
+    if mask is not None:
+        _dev(mask, "mask", torch.uint8, (pb.g, pb.g))
+    if step_counter is not None:
+        _dev(step_counter, "step_counter", torch.int32, (2,))
+    if ws is None:
+        ws = _ws(sos_to_delays_adj_workspace_size(pb), sos.device)
+    _check(L.pact_sos_to_delays_adj_adam(pb.gp(), pb.pp(), _ptr(sos), _ptr(dL_dw), _ptr(tv_ws), _ptr(loss),
+                                         _ptr(grad), _ptr(m), _ptr(v), int(step), _ptr(step_counter), float(lr),
+                                         float(beta1), float(beta2), float(eps), _ptr(mask), _ptr(ws), ws.numel(),
+                                         _stream()), "sos_to_delays_adj_adam")
+    return sos
 
 
 def sos_to_delays_adj_workspace_size(pb: Problem) -> int:

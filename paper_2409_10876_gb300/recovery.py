@@ -75,27 +75,31 @@ class PGRecovery:
         self.tables = pact.McdTables(pb, self.d, dev)       # geometry/delay tables, built once
         self.ws_mcd = pact._ws(self.tables.scratch_bytes, dev)
         self.ws_adj = pact._ws(pact.sos_to_delays_adj_workspace_size(pb), dev)
+        self.ws_tv = pact._ws(pact.sos_to_delays_tv_workspace_size(pb), dev) if self.lam != 0.0 else None
         self.graph = None
 
-    # one iteration, enqueued on the current stream (one chain of kernels;
-    # running the TV term on a side stream next to the rays measured slower).
-    # `mark(k)`, if given, is called between the parts (k = 0 start, 1 after the
-    # rays, 2 after the fused pass, 4 after the ray adjoint, 3 end).
+    # one iteration, enqueued on the current stream: four kernels -- rays (with
+    # the clearing of dL/dw and the TV terms), the fused pass, the ray adjoint,
+    # and one tail kernel (partial-grid sum + TV subgradient + Adam).  `mark(k)`,
+    # if given, is called between the parts (k = 0 start, 1 after the rays, 2
+    # after the fused pass, 4 after the ray adjoint and Adam, 3 end).
     def step(self, mark=None):
         pb = self.pb
         mark = mark or (lambda k: None)
         mark(0)
-        pact.sos_to_delays(pb, self.sos, self.w, clear=self.out["dL_dw"])
+        if self.ws_tv is not None:
+            pact.sos_to_delays_tv(pb, self.sos, self.w, self.out["dL_dw"], self.lam, self.ws_tv)
+        else:
+            pact.sos_to_delays(pb, self.sos, self.w, clear=self.out["dL_dw"])
         mark(1)
         pact.mc_deconv_loss(pb, self.w, self.Y, self.d, self.eps, want_grad=True, out=self.out, ws=self.ws_mcd,
                             tables=self.tables, accumulate=True)
         mark(2)
-        pact.sos_to_delays_adj(pb, self.sos, self.out["dL_dw"], self.grad, accumulate=False, ws=self.ws_adj)
+        pact.sos_to_delays_adj_adam(pb, self.sos, self.out["dL_dw"], self.adam_m, self.adam_v, self.lr,
+                                    self.betas[0], self.betas[1], self.adam_eps, mask=self.mask,
+                                    step_counter=self.counter, tv_ws=self.ws_tv, loss=self.out["loss"],
+                                    grad=self.grad, ws=self.ws_adj)
         mark(4)
-        if self.lam != 0.0:
-            pact.tv(pb, self.sos, self.lam, value=self.out["loss"], grad=self.grad, accumulate=True)
-        pact.adam_step(self.sos, self.grad, self.adam_m, self.adam_v, 1, self.lr, self.betas[0], self.betas[1],
-                       self.adam_eps, mask=self.mask, step_counter=self.counter)
         mark(3)
 
     def state(self):
