@@ -250,7 +250,8 @@ __device__ __forceinline__ float ray_part(const RayArgs& a, const float* dv, int
 #pragma unroll 8
     for (int m = m0; m < mf; ++m, uf += 1.f) acc += excess(uf);
     acc *= h;
-    if (m1 > ry.nfull) acc = fmaf(ry.rem, excess(ry.nfull + 0.5f * (ry.rem / h)), acc);
+    if (m0 <= ry.nfull && m1 > ry.nfull)    // the lane whose run holds the partial sample
+        acc = fmaf(ry.rem, excess(ry.nfull + 0.5f * (ry.rem / h)), acc);
     return acc;
 }
 
