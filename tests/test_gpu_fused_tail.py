@@ -42,6 +42,10 @@ class _State:
 
 @pytest.mark.parametrize("name,lam", [("small", 0.5), ("small", 0.0), ("full", 1.0)])
 def test_fused_iteration_equals_separate_calls(name, lam):
+    """Each step from the same state (the separate path starts from the fused
+    path's state): the two differ only by summation order (and the fused pass's
+    float atomics), which Adam's sign-like first steps would amplify along two
+    separate trajectories."""
     cfg = inputs.config_small() if name == "small" else inputs.config_full()
     pb, case, Y, mask = _setup(cfg, 21)
     d, eps, lr = case["d"], cfg.eps, 2.0
@@ -51,6 +55,9 @@ def test_fused_iteration_equals_separate_calls(name, lam):
     ws_tv = pact._ws(pact.sos_to_delays_tv_workspace_size(pb), DEV) if lam else None
     A, B = _State(pb, case), _State(pb, case)
     for it in range(4):
+        for name_ in ("sos", "m", "v", "counter"):
+            getattr(B, name_).copy_(getattr(A, name_))
+        sos0 = A.sos.clone()
         # fused: four kernels
         if ws_tv is not None:
             pact.sos_to_delays_tv(pb, A.sos, A.w, A.out["dL_dw"], lam, ws_tv)
@@ -59,7 +66,7 @@ def test_fused_iteration_equals_separate_calls(name, lam):
         pact.mc_deconv_loss(pb, A.w, Y, d, eps, want_grad=True, out=A.out, ws=ws_mcd, tables=tables, accumulate=True)
         pact.sos_to_delays_adj_adam(pb, A.sos, A.out["dL_dw"], A.m, A.v, lr, mask=mask, step_counter=A.counter,
                                     tv_ws=ws_tv, loss=A.out["loss"], grad=A.grad, ws=ws_adj)
-        # separate entry points
+        # separate entry points, same starting state
         pact.sos_to_delays(pb, B.sos, B.w, clear=B.out["dL_dw"])
         pact.mc_deconv_loss(pb, B.w, Y, d, eps, want_grad=True, out=B.out, ws=ws_mcd, tables=tables, accumulate=True)
         pact.sos_to_delays_adj(pb, B.sos, B.out["dL_dw"], B.grad, accumulate=False, ws=ws_adj)
@@ -69,9 +76,15 @@ def test_fused_iteration_equals_separate_calls(name, lam):
         torch.cuda.synchronize()
         la, lb = float(A.out["loss"].item()), float(B.out["loss"].item())
         assert abs(la - lb) <= 1e-6 * abs(lb), (it, la, lb)
-        assert _rel(A.grad.cpu(), B.grad.cpu()) <= 1e-6, it
-        assert _rel(A.sos.cpu() - 1500.0, B.sos.cpu() - 1500.0) <= 1e-5, it
+        assert _rel(A.w.cpu(), B.w.cpu()) == 0.0, it
+        gB = B.grad.cpu().numpy()
+        assert _rel(A.grad.cpu(), gB) <= 1e-5, it
         assert _rel(A.m.cpu(), B.m.cpu()) <= 1e-5 and _rel(A.v.cpu(), B.v.cpu()) <= 1e-5, it
+        # the Adam update where the gradient is clear of rounding noise
+        dA, dB = (A.sos - sos0).cpu().numpy(), (B.sos - sos0).cpu().numpy()
+        firm = np.abs(gB) > 1e-3 * np.abs(gB).max()
+        assert firm.sum() > 0.2 * case["mask"].sum(), it
+        np.testing.assert_allclose(dA[firm], dB[firm], rtol=1e-4, atol=1e-4 * lr)
         assert A.counter.cpu().tolist() == B.counter.cpu().tolist() == [it + 1, 0]
     # masked nodes never move
     off = ~case["mask"].astype(bool)
