@@ -733,22 +733,36 @@ __global__ void __launch_bounds__(256) adj_adam_kernel(const TailArgs a) {
         bc2 = 1.f - powf(a.b2, t);
     }
     const int q = blockIdx.x * 32 + (threadIdx.x & 31);
-    float g = sum_parts32(a.part, a.np, a.GG, blockIdx.x * 32, red);
-    if (threadIdx.x < 32 && q < a.GG) {
-        if (a.tv_grad) g += a.tv_grad[q];
-        if (a.grad_out) a.grad_out[q] = g;
-        if (!a.mask || a.mask[q]) {
-            const float mq = fmaf(a.b1, a.m[q], (1.f - a.b1) * g);
-            const float vq = fmaf(a.b2, a.v[q], (1.f - a.b2) * g * g);
-            a.m[q] = mq;
-            a.v[q] = vq;
-            a.param[q] -= a.lr * (mq / bc1) / (sqrtf(vq / bc2) + a.eps);
+    const bool mine = threadIdx.x < 32 && q < a.GG;
+    // this node's Adam operands first: their loads overlap the partial-grid sum
+    float m0 = 0.f, v0 = 0.f, p0 = 0.f, tg = 0.f;
+    bool train = false;
+    if (mine) {
+        train = !a.mask || a.mask[q];
+        tg = a.tv_grad ? a.tv_grad[q] : 0.f;
+        if (train) {
+            m0 = a.m[q];
+            v0 = a.v[q];
+            p0 = a.param[q];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.loss && a.tv_part) {
-        float s = 0.f;
-        for (int k = 0; k < a.ntv; ++k) s += a.tv_part[k];
-        a.loss[0] += s;
+    float g = sum_parts32(a.part, a.np, a.GG, blockIdx.x * 32, red);
+    if (mine) {
+        g += tg;
+        if (a.grad_out) a.grad_out[q] = g;
+        if (train) {
+            const float mq = fmaf(a.b1, m0, (1.f - a.b1) * g);
+            const float vq = fmaf(a.b2, v0, (1.f - a.b2) * g * g);
+            a.m[q] = mq;
+            a.v[q] = vq;
+            a.param[q] = p0 - a.lr * (mq / bc1) / (sqrtf(vq / bc2) + a.eps);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 32 && a.loss && a.tv_part) {   // warp 0: loads in parallel,
+        float s = 0.f;                                                        // a fixed-order butterfly
+        for (int k = threadIdx.x; k < a.ntv; k += 32) s += a.tv_part[k];
+        s = warp_sum(s);
+        if (threadIdx.x == 0) a.loss[0] += s;
     }
     if (a.counter) {
         __syncthreads();          // every thread of the CTA has read counter[0]
