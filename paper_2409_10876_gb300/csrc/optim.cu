@@ -65,9 +65,11 @@ __global__ void adam_kernel(int n, float* param, const float* grad, float* m, fl
         param[q] -= lr * (mq / bc1) / (sqrtf(vq / bc2) + eps);
     }
     if (counter) {
-        __syncthreads();                 // every thread of the CTA has read counter[0]
+        // every thread of the CTA has used its read of counter[0] before this
+        // barrier, and nothing else in the kernel depends on the counter, so
+        // the completion count needs no fence
+        __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
             if (atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {   // all CTAs have read it
                 counter[0] += 1;
                 counter[1] = 0;

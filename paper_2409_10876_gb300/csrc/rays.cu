@@ -672,12 +672,12 @@ __device__ __forceinline__ float sum_parts32(const float* part, int np, int GG, 
     float s = 0.f;
     if (q < GG) {
         int r = r0;
-        for (; r + 8 <= r1; r += 8) {            // eight loads in flight, added in order
-            float v[8];
+        for (; r + 16 <= r1; r += 16) {          // sixteen loads in flight, added in order
+            float v[16];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = __ldcg(part + (size_t)(r + k) * GG + q);
+            for (int k = 0; k < 16; ++k) v[k] = __ldcg(part + (size_t)(r + k) * GG + q);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) s += v[k];
+            for (int k = 0; k < 16; ++k) s += v[k];
         }
         for (; r < r1; ++r) s += __ldcg(part + (size_t)r * GG + q);
     }
@@ -765,9 +765,11 @@ __global__ void __launch_bounds__(256) adj_adam_kernel(const TailArgs a) {
         if (threadIdx.x == 0) a.loss[0] += s;
     }
     if (a.counter) {
-        __syncthreads();          // every thread of the CTA has read counter[0]
+        // every thread of the CTA has used its read of counter[0] before this
+        // barrier, and nothing else in the kernel depends on the counter, so
+        // the completion count needs no fence
+        __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
             if (atomicAdd(a.counter + 1, 1) == (int)gridDim.x - 1) {   // all CTAs have read it
                 a.counter[0] += 1;
                 a.counter[1] = 0;
