@@ -125,3 +125,31 @@ def test_rf_synth_rejects_bad_parameters(lib):
         assert msg in lib.pact_last_error_message()
     rp = pact.RfParams(40e6, 0.0, 100, 4e-8, 0.0, 0.0)
     assert lib.pact_rf_synth(ctypes.byref(g), fake, fake, ctypes.byref(rp), fake, fake, 16, None) == 1
+
+
+def test_fused_iteration_ends_reject_bad_arguments(lib):
+    cfg = inputs.config_tiny()
+    g = _geom(cfg)
+    pt = pact._PatchesC(4, 16, 1234, 1e-3)
+    need = lib.pact_sos_to_delays_tv_workspace_size(ctypes.byref(g), ctypes.byref(pt))
+    assert need >= (cfg.sos_g ** 2) * 4 and need % 256 == 0
+    # TV workspace: NULL, misaligned, too small, non-finite lambda
+    assert lib.pact_sos_to_delays_tv(ctypes.byref(g), ctypes.byref(pt), 256, 256, 256, 16, 1.0, None, need, None) == 1
+    assert lib.pact_sos_to_delays_tv(ctypes.byref(g), ctypes.byref(pt), 256, 256, 256, 16, 1.0, 272, need, None) == 1
+    assert lib.pact_sos_to_delays_tv(ctypes.byref(g), ctypes.byref(pt), 256, 256, 256, 16, 1.0, 256, 16, None) == 1
+    assert b"too small" in lib.pact_last_error_message()
+    assert lib.pact_sos_to_delays_tv(ctypes.byref(g), ctypes.byref(pt), 256, 256, 256, 16, float("nan"), 256, need,
+                                     None) == 1
+    # adjoint + Adam: NULL moments, step 0 without a counter, betas out of range, NULL workspace
+    args = lambda **kw: dict(dict(sos=256, dLdw=256, tv=None, loss=None, grad=None, m=256, v=256, step=1, cnt=None,
+                                  lr=0.1, b1=0.9, b2=0.999, eps=1e-8, mask=None, ws=256, wsb=1 << 30), **kw)
+    def call(a):
+        return lib.pact_sos_to_delays_adj_adam(ctypes.byref(g), ctypes.byref(pt), a["sos"], a["dLdw"], a["tv"],
+                                               a["loss"], a["grad"], a["m"], a["v"], a["step"], a["cnt"], a["lr"],
+                                               a["b1"], a["b2"], a["eps"], a["mask"], a["ws"], a["wsb"], None)
+    assert call(args(m=None)) == 1
+    assert call(args(step=0)) == 1
+    assert call(args(b1=1.5)) == 1
+    assert call(args(ws=None)) == 1
+    assert call(args(ws=272)) == 1
+    assert call(args(tv=272)) == 1
