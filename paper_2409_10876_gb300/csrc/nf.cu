@@ -94,9 +94,6 @@ __device__ __forceinline__ void st8(unsigned char* tile, int r, int k0, int K, c
     *reinterpret_cast<uint4*>(tile + umma::kmaj_off(r, k0, K)) = u;
 }
 
-__device__ __forceinline__ float bfv(const unsigned char* tile, int r, int k, int K) {
-    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + umma::kmaj_off(r, k, K)));
-}
 
 // Element u (0..7) of eight BF16 values packed in a uint4, as FP32 (a BF16 is
 // the upper half of the FP32 with the same bits).
@@ -245,8 +242,9 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     auto Hb = [](int i) { return sm + (1 + i) * kTileBytes; };   // h_{l-1} [128 nodes x in]  2 x 32 KB
     auto Wb = [](int i) { return sm + (3 + i) * kTileBytes; };   // W_l     [out x in]        2 x 32 KB
     unsigned char* ones = sm + 5 * kTileBytes;    // [16 x 128 nodes] of 1.0: db = dz^T 1 on the tensor core   4 KB
-    __shared__ float g5_s[kRows];
+    unsigned char* gsplit = ones + kOnesBytes;    // [16 x 128 nodes]: rows 0, 1 = g5 as BF16 high part + remainder  4 KB
     __shared__ float w5_s[kH];
+    __shared__ float red_s[kRows / 32];
     __shared__ uint32_t tmem_s;
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -277,9 +275,7 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         mbar_init_fence();
     }
     __syncthreads();
-    // dz4 = g5 w5 (h4 > 0) for this node; dW5 = sum_nodes g5 h4 for column `tid`
-    // and db5 = sum g5, both in a fixed order
-    g5_s[tid] = g5;
+    // dz4 = g5 w5 (h4 > 0) for this node
     w5_s[tid] = __bfloat162float(a.wbf[kOffW5 + tid]);
     __syncthreads();
 #pragma unroll 1
@@ -290,21 +286,50 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         for (int u = 0; u < 8; ++u) dz[u] = bf16_at(hv, u) > 0.f ? g5 * w5_s[c + u] : 0.f;
         st8(dzA, tid, c, kH, dz);
     }
+    // dW5 = h4^T g5 on the tensor core: g5 split into a BF16 high part and the
+    // BF16 remainder (rows 0 and 1 of a [16 x nodes] tile; together about 16
+    // significant bits), the two result columns added in FP32
     {
-        float s = 0.f;
-        for (int r = 0; r < kRows; ++r) s = fmaf(g5_s[r], bfv(H4, r, tid, kH), s);
-        part[kOffW5 + tid] = s;
-        if (tid == 0) {
-            float b = 0.f;
-            for (int r = 0; r < kRows; ++r) b += g5_s[r];
-            part[kOffB5] = b;
-        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn(g5);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(g5 - __bfloat162float(hi));
+        const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+            *reinterpret_cast<__nv_bfloat16*>(gsplit + umma::kmaj_off(n, tid, kRows)) = n == 0 ? hi : (n == 1 ? lo : zero);
     }
+    umma::fence_smem_to_async();
+    umma::fence_before();
     __syncthreads();
+    umma::fence_after();
+    if (tid == 0) {
+        for (int kk = 0; kk < kRows / 16; ++kk)
+            umma::mma(tmem_s + 256, umma::mn_slice(H4, kH, kk), umma::kslice(gsplit, kRows, kk),
+                      umma::idesc_bf16(128, 16) | (1u << 15), kk > 0);
+        umma::commit(&bar);
+    }
+    // db5 = sum over nodes of g5, a fixed-order block reduction
+    {
+        const float b = warp_sum(g5);
+        if ((tid & 31) == 0) red_s[warp] = b;
+    }
+    wait_bar(&bar, 0u, a.status, a.limit_ns);
+    umma::fence_after();
+    {
+        const uint32_t lb = (uint32_t)(warp * 32) << 16;
+        part[kOffW5 + tid] = umma::ld1(tmem_s + 256 + lb) + umma::ld1(tmem_s + 257 + lb);
+    }
+    if (tid == 0) {
+        float b = 0.f;
+        for (int w = 0; w < kRows / 32; ++w) b += red_s[w];
+        part[kOffB5] = b;
+    }
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
 
     const uint32_t tmem = tmem_s;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    uint32_t phase = 0;
+    uint32_t phase = 1;                             // phase 0 was the dW5 product
     for (int l = kL; l >= 1; --l) {
         const int K_in = in_dim(l);
         unsigned char* Hr = Hb(l & 1);
@@ -414,7 +439,7 @@ NfPlan nf_plan(const pact_geometry* g) {
     o += 256;
     p.total = o;
     p.smem_fwd = 16384 + 2 * kTileBytes + 16384 + (kL - 1) * kTileBytes;
-    p.smem_bwd = 5 * kTileBytes + kOnesBytes;
+    p.smem_bwd = 5 * kTileBytes + 2 * kOnesBytes;
     return p;
 }
 
