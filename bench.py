@@ -560,15 +560,27 @@ def nf_variant(args, cfg, case, pb, Y, flush, stream):
     import torch
     from paper_2409_10876_gb300 import inputs
     from paper_2409_10876_gb300.recovery import NFRecovery
-    rec = NFRecovery(pb, Y, case["d"], cfg.eps, 5e-3, inputs.nf_init(args.seed), case["mask"])
+    rec = NFRecovery(pb, Y, case["d"], cfg.eps, inputs.NF_LR, inputs.nf_init(args.seed), case["mask"])
     g = rec.capture()
     for _ in range(3):
         g.replay()
     steps = max(20, min(args.steps, 500))
     ms = _time_graph(g, flush, stream, steps)
-    return {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
-            "dtype": "bf16 (field) + f32 (forward model)", "params": int(rec.params.numel()),
-            "gpu_launches_per_step": 9}
+    out = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_step": statistics.mean(ms), "steps": steps,
+           "dtype": "bf16 (field) + f32 (forward model)", "params": int(rec.params.numel()),
+           "gpu_launches_per_step": 9, "lr": inputs.NF_LR}
+    del rec, g
+    # what the field recovers: a fresh run of the configuration's iterations
+    rec = NFRecovery(pb, Y, case["d"], cfg.eps, inputs.NF_LR, inputs.nf_init(args.seed), case["mask"])
+    rec.capture()
+    hist = rec.run(cfg.steps, record_every=cfg.steps // 4)
+    m = case["mask"].astype(bool)
+    sos = rec.sos.cpu().numpy().astype(np.float64)
+    t = (sos[m] - 1525.0) / 125.0
+    out["recovery"] = {"iters": cfg.steps, "loss": hist,
+                       "sos_rms_mps": float(np.sqrt(np.mean((sos[m] - case["sos_true"][m]) ** 2))),
+                       "saturated_nodes": int((np.abs(t) > 0.99).sum())}
+    return out
 
 
 def channels_variant(args, cfg, dev, flush, stream):
@@ -701,7 +713,7 @@ def channel_data_variant(args, dev, flush, stream):
     out["mc_deconv_loss"] = {"ms": statistics.mean(ms), "algorithmic_bytes": alg, "achieved_gbs": ach,
                              "peak_gbs": peak, "peak_source": src, "frac": ach / peak}
     del rec, g, gm
-    nf = NFRecovery(pb, Y, case["d"], cfg.eps, 5e-3, inputs.nf_init(args.seed), case["mask"])
+    nf = NFRecovery(pb, Y, case["d"], cfg.eps, inputs.NF_LR, inputs.nf_init(args.seed), case["mask"])
     g = nf.capture()
     for _ in range(3):
         g.replay()
@@ -910,16 +922,17 @@ def table1_run(args, cfg, pb, dev, net1, seeds=(0, 1, 2, 3, 4)):
     the mask nodes, range sos_hi - sos_lo; RMS error) for deconvolution at the
     uniform SOS, the pixel-grid recovery from uniform (1000 iterations), the
     warm-started one (recover_warm, run until it settles), the paper's SIREN
-    field (1000 iterations) and the true SOS ("SOS oracle"), with GPU wall
-    times (synchronised host clock)."""
+    field and the Fourier-feature MLP field (1000 iterations each) and the true
+    SOS ("SOS oracle"), with GPU wall times (synchronised host clock)."""
     import torch
     from paper_2409_10876_gb300 import inputs, quality, warmstart
-    from paper_2409_10876_gb300.recovery import PGRecovery, SirenRecovery, measurement_spectra, synthesize_stack
+    from paper_2409_10876_gb300.recovery import (NFRecovery, PGRecovery, SirenRecovery, measurement_spectra,
+                                                 synthesize_stack)
     pm = quality.image_mask(cfg)
     nm = inputs.sos_mask(cfg).astype(bool)
     mask_d = torch.as_tensor(nm.astype(np.uint8), device=dev)
     rng_sos = cfg.sos_hi - cfg.sos_lo
-    rows = {k: [] for k in ("uniform_sos", "pg_cold", "pg_warm", "siren", "sos_oracle")}
+    rows = {k: [] for k in ("uniform_sos", "pg_cold", "pg_warm", "siren", "nf_mlp", "sos_oracle")}
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -954,8 +967,16 @@ def table1_run(args, cfg, pb, dev, net1, seeds=(0, 1, 2, 3, 4)):
                 rec.iterate()
             return rec.sos
 
+        def nf_mlp():
+            rec = NFRecovery(pb, Y, case["d"], cfg.eps, inputs.NF_LR, inputs.nf_init(seed), case["mask"])
+            rec.capture()
+            for _ in range(cfg.steps):
+                rec.iterate()
+            return rec.sos
+
         for name, fn in (("uniform_sos", lambda: v_u), ("pg_cold", pg_cold), ("pg_warm", pg_warm),
-                         ("siren", siren), ("sos_oracle", lambda: torch.as_tensor(case["sos_true"], device=dev))):
+                         ("siren", siren), ("nf_mlp", nf_mlp),
+                         ("sos_oracle", lambda: torch.as_tensor(case["sos_true"], device=dev))):
             v, secs = timed(fn)
             img, s_img = timed(lambda: quality.recovered_image(pb, Y, case["d"], cfg.eps, v))
             vs = v.cpu().numpy().astype(np.float64)

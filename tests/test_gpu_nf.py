@@ -175,3 +175,30 @@ def test_siren_objective_gradient_end_to_end_and_recovery():
     rec.capture()
     h = rec.run(60, record_every=1)
     assert np.all(np.isfinite(h)) and h[-1] < 0.9 * h[0]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_nf_field_recovers_on_the_benchmark_workload(seed):
+    """The Fourier-feature MLP field at its learning rate (inputs.NF_LR), 1000
+    Adam iterations from a uniform 1500 m/s field on phantoms 0 and 1 of the
+    benchmark workload: no node's tanh output saturates, the loss falls, and
+    on phantom 1 the field reaches the data loss of the true SOS (the noise
+    floor) with an SOS error of a few m/s."""
+    from paper_2409_10876_gb300.recovery import measurement_spectra
+    cfg = inputs.config_full()
+    pb = pact.Problem(cfg, "cuda")
+    case = inputs.make_case(cfg, seed)
+    Y = measurement_spectra(pb, case, "cuda")
+    rec = NFRecovery(pb, Y, case["d"], cfg.eps, inputs.NF_LR, inputs.nf_init(seed), case["mask"])
+    rec.capture()
+    hist = rec.run(1000, record_every=250)
+    m = case["mask"].astype(bool)
+    sos = rec.sos.cpu().numpy().astype(np.float64)
+    t = (sos[m] - inputs.NF_V_MID) / inputs.NF_V_HALF
+    assert np.all(np.isfinite(hist)) and np.abs(t).max() < 0.99
+    assert hist[-1] < 0.6 * hist[0]
+    if seed == 1:
+        w_true = pact.sos_to_delays(pb, torch.as_tensor(case["sos_true"], device="cuda"))
+        floor = float(pact.mc_deconv_loss(pb, w_true, Y, case["d"], cfg.eps, want_grad=False)["loss"].item())
+        rms = float(np.sqrt(np.mean((sos[m] - case["sos_true"][m]) ** 2)))
+        assert hist[-1] < 1.05 * floor and rms < 3.0, (hist, floor, rms)
