@@ -126,6 +126,56 @@ def das_at(g, rf, fs: float, t0: float, d, rows, cols) -> torch.Tensor:
     return out
 
 
+# ---------------------------------------------------------------------------
+# Transducer band-limit (a model mismatch for robustness studies: the method
+# assumes the channel data above; a real transducer also band-passes it).
+#
+# Reading: the transducer's impulse response is a Gaussian-windowed cosine at
+# the centre frequency fc,
+#     h(tau) = (2 / Z) exp(-tau^2 / (2 s_t^2)) cos(2 pi fc tau),
+# sampled at tau_k = k / fs for |k| <= K = ceil(4 s_t fs), Z = sum_k of the
+# window (unit gain at fc up to the image at -fc), zero phase (no shift of
+# the times of flight).  Its amplitude response near fc is a Gaussian in f
+# whose full width at half amplitude is frac_bw * fc:
+#     s_f = frac_bw fc / (2 sqrt(2 ln 2)),   s_t = 1 / (2 pi s_f).
+# Every channel is filtered along time, zero outside the record.
+# ---------------------------------------------------------------------------
+
+def bandpass_taps(fs: float, fc: float, frac_bw: float) -> torch.Tensor:
+    """Taps h_k, k = -K .. K, of the transducer impulse response (see above)."""
+    s_f = frac_bw * fc / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    s_t = 1.0 / (2.0 * math.pi * s_f)
+    K = int(math.ceil(4.0 * s_t * fs))
+    tau = torch.arange(-K, K + 1, dtype=DT) / fs
+    env = torch.exp(-0.5 * (tau / s_t) ** 2)
+    return 2.0 * env * torch.cos(2.0 * math.pi * fc * tau) / env.sum()
+
+
+def bandpass_response(fs: float, fc: float, frac_bw: float, f) -> torch.Tensor:
+    """|H(f)| of the sampled taps: the magnitude of sum_k h_k exp(-2 pi j f k / fs)."""
+    h = bandpass_taps(fs, fc, frac_bw)
+    K = (h.numel() - 1) // 2
+    k = torch.arange(-K, K + 1, dtype=DT)
+    f = O._t(f).reshape(-1, 1)
+    ph = 2.0 * math.pi * f * k / fs
+    return torch.sqrt((h * torch.cos(ph)).sum(1) ** 2 + (h * torch.sin(ph)).sum(1) ** 2)
+
+
+def rf_bandpass(rf, fs: float, fc: float, frac_bw: float) -> torch.Tensor:
+    """out[n, q] = sum_k h_k rf[n, q - k], zero outside 0 <= q - k < n_s."""
+    rf = O._t(rf)
+    h = bandpass_taps(fs, fc, frac_bw)
+    K = (h.numel() - 1) // 2
+    n_t, n_s = rf.shape
+    pad = torch.zeros((n_t, n_s + 2 * K), dtype=DT)
+    pad[:, K:K + n_s] = rf
+    out = torch.zeros((n_t, n_s), dtype=DT)
+    for j in range(2 * K + 1):                # tap k = j - K reads rf[q - k] = pad[q - k + K]
+        k = j - K
+        out += h[j] * pad[:, K - k:K - k + n_s]
+    return out
+
+
 def pulse_band(sigma: float, level: float = 0.5):
     """Frequencies [Hz] where the amplitude spectrum of psi falls to `level`
     of its peak, from the closed form x^2 exp(1 - x^2) = level with

@@ -172,3 +172,30 @@ def test_das_at_equals_the_full_stack():
     rows, cols = np.array([0, 5, 16, 32]), np.array([32, 7, 16, 0])
     part = R.das_at(g, rf, 40e6, 1e-6, d, torch.tensor(rows), torch.tensor(cols)).numpy()
     assert np.abs(part - full[:, rows, cols]).max() < 1e-12
+
+
+def test_bandpass_taps_closed_forms():
+    """The band-limit filter against its definition: an impulse gives the
+    taps back, a constant gives their sum, a long cosine at fc keeps its
+    amplitude (|H(fc)| = 1 + the image term), and the half-amplitude points
+    sit at fc -/+ frac_bw fc / 2 (the Gaussian response)."""
+    import math
+    fs, fc, bw = 40e6, 5e6, 0.6
+    h = R.bandpass_taps(fs, fc, bw).numpy()
+    K = (h.size - 1) // 2
+    assert np.allclose(h, h[::-1])                                     # zero phase
+    n_s = 600
+    x = np.zeros((3, n_s))
+    x[0, 300] = 1.0
+    x[1, :] = 1.0
+    q = np.arange(n_s)
+    x[2] = np.cos(2 * math.pi * fc * q / fs)
+    y = R.rf_bandpass(torch.as_tensor(x), fs, fc, bw).numpy()
+    assert np.allclose(y[0, 300 - K:300 + K + 1], h, atol=1e-15) and abs(y[0]).sum() == pytest.approx(abs(h).sum())
+    assert np.allclose(y[1, K:n_s - K], h.sum(), atol=1e-12)
+    gain = float(R.bandpass_response(fs, fc, bw, [fc])[0])
+    assert abs(gain - 1.0) < 1e-3
+    assert np.allclose(y[2, K:n_s - K], gain * x[2, K:n_s - K], atol=1e-9)
+    lo, hi = R.bandpass_response(fs, fc, bw, [fc * (1 - bw / 2), fc * (1 + bw / 2)]).numpy()
+    assert abs(lo - 0.5) < 0.02 and abs(hi - 0.5) < 0.02
+    assert float(R.bandpass_response(fs, fc, bw, [0.0])[0]) < 1e-3    # DC rejected
