@@ -726,7 +726,7 @@ def channel_data_variant(args, dev, flush, stream):
 
 def mismatch_study(pb, cfg, case, dev, iters: int = 200):
     """Model mismatch in the channel data (geometric spreading, a ring-radius
-    offset): channel data -> DAS -> patch spectra, then the data loss at the
+    offset, a transducer band-limit): channel data -> DAS -> patch spectra, then the data loss at the
     true SOS against uniform 1500 m/s, and how far the pixel-grid recovery
     started at the true SOS drifts from it in `iters` iterations (RMS over
     the mask; lambda = 0)."""
@@ -738,9 +738,10 @@ def mismatch_study(pb, cfg, case, dev, iters: int = 200):
     truth = case["sos_true"].astype(np.float64)
     rms = lambda s: float(np.sqrt(np.mean((s.astype(np.float64)[mask] - truth[mask]) ** 2)))
     res = {}
-    for name, spread, dr in (("model", 0.0, 0.0), ("spreading_r^-1/2", 0.5, 0.0), ("ring_+0.1mm", 0.0, 0.1e-3),
-                             ("ring_+0.3mm", 0.0, 0.3e-3)):
-        Y = pact.patch_fft(pb, channel_data_stack(pb, case, dev, spread, dr))
+    for name, spread, dr, bp in (("model", 0.0, 0.0, None), ("spreading_r^-1/2", 0.5, 0.0, None),
+                                 ("ring_+0.1mm", 0.0, 0.1e-3, None), ("ring_+0.3mm", 0.0, 0.3e-3, None),
+                                 ("bandlimit_5MHz_60%", 0.0, 0.0, (5e6, 0.6))):
+        Y = pact.patch_fft(pb, channel_data_stack(pb, case, dev, spread, dr, bandpass=bp))
         losses = {}
         for start in ("sos_init", "sos_true"):
             r = PGRecovery(pb, Y, case["d"], cfg.eps, 0.0, 0.0, torch.as_tensor(case[start]),

@@ -159,6 +159,24 @@ pact_status pact_rf_synth(const pact_geometry* g, const float* p0, const float* 
                           float* rf, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * Transducer band-limit for channel data (no counterpart in the paper: a model
+ * mismatch for robustness studies, next to the spreading and ring-radius
+ * offsets of pact_rf_synth).  Every channel is filtered along time by the
+ * zero-phase impulse response
+ *   h_k = (2 / Z) exp(-tau_k^2 / (2 s_t^2)) cos(2 pi fc tau_k),  tau_k = k / fs,
+ * |k| <= K = ceil(4 s_t fs), Z = sum_k exp(-tau_k^2 / (2 s_t^2)) (unit gain at
+ * fc), s_t = 1 / (2 pi s_f), s_f = frac_bw fc / (2 sqrt(2 ln 2)): the amplitude
+ * response is a Gaussian in f of full width frac_bw fc at half amplitude.
+ *   rf_in   DEVICE float [n_t][n_s]
+ *   rf_out  DEVICE float [n_t][n_s], output; a different buffer from rf_in
+ *   rf_out[n][q] = sum_k h_k rf_in[n][q - k], zero outside the record.
+ * Errors: INVALID_ARG for NULL or equal buffers, sizes < 1, fs <= 0, fc not
+ * in (0, fs/2), frac_bw not in (0, 2]; SHAPE for n_t > 65535 or K > 512.
+ */
+pact_status pact_rf_bandpass(const float* rf_in, float* rf_out, int n_t, int n_s, float fs, float fc, float frac_bw,
+                             void* stream);
+
+/*
  * Patch spectra (Sec. S1.5, the Y_i(k; d_j) of Eq. 5): crop each of the m
  * channels around every patch centre, multiply by the Gaussian window
  * exp(-|rho|^2 / (2 sigma^2)), FWHM = 2 sqrt(2 ln 2) sigma, rho measured from

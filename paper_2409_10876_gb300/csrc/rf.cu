@@ -11,6 +11,7 @@
 //      the lanes covering consecutive samples around the arrival, and the CTA
 //      writes the record back (first pass: from zero).
 #include <algorithm>
+#include <cmath>
 
 #include "pact_internal.cuh"
 
@@ -90,10 +91,74 @@ __global__ void __launch_bounds__(kThreads) rf_scatter_kernel(const RfArgs a) {
     for (int q = threadIdx.x; q < a.n_s; q += blockDim.x) row[q] = rec[q];
 }
 
+// Transducer band-limit (a model mismatch for robustness studies): every
+// channel filtered along time by the zero-phase impulse response
+//   h_k = (2 / Z) exp(-tau_k^2 / (2 s_t^2)) cos(2 pi fc tau_k),  tau_k = k / fs,
+// |k| <= K, Z the sum of the window, s_t = 1 / (2 pi s_f) and s_f = frac_bw fc
+// / (2 sqrt(2 ln 2)) (full width at half amplitude frac_bw fc); samples
+// outside the record are zero.  CTA (tile of kBpTile samples, channel): the
+// taps (computed per CTA, the window sum in a fixed order) and the tile with
+// its K-sample halos in shared memory; one thread per output sample.
+constexpr int kBpTile = 256;
+constexpr int kBpMaxK = 512;
+
+__global__ void __launch_bounds__(kBpTile) rf_bandpass_kernel(const float* in, float* out, int n_s, float inv_fs,
+                                                              float fc, float s_t, int K) {
+    extern __shared__ float sm_bp[];
+    float* taps = sm_bp;                     // [2K + 1]
+    float* x = sm_bp + 2 * K + 1;            // [kBpTile + 2K]
+    __shared__ float red[kBpTile / 32];
+    const int n = blockIdx.y, q0 = blockIdx.x * kBpTile, tid = threadIdx.x;
+    float zs = 0.f;
+    for (int j = tid; j <= 2 * K; j += blockDim.x) {
+        const float tau = (float)(j - K) * inv_fs, u = tau / s_t;
+        const float env = expf(-0.5f * u * u);
+        taps[j] = env * cospif(2.f * fc * tau);
+        zs += env;
+    }
+    const float z = block_sum(zs, red);      // valid in thread 0
+    if (tid == 0) red[0] = 2.f / z;
+    const float* row = in + (size_t)n * n_s;
+    for (int j = tid; j < kBpTile + 2 * K; j += blockDim.x) {
+        const int q = q0 - K + j;
+        x[j] = q >= 0 && q < n_s ? row[q] : 0.f;
+    }
+    __syncthreads();
+    const float scale = red[0];
+    const int q = q0 + tid;
+    if (q >= n_s) return;
+    // out[q] = sum_k h_k in[q - k]: x[tid + K - k] with k = j - K
+    float acc = 0.f;
+    for (int j = 0; j <= 2 * K; ++j) acc = fmaf(taps[j], x[tid + 2 * K - j], acc);
+    out[(size_t)n * n_s + q] = scale * acc;
+}
+
 }  // namespace
 }  // namespace pact
 
 using namespace pact;
+
+extern "C" pact_status pact_rf_bandpass(const float* rf_in, float* rf_out, int n_t, int n_s, float fs, float fc,
+                                        float frac_bw, void* stream) {
+    if (!rf_in || !rf_out) return fail(PACT_ERR_INVALID_ARG, "rf_bandpass: rf_in and rf_out must not be NULL");
+    if (rf_in == rf_out) return fail(PACT_ERR_INVALID_ARG, "rf_bandpass: rf_in and rf_out must be different buffers");
+    if (n_t < 1 || n_s < 1) return fail(PACT_ERR_INVALID_ARG, "rf_bandpass: n_t and n_s must be >= 1");
+    if (n_t > 65535) return fail(PACT_ERR_SHAPE, "rf_bandpass: n_t must be <= 65535");
+    if (!(fs > 0.f) || !isfinite(fs)) return fail(PACT_ERR_INVALID_ARG, "rf_bandpass: fs must be finite and > 0");
+    if (!(fc > 0.f) || !(fc < 0.5f * fs)) return fail(PACT_ERR_INVALID_ARG, "rf_bandpass: fc must be in (0, fs / 2)");
+    if (!(frac_bw > 0.f) || !(frac_bw <= 2.f)) return fail(PACT_ERR_INVALID_ARG, "rf_bandpass: frac_bw must be in (0, 2]");
+    const double s_f = (double)frac_bw * fc / (2.0 * sqrt(2.0 * log(2.0)));
+    const double s_t = 1.0 / (2.0 * 3.141592653589793 * s_f);
+    const double Kd = ceil(4.0 * s_t * fs);
+    if (Kd > kBpMaxK) return fail(PACT_ERR_SHAPE, "rf_bandpass: %g taps per side, at most %d", Kd, kBpMaxK);
+    const int K = (int)Kd;
+    const size_t smem = (size_t)(2 * K + 1 + kBpTile + 2 * K) * sizeof(float);
+    PACT_TRY(ensure_smem((const void*)rf_bandpass_kernel, smem, "rf_bandpass: shared memory attribute"));
+    const dim3 grid((n_s + kBpTile - 1) / kBpTile, n_t);
+    rf_bandpass_kernel<<<grid, kBpTile, smem, as_stream(stream)>>>(rf_in, rf_out, n_s, (float)(1.0 / fs), fc,
+                                                                  (float)s_t, K);
+    return check_launch("rf_bandpass kernel");
+}
 
 extern "C" size_t pact_rf_synth_workspace_size(const pact_geometry* g, int pixels_per_pass) {
     if (check_geometry(g) != PACT_OK || pixels_per_pass < 1) return 0;

@@ -60,6 +60,7 @@ _SIGS = {
     "pact_das_stack": ([_GP, _VP, _I, _F, _F, _VP, _I, _VP, _VP], _I),
     "pact_rf_synth_workspace_size": ([_GP, _I], _SZ),
     "pact_rf_synth": ([_GP, _VP, _VP, ctypes.POINTER(RfParams), _VP, _VP, _SZ, _VP], _I),
+    "pact_rf_bandpass": ([_VP, _VP, _I, _I, _F, _F, _F, _VP], _I),
     "pact_patch_fft": ([_GP, _PP, _VP, _I, _VP, _VP], _I),
     "pact_sos_to_delays": ([_GP, _PP, _VP, _VP, _VP], _I),
     "pact_sos_to_delays_clear": ([_GP, _PP, _VP, _VP, _VP, _SZ, _VP], _I),
@@ -244,6 +245,21 @@ def rf_synth(pb: Problem, p0, sos, fs: float, t0: float, n_s: int, sigma: float,
                            _stream()), "rf_synth")
     return rf
 
+
+
+def rf_bandpass(rf, fs: float, fc: float, frac_bw: float, out=None):
+    """Channel data [N_t, n_s] filtered along time by the transducer band-limit
+    (zero-phase Gaussian-windowed cosine at fc, half-amplitude width frac_bw fc)."""
+    L = load()
+    rf = _dev(rf, "rf", torch.float32)
+    if rf.dim() != 2:
+        raise ValueError("rf must be [N_t, n_s]")
+    if out is None:
+        out = torch.empty_like(rf)
+    _dev(out, "out", torch.float32, tuple(rf.shape))
+    _check(L.pact_rf_bandpass(_ptr(rf), _ptr(out), rf.shape[0], rf.shape[1], float(fs), float(fc), float(frac_bw),
+                              _stream()), "rf_bandpass")
+    return out
 
 def patch_fft(pb: Problem, stack, Y=None):
     """Sec. S1.5: windowed patch spectra Y [N, M, P, P/2+1] (complex64)."""

@@ -272,14 +272,18 @@ def measurement_spectra(pb: "pact.Problem", case: dict, device) -> torch.Tensor:
 
 
 def channel_data_stack(pb: "pact.Problem", case: dict, device, spread: float = 0.0, ring_dr: float = 0.0,
-                       ws=None) -> torch.Tensor:
+                       ws=None, bandpass=None) -> torch.Tensor:
     """Delay stack [M, H, W] made end to end from synthetic ring channel data:
     pact_rf_synth (straight-ray times of flight through the ground-truth SOS,
     differentiated pulses from the ground-truth IP; optional spreading and
-    ring-radius mismatch) followed by DAS (Eq. 1) at the M delays."""
+    ring-radius mismatch), optionally a transducer band-limit
+    (bandpass = (fc, frac_bw), pact_rf_bandpass), then DAS (Eq. 1) at the M
+    delays."""
     cfg = pb.cfg
     rf = pact.rf_synth(pb, torch.as_tensor(case["ip"], device=device), torch.as_tensor(case["sos_true"], device=device),
                        cfg.rf_fs, cfg.rf_t0, cfg.rf_ns, cfg.rf_sigma, spread, ring_dr, ws=ws)
+    if bandpass is not None:
+        rf = pact.rf_bandpass(rf, cfg.rf_fs, bandpass[0], bandpass[1])
     return pact.das_stack(pb, rf, cfg.rf_fs, cfg.rf_t0, case["d"])
 
 

@@ -120,3 +120,28 @@ def test_rf_to_das_centred_source_closed_form():
     uu = (wn[None, :] - d[:, None].astype(np.float64)) / cfg.v0 / sig
     ref = ((1.0 - uu * uu) * np.exp(-0.5 * uu * uu)).sum(1)
     assert np.abs(st - ref).max() <= 2e-3 * cfg.n_t
+
+
+@pytest.mark.parametrize("n_t,n_s,fc,bw", [(12, 1000, 5e6, 0.6), (3, 20, 8e6, 0.3), (1024, 4096, 4e6, 1.0)])
+def test_rf_bandpass_matches_oracle(n_t, n_s, fc, bw):
+    """pact_rf_bandpass against the FP64 oracle: random channel data, the
+    channel-data size (8 channels compared), and a record shorter than the
+    filter (n_s = 20 < 2K + 1)."""
+    from oracle import rf_oracle as R
+    fs = 40e6
+    rng = np.random.default_rng(n_t + n_s)
+    x = rng.standard_normal((n_t, n_s)).astype(np.float32)
+    y = pact.rf_bandpass(torch.as_tensor(x, device="cuda"), fs, fc, bw).cpu().numpy()
+    rows = np.arange(n_t) if n_t <= 16 else rng.choice(n_t, 8, replace=False)
+    ref = R.rf_bandpass(torch.as_tensor(x[rows].astype(np.float64)), fs, fc, bw).numpy()
+    err = np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref)
+    assert err <= 1e-5, err
+
+
+def test_rf_bandpass_rejects_bad_arguments():
+    x = torch.zeros((4, 64), device="cuda")
+    for args in ((40e6, 25e6, 0.5), (40e6, 5e6, 0.0), (40e6, 5e6, 3.0), (0.0, 5e6, 0.5), (40e6, 1e3, 0.01)):
+        with pytest.raises(pact.PactError):
+            pact.rf_bandpass(x, *args)
+    with pytest.raises(pact.PactError):
+        pact.rf_bandpass(x, 40e6, 5e6, 0.5, out=x)
