@@ -585,7 +585,8 @@ def nf_variant(args, cfg, case, pb, Y, flush, stream):
 
 def channels_variant(args, cfg, dev, flush, stream):
     """Iterations/s against the number of delay channels M at the same delay
-    range (the trade-off behind the paper's channel-count ablation, Sec. S3.1)."""
+    range, and the SOS error after the configuration's iterations (the
+    trade-off behind the paper's channel-count ablation, Sec. S3.1)."""
     import torch
     from paper_2409_10876_gb300 import inputs, pact
     from paper_2409_10876_gb300.recovery import PGRecovery, measurement_spectra
@@ -602,6 +603,17 @@ def channels_variant(args, cfg, dev, flush, stream):
             g.replay()
         ms = _time_graph(g, flush, stream, 200)
         out[str(m)] = {"iters_per_s": 1e3 / statistics.mean(ms), "ms_per_iter": statistics.mean(ms)}
+        del rec, g
+        # what M channels recover: the configuration's iterations from uniform
+        rec = PGRecovery(pb, Y, case["d"], c.eps, c.tv_lambda, c.lr, torch.as_tensor(case["sos_init"]),
+                         torch.as_tensor(case["mask"]))
+        rec.capture()
+        rec.run(c.steps)
+        mk = case["mask"].astype(bool)
+        sos = rec.sos.cpu().numpy().astype(np.float64)
+        out[str(m)]["sos_rms_mps_after"] = float(np.sqrt(np.mean((sos[mk] - case["sos_true"][mk]) ** 2)))
+        out[str(m)]["iters"] = c.steps
+        del rec
     return out
 
 
