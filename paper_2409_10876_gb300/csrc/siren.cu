@@ -37,23 +37,37 @@ struct SirenArgs {
 
 __device__ __forceinline__ float coord(int q, int G) { return (q - 0.5f * (G - 1)) / (0.5f * (G - 1)); }
 
+// kFwdLanes threads per node, lane l taking features l, l + kFwdLanes, ...
+// (neighbouring lanes read neighbouring parameters, every node of a warp the
+// same ones), the lanes' sums combined by a fixed butterfly.
+constexpr int kFwdLanes = 4;
+
 __global__ void __launch_bounds__(256) siren_fwd_kernel(const SirenArgs a) {
     __shared__ float p_s[kNP];
     for (int e = threadIdx.x; e < kNP; e += blockDim.x) p_s[e] = a.params[e];
     __syncthreads();
-    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int node = t / kFwdLanes, part = t % kFwdLanes;
     const int GG = a.G * a.G;
-    if (node >= GG) return;
-    const float x = coord(node % a.G, a.G), y = coord(node / a.G, a.G);
+    const bool valid = node < GG;
+    const int nd = valid ? node : 0;
+    const float x = coord(nd % a.G, a.G), y = coord(nd / a.G, a.G);
+    // sin(omega0 t) as sinpi((omega0 / pi) t): the argument reduction is exact in units of pi
+    const float om_pi = a.omega0 * 0.3183098861837907f;
     float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll 4
-    for (int f = 0; f < kF; f += 2) {
-        const float s0 = sinf(a.omega0 * fmaf(p_s[2 * f], x, fmaf(p_s[2 * f + 1], y, p_s[kOffB1 + f])));
-        const float s1 = sinf(a.omega0 * fmaf(p_s[2 * f + 2], x, fmaf(p_s[2 * f + 3], y, p_s[kOffB1 + f + 1])));
+    for (int f = part; f < kF; f += 2 * kFwdLanes) {
+        const int f1 = f + kFwdLanes;
+        const float s0 = sinpif(om_pi * fmaf(p_s[2 * f], x, fmaf(p_s[2 * f + 1], y, p_s[kOffB1 + f])));
+        const float s1 = sinpif(om_pi * fmaf(p_s[2 * f1], x, fmaf(p_s[2 * f1 + 1], y, p_s[kOffB1 + f1])));
         acc0 = fmaf(p_s[kOffW2 + f], s0, acc0);
-        acc1 = fmaf(p_s[kOffW2 + f + 1], s1, acc1);
+        acc1 = fmaf(p_s[kOffW2 + f1], s1, acc1);
     }
-    const float z = acc0 + acc1 + p_s[kOffB2];
+    float acc = acc0 + acc1;
+#pragma unroll
+    for (int o = 1; o < kFwdLanes; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!valid || part != 0) return;
+    const float z = acc + p_s[kOffB2];
     a.z[node] = z;
     const bool inside = a.mask ? a.mask[node] != 0 : true;
     a.sos[node] = inside ? fmaf(p_s[kOffScale], z, p_s[kOffOffset]) : a.v_bg;
@@ -85,12 +99,12 @@ __global__ void __launch_bounds__(kF) siren_bwd_kernel(const SirenArgs a) {
     __syncthreads();
     const int f = threadIdx.x;
     const float w1x = a.params[2 * f], w1y = a.params[2 * f + 1], b1 = a.params[kOffB1 + f];
-    const float w2 = a.params[kOffW2 + f], om = a.omega0;
+    const float w2 = a.params[kOffW2 + f], om = a.omega0, om_pi = om * 0.3183098861837907f;
     float sx = 0.f, sy = 0.f, sb = 0.f, sw = 0.f;
     for (int e = 0; e < nn; ++e) {
         const float dz = dz_s[e];
         float sn, cs;
-        sincosf(om * fmaf(w1x, gx_s[e], fmaf(w1y, gy_s[e], b1)), &sn, &cs);
+        sincospif(om_pi * fmaf(w1x, gx_s[e], fmaf(w1y, gy_s[e], b1)), &sn, &cs);
         const float t = dz * cs;
         sx = fmaf(t, gx_s[e], sx);
         sy = fmaf(t, gy_s[e], sy);
@@ -121,8 +135,10 @@ __global__ void __launch_bounds__(256) siren_reduce_kernel(const float* part, in
     const int e = blockIdx.x * 32 + lane;
     const int c0 = chunks * w / 8, c1 = chunks * (w + 1) / 8;
     float s = 0.f;
-    if (e < kNP)
-        for (int c = c0; c < c1; ++c) s += part[(size_t)c * kStride + e];
+    if (e < kNP) {
+#pragma unroll 8
+        for (int c = c0; c < c1; ++c) s += part[(size_t)c * kStride + e];     // in order; loads run ahead
+    }
     red[w][lane] = s;
     __syncthreads();
     if (w == 0 && e < kNP) {
@@ -189,7 +205,7 @@ extern "C" pact_status pact_siren_forward(const pact_geometry* g, const float* p
     if (!sos) return fail(PACT_ERR_INVALID_ARG, "siren_forward: sos is NULL");
     a.sos = sos;
     const int GG = g->sos_g * g->sos_g;
-    siren_fwd_kernel<<<(GG + 255) / 256, 256, 0, as_stream(stream)>>>(a);
+    siren_fwd_kernel<<<(GG * kFwdLanes + 255) / 256, 256, 0, as_stream(stream)>>>(a);
     return check_launch("siren forward kernel");
 }
 
