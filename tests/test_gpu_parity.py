@@ -477,6 +477,40 @@ def test_mc_deconv_loss_overwrites_dl_dw_back_to_back():
             assert rel(cpu(o["dL_dw"]), g_ref) <= 1e-6
 
 
+def test_accumulating_pass_behind_the_ray_kernel():
+    """In a recovery iteration the fused pass adds to the dL/dw that the ray
+    kernel ahead of it clears and reads the w that kernel writes, while the
+    copies and channel sums of each CTA's first unit may run before that kernel
+    has ended.  Queued back to back on one stream for three SOS fields, each
+    pass equals a separate clearing call on the same w: bit-equal loss (fixed
+    order sums) and dL/dw up to the order of the atomics; small case and the
+    full-size launch."""
+    for cfg in (inputs.config_small(), inputs.config_full()):
+        case = inputs.make_case(cfg, 3)
+        Y, _, d = _mcd_case(cfg, 8)
+        pb = pact.Problem(cfg, DEV)
+        Yt = to_dev_c(Y)
+        tab = pact.McdTables(pb, d)
+        tv_ws = pact._ws(pact.sos_to_delays_tv_workspace_size(pb), DEV)
+        w = torch.empty(pb.n, pb.n_t, device=DEV)
+        out = {"loss": torch.zeros(1, device=DEV), "dL_dw": torch.full((pb.n, pb.n_t), 5.0, device=DEV)}
+        sos = [torch.as_tensor(case["sos_init"] + a * (case["sos_true"] - case["sos_init"]), device=DEV)
+               for a in (0.3, 1.0, 0.6)]
+        got = []
+        torch.cuda.synchronize()
+        for s in sos:
+            pact.sos_to_delays_tv(pb, s, w, out["dL_dw"], cfg.tv_lambda, tv_ws)
+            pact.mc_deconv_loss(pb, w, Yt, d, cfg.eps, out=out, tables=tab, accumulate=True)
+            got.append((out["loss"].clone(), out["dL_dw"].clone()))
+        torch.cuda.synchronize()
+        for s, (loss, gw) in zip(sos, got):
+            ref = pact.mc_deconv_loss(pb, pact.sos_to_delays(pb, s), Yt, d, cfg.eps)
+            assert float(loss.item()) == float(ref["loss"].item())
+            g_ref = cpu(ref["dL_dw"])
+            assert np.isfinite(g_ref).all() and np.abs(g_ref).max() > 0
+            assert rel(cpu(gw), g_ref) <= 1e-6
+
+
 def test_mc_deconv_loss_misaligned_w_takes_the_general_path():
     """w not 16-byte aligned (the streaming kernel copies w rows in bulk): the
     two-pass kernel serves the call with the same results."""
