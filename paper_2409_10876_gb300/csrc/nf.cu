@@ -11,15 +11,18 @@
 // pact_nf_forward: one CTA per 128 nodes; the four hidden layers are four
 // 128 x 128 (x 64 / 128) GEMMs on the tensor cores with the accumulator in
 // TMEM; each thread owns one node (one TMEM lane) for the bias/ReLU epilogue,
-// which writes the next layer's operand straight into shared memory.  Each
-// layer's output tile is also copied (in its shared-memory layout) to the
-// workspace for the backward pass.
+// which writes the next layer's operand straight into shared memory.  The BF16
+// weights are cast into their operand-tile layout once per call, so each tile
+// arrives by one bulk copy (TMA) on its own mbarrier; each layer's output tile
+// goes (in its shared-memory layout) to the workspace for the backward pass by
+// one bulk store that runs while the next layer computes.
 // pact_nf_backward: per CTA and layer, dW = dz^T h (M = out, N = in, K = 128
 // nodes; dz and h are the K-major node tiles read as MN-major operands, so no
 // transposed copies) and dh = dz W (M = nodes, N = in, K = out) on the tensor
-// cores; the
-// per-CTA weight gradients go to the workspace and a second kernel sums them
-// in a fixed order.
+// cores, the layer's h and W tiles arriving by bulk copies into a second buffer
+// pair while the layer before runs; the per-CTA weight gradients go to the
+// workspace (coalesced, [in/4][out][4] per block) and a second kernel sums
+// them in a fixed order.
 #include <math.h>
 
 #include <algorithm>
@@ -42,9 +45,17 @@ constexpr int kOffW5 = off_w(kL + 1);
 constexpr int kOffB5 = kOffW5 + kH;
 constexpr int kNParam = kOffB5 + 1;
 constexpr int kPartStride = (kNParam + 63) / 64 * 64;   // per-CTA gradient row, 256-byte aligned
-constexpr int kWbf = kOffW5 + kH;             // bf16 weight copy: W1..W4 with their biases' slots unused, w5
 constexpr int kTileBytes = kRows * kH * 2;    // one 128 x 128 bf16 operand tile
 constexpr int kOnesBytes = 16 * kRows * 2;    // the backward's [16 x 128] tile of ones
+// BF16 copy of the weights in the workspace: W_1 .. W_4 each already in its
+// K-major operand-tile layout (one bulk copy per tile; the tiles are contiguous
+// in the forward's shared memory too), then w5
+__host__ __device__ constexpr int wtile_off(int l) { return l == 1 ? 0 : kRows * kF * 2 + (l - 2) * kTileBytes; }
+constexpr int kW5 = (kRows * kF * 2 + (kL - 1) * kTileBytes) / 2;   // bf16 index of w5
+constexpr int kWbf = kW5 + kH;                // one copy (114,944 bytes, a multiple of 256)
+// Every CTA reads the same weights: kWRep copies (CTA b reads copy b % kWRep)
+// spread those reads over more L2 lines than one copy would.
+constexpr int kWRep = 8;
 
 struct NfArgs {
     int G;                 // nodes per side
@@ -53,7 +64,7 @@ struct NfArgs {
     float v_mid, v_half, v_bg;
     const float* params;   // [kNParam] FP32 master parameters
     const unsigned char* mask;   // [G*G] or NULL (all inside)
-    __nv_bfloat16* wbf;    // [kWbf] BF16 copy of the weights (workspace)
+    __nv_bfloat16* wbf;    // [kWRep][kWbf] BF16 copies of the weights (workspace)
     unsigned char* htiles; // [cta][kL][kTileBytes] layer outputs in operand layout (workspace)
     float* t5;             // [rows] tanh of the output pre-activation (workspace)
     float* sos;            // [G*G] forward output
@@ -102,78 +113,88 @@ __device__ __forceinline__ float bf16_at(const uint4& v, int u) {
     return __uint_as_float((u & 1) ? (w & 0xFFFF0000u) : (w << 16));
 }
 
-// Weight W_l (bf16 [out][in]) into a K-major [out x in] tile (B operand of h W^T).
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+// 1-D bulk copy shared -> global in this thread's bulk group (16-byte aligned,
+// bytes a multiple of 16), and the waits on this thread's bulk groups: until
+// at most N are still reading shared memory, and until all have completed.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Weight tile W_l (workspace, operand layout) -> dst by one bulk copy on `bar`.
+__device__ __forceinline__ const __nv_bfloat16* my_wbf(const NfArgs& a) {
+    return a.wbf + (size_t)(blockIdx.x % kWRep) * kWbf;
+}
+__device__ __forceinline__ void fetch_w(unsigned char* dst, const NfArgs& a, int l, uint64_t* bar) {
+    tma_bulk_g2s(dst, reinterpret_cast<const unsigned char*>(my_wbf(a)) + wtile_off(l),
+                 (uint32_t)(kH * in_dim(l) * 2), bar);
 }
 
-// W [kH x K] (row-major, 16-byte aligned) into a K-major tile by asynchronous
-// 16-byte copies; the caller waits with cp_wait_all and a barrier.
-__device__ __forceinline__ void load_w(unsigned char* tile, const __nv_bfloat16* w, int K) {
-    const int chunks = kH * K / 8;
-    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-        const int o = c / (K / 8), k8 = c - (c / (K / 8)) * (K / 8);
-        cp16(tile + umma::kmaj_off(o, 8 * k8, K), reinterpret_cast<const uint4*>(w) + c);
-    }
-}
-// A whole operand tile (kTileBytes) from global memory, asynchronously.
-__device__ __forceinline__ void load_tile(unsigned char* tile, const unsigned char* src) {
-    for (int c = threadIdx.x; c < kTileBytes / 16; c += blockDim.x) cp16(tile + 16 * c, src + 16 * c);
-}
-
-// W_l^T as a K-major [in x out] tile (B operand of dz W): element (n = in, k = out).
-
+// Bounded mbarrier wait; a wait that gives up sets the status word.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status, unsigned long long limit) {
     const bool ok = mbar_wait_bounded(bar, parity, limit);
     if (!ok) atomicExch(status, 1);
     return ok;
 }
 
-// BF16 copy of the weights (W1..W4 in their own slots, w5).
+// BF16 copies of the weights: W_l element (o, c) to its place in the K-major
+// [out x in] tile of layer l, w5 after the tiles (biases stay FP32).
 __global__ void nf_cast_kernel(const float* params, __nv_bfloat16* wbf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kWbf) return;
-    bool is_w = i >= kOffW5;
-    for (int l = 1; l <= kL; ++l) is_w = is_w || (i >= off_w(l) && i < off_b(l));
-    wbf[i] = __float2bfloat16_rn(is_w ? params[i] : 0.f);
+    if (i >= kOffW5 + kH) return;
+    int dst = -1;
+    if (i >= kOffW5) dst = kW5 + (i - kOffW5);
+#pragma unroll
+    for (int l = 1; l <= kL; ++l)
+        if (i >= off_w(l) && i < off_b(l)) {
+            const int K = in_dim(l), o = (i - off_w(l)) / K, c = i - off_w(l) - o * K;
+            dst = (wtile_off(l) + umma::kmaj_off(o, c, K)) / 2;
+        }
+    if (dst < 0) return;                            // a bias
+    const __nv_bfloat16 v = __float2bfloat16_rn(params[i]);
+#pragma unroll
+    for (int r = 0; r < kWRep; ++r) wbf[(size_t)r * kWbf + dst] = v;
 }
 
 __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* A0 = sm;                                 // features  [128 x 64]   16 KB
     auto Hb = [](int i) { return sm + 16384 + i * kTileBytes; };            // layer outputs  2 x 32 KB
-    auto Wt = [](int i) {                                   // W1 (16 KB), W2..W4 (32 KB each)
-        return sm + 16384 + 2 * kTileBytes + (i == 0 ? 0 : 16384 + (i - 1) * kTileBytes);
-    };
+    unsigned char* Wt = sm + 16384 + 2 * kTileBytes;        // W1 (16 KB), W2..W4 (32 KB each), as in the workspace
     __shared__ __align__(16) float bias_s[kL][kH];
     __shared__ float w5_s[kH];
     __shared__ uint32_t tmem_s;
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, wbar[kL];
+    __shared__ int wbad_s;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = blockIdx.x * kRows + tid;
     const bool valid = row < a.rows;
 
-    for (int l = 1; l <= kL; ++l) load_w(Wt(l - 1), a.wbf + off_w(l), in_dim(l));
+    if (tid == 0) {                                 // the four weight tiles, one bulk copy each
+        mbar_init(&bar, 1);
+        for (int l = 0; l < kL; ++l) mbar_init(&wbar[l], 1);
+        mbar_init_fence();
+        wbad_s = 0;
+        for (int l = 1; l <= kL; ++l) {
+            mbar_arrive_expect_tx(&wbar[l - 1], (uint32_t)(kH * in_dim(l) * 2));
+            fetch_w(Wt + wtile_off(l), a, l, &wbar[l - 1]);
+        }
+    }
     for (int c = tid; c < kL * kH; c += blockDim.x) bias_s[c / kH][c % kH] = a.params[off_b(c / kH + 1) + c % kH];
-    for (int c = tid; c < kH; c += blockDim.x) w5_s[c] = __bfloat162float(a.wbf[kOffW5 + c]);
+    for (int c = tid; c < kH; c += blockDim.x) w5_s[c] = __bfloat162float(my_wbf(a)[kW5 + c]);
     {
         float f[kF];
         features(a, valid ? row : 0, f);
 #pragma unroll
         for (int k0 = 0; k0 < kF; k0 += 8) st8(A0, tid, k0, kF, f + k0);
     }
-    cp_wait_all();                                  // the weight tiles
     if (warp == 0) umma::tmem_alloc(&tmem_s, 128);
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        mbar_init_fence();
-    }
     umma::fence_smem_to_async();
     umma::fence_before();
     __syncthreads();
@@ -181,15 +202,19 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
     const uint32_t tmem = tmem_s;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     bool ok = true;
-    float z5 = 0.f;
+    float z5p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // independent partial sums of the head
+    const float b5 = a.params[kOffB5];
+    const bool inside = valid && (a.mask ? a.mask[row] != 0 : true);
     for (int l = 1; l <= kL; ++l) {
         const unsigned char* in = l == 1 ? A0 : Hb(l % 2);
         unsigned char* out = Hb((l + 1) % 2);
         const int K = in_dim(l);
         if (tid == 0) {
+            if (!wait_bar(&wbar[l - 1], 0u, a.status, a.limit_ns)) wbad_s = 1;   // W_l has landed
+            if (l >= 3) bulk_wait_read<1>();       // `out` (layer l - 2's output) has been read by its store
             for (int kk = 0; kk < K / 16; ++kk)
-                umma::mma(tmem, umma::kslice(in, K, kk), umma::kslice(Wt(l - 1), K, kk), umma::idesc_bf16(128, 128),
-                          kk > 0);
+                umma::mma(tmem, umma::kslice(in, K, kk), umma::kslice(Wt + wtile_off(l), K, kk),
+                          umma::idesc_bf16(128, 128), kk > 0);
             umma::commit(&bar);
         }
         ok = wait_bar(&bar, (uint32_t)((l - 1) & 1), a.status, a.limit_ns) && ok;
@@ -207,7 +232,8 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
             }
             if (l == kL) {                          // the head sees the BF16 values the tile holds
 #pragma unroll
-                for (int j = 0; j < 64; ++j) z5 = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), w5_s[c0 + j], z5);
+                for (int j = 0; j < 64; ++j)
+                    z5p[j & 7] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), w5_s[c0 + j], z5p[j & 7]);
             }
 #pragma unroll
             for (int j = 0; j < 64; j += 8) st8(out, tid, c0 + j, kH, v + j);
@@ -216,16 +242,21 @@ __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
         umma::fence_before();
         __syncthreads();
         umma::fence_after();
-        // layer output tile (operand layout) to the workspace for the backward pass
-        const uint4* src = reinterpret_cast<const uint4*>(out);
-        uint4* dst = reinterpret_cast<uint4*>(a.htiles + ((size_t)blockIdx.x * kL + (l - 1)) * kTileBytes);
-        for (int c = tid; c < kTileBytes / 16; c += blockDim.x) dst[c] = src[c];
+        // layer output tile (operand layout) to the workspace for the backward pass,
+        // by one bulk copy that runs on while the next layer computes
+        if (tid == 0) bulk_s2g(a.htiles + ((size_t)blockIdx.x * kL + (l - 1)) * kTileBytes, out, kTileBytes);
     }
-    const float t = tanhf(z5 + a.params[kOffB5]);
+    ok = ok && !wbad_s;                             // (set before the last layer's barrier)
+    const float z5 = ((z5p[0] + z5p[1]) + (z5p[2] + z5p[3])) + ((z5p[4] + z5p[5]) + (z5p[6] + z5p[7]));
+    const float t = tanhf(z5 + b5);
     if (valid) {
         a.t5[row] = ok ? t : __int_as_float(0x7fc00000);
-        const bool inside = a.mask ? a.mask[row] != 0 : true;
         a.sos[row] = inside ? (ok ? fmaf(a.v_half, t, a.v_mid) : __int_as_float(0x7fc00000)) : a.v_bg;
+    }
+    if (tid == 0) {
+        bulk_wait_all();                            // the tiles are in the workspace
+        if (wbad_s)                                 // a weight copy gave up: let it land before the CTA ends
+            for (int l = 0; l < kL; ++l) mbar_wait_bounded(&wbar[l], 0u, a.limit_ns);
     }
     umma::fence_before();
     __syncthreads();
@@ -246,7 +277,9 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
     __shared__ float w5_s[kH];
     __shared__ float red_s[kRows / 32];
     __shared__ uint32_t tmem_s;
-    __shared__ __align__(8) uint64_t bar;
+    // bbar[i]: bulk copies into the buffer pair (Hb(i), Wb(i)); bbar[1] phase 0
+    // is h4 alone, then each pair is filled for one layer at a time
+    __shared__ __align__(8) uint64_t bar, bbar[2];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = blockIdx.x * kRows + tid;
     const bool valid = row < a.rows;
@@ -259,25 +292,27 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         const float t = a.t5[row];
         g5 = a.dL_dsos[row] * a.v_half * (1.f - t * t);
     }
-    // h4 of this CTA (operand layout) -> Hb(1); then layer kL's h3 and W4 -> Hb(0), Wb(0)
+    // h4 of this CTA (operand layout) -> Hb(1); then layer kL's h3 and W4 -> Hb(0), Wb(0);
+    // one bulk copy per tile
     unsigned char* H4 = Hb(1);
-    load_tile(H4, tiles + (size_t)(kL - 1) * kTileBytes);
-    cp_async_commit_group();
-    load_tile(Hb(kL & 1), tiles + (size_t)(kL - 2) * kTileBytes);
-    load_w(Wb(kL & 1), a.wbf + off_w(kL), kH);
-    cp_async_commit_group();
-    cp_async_wait_group<1>();                       // h4 has landed
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init(&bbar[0], 1);
+        mbar_init(&bbar[1], 1);
+        mbar_init_fence();
+        mbar_arrive_expect_tx(&bbar[1], kTileBytes);
+        tma_bulk_g2s(H4, tiles + (size_t)(kL - 1) * kTileBytes, kTileBytes, &bbar[1]);
+        mbar_arrive_expect_tx(&bbar[0], 2 * kTileBytes);
+        tma_bulk_g2s(Hb(kL & 1), tiles + (size_t)(kL - 2) * kTileBytes, kTileBytes, &bbar[0]);
+        fetch_w(Wb(kL & 1), a, kL, &bbar[0]);
+    }
     for (int c = tid; c < kOnesBytes / 16; c += blockDim.x)
         reinterpret_cast<uint4*>(ones)[c] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
     if (warp == 0) umma::tmem_alloc(&tmem_s, 512);
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        mbar_init_fence();
-    }
+    w5_s[tid] = __bfloat162float(my_wbf(a)[kW5 + tid]);
     __syncthreads();
+    bool ok = wait_bar(&bbar[1], 0u, a.status, a.limit_ns);   // h4 has landed
     // dz4 = g5 w5 (h4 > 0) for this node
-    w5_s[tid] = __bfloat162float(a.wbf[kOffW5 + tid]);
-    __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < kH; c += 8) {
         const uint4 hv = *reinterpret_cast<const uint4*>(H4 + umma::kmaj_off(tid, c, kH));
@@ -334,14 +369,17 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         const int K_in = in_dim(l);
         unsigned char* Hr = Hb(l & 1);
         unsigned char* WT = Wb(l & 1);
-        // copies for layer l - 1 (h_{l-2}, W_{l-1}) into the other pair, then wait for layer l's
-        if (l - 1 >= 2) {
-            load_tile(Hb((l - 1) & 1), tiles + (size_t)(l - 3) * kTileBytes);
-            load_w(Wb((l - 1) & 1), a.wbf + off_w(l - 1), kH);   // W [out x in] K-major = W^T read MN-major
+        // copies for layer l - 1 (h_{l-2}, W_{l-1}) into the other pair (read by layer
+        // l + 1, finished), then wait for layer l's
+        if (l - 1 >= 2 && tid == 0) {
+            fence_proxy_async_smem();
+            uint64_t* nb = &bbar[(l - 1) & 1];
+            mbar_arrive_expect_tx(nb, 2 * kTileBytes);
+            tma_bulk_g2s(Hb((l - 1) & 1), tiles + (size_t)(l - 3) * kTileBytes, kTileBytes, nb);
+            fetch_w(Wb((l - 1) & 1), a, l - 1, nb);   // W [out x in] K-major = W^T read MN-major
         }
-        cp_async_commit_group();
-        if (l > 1) {
-            cp_async_wait_group<1>();              // h_{l-1} and W_l have landed
+        if (l > 1) {                                // h_{l-1} and W_l have landed
+            ok = wait_bar(&bbar[l & 1], l < kL ? 1u : 0u, a.status, a.limit_ns) && ok;
         } else {
             float f[kF];
             features(a, valid ? row : 0, f);
@@ -373,13 +411,14 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         phase ^= 1u;
         umma::fence_after();
         part[off_b(l) + tid] = umma::ld1(tmem + 256 + lane_base);   // db_l[tid]
-        // weight-gradient row `tid` (TMEM lane = output unit)
+        // weight-gradient row `tid` (TMEM lane = output unit), stored as [in/4][out][4]
+        // so that a warp's float4 stores are 512 contiguous bytes
         for (int c0 = 0; c0 < K_in; c0 += 64) {
             float v[64];
             umma::ld64(tmem + lane_base + c0, v);
-            float4* dst = reinterpret_cast<float4*>(part + off_w(l) + tid * K_in + c0);
+            float4* dst = reinterpret_cast<float4*>(part + off_w(l)) + tid;
 #pragma unroll
-            for (int j = 0; j < 64; j += 4) dst[j / 4] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            for (int j = 0; j < 64; j += 4) dst[((c0 + j) >> 2) * kH] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
         if (l > 1) {
             // dz_{l-1} = dh (h_{l-1} > 0), node `tid`
@@ -400,21 +439,40 @@ __global__ void __launch_bounds__(kRows, 1) nf_bwd_kernel(const NfArgs a) {
         __syncthreads();
         umma::fence_after();
     }
+    if (!ok) part[off_b(1) + tid] = __int_as_float(0x7fc00000);   // a copy never landed: poison the gradient
+    if (tid == 0 && !ok)                            // and let the copies in flight land before the CTA ends
+        for (int i = 0; i < 2; ++i) mbar_wait_bounded(&bbar[i], 1u, a.limit_ns);
     umma::fence_before();
     __syncthreads();
     if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
+// Parameter index of slot q of a per-CTA gradient row: each weight block is
+// stored as [in/4][out][4] (the backward's coalesced stores from TMEM rows),
+// biases, w5 and b5 in parameter order.
+__device__ __forceinline__ int param_of_slot(int q) {
+#pragma unroll
+    for (int l = 1; l <= kL; ++l)
+        if (q >= off_w(l) && q < off_b(l)) {
+            const int r = q - off_w(l);
+            return off_w(l) + ((r >> 2) & (kH - 1)) * in_dim(l) + 4 * (r >> 9) + (r & 3);
+        }
+    return q;
+}
+
+// dL/dparams = sum over CTAs of the per-CTA rows, in CTA order; one thread per
+// row slot (coalesced reads), written to its parameter.
 __global__ void nf_reduce_kernel(const float* part, int nct, float* out, int accumulate) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= kNParam) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kNParam) return;
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int c = 0;
     for (; c + 8 <= nct; c += 8)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s[u] += part[(size_t)(c + u) * kPartStride + p];
-    for (; c < nct; ++c) s[0] += part[(size_t)c * kPartStride + p];
+        for (int u = 0; u < 8; ++u) s[u] += part[(size_t)(c + u) * kPartStride + q];
+    for (; c < nct; ++c) s[0] += part[(size_t)c * kPartStride + q];
     const float t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    const int p = param_of_slot(q);
     out[p] = accumulate ? out[p] + t : t;
 }
 
@@ -428,7 +486,7 @@ NfPlan nf_plan(const pact_geometry* g) {
     NfPlan p;
     p.rows = g->sos_g * g->sos_g;
     p.nct = (p.rows + kRows - 1) / kRows;
-    size_t o = align_up((size_t)kWbf * sizeof(__nv_bfloat16), 256);
+    size_t o = align_up((size_t)kWRep * kWbf * sizeof(__nv_bfloat16), 256);
     p.off_htiles = o;
     o += align_up((size_t)p.nct * kL * kTileBytes, 256);
     p.off_t5 = o;
@@ -495,7 +553,7 @@ extern "C" pact_status pact_nf_forward(const pact_geometry* g, const float* para
     a.sos = sos;
     cudaStream_t st = as_stream(stream);
     if (cudaMemsetAsync(a.status, 0, sizeof(int), st) != cudaSuccess) return check_launch("nf_forward: memset");
-    nf_cast_kernel<<<(kWbf + 255) / 256, 256, 0, st>>>(params, a.wbf);
+    nf_cast_kernel<<<(kOffW5 + kH + 255) / 256, 256, 0, st>>>(params, a.wbf);
     PACT_TRY(check_launch("nf_forward: weight cast"));
     PACT_TRY(ensure_smem((const void*)nf_fwd_kernel, pl.smem_fwd, "nf_forward: shared memory attribute"));
     nf_fwd_kernel<<<pl.nct, kRows, pl.smem_fwd, st>>>(a);
