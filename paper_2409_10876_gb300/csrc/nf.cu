@@ -143,23 +143,39 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* st
     return ok;
 }
 
-// BF16 copies of the weights: W_l element (o, c) to its place in the K-major
-// [out x in] tile of layer l, w5 after the tiles (biases stay FP32).
+// BF16 copies of the weights: eight consecutive elements (o, c .. c + 7) of
+// W_l to their 16-byte row of the K-major [out x in] tile of layer l, w5 after
+// the tiles (biases stay FP32).  One thread per eight weights.
+constexpr int kCast8 = (kH * kF + (kL - 1) * kH * kH + kH) / 8;
 __global__ void nf_cast_kernel(const float* params, __nv_bfloat16* wbf) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kOffW5 + kH) return;
-    int dst = -1;
-    if (i >= kOffW5) dst = kW5 + (i - kOffW5);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kCast8) return;
+    int src, dst;                                   // first parameter; destination in bytes
+    if (t < kH * kF / 8) {                          // W_1: [128 x 64]
+        const int o = t / (kF / 8), c = (t - o * (kF / 8)) * 8;
+        src = off_w(1) + o * kF + c;
+        dst = wtile_off(1) + (int)umma::kmaj_off(o, c, kF);
+    } else if (t < kCast8 - kH / 8) {               // W_2 .. W_4: [128 x 128]
+        const int u = t - kH * kF / 8, l = 2 + u / (kH * kH / 8), v = u - (l - 2) * (kH * kH / 8);
+        const int o = v / (kH / 8), c = (v - o * (kH / 8)) * 8;
+        src = off_w(l) + o * kH + c;
+        dst = wtile_off(l) + (int)umma::kmaj_off(o, c, kH);
+    } else {                                        // w5
+        const int c = (t - (kCast8 - kH / 8)) * 8;
+        src = kOffW5 + c;
+        dst = 2 * (kW5 + c);
+    }
+    float v[8];
 #pragma unroll
-    for (int l = 1; l <= kL; ++l)
-        if (i >= off_w(l) && i < off_b(l)) {
-            const int K = in_dim(l), o = (i - off_w(l)) / K, c = i - off_w(l) - o * K;
-            dst = (wtile_off(l) + umma::kmaj_off(o, c, K)) / 2;
-        }
-    if (dst < 0) return;                            // a bias
-    const __nv_bfloat16 v = __float2bfloat16_rn(params[i]);
+    for (int u = 0; u < 8; ++u) v[u] = params[src + u];
+    uint4 q;
+    q.x = pack2(v[0], v[1]);
+    q.y = pack2(v[2], v[3]);
+    q.z = pack2(v[4], v[5]);
+    q.w = pack2(v[6], v[7]);
 #pragma unroll
-    for (int r = 0; r < kWRep; ++r) wbf[(size_t)r * kWbf + dst] = v;
+    for (int r = 0; r < kWRep; ++r)
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(wbf + (size_t)r * kWbf) + dst) = q;
 }
 
 __global__ void __launch_bounds__(kRows, 1) nf_fwd_kernel(const NfArgs a) {
@@ -460,18 +476,28 @@ __device__ __forceinline__ int param_of_slot(int q) {
     return q;
 }
 
-// dL/dparams = sum over CTAs of the per-CTA rows, in CTA order; one thread per
-// row slot (coalesced reads), written to its parameter.
-__global__ void nf_reduce_kernel(const float* part, int nct, float* out, int accumulate) {
+// dL/dparams = sum over CTAs of the per-CTA rows, in a fixed order; one thread
+// per row slot (coalesced reads, sixteen in flight), written to its parameter.
+__global__ void __launch_bounds__(128) nf_reduce_kernel(const float* part, int nct, float* out, int accumulate) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= kNParam) return;
-    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int c = 0;
-    for (; c + 8 <= nct; c += 8)
+    float s[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s[u] += part[(size_t)(c + u) * kPartStride + q];
+    for (int u = 0; u < 16; ++u) s[u] = 0.f;
+    int c = 0;
+    for (; c + 16 <= nct; c += 16) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = __ldcg(part + (size_t)(c + u) * kPartStride + q);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s[u] += v[u];
+    }
     for (; c < nct; ++c) s[0] += part[(size_t)c * kPartStride + q];
-    const float t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int u = 0; u < w; ++u) s[u] += s[u + w];
+    const float t = s[0];
     const int p = param_of_slot(q);
     out[p] = accumulate ? out[p] + t : t;
 }
@@ -553,7 +579,7 @@ extern "C" pact_status pact_nf_forward(const pact_geometry* g, const float* para
     a.sos = sos;
     cudaStream_t st = as_stream(stream);
     if (cudaMemsetAsync(a.status, 0, sizeof(int), st) != cudaSuccess) return check_launch("nf_forward: memset");
-    nf_cast_kernel<<<(kOffW5 + kH + 255) / 256, 256, 0, st>>>(params, a.wbf);
+    nf_cast_kernel<<<(kCast8 + 255) / 256, 256, 0, st>>>(params, a.wbf);
     PACT_TRY(check_launch("nf_forward: weight cast"));
     PACT_TRY(ensure_smem((const void*)nf_fwd_kernel, pl.smem_fwd, "nf_forward: shared memory attribute"));
     nf_fwd_kernel<<<pl.nct, kRows, pl.smem_fwd, st>>>(a);
@@ -572,7 +598,7 @@ extern "C" pact_status pact_nf_backward(const pact_geometry* g, const float* par
     PACT_TRY(ensure_smem((const void*)nf_bwd_kernel, pl.smem_bwd, "nf_backward: shared memory attribute"));
     nf_bwd_kernel<<<pl.nct, kRows, pl.smem_bwd, st>>>(a);
     PACT_TRY(check_launch("nf_backward kernel"));
-    nf_reduce_kernel<<<(kNParam + 255) / 256, 256, 0, st>>>(a.part, pl.nct, dL_dparams, accumulate);
+    nf_reduce_kernel<<<(kNParam + 127) / 128, 128, 0, st>>>(a.part, pl.nct, dL_dparams, accumulate);
     return check_launch("nf_backward reduction");
 }
 
