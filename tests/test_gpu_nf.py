@@ -5,6 +5,8 @@ Tolerances: BF16 keeps 8 significant bits (relative rounding 2^-9); features,
 weights and the activations of 4 hidden layers of width 128 are rounded, so
 the field deviation v - v_bg and the gradients are compared at relative L2
 3e-2 / 5e-2 (the FP32 path of the pixel grid keeps its 1e-4 / 2e-3)."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -72,6 +74,37 @@ def test_nf_backward_matches_oracle_vjp(cfg):
     gp2 = pact.nf_backward(nf, torch.as_tensor(up, device="cuda"), torch.ones(prm.size, device="cuda"),
                            accumulate=True).cpu().numpy()
     assert _rel(gp2 - 1.0, gp) <= 1e-5
+
+
+@pytest.mark.parametrize("G", [40, 72])
+def test_nf_ragged_node_count_and_every_parameter_group(G):
+    """Node counts that are not a multiple of the 128-node CTA tile (1600 and
+    5184 nodes: the last CTA holds 64 rows past the grid, which must enter no
+    sum): the field against the oracle, and the gradient of every parameter
+    group on its own (a mis-placed weight block or a bias sum over the wrong
+    rows shows up in its group, even where the whole vector would hide it)."""
+    cfg = dataclasses.replace(inputs.config_small(), sos_g=G)
+    pb = pact.Problem(cfg, "cuda")
+    prm = _params(4)
+    mask = inputs.sos_mask(cfg)
+    nf = pact.NeuralField(pb, prm, mask)
+    v = pact.nf_forward(nf).cpu().numpy()
+    g, sh, f, _, vm, vh = _oracle_args(cfg)
+    ref = O.nf_sos(g, O._t(prm), sh, f, mask, vm, vh).numpy()
+    assert np.all(v[mask == 0] == cfg.v_bg)
+    assert _rel(v - cfg.v_bg, ref - cfg.v_bg) <= FWD_TOL
+    up = np.random.default_rng(5).standard_normal((G, G)).astype(np.float32)
+    gp = pact.nf_backward(nf, torch.as_tensor(up, device="cuda")).cpu().numpy()
+    pact.nf_status(nf)
+    p64 = O._t(prm).clone().requires_grad_(True)
+    (gr,) = torch.autograd.grad((O.nf_sos(g, p64, sh, f, mask, vm, vh) * O._t(up)).sum(), p64)
+    gr = gr.numpy()
+    assert _rel(gp, gr) <= GRAD_TOL
+    off = 0
+    for name, shape in inputs.nf_shapes():
+        n = int(np.prod(shape))
+        assert _rel(gp[off:off + n], gr[off:off + n]) <= 2 * GRAD_TOL, name
+        off += n
 
 
 def test_nf_objective_gradient_end_to_end():
