@@ -548,7 +548,9 @@ size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt
  * Stitching (Sec. S1.5): every deconvolved patch irfft2(Xhat_i) (orthonormal
  * inverse of the half-spectrum, window already applied at cropping) is
  * translated to its centre and summed; the sum is divided by the summed
- * Gaussian windows (0 where no window reaches).
+ * Gaussian windows (0 where no window reaches).  The sums run in FP64 (the
+ * workspace holds FP64 images), where the few FP32 terms of a pixel add
+ * exactly: the image is the same in every run.
  *   Xhat   DEVICE c64 [N][P][P/2+1];  image DEVICE float [H][W] output
  */
 pact_status pact_stitch(const pact_geometry* g, const pact_patches* pt, const float* Xhat,

@@ -359,8 +359,10 @@ __global__ void wgrad_reduce_kernel(const float* part, int nchunks, int groups, 
 
 // -------------------------------------------------------------- elementwise kernels
 
-// pooled[b][y][x][c] = mean of the 4 x 4 block of stack[c]; also sum of squares.
-__global__ void pool4_kernel(const float* stack, int m, int H, int W, float* pooled, int cp, float* sumsq) {
+// pooled[b][y][x][c] = mean of the 4 x 4 block of stack[c]; also sum of squares
+// (per-CTA fixed-order sums added in FP64: the result does not depend on the
+// order of the atomic additions to within far less than one FP32 unit).
+__global__ void pool4_kernel(const float* stack, int m, int H, int W, float* pooled, int cp, double* sumsq) {
     const int R = H / 4, C = W / 4;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     float q = 0.f;
@@ -376,13 +378,13 @@ __global__ void pool4_kernel(const float* stack, int m, int H, int W, float* poo
     }
     __shared__ float red[8];
     q = block_sum(q, red);
-    if (threadIdx.x == 0) atomicAdd(sumsq, q);
+    if (threadIdx.x == 0) atomicAdd(sumsq, (double)q);
 }
 
-__global__ void scale_cast_kernel(const float* pooled, int n, const float* sumsq, float count, bf16* x) {
+__global__ void scale_cast_kernel(const float* pooled, int n, const double* sumsq, float count, bf16* x) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
-    const float rms = sqrtf(*sumsq / count);
+    const float rms = sqrtf((float)(*sumsq / (double)count));
     x[e] = __float2bfloat16_rn(pooled[e] / (rms + 1e-12f));
 }
 
@@ -763,7 +765,7 @@ extern "C" int pact_cnn_input_channels(int m) { return m < 1 || m > PACT_MAX_CHA
 
 extern "C" size_t pact_cnn_pool_workspace_size(const pact_geometry* g, int m) {
     if (check_cnn(g, m, 1) != PACT_OK) return 0;
-    return align_up(((size_t)g->sos_g * g->sos_g * pad_channels(m) + 1) * sizeof(float), 256);
+    return align_up((size_t)g->sos_g * g->sos_g * pad_channels(m) * sizeof(float), 16) + sizeof(double);
 }
 
 extern "C" pact_status pact_cnn_pool_stack(const pact_geometry* g, const float* stack, int m, void* x, void* ws,
@@ -777,8 +779,8 @@ extern "C" pact_status pact_cnn_pool_stack(const pact_geometry* g, const float* 
     const int R = g->sos_g, cp = pad_channels(m);
     const int n = R * R * cp;
     float* pooled = static_cast<float*>(ws);
-    float* sumsq = pooled + n;
-    if (cudaMemsetAsync(sumsq, 0, sizeof(float), st) != cudaSuccess) return check_launch("cnn_pool_stack: memset");
+    double* sumsq = reinterpret_cast<double*>(static_cast<char*>(ws) + align_up((size_t)n * sizeof(float), 16));
+    if (cudaMemsetAsync(sumsq, 0, sizeof(double), st) != cudaSuccess) return check_launch("cnn_pool_stack: memset");
     pool4_kernel<<<(n + 255) / 256, 256, 0, st>>>(stack, m, g->img_h, g->img_w, pooled, cp, sumsq);
     PACT_TRY(check_launch("cnn pool kernel"));
     scale_cast_kernel<<<(n + 255) / 256, 256, 0, st>>>(pooled, n, sumsq, (float)R * R * m, static_cast<bf16*>(x));

@@ -167,7 +167,10 @@ constexpr int kSA = 4, kSB = 4;
 
 // Inverse half-spectrum DFT of patch i = blockIdx.x, channel j = blockIdx.y
 // (X [N][m][P][P/2+1]), then scatter-add into the channel's numerator image
-// and, for channel 0, into the window-sum image.
+// and, for channel 0, into the window-sum image.  Both images are FP64: a pixel
+// sums a few FP32 terms (one per overlapping patch), which FP64 holds exactly,
+// so the order of the atomic additions cannot change the result (the stitched
+// image is the same in every run).
 // Column pass: Z[a][v] = sum_u X[u][v] exp(+2 pi j a u / P), pairing u with
 // P - u as the forward column pass does.  Row pass: every row of Z is the
 // half of a Hermitian row spectrum, so with C = sum_v c_v Re Z[a][v] cos(2 pi v b / P)
@@ -175,7 +178,7 @@ constexpr int kSA = 4, kSB = 4;
 // the pixel pair is x[a][b] = (C - S) / P, x[a][P - b] = (C + S) / P: one set
 // of sums gives both.
 __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* centres, float inv_2s2,
-                                                     const float2* X, float* num, float* den) {
+                                                     const float2* X, double* num, double* den) {
     extern __shared__ float4 sm4[];
     const int half = P / 2 + 1, h2 = P / 2, HS = fft_hs(P);
     float2* Xs = reinterpret_cast<float2*>(sm4);   // [P][HS]
@@ -291,10 +294,10 @@ __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* c
                     const int col = c0 + bc;
                     if (col < 0 || col >= g.W) continue;
                     const float val = (side ? C[r][k] + S[r][k] : C[r][k] - S[r][k]) * inv_p;
-                    atomicAdd(num + (size_t)row * g.W + col, val);
+                    atomicAdd(num + (size_t)row * g.W + col, (double)val);
                     if (j == 0) {
                         const float ob = (bc - P / 2) * g.dx;
-                        atomicAdd(den + (size_t)row * g.W + col, expf(-(oa * oa + ob * ob) * inv_2s2));
+                        atomicAdd(den + (size_t)row * g.W + col, (double)expf(-(oa * oa + ob * ob) * inv_2s2));
                     }
                 }
             }
@@ -303,12 +306,12 @@ __global__ void __launch_bounds__(256) stitch_kernel(Geo g, int P, const int2* c
 }
 
 // out[j][q] = num[j][q] / den[q] (0 where no window reaches), j = blockIdx.y.
-__global__ void stitch_divide_kernel(int n, const float* num, const float* den, float* out) {
+__global__ void stitch_divide_kernel(int n, const double* num, const double* den, float* out) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const size_t o = (size_t)blockIdx.y * n + q;
-    const float d = den[q];
-    out[o] = d > 0.f ? num[o] / d : 0.f;
+    const float d = (float)den[q];
+    out[o] = d > 0.f ? (float)num[o] / d : 0.f;
 }
 
 float inv_two_sigma2(float fwhm) {
@@ -356,12 +359,12 @@ pact_status run_stitch(const pact_geometry* g, const pact_patches* pt, int m, co
     if (!Xhat || !image || !ws) return fail(PACT_ERR_INVALID_ARG, "stitch: Xhat, image and ws must not be NULL");
     if (m < 1 || m > 65535) return fail(PACT_ERR_INVALID_ARG, "stitch: channel count %d out of range", m);
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(PACT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    const size_t plane = (size_t)g->img_h * g->img_w * sizeof(float);
+    const size_t plane = (size_t)g->img_h * g->img_w * sizeof(double);
     const size_t need = align_up((size_t)(m + 1) * plane, 256);
     if (ws_bytes < need) return fail(PACT_ERR_INVALID_ARG, "stitch: workspace too small: %zu < %zu", ws_bytes, need);
     cudaStream_t st = as_stream(stream);
-    float* num = static_cast<float*>(ws);
-    float* den = num + (size_t)m * g->img_h * g->img_w;
+    double* num = static_cast<double*>(ws);
+    double* den = num + (size_t)m * g->img_h * g->img_w;
     if (cudaMemsetAsync(ws, 0, (size_t)(m + 1) * plane, st) != cudaSuccess) return check_launch("stitch: memset");
     const int P = pt->p;
     const size_t shm = stitch_smem(P);
@@ -380,7 +383,7 @@ pact_status run_stitch(const pact_geometry* g, const pact_patches* pt, int m, co
 
 extern "C" size_t pact_stitch_workspace_size(const pact_geometry* g, const pact_patches* pt) {
     if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK) return 0;
-    return align_up(2 * (size_t)g->img_h * g->img_w * sizeof(float), 256);
+    return align_up(2 * (size_t)g->img_h * g->img_w * sizeof(double), 256);
 }
 
 extern "C" pact_status pact_stitch(const pact_geometry* g, const pact_patches* pt, const float* Xhat,
@@ -390,7 +393,7 @@ extern "C" pact_status pact_stitch(const pact_geometry* g, const pact_patches* p
 
 extern "C" size_t pact_stitch_channels_workspace_size(const pact_geometry* g, const pact_patches* pt, int m) {
     if (check_geometry(g) != PACT_OK || check_patches(pt) != PACT_OK || m < 1) return 0;
-    return align_up((size_t)(m + 1) * g->img_h * g->img_w * sizeof(float), 256);
+    return align_up((size_t)(m + 1) * g->img_h * g->img_w * sizeof(double), 256);
 }
 
 extern "C" pact_status pact_stitch_channels(const pact_geometry* g, const pact_patches* pt, int m, const float* Y,
