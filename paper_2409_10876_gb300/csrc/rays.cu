@@ -554,6 +554,11 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                 const Ray ry = make_ray(a.g, pixel_xy(a.g, cc.x, cc.y), n);
                 const float hbx = h * ry.bx, hby = h * ry.by;
                 const float ax = ry.ax + 2.f, ay = ry.ay + 2.f;
+                // the last cell's four corner excesses: consecutive samples of a run
+                // are half a cell apart and often share a cell, whose corners then
+                // need no second load (lanes that skip it add no shared traffic)
+                int cell = -1;
+                float d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
                 // one midpoint sample at ray parameter u (in steps), its weight
                 // (step length x dL/dw x v0 x S) given: dw/dv = weight / v^2, spread
                 // bilinearly over the four nodes as fixed-point integers
@@ -570,8 +575,14 @@ __global__ void __launch_bounds__(1024, 1) rays_adj_kernel(const RayArgs a, int 
                     const int ix = __float_as_int(tX) - 0x4B000000;
                     const float tx = x - (tX - 8388608.f), ty = y - (tY - 8388608.f);
                     const int idx = (ONE ? iy : iy - r0) * pitch + ix;
-                    const float* q = dv_s + idx;
-                    const float d00 = q[0], d01 = q[1], d10 = q[pitch], d11 = q[pitch + 1];
+                    if (idx != cell) {
+                        const float* q = dv_s + idx;
+                        d00 = q[0];
+                        d01 = q[1];
+                        d10 = q[pitch];
+                        d11 = q[pitch + 1];
+                        cell = idx;
+                    }
                     const float top = fmaf(tx, d01 - d00, d00), bot = fmaf(tx, d11 - d10, d10);
                     const float d = fmaf(ty, bot - top, top);
                     const float iv = __fdividef(1.f, v0 + d);
